@@ -1,0 +1,246 @@
+/*
+ * rpp.h -- C ABI of the GB300 Vietoris-Rips barcode library (librpp.so).
+ *
+ * Computes persistence barcodes over Z/2 of the Vietoris-Rips filtration
+ * Rips_s(X) = { sigma : diam(sigma) <= s }, s <= t (Sec. 2, definition of the
+ * Rips filtration and of persistence pairs), following the method of
+ * Zhang, Xiao, Wang, "GPU-Accelerated Computation of Vietoris-Rips Persistence
+ * Barcodes" (arXiv 2003.07989):
+ *   - filtration construction with clearing on the GPU (Alg. 6 and Alg. 7):
+ *     every p-simplex is indexed in the combinatorial number system
+ *     (Sec. "The Combinatorial Number System"), its diameter is the largest
+ *     distance among its vertices, simplices above the threshold and cleared
+ *     simplices are dropped, the rest are sorted by decreasing diameter then
+ *     increasing index (coboundary order, Sec. "The Coboundary Matrix");
+ *   - apparent pairs found with one independent test per column (Alg. 3 and
+ *     the Apparent Pairs Lemma) and partitioned into a sorted pair array and
+ *     the leftover columns (Fig. "post-apparent", Sec. "Core System
+ *     Optimizations");
+ *   - submatrix reduction of the leftover columns on the host with the
+ *     two-layer pair store (hash map over the sorted apparent array) and the
+ *     reduction-matrix technique (Sec. "Reduction Matrix vs. Oblivious Matrix
+ *     Reduction"); H0 by Kruskal's union-find (Sec. "Zero-Dimensional
+ *     Persistence Computation").
+ *
+ * Conventions common to every entry point:
+ *   - Every call returns an rpp_status and never aborts the process. Invalid
+ *     arguments are reported before any GPU work is queued. rpp_last_error()
+ *     returns a thread-local message describing the last failure.
+ *   - Input buffers are owned by the caller; the library never frees them.
+ *     A data pointer may be device memory or host memory (pageable or pinned);
+ *     the library asks the CUDA runtime which one it is.
+ *   - Results are owned by the library and freed with rpp_result_free.
+ *   - All GPU work of a call runs on the given CUDA stream (cudaStream_t passed
+ *     as void*; NULL means the legacy default stream). A call returns after its
+ *     results are complete on the host.
+ *   - Distances are float32. Diameters and interval endpoints are exact
+ *     distance-matrix entries; there is no rounding of the filtration order.
+ *   - Ordering of simplices (the simplex-wise refinement, Sec. "The Simplex-wise
+ *     Refinement"): increasing diameter, then increasing dimension, then
+ *     decreasing combinatorial index.
+ *   - A context may be used from several threads; calls on one context are
+ *     serialised internally per workspace.
+ */
+#ifndef RPP_H
+#define RPP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RPP_OK = 0,
+    RPP_E_INVALID = 1,   /* bad argument or input (non-finite, negative, asymmetric ...) */
+    RPP_E_NOMEM = 2,     /* device or host allocation failed, or the budget is exceeded */
+    RPP_E_OVERFLOW = 3,  /* C(n, max_dim + 2) does not fit the 63-bit index */
+    RPP_E_CUDA = 4,      /* a CUDA runtime call failed (message in rpp_last_error) */
+    RPP_E_TIMEOUT = 5,   /* a bounded wait ran out (poll deadline, device wait limit) */
+    RPP_E_BUSY = 6       /* admission refused: no slot or memory free right now */
+} rpp_status;
+
+typedef enum {
+    RPP_INPUT_POINTS = 0,    /* data is n x dim float32, row-major */
+    RPP_INPUT_DISTANCES = 1  /* data is n x n float32, row-major, symmetric, zero
+                                diagonal, non-negative, finite */
+} rpp_input_kind;
+
+/* One persistence interval [birth, death); death = +INFINITY for an essential
+ * class. Zero-length intervals are never reported. */
+typedef struct {
+    float birth, death;
+} rpp_interval;
+
+/* The edges that realise an interval's endpoints: (bu, bv) is the youngest
+ * edge of the birth simplex (its longest edge; ties broken by the filtration
+ * order), (du, dv) the youngest edge of the death simplex. -1 where there is
+ * none (H0 births, essential deaths). */
+typedef struct {
+    int32_t bu, bv, du, dv;
+} rpp_critical;
+
+#define RPP_MAX_DIM 4
+
+/* Per-call counters and stage times. Index p of the arrays is the column
+ * dimension p (p = 1 .. max_dim). */
+typedef struct {
+    int64_t n;
+    int32_t max_dim;
+    float threshold;                     /* the threshold actually used */
+    float enclosing_radius;
+    int64_t candidates[RPP_MAX_DIM + 1];  /* C(n, p+1) */
+    int64_t columns[RPP_MAX_DIM + 1];     /* columns after threshold and clearing */
+    int64_t cleared[RPP_MAX_DIM + 1];     /* columns removed by clearing */
+    int64_t apparent[RPP_MAX_DIM + 1];    /* apparent pairs (sigma of dim p) */
+    int64_t leftover[RPP_MAX_DIM + 1];    /* columns handed to the submatrix reduction */
+    int64_t free_pivot[RPP_MAX_DIM + 1];  /* leftover columns whose first pivot was free */
+    int64_t additions[RPP_MAX_DIM + 1];   /* column additions in the submatrix reduction */
+    int64_t store_reads[RPP_MAX_DIM + 1]; /* pair-store lookups in the reduction */
+    int64_t intervals[RPP_MAX_DIM + 1];   /* nonzero intervals reported (index 0 = H0) */
+    double ms_device;                     /* wall time spent waiting on the GPU */
+    double ms_host_reduce;                /* wall time of the submatrix reductions */
+    double ms_host_h0;                    /* wall time of Kruskal */
+    double ms_total;
+} rpp_stats;
+
+typedef struct rpp_context rpp_context;
+typedef struct rpp_result rpp_result;
+
+/* Create a context on CUDA device `device`. mem_budget_bytes bounds the device
+ * workspace the context may hold (0 = no bound). Allocation is lazy. */
+rpp_status rpp_context_create(int device, size_t mem_budget_bytes, rpp_context **out);
+void rpp_context_destroy(rpp_context *ctx);
+
+/* Barcodes of dimensions 0..max_dim of Rips_t.
+ *   data       points (n x dim) or distances (n x n), float32, device or host.
+ *   kind       RPP_INPUT_POINTS or RPP_INPUT_DISTANCES (dim ignored).
+ *   n          number of points, n >= 1.
+ *   max_dim    0 <= max_dim <= RPP_MAX_DIM.
+ *   threshold  closed threshold t >= 0; +INFINITY means the full filtration.
+ *              The enclosing radius R bounds the work: min(t, R) is used,
+ *              which leaves every nonzero interval unchanged (Proposition in
+ *              Sec. "Filtering Out Simplices by Diameter Equal to the
+ *              Enclosing Radius").
+ *   stream     cudaStream_t or NULL.
+ *   out        receives a result handle on success.
+ * Errors: RPP_E_INVALID, RPP_E_OVERFLOW, RPP_E_NOMEM, RPP_E_CUDA. */
+rpp_status rpp_barcodes(rpp_context *ctx, const float *data, rpp_input_kind kind, int64_t n,
+                        int32_t dim, int32_t max_dim, float threshold, void *stream,
+                        rpp_result **out);
+
+/* As rpp_barcodes, with the threshold given as the nearest-rank quantile q in
+ * (0, 1] of the C(n,2) pairwise distances (the ceil(q * C(n,2))-th smallest
+ * distance). */
+rpp_status rpp_barcodes_quantile(rpp_context *ctx, const float *data, rpp_input_kind kind,
+                                 int64_t n, int32_t dim, int32_t max_dim, float quantile,
+                                 void *stream, rpp_result **out);
+
+/* Number of intervals of dimension p (0 <= p <= max_dim) in a result. */
+int64_t rpp_result_count(const rpp_result *res, int32_t p);
+/* Intervals of dimension p, host memory owned by the result, sorted by
+ * (birth, death). */
+const rpp_interval *rpp_result_intervals(const rpp_result *res, int32_t p);
+/* Realising edges, parallel to rpp_result_intervals. */
+const rpp_critical *rpp_result_critical(const rpp_result *res, int32_t p);
+rpp_status rpp_result_stats(const rpp_result *res, rpp_stats *out);
+void rpp_result_free(rpp_result *res);
+
+/* Many independent clouds in one call. Clouds are processed together: their
+ * distance matrices, filtrations and apparent-pair tests run as shared
+ * launches over all clouds, and the host reductions run on a thread pool.
+ *   data[i]       points of cloud i (n[i] x dim[i]), device or host.
+ *   thresholds    per cloud threshold (+INFINITY = full), or NULL for all full.
+ *   quantiles     per cloud quantile in (0,1] overriding the threshold, or NULL.
+ *   out[i]        result of cloud i.
+ * On error no result is returned. */
+rpp_status rpp_barcodes_batched(rpp_context *ctx, int32_t batch, const float *const *data,
+                                const int64_t *n, const int32_t *dim, int32_t max_dim,
+                                const float *thresholds, const float *quantiles, void *stream,
+                                rpp_result **out);
+
+/* Backward of the interval endpoints to the point coordinates.
+ * For every finite interval of dimension p >= 0 of result i, with birth edge
+ * (u, v) and death edge (u', v'):
+ *   grad_points[u]  += g_birth * (x_u - x_v) / |x_u - x_v|, grad_points[v] -= same,
+ *   grad_points[u'] += g_death * (x_u' - x_v') / |x_u' - x_v'|, grad_points[v'] -= same.
+ * (An endpoint is a distance |x_u - x_v|; this is its gradient.)
+ *   points       device, batch clouds stored back to back (cloud i at offset
+ *                sum_{j<i} n[j] * dim), float32.
+ *   results      the forward results, one per cloud (points input, same dim).
+ *   grad_birth, grad_death  device float32, one entry per interval of every
+ *                cloud, concatenated in (cloud, dimension, interval) order;
+ *                entries of essential deaths are ignored.
+ *   grad_points  device float32, same layout as points, overwritten.
+ * Zero-length intervals are not in the result, so they receive no gradient. */
+rpp_status rpp_barcodes_backward(rpp_context *ctx, int32_t batch, const float *points,
+                                 const int64_t *n, int32_t dim,
+                                 const rpp_result *const *results, const float *grad_birth,
+                                 const float *grad_death, float *grad_points, void *stream);
+
+/* Total interval count of a result over dimensions 0..max_dim. */
+int64_t rpp_result_total(const rpp_result *res);
+
+/* The distance matrix of points with the library's fixed float32 formula
+ * (Sec. 2: D[i,j] = d(point i, point j), D[i,i] = 0; per pair, s = 0,
+ * s = s + (x_k - y_k)^2 for k = 0..dim-1 rounded to nearest without fused
+ * multiply-add, then a correctly rounded square root).
+ *   points  n x dim float32, device or host.
+ *   out     n x n float32 row-major, device or host, caller-owned, overwritten. */
+rpp_status rpp_distance_matrix(rpp_context *ctx, const float *points, int64_t n, int32_t dim,
+                               float *out, void *stream);
+
+/* ---- recording of intermediate arrays (inspection and parity checks) ---- */
+
+#define RPP_RECORD_COLUMNS 1  /* keep each dimension's column array */
+#define RPP_RECORD_APPARENT 2 /* keep each dimension's apparent pairs */
+
+/* Make later calls on ctx copy the selected intermediate arrays into their
+ * results (0 turns recording off). Costs host memory and copy time. */
+rpp_status rpp_context_set_record(rpp_context *ctx, int32_t flags);
+
+/* The columns of dimension p (p >= 1) after the threshold and clearing, in
+ * coboundary order: decreasing diameter, then increasing combinatorial index
+ * (the output of Alg. 7). Sets *diam and *cidx to arrays owned by the result
+ * and returns their length, or -1 if the result did not record them. */
+int64_t rpp_result_columns(const rpp_result *res, int32_t p, const float **diam,
+                           const uint64_t **cidx);
+
+/* The apparent pairs (sigma of dimension p, tau of dimension p+1) found by the
+ * apparent-pair pass (Alg. 3), sorted by tau (the second layer of the pair
+ * store). Returns their number, or -1 if the result did not record them. */
+int64_t rpp_result_apparent(const rpp_result *res, int32_t p, const uint64_t **sigma,
+                            const uint64_t **tau);
+
+/* ---- serving: continuous batching of requests that arrive over time ---- */
+
+typedef struct rpp_server rpp_server;
+
+typedef struct {
+    int32_t max_slots;          /* requests in flight on the device at once */
+    size_t device_bytes;        /* device memory the admitted requests may hold */
+    int32_t host_threads;       /* threads for the host reductions (0 = auto) */
+    int32_t max_batch;          /* most requests fused into one launch */
+} rpp_server_config;
+
+rpp_status rpp_server_create(rpp_context *ctx, const rpp_server_config *cfg, rpp_server **out);
+/* Submit one request (points copied at submission, host or device memory).
+ * Returns RPP_E_BUSY if the request alone can never fit the memory bound. */
+rpp_status rpp_server_submit(rpp_server *srv, const float *points, int64_t n, int32_t dim,
+                             int32_t max_dim, float threshold, float quantile,
+                             uint64_t *ticket);
+/* Wait up to timeout_ms (< 0: forever) for a request; RPP_E_TIMEOUT if not done. */
+rpp_status rpp_server_poll(rpp_server *srv, uint64_t ticket, int32_t timeout_ms,
+                           rpp_result **out);
+/* Drain every outstanding request and stop the worker threads. */
+void rpp_server_destroy(rpp_server *srv);
+
+const char *rpp_status_string(rpp_status s);
+const char *rpp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RPP_H */

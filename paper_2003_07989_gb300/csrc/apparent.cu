@@ -1,0 +1,243 @@
+// apparent.cu -- the apparent-pair pass (Alg. 3, the Apparent Pairs Lemma and
+// Corollary "massively parallel") and the partition of its output (Fig.
+// "post-apparent", Sec. "Core System Optimizations").
+//
+// Column sigma (a p-simplex, vertices v_0 > ... > v_p) is tested on its own:
+//  (1) tau = sigma + {w*} where w* is the LARGEST vertex outside sigma with
+//      max_i D[v_i][w*] <= diam(sigma). Cofacet indices grow with the added
+//      vertex, so tau is the lexicographically greatest cofacet of equal
+//      diameter, i.e. the oldest cofacet (condition 1 of the lemma). If no
+//      such vertex exists sigma is not apparent.
+//  (2) The facets of tau in increasing index order drop its vertices in
+//      decreasing order (Alg. 5); the facets before sigma drop a vertex
+//      w > w*. sigma is apparent iff none of them has diam == diam(sigma)
+//      (condition 2; Proposition "apparent-support").
+// The paper runs one thread per column. Here a group of G lanes owns a column
+// and tests G candidate vertices w = scan, scan-1, ..., scan-G+1 per step: the
+// G reads D[v_i][w] of each row are contiguous, so every step is a coalesced
+// load of (p+1) short row segments (the rows are L2-resident). A warp ballot
+// picks the lowest qualifying lane, i.e. the largest w. Groups of one warp
+// advance independently: a group that finishes takes its next column in the
+// same iteration, so no lane idles while a neighbour scans a long column.
+// While scanning, each lane also tracks its oldest cofacet inside the
+// threshold (smallest diameter, then largest vertex); for a column with no
+// equal-diameter cofacet the scan covers every vertex, and the group reduces
+// these minima into the column's unreduced pivot, which the host reduction
+// uses to skip columns whose pivot nobody owns.
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace rpp {
+
+namespace {
+
+template <int P, int G>
+__global__ void __launch_bounds__(256) k_apparent(
+    const float *__restrict__ D, int64_t ld, int64_t n, const uint64_t *__restrict__ gB,
+    bool smem_table, const uint32_t *__restrict__ key_hi, const uint64_t *__restrict__ key_lo,
+    uint64_t ncols, const DevState *__restrict__ st, uint8_t *__restrict__ status,
+    uint64_t *__restrict__ pivot, float *__restrict__ pdiam) {
+    extern __shared__ uint64_t sB[];
+    const uint64_t *B = stage_binomial(gB, n, P + 2, sB, smem_table);
+    const float t = st->t;
+    const int lane = threadIdx.x & 31;
+    const int grp = lane / G, gl = lane % G;
+    const unsigned gmask = (G == 32) ? FULL_MASK : (((1u << G) - 1u) << (grp * G));
+    const uint64_t ngroups = ((uint64_t)gridDim.x * blockDim.x) / G;
+    uint64_t c = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+
+    bool have = false;
+    int v[P + 1];
+    float diam = 0.0f, best_d = 0.0f;
+    int scan = 0, best_v = -1;
+
+    for (;;) {
+        if (!have) {
+            while (c < ncols && status[c] == COL_CLEARED) c += ngroups;
+            if (c < ncols) {
+                have = true;
+                diam = __uint_as_float(~key_hi[c]);
+                decode_simplex<P>(key_lo[c], B, n, v);
+                scan = (int)n - 1;
+                best_d = __uint_as_float(0x7f800000u);
+                best_v = -1;
+            }
+        }
+        if (!__any_sync(FULL_MASK, have)) break;
+
+        bool ok = false;
+        float dv[P + 1];
+        const int x = scan - gl;
+        if (have && x >= 0) {
+            bool member = false;
+#pragma unroll
+            for (int i = 0; i <= P; ++i) member |= (x == v[i]);
+            if (!member) {
+                float m = 0.0f;
+#pragma unroll
+                for (int i = 0; i <= P; ++i) {
+                    dv[i] = D[(int64_t)v[i] * ld + x];
+                    m = fmaxf(m, dv[i]);
+                }
+                ok = m <= diam;
+                const float cd = fmaxf(m, diam);
+                if (cd <= t && cd < best_d) {
+                    best_d = cd;
+                    best_v = x;
+                }
+            }
+        }
+        const unsigned ball = __ballot_sync(FULL_MASK, ok);
+        if (have) {
+            const unsigned gb = (ball & gmask) >> (grp * G);
+            if (gb) {
+                const int first = __ffs(gb) - 1;  // lowest lane = largest vertex
+                if (gl == first) {
+                    bool apparent = true;
+#pragma unroll
+                    for (int i = 0; i <= P; ++i) {
+                        if (v[i] > x) {  // facet tau - {v_i} precedes sigma
+                            float fd = 0.0f;
+#pragma unroll
+                            for (int k = 0; k <= P; ++k)
+                                if (k != i) fd = fmaxf(fd, dv[k]);
+#pragma unroll
+                            for (int a = 0; a <= P; ++a)
+#pragma unroll
+                                for (int b = a + 1; b <= P; ++b)
+                                    if (a != i && b != i)
+                                        fd = fmaxf(fd, D[(int64_t)v[a] * ld + v[b]]);
+                            if (fd == diam) apparent = false;
+                        }
+                    }
+                    status[c] = apparent ? COL_APPARENT : COL_LEFTOVER;
+                    pivot[c] = cofacet_index<P>(v, x, B, n);
+                    pdiam[c] = diam;
+                }
+                have = false;
+                c += ngroups;
+            } else if (scan - G < 0) {
+                // every vertex seen, none of equal diameter: reduce the oldest cofacet
+#pragma unroll
+                for (int o = G / 2; o > 0; o >>= 1) {
+                    const float od = __shfl_xor_sync(gmask, best_d, o);
+                    const int ov = __shfl_xor_sync(gmask, best_v, o);
+                    if (od < best_d || (od == best_d && ov > best_v)) {
+                        best_d = od;
+                        best_v = ov;
+                    }
+                }
+                if (gl == 0) {
+                    status[c] = COL_LEFTOVER;
+                    pivot[c] = best_v >= 0 ? cofacet_index<P>(v, best_v, B, n) : NO_PIVOT;
+                    pdiam[c] = best_d;
+                }
+                have = false;
+                c += ngroups;
+            } else {
+                scan -= G;
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_partition(
+    const uint8_t *__restrict__ status, const uint32_t *__restrict__ key_hi,
+    const uint64_t *__restrict__ key_lo, const uint64_t *__restrict__ pivot,
+    const float *__restrict__ pdiam, uint64_t ncols, uint64_t *__restrict__ app_tau,
+    uint64_t *__restrict__ app_sigma, Leftover *__restrict__ left, DevState *st) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < ncols;
+         base += stride) {
+        const uint64_t c = base + lane;
+        const uint8_t s = c < ncols ? status[c] : (uint8_t)COL_CLEARED;
+        const bool a = s == COL_APPARENT, l = s == COL_LEFTOVER;
+        const unsigned ba = __ballot_sync(FULL_MASK, a), bl = __ballot_sync(FULL_MASK, l);
+        if (ba) {
+            unsigned long long off = 0;
+            if (lane == 0) off = atomicAdd(&st->napp, (unsigned long long)__popc(ba));
+            off = __shfl_sync(FULL_MASK, off, 0);
+            if (a) {
+                const uint64_t pos = off + __popc(ba & lanemask_lt());
+                app_tau[pos] = pivot[c];
+                app_sigma[pos] = key_lo[c];
+            }
+        }
+        if (bl) {
+            unsigned long long off = 0;
+            if (lane == 0) off = atomicAdd(&st->nleft, (unsigned long long)__popc(bl));
+            off = __shfl_sync(FULL_MASK, off, 0);
+            if (l) {
+                const uint64_t pos = off + __popc(bl & lanemask_lt());
+                Leftover L;
+                L.sigma = key_lo[c];
+                L.pivot = pivot[c];
+                L.diam = __uint_as_float(~key_hi[c]);
+                L.pdiam = pdiam[c];
+                L.index = c;
+                left[pos] = L;
+            }
+        }
+    }
+}
+
+template <int P, int G>
+void apparent_pg(const float *D, int64_t ld, int64_t n, const uint64_t *binom,
+                 const uint32_t *key_hi, const uint64_t *key_lo, uint64_t ncols,
+                 const DevState *st, uint8_t *status, uint64_t *pivot, float *pdiam, int sms,
+                 cudaStream_t s) {
+    const size_t table = (size_t)(P + 3) * (n + 1) * sizeof(uint64_t);
+    const bool smem = table <= 48 * 1024;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apparent<P, G>, 256,
+                                                  smem ? table : 0);
+    if (per_sm < 1) per_sm = 1;
+    uint64_t blocks = (uint64_t)sms * per_sm;
+    const uint64_t need = (ncols * G + 255) / 256;
+    if (need < blocks) blocks = need;
+    if (blocks == 0) return;
+    k_apparent<P, G><<<(unsigned)blocks, 256, smem ? table : 0, s>>>(
+        D, ld, n, binom, smem, key_hi, key_lo, ncols, st, status, pivot, pdiam);
+}
+
+template <int P>
+void apparent_p(int group, const float *D, int64_t ld, int64_t n, const uint64_t *binom,
+                const uint32_t *key_hi, const uint64_t *key_lo, uint64_t ncols,
+                const DevState *st, uint8_t *status, uint64_t *pivot, float *pdiam, int sms,
+                cudaStream_t s) {
+    switch (group) {
+        case 4: apparent_pg<P, 4>(D, ld, n, binom, key_hi, key_lo, ncols, st, status, pivot, pdiam, sms, s); break;
+        case 16: apparent_pg<P, 16>(D, ld, n, binom, key_hi, key_lo, ncols, st, status, pivot, pdiam, sms, s); break;
+        case 32: apparent_pg<P, 32>(D, ld, n, binom, key_hi, key_lo, ncols, st, status, pivot, pdiam, sms, s); break;
+        default: apparent_pg<P, 8>(D, ld, n, binom, key_hi, key_lo, ncols, st, status, pivot, pdiam, sms, s); break;
+    }
+}
+
+}  // namespace
+
+void launch_apparent(const float *D, int64_t ld, int64_t n, int p, const uint64_t *binom,
+                     const uint32_t *key_hi, const uint64_t *key_lo, uint64_t ncols,
+                     const DevState *st, uint8_t *status, uint64_t *pivot, float *pdiam, int group,
+                     int sms, cudaStream_t s) {
+    if (ncols == 0) return;
+    switch (p) {
+        case 1: apparent_p<1>(group, D, ld, n, binom, key_hi, key_lo, ncols, st, status, pivot, pdiam, sms, s); break;
+        case 2: apparent_p<2>(group, D, ld, n, binom, key_hi, key_lo, ncols, st, status, pivot, pdiam, sms, s); break;
+        case 3: apparent_p<3>(group, D, ld, n, binom, key_hi, key_lo, ncols, st, status, pivot, pdiam, sms, s); break;
+        case 4: apparent_p<4>(group, D, ld, n, binom, key_hi, key_lo, ncols, st, status, pivot, pdiam, sms, s); break;
+        default: break;
+    }
+}
+
+void launch_partition(const uint8_t *status, const uint32_t *key_hi, const uint64_t *key_lo,
+                      const uint64_t *pivot, const float *pdiam, uint64_t ncols, uint64_t *app_tau,
+                      uint64_t *app_sigma, Leftover *left, DevState *st, cudaStream_t s) {
+    if (ncols == 0) return;
+    uint64_t blocks = (ncols + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    k_partition<<<(unsigned)blocks, 256, 0, s>>>(status, key_hi, key_lo, pivot, pdiam, ncols,
+                                                  app_tau, app_sigma, left, st);
+}
+
+}  // namespace rpp

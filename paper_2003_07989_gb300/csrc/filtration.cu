@@ -1,0 +1,134 @@
+// filtration.cu -- filtration construction with clearing (Alg. 6 and Alg. 7,
+// Sec. "Filtration Construction with Clearing").
+//
+// Every index c in [0, C(n, p+1)) names one p-simplex. A thread decodes c with
+// the binomial table staged in shared memory, takes the diameter (the largest
+// of the C(p+1, 2) distances among its vertices, Sec. 2), and keeps the simplex
+// when diam <= t and it was not paired as a death in dimension p-1 (the
+// clearing lemma, Sec. "Clearing Lemma"; the previous dimension's deaths are a
+// bitmap over indices). Instead of writing (-inf, +inf) sentinels for dropped
+// simplices and sorting everything as Alg. 6/7 do, kept simplices are
+// compacted with warp-aggregated atomics (Sec. "Warp-based Filtering"): one
+// atomic per warp reserves space, lanes write at their ballot rank. The sort
+// key is (~bits(diam), cidx): ascending key order is decreasing diameter, then
+// increasing index, which is coboundary order.
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace rpp {
+
+namespace {
+
+template <int P>
+__global__ void __launch_bounds__(256) k_build_columns(const float *__restrict__ D, int64_t ld,
+                                                        int64_t n, const uint64_t *__restrict__ gB,
+                                                        bool smem_table, uint64_t total,
+                                                        const uint32_t *__restrict__ cleared,
+                                                        DevState *st, uint32_t *__restrict__ key_hi,
+                                                        uint64_t *__restrict__ key_lo) {
+    extern __shared__ uint64_t sB[];
+    const uint64_t *B = stage_binomial(gB, n, P + 1, sB, smem_table);
+    const float t = st->t;
+    const int lane = threadIdx.x & 31;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < total;
+         base += stride) {
+        const uint64_t c = base + lane;
+        bool keep = false;
+        float d = 0.0f;
+        if (c < total && !(cleared && ((cleared[c >> 5] >> (c & 31)) & 1u))) {
+            int v[P + 1];
+            decode_simplex<P>(c, B, n, v);
+#pragma unroll
+            for (int a = 0; a <= P; ++a)
+#pragma unroll
+                for (int b = a + 1; b <= P; ++b) d = fmaxf(d, D[(int64_t)v[a] * ld + v[b]]);
+            keep = d <= t;
+        }
+        const unsigned ball = __ballot_sync(FULL_MASK, keep);
+        if (ball) {
+            unsigned long long off = 0;
+            if (lane == 0) off = atomicAdd(&st->ncols, (unsigned long long)__popc(ball));
+            off = __shfl_sync(FULL_MASK, off, 0);
+            if (keep) {
+                const uint64_t pos = off + __popc(ball & lanemask_lt());
+                key_hi[pos] = ~__float_as_uint(d);
+                key_lo[pos] = c;
+            }
+        }
+    }
+}
+
+__global__ void k_mark_cleared(const uint32_t *__restrict__ pos, int64_t count,
+                               uint8_t *__restrict__ status) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) status[pos[i]] = COL_CLEARED;
+}
+
+__global__ void k_bitmap_set(const uint64_t *__restrict__ idx, uint64_t count,
+                             uint32_t *__restrict__ bitmap) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) {
+        const uint64_t c = idx[i];
+        atomicOr(&bitmap[c >> 5], 1u << (c & 31));
+    }
+}
+
+// First position i in [0, n) with a[i] >= key (a ascending), into *out.
+__global__ void k_lower_bound_u32(const uint32_t *__restrict__ a, uint64_t n, uint32_t key,
+                                  unsigned long long *out) {
+    uint64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const uint64_t mid = (lo + hi) >> 1;
+        if (a[mid] < key) lo = mid + 1;
+        else hi = mid;
+    }
+    *out = lo;
+}
+
+template <int P>
+void build_p(const float *D, int64_t ld, int64_t n, const uint64_t *binom, uint64_t total,
+             const uint32_t *cleared, DevState *st, uint32_t *key_hi, uint64_t *key_lo,
+             cudaStream_t s) {
+    const size_t table = (size_t)(P + 2) * (n + 1) * sizeof(uint64_t);
+    const bool smem = table <= 160 * 1024;
+    if (smem) cudaFuncSetAttribute(k_build_columns<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)table);
+    uint64_t blocks = (total + 255) / 256;
+    const uint64_t cap = 152ull * 8;
+    if (blocks > cap) blocks = cap;
+    if (blocks == 0) return;
+    k_build_columns<P><<<(unsigned)blocks, 256, smem ? table : 0, s>>>(
+        D, ld, n, binom, smem, total, cleared, st, key_hi, key_lo);
+}
+
+}  // namespace
+
+void launch_build_columns(const float *D, int64_t ld, int64_t n, int p, const uint64_t *binom,
+                          uint64_t total, const uint32_t *cleared, DevState *st, uint32_t *key_hi,
+                          uint64_t *key_lo, cudaStream_t s) {
+    switch (p) {
+        case 1: build_p<1>(D, ld, n, binom, total, cleared, st, key_hi, key_lo, s); break;
+        case 2: build_p<2>(D, ld, n, binom, total, cleared, st, key_hi, key_lo, s); break;
+        case 3: build_p<3>(D, ld, n, binom, total, cleared, st, key_hi, key_lo, s); break;
+        case 4: build_p<4>(D, ld, n, binom, total, cleared, st, key_hi, key_lo, s); break;
+        default: break;
+    }
+}
+
+void launch_mark_cleared(const uint32_t *pos, int64_t count, uint8_t *status, cudaStream_t s) {
+    if (count <= 0) return;
+    k_mark_cleared<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(pos, count, status);
+}
+
+void launch_lower_bound_u32(const uint32_t *a, uint64_t n, uint32_t key, unsigned long long *out,
+                            cudaStream_t s) {
+    k_lower_bound_u32<<<1, 1, 0, s>>>(a, n, key, out);
+}
+
+void launch_bitmap_set(const uint64_t *idx, uint64_t count, uint32_t *bitmap, cudaStream_t s) {
+    if (count == 0) return;
+    k_bitmap_set<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(idx, count, bitmap);
+}
+
+}  // namespace rpp

@@ -1,0 +1,78 @@
+// host.h -- host-side stages of the pipeline: H0 by Kruskal, the submatrix
+// reduction of the leftover columns, and barcode assembly.
+#pragma once
+
+#include <stdint.h>
+
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/rpp.h"
+#include "internal.h"
+
+namespace rpp {
+
+// Read-only view of one instance for the host stages.
+struct HostInstance {
+    int64_t n = 0;
+    const float *D = nullptr;  // host copy, row stride ld
+    int64_t ld = 0;
+    const Binomial *B = nullptr;
+    float t = 0.0f;            // threshold in use
+    float dist(int a, int b) const { return D[(int64_t)a * ld + b]; }
+};
+
+// Vertices v[0] > ... > v[p] of a p-simplex index.
+void decode_host(const Binomial &B, uint64_t c, int p, int64_t n, int *v);
+// Youngest edge of a simplex (largest distance; ties: smallest edge index),
+// returned as (u, w) with u > w.
+void youngest_edge(const HostInstance &I, const int *v, int k, int32_t *u, int32_t *w);
+
+// One persistence pair found on the host (or an essential class, tau = NO_PIVOT).
+struct HostPair {
+    uint64_t sigma, tau;
+    float birth, death;
+};
+
+// ---- H0 -------------------------------------------------------------------
+// Union-find over edges given in filtration order (increasing diameter, then
+// decreasing index). Keeps state across chunks of edges.
+struct Kruskal {
+    std::vector<int32_t> parent, size_;
+    int64_t components = 0;
+    std::vector<HostPair> deaths;     // (vertex index in sigma, edge in tau)
+    std::vector<uint32_t> mst_pos;    // positions (in the edge array) of merging edges
+    void init(int64_t n);
+    int32_t find(int32_t x);
+    // Process edges e[k] for k = 0..count-1 in this order; pos0 - k is the
+    // position of e[k] in the coboundary-ordered edge array.
+    void run(const uint32_t *hi, const uint64_t *lo, int64_t count, int64_t pos0,
+             const Binomial &B, int64_t n);
+};
+
+// ---- submatrix reduction ----------------------------------------------------
+// Two-layer pair store (Sec. "Core System Optimizations", Fig. "two-layer
+// data structure"): pairs found by the reduction live in a hash map, apparent
+// pairs in an array sorted by tau searched with binary search.
+struct PairStore {
+    const uint64_t *app_tau = nullptr;    // sorted ascending
+    const uint64_t *app_sigma = nullptr;
+    uint64_t napp = 0;
+    std::unordered_map<uint64_t, int64_t> reduced;  // tau -> leftover slot
+    int64_t reads = 0;
+    // 0: free; 1: apparent (sigma in *sigma); 2: reduced (slot in *slot)
+    int lookup(uint64_t tau, uint64_t *sigma, int64_t *slot);
+};
+
+struct ReduceStats {
+    int64_t free_pivot = 0, additions = 0, reads = 0;
+};
+
+// Reduce the leftover columns of dimension p (given in coboundary order) with
+// the reduction-matrix technique (Sec. "Reduction Matrix vs. Oblivious Matrix
+// Reduction"): each column is reduced by adding the reduced columns that own
+// its current pivot. Appends pairs (zero-length included) and essential classes.
+void reduce_leftovers(const HostInstance &I, int p, const Leftover *left, int64_t nleft,
+                      PairStore &store, std::vector<HostPair> &out, ReduceStats &stats);
+
+}  // namespace rpp

@@ -1,0 +1,611 @@
+// pipeline.cpp -- one instance end to end: distances, threshold, H0, and per
+// dimension p the filtration with clearing, the apparent-pair pass, the
+// partition and the submatrix reduction (the flow of Fig. "framework" (b)).
+//
+// Host <-> device crossings, as in the paper's hybrid design:
+//   * after the dimension-1 filtration is sorted, its shortest edges go to the
+//     host for Kruskal; the merging edges come back as cleared columns;
+//   * after the partition of dimension p, the leftover columns and the apparent
+//     pairs (sorted by tau) go to the host for the submatrix reduction;
+//   * the deaths the host found return to the device as the clearing bitmap of
+//     dimension p + 1, together with the apparent taus already there.
+#include "pipeline.h"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+namespace rpp {
+
+namespace {
+
+double now_ms() {
+    return std::chrono::duration<double, std::milli>(
+               std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
+int bits_for(uint64_t x) {  // bits needed to write x (0 for x = 0)
+    int b = 0;
+    while (b < 64 && (x >> b)) ++b;
+    return b;
+}
+
+#define RPP_CK(call)                                                                  \
+    do {                                                                              \
+        cudaError_t e_ = (call);                                                      \
+        if (e_ != cudaSuccess) {                                                      \
+            Status st_;                                                               \
+            st_.code = RPP_E_CUDA;                                                    \
+            st_.msg = std::string(#call) + ": " + cudaGetErrorString(e_);             \
+            return st_;                                                               \
+        }                                                                             \
+    } while (0)
+
+#define RPP_TRY(expr)             \
+    do {                          \
+        Status s_ = (expr);       \
+        if (!s_.ok()) return s_;  \
+    } while (0)
+
+Status fail(rpp_status code, const std::string &msg) {
+    Status s;
+    s.code = code;
+    s.msg = msg;
+    return s;
+}
+
+float bits_to_float(uint32_t b) {
+    float f;
+    std::memcpy(&f, &b, sizeof f);
+    return f;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// workspace
+
+Workspace::~Workspace() {
+    DevBuf *d[] = {&X,    &Dsrc,  &D,      &state,   &binom,     &key_hi, &key_lo,
+                   &tmp_hi, &tmp_lo, &tmp_val, &tiles, &hist,      &status, &pivot,
+                   &pdiam, &app_tau, &app_sigma, &left, &bitmap, &mst,    &up};
+    for (DevBuf *b : d)
+        if (b->p) cudaFree(b->p);
+    HostBuf *h[] = {&h_hi, &h_lo, &h_tau, &h_sigma, &h_left, &h_D, &h_state, &h_mst, &h_up};
+    for (HostBuf *b : h)
+        if (b->p) cudaFreeHost(b->p);
+}
+
+Status Workspace::dev(DevBuf &b, size_t bytes, void **out) {
+    if (bytes == 0) bytes = 256;
+    if (b.bytes < bytes) {
+        size_t want = ((bytes + bytes / 4) + 255) & ~(size_t)255;
+        const size_t others = device_bytes - b.bytes;
+        if (budget && others + want > budget) want = (bytes + 255) & ~(size_t)255;
+        if (budget && others + want > budget)
+            return fail(RPP_E_NOMEM, "device workspace would exceed the context's memory budget");
+        if (b.p) {
+            cudaFree(b.p);
+            device_bytes -= b.bytes;
+            b.p = nullptr;
+            b.bytes = 0;
+        }
+        cudaError_t e = cudaMalloc(&b.p, want);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            b.p = nullptr;
+            return fail(RPP_E_NOMEM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+        }
+        b.bytes = want;
+        device_bytes += want;
+    }
+    *out = b.p;
+    return Status();
+}
+
+Status Workspace::host(HostBuf &b, size_t bytes, void **out) {
+    if (bytes == 0) bytes = 256;
+    if (b.bytes < bytes) {
+        size_t want = ((bytes + bytes / 4) + 4095) & ~(size_t)4095;
+        if (b.p) cudaFreeHost(b.p);
+        b.p = nullptr;
+        b.bytes = 0;
+        cudaError_t e = cudaMallocHost(&b.p, want);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(RPP_E_NOMEM, std::string("cudaMallocHost failed: ") + cudaGetErrorString(e));
+        }
+        b.bytes = want;
+    }
+    *out = b.p;
+    return Status();
+}
+
+// ---------------------------------------------------------------------------
+// helpers
+
+void fill_binomial(int64_t n, int kmax, std::vector<uint64_t> &store, Binomial &B) {
+    store.assign((size_t)(kmax + 1) * (n + 1), 0);
+    const uint64_t SAT = ~0ull;
+    for (int64_t v = 0; v <= n; ++v) {
+        store[v] = 1;  // C(v, 0)
+        for (int k = 1; k <= kmax; ++k) {
+            if (v == 0) {
+                store[(size_t)k * (n + 1)] = 0;
+                continue;
+            }
+            // C(v, k) = C(v-1, k-1) + C(v-1, k)
+            const uint64_t a = store[(size_t)(k - 1) * (n + 1) + v - 1];
+            const uint64_t b = store[(size_t)k * (n + 1) + v - 1];
+            store[(size_t)k * (n + 1) + v] =
+                (a == SAT || b == SAT || a + b < a || a + b > (1ull << 63)) ? SAT : a + b;
+        }
+    }
+    B.n = n;
+    B.kmax = kmax;
+    B.host = store.data();
+}
+
+bool is_device_pointer(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+Status validate_instance(const Instance &in) {
+    if (!in.data) return fail(RPP_E_INVALID, "data is NULL");
+    if (in.n < 1) return fail(RPP_E_INVALID, "n must be >= 1");
+    if (in.n > (1ll << 31) - 2) return fail(RPP_E_INVALID, "n too large");
+    if (in.max_dim < 0 || in.max_dim > RPP_MAX_DIM)
+        return fail(RPP_E_INVALID, "max_dim must be in [0, RPP_MAX_DIM]");
+    if (in.kind != RPP_INPUT_POINTS && in.kind != RPP_INPUT_DISTANCES)
+        return fail(RPP_E_INVALID, "unknown input kind");
+    if (in.kind == RPP_INPUT_POINTS && in.dim < 1) return fail(RPP_E_INVALID, "dim must be >= 1");
+    if (std::isnan(in.threshold) || in.threshold < 0.0f)
+        return fail(RPP_E_INVALID, "threshold must be >= 0 or +INFINITY");
+    if (in.quantile != 0.0f && !(in.quantile > 0.0f && in.quantile <= 1.0f))
+        return fail(RPP_E_INVALID, "quantile must be in (0, 1]");
+    // every index up to dimension max_dim + 1 must fit in 63 bits
+    std::vector<uint64_t> store;
+    Binomial B;
+    fill_binomial(in.n, in.max_dim + 2, store, B);
+    if (B.at(in.max_dim + 2, in.n) == ~0ull)
+        return fail(RPP_E_OVERFLOW, "C(n, max_dim + 2) does not fit the 63-bit index");
+    for (int p = 1; p <= in.max_dim; ++p)
+        if (B.at(p + 1, in.n) >= (1ull << 32))
+            return fail(RPP_E_NOMEM, "more than 2^32 candidate simplices in one dimension");
+    return Status();
+}
+
+// Device bytes run_instance requests for an instance, including the growth
+// slack of Workspace::dev (what a workspace holds after running it).
+size_t instance_device_bytes(const Instance &in) {
+    std::vector<uint64_t> store;
+    Binomial B;
+    const int kmax = in.max_dim + 2 < 3 ? 3 : in.max_dim + 2;
+    fill_binomial(in.n, kmax, store, B);
+    const int64_t n = in.n, ld = (n + 31) / 32 * 32;
+    uint64_t maxcand = 0;
+    for (int p = 1; p <= std::max(1, in.max_dim); ++p) maxcand = std::max(maxcand, B.at(p + 1, n));
+    auto slack = [](size_t b) { return ((b + b / 4) + 255) & ~(size_t)255; };
+    size_t total = 0;
+    total += slack(store.size() * 8) + slack(sizeof(DevState)) + slack((size_t)n * ld * 4);
+    if (in.kind == RPP_INPUT_POINTS) total += slack((size_t)n * in.dim * 4);
+    else total += slack((size_t)n * n * 4);
+    const size_t per = 4 + 8 + 4 + 8 + 8 + 1 + 8 + 4 + 8 + 8 + sizeof(Leftover);
+    total += slack(maxcand * per) + slack(radix_tile_counts_size(maxcand) * 4) + slack(12 * 256 * 4);
+    total += slack((size_t)n * 4) + slack(maxcand / 8 + 8) + slack(maxcand * 8);
+    return total + 64 * 256;  // per-buffer rounding
+}
+
+// ---------------------------------------------------------------------------
+// the pipeline
+
+namespace {
+
+struct DimOutput {
+    std::vector<HostPair> pairs;  // host-found pairs (zero-length included) and essentials
+};
+
+void add_interval(rpp_result *res, int q, float b, float d, const rpp_critical &c) {
+    rpp_interval iv;
+    iv.birth = b;
+    iv.death = d;
+    res->iv[q].push_back(iv);
+    res->cr[q].push_back(c);
+}
+
+void sort_result(rpp_result *res, int q) {
+    std::vector<size_t> idx(res->iv[q].size());
+    for (size_t i = 0; i < idx.size(); ++i) idx[i] = i;
+    auto &iv = res->iv[q];
+    auto &cr = res->cr[q];
+    std::sort(idx.begin(), idx.end(), [&](size_t a, size_t b) {
+        if (iv[a].birth != iv[b].birth) return iv[a].birth < iv[b].birth;
+        if (iv[a].death != iv[b].death) return iv[a].death < iv[b].death;
+        const int32_t ka[4] = {cr[a].bu, cr[a].bv, cr[a].du, cr[a].dv};
+        const int32_t kb[4] = {cr[b].bu, cr[b].bv, cr[b].du, cr[b].dv};
+        return std::lexicographical_compare(ka, ka + 4, kb, kb + 4);
+    });
+    std::vector<rpp_interval> iv2(idx.size());
+    std::vector<rpp_critical> cr2(idx.size());
+    for (size_t i = 0; i < idx.size(); ++i) {
+        iv2[i] = iv[idx[i]];
+        cr2[i] = cr[idx[i]];
+    }
+    iv.swap(iv2);
+    cr.swap(cr2);
+}
+
+}  // namespace
+
+Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStream_t s,
+                    rpp_result *res) {
+    const double t0 = now_ms();
+    double dev_ms = 0.0, red_ms = 0.0, h0_ms = 0.0;
+    RPP_TRY(validate_instance(in));
+    RPP_CK(cudaSetDevice(ws.device));
+    const int64_t n = in.n;
+    const int max_dim = in.max_dim;
+    const int64_t ld = (n + 31) / 32 * 32;
+    res->max_dim = max_dim;
+    for (int q = 0; q <= RPP_MAX_DIM; ++q) {
+        res->iv[q].clear();
+        res->cr[q].clear();
+    }
+    rpp_stats &S = res->stats;
+    std::memset(&S, 0, sizeof S);
+    S.n = n;
+    S.max_dim = max_dim;
+
+    // binomial table, cached per (n, kmax)
+    const int kmax = max_dim + 2 < 3 ? 3 : max_dim + 2;
+    void *vp;
+    if (ws.binom_n != n || ws.binom_k < kmax) {
+        fill_binomial(n, kmax, ws.binom_store, ws.binom_host);
+        ws.binom_n = n;
+        ws.binom_k = kmax;
+        ws.binom_on_device = false;
+    }
+    const Binomial &B = ws.binom_host;
+    RPP_TRY(ws.dev(ws.binom, ws.binom_store.size() * 8, &vp));
+    uint64_t *d_binom = (uint64_t *)vp;
+    if (!ws.binom_on_device) {
+        RPP_CK(cudaMemcpyAsync(d_binom, ws.binom_store.data(), ws.binom_store.size() * 8,
+                               cudaMemcpyHostToDevice, s));
+        RPP_CK(cudaStreamSynchronize(s));  // the host table may be refilled later
+        ws.binom_on_device = true;
+    }
+
+    // device state
+    RPP_TRY(ws.dev(ws.state, sizeof(DevState), &vp));
+    DevState *st = (DevState *)vp;
+    RPP_TRY(ws.host(ws.h_state, sizeof(DevState), &vp));
+    DevState *hst = (DevState *)vp;
+    RPP_CK(cudaMemsetAsync(st, 0, sizeof(DevState), s));
+
+    // distances
+    RPP_TRY(ws.dev(ws.D, (size_t)n * ld * sizeof(float), &vp));
+    float *D = (float *)vp;
+    if (in.kind == RPP_INPUT_POINTS) {
+        const float *X = in.data;
+        if (!is_device_pointer(X)) {
+            RPP_TRY(ws.dev(ws.X, (size_t)n * in.dim * sizeof(float), &vp));
+            RPP_CK(cudaMemcpyAsync(vp, X, (size_t)n * in.dim * sizeof(float),
+                                   cudaMemcpyHostToDevice, s));
+            X = (const float *)vp;
+        }
+        launch_distance_matrix(X, n, in.dim, D, ld, s);
+    } else {
+        const float *src = in.data;
+        if (!is_device_pointer(src)) {
+            RPP_TRY(ws.dev(ws.Dsrc, (size_t)n * n * sizeof(float), &vp));
+            RPP_CK(cudaMemcpyAsync(vp, src, (size_t)n * n * sizeof(float), cudaMemcpyHostToDevice,
+                                   s));
+            src = (const float *)vp;
+        }
+        launch_copy_validate_distances(src, n, D, ld, st, s);
+    }
+    const float t_user = in.quantile > 0.0f ? INFINITY : in.threshold;
+    launch_enclosing_radius(D, n, ld, st, t_user, s);
+    RPP_CK(cudaGetLastError());
+
+    // host copy of D for the reduction and the realising edges
+    RPP_TRY(ws.host(ws.h_D, (size_t)n * ld * sizeof(float), &vp));
+    float *hD = (float *)vp;
+    RPP_CK(cudaMemcpyAsync(hD, D, (size_t)n * ld * sizeof(float), cudaMemcpyDeviceToHost, s));
+
+    // buffers sized for the largest dimension
+    uint64_t maxcand = 0;
+    for (int p = 1; p <= std::max(1, max_dim); ++p) maxcand = std::max(maxcand, B.at(p + 1, n));
+    uint32_t *key_hi, *tmp_hi, *tiles, *hist, *mst;
+    uint64_t *key_lo, *tmp_lo, *tmp_val, *pivot, *app_tau, *app_sigma;
+    uint8_t *status;
+    float *pdiam;
+    Leftover *left;
+    RPP_TRY(ws.dev(ws.key_hi, maxcand * 4, (void **)&key_hi));
+    RPP_TRY(ws.dev(ws.key_lo, maxcand * 8, (void **)&key_lo));
+    RPP_TRY(ws.dev(ws.tmp_hi, maxcand * 4, (void **)&tmp_hi));
+    RPP_TRY(ws.dev(ws.tmp_lo, maxcand * 8, (void **)&tmp_lo));
+    RPP_TRY(ws.dev(ws.tmp_val, maxcand * 8, (void **)&tmp_val));
+    RPP_TRY(ws.dev(ws.tiles, radix_tile_counts_size(maxcand) * 4, (void **)&tiles));
+    RPP_TRY(ws.dev(ws.hist, 12 * 256 * 4, (void **)&hist));
+    RPP_TRY(ws.dev(ws.status, maxcand, (void **)&status));
+    RPP_TRY(ws.dev(ws.pivot, maxcand * 8, (void **)&pivot));
+    RPP_TRY(ws.dev(ws.pdiam, maxcand * 4, (void **)&pdiam));
+    RPP_TRY(ws.dev(ws.app_tau, maxcand * 8, (void **)&app_tau));
+    RPP_TRY(ws.dev(ws.app_sigma, maxcand * 8, (void **)&app_sigma));
+    RPP_TRY(ws.dev(ws.left, maxcand * sizeof(Leftover), (void **)&left));
+    RPP_TRY(ws.dev(ws.mst, (size_t)n * 4, (void **)&mst));
+
+    auto read_state = [&]() -> Status {
+        double a = now_ms();
+        RPP_CK(cudaMemcpyAsync(hst, st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+        RPP_CK(cudaStreamSynchronize(s));
+        dev_ms += now_ms() - a;
+        return Status();
+    };
+
+    RPP_TRY(read_state());
+    if (hst->err) {
+        std::string m = "invalid input:";
+        if (hst->err & ERR_NONFINITE) m += " non-finite value;";
+        if (hst->err & ERR_NEGATIVE) m += " negative distance;";
+        if (hst->err & ERR_ASYMMETRIC) m += " asymmetric matrix;";
+        if (hst->err & ERR_DIAGONAL) m += " nonzero diagonal;";
+        return fail(RPP_E_INVALID, m);
+    }
+    S.enclosing_radius = hst->R;
+    float t = hst->t;
+
+    HostInstance I;
+    I.n = n;
+    I.D = hD;
+    I.ld = ld;
+    I.B = &B;
+
+    Kruskal K;
+    K.init(n);
+    std::vector<uint64_t> prev_deaths;  // host-found deaths of the previous dimension
+    uint64_t prev_napp = 0;
+
+    if (n >= 2) {
+        // ---- dimension 1 columns: every edge inside the threshold, sorted ----
+        const uint64_t m = B.at(2, n);
+        S.candidates[1] = (int64_t)m;
+        launch_build_columns(D, ld, n, 1, d_binom, m, nullptr, st, key_hi, key_lo, s);
+        RPP_CK(cudaGetLastError());
+        RPP_TRY(read_state());
+        const uint64_t N = hst->ncols;
+        radix_sort(key_hi, key_lo, nullptr, tmp_hi, tmp_lo, nullptr, tiles, hist, N,
+                   bits_for(m - 1), 32, s);
+        RPP_CK(cudaGetLastError());
+        uint64_t begin = 0;
+        if (in.quantile > 0.0f) {
+            // threshold = ceil(q m)-th smallest distance; distances above R were
+            // dropped, and if the quantile lies above R, R itself is used.
+            uint64_t r = (uint64_t)std::ceil((double)in.quantile * (double)m);
+            r = std::max<uint64_t>(1, std::min<uint64_t>(r, m));
+            if (r <= N) {
+                uint32_t kh;
+                RPP_CK(cudaMemcpyAsync(&kh, key_hi + (N - r), 4, cudaMemcpyDeviceToHost, s));
+                RPP_CK(cudaStreamSynchronize(s));
+                t = bits_to_float(~kh);
+                launch_lower_bound_u32(key_hi, N, kh, &st->begin, s);
+                RPP_CK(cudaMemcpyAsync(&st->t, &t, sizeof(float), cudaMemcpyHostToDevice, s));
+                RPP_TRY(read_state());
+                begin = hst->begin;
+            }
+        }
+        S.threshold = t;
+        I.t = t;
+        const uint64_t cols = N - begin;
+
+        // ---- H0: Kruskal on the shortest edges, copied from the tail ----
+        {
+            uint64_t done = 0, chunk = std::min<uint64_t>(cols, 1ull << 16);
+            while (K.components > 1 && done < cols) {
+                const uint64_t cnt = std::min<uint64_t>(chunk, cols - done);
+                const uint64_t first = N - done - cnt;  // array position of the chunk start
+                RPP_TRY(ws.host(ws.h_hi, cnt * 4, &vp));
+                uint32_t *hhi = (uint32_t *)vp;
+                RPP_TRY(ws.host(ws.h_lo, cnt * 8, &vp));
+                uint64_t *hlo = (uint64_t *)vp;
+                double a = now_ms();
+                RPP_CK(cudaMemcpyAsync(hhi, key_hi + first, cnt * 4, cudaMemcpyDeviceToHost, s));
+                RPP_CK(cudaMemcpyAsync(hlo, key_lo + first, cnt * 8, cudaMemcpyDeviceToHost, s));
+                RPP_CK(cudaStreamSynchronize(s));
+                dev_ms += now_ms() - a;
+                a = now_ms();
+                std::reverse(hhi, hhi + cnt);
+                std::reverse(hlo, hlo + cnt);
+                K.run(hhi, hlo, (int64_t)cnt, (int64_t)(first + cnt - 1), B, n);
+                h0_ms += now_ms() - a;
+                done += cnt;
+                chunk *= 4;
+            }
+        }
+        S.cleared[1] = (int64_t)K.mst_pos.size();
+        S.columns[1] = (int64_t)cols - S.cleared[1];
+        if ((ctx->record & RPP_RECORD_COLUMNS) && max_dim >= 1) {
+            std::vector<uint32_t> hh(cols);
+            std::vector<uint64_t> ll(cols);
+            RPP_CK(cudaMemcpyAsync(hh.data(), key_hi + begin, cols * 4, cudaMemcpyDeviceToHost, s));
+            RPP_CK(cudaMemcpyAsync(ll.data(), key_lo + begin, cols * 8, cudaMemcpyDeviceToHost, s));
+            RPP_CK(cudaStreamSynchronize(s));
+            std::vector<char> cl(cols, 0);
+            for (uint32_t pos : K.mst_pos) cl[pos - begin] = 1;
+            for (uint64_t i = 0; i < cols; ++i)
+                if (!cl[i]) {
+                    res->col_diam[1].push_back(bits_to_float(~hh[i]));
+                    res->col_idx[1].push_back(ll[i]);
+                }
+            res->has_cols[1] = true;
+        }
+
+        if (max_dim >= 1 && cols > 0) {
+            const uint32_t *hi1 = key_hi + begin;
+            const uint64_t *lo1 = key_lo + begin;
+            RPP_CK(cudaMemsetAsync(status, 0, cols, s));
+            if (!K.mst_pos.empty()) {
+                RPP_TRY(ws.host(ws.h_mst, K.mst_pos.size() * 4, &vp));
+                uint32_t *hm = (uint32_t *)vp;
+                for (size_t i = 0; i < K.mst_pos.size(); ++i)
+                    hm[i] = (uint32_t)(K.mst_pos[i] - begin);
+                RPP_CK(cudaMemcpyAsync(mst, hm, K.mst_pos.size() * 4, cudaMemcpyHostToDevice, s));
+                launch_mark_cleared(mst, (int64_t)K.mst_pos.size(), status, s);
+            }
+            const Tuning tu = ctx->tuning_for(n, 1);
+            launch_apparent(D, ld, n, 1, d_binom, hi1, lo1, cols, st, status, pivot, pdiam,
+                            tu.group, ctx->sms, s);
+            launch_partition(status, hi1, lo1, pivot, pdiam, cols, app_tau, app_sigma, left, st, s);
+            RPP_CK(cudaGetLastError());
+        }
+    } else {
+        S.threshold = t;
+        I.t = t;
+    }
+
+    // H0 intervals
+    {
+        int v[2];
+        for (const HostPair &P : K.deaths) {
+            if (!(P.death > 0.0f)) continue;  // zero-length (duplicate points)
+            decode_host(B, P.tau, 1, n, v);
+            rpp_critical c = {-1, -1, v[0], v[1]};
+            add_interval(res, 0, 0.0f, P.death, c);
+        }
+        for (int64_t i = 0; i < K.components; ++i) {
+            rpp_critical c = {-1, -1, -1, -1};
+            add_interval(res, 0, 0.0f, INFINITY, c);
+        }
+    }
+
+    // ---- dimensions p = 1 .. max_dim ----
+    for (int p = 1; p <= max_dim && n >= 2; ++p) {
+        if (p >= 2) {
+            // clearing bitmap from the deaths of dimension p-1
+            const uint64_t cand = B.at(p + 1, n);
+            S.candidates[p] = (int64_t)cand;
+            uint32_t *bitmap;
+            RPP_TRY(ws.dev(ws.bitmap, (cand + 31) / 32 * 4, (void **)&bitmap));
+            RPP_CK(cudaMemsetAsync(bitmap, 0, (cand + 31) / 32 * 4, s));
+            launch_bitmap_set(app_tau, prev_napp, bitmap, s);
+            if (!prev_deaths.empty()) {
+                uint64_t *up;
+                RPP_TRY(ws.dev(ws.up, prev_deaths.size() * 8, (void **)&up));
+                RPP_TRY(ws.host(ws.h_up, prev_deaths.size() * 8, &vp));
+                std::memcpy(vp, prev_deaths.data(), prev_deaths.size() * 8);
+                RPP_CK(cudaMemcpyAsync(up, vp, prev_deaths.size() * 8, cudaMemcpyHostToDevice, s));
+                launch_bitmap_set(up, prev_deaths.size(), bitmap, s);
+            }
+            RPP_CK(cudaMemsetAsync(&st->ncols, 0, sizeof(unsigned long long), s));
+            launch_build_columns(D, ld, n, p, d_binom, cand, bitmap, st, key_hi, key_lo, s);
+            RPP_CK(cudaGetLastError());
+            RPP_TRY(read_state());
+            const uint64_t N = hst->ncols;
+            S.columns[p] = (int64_t)N;
+            S.cleared[p] = (int64_t)(prev_napp + prev_deaths.size());
+            radix_sort(key_hi, key_lo, nullptr, tmp_hi, tmp_lo, nullptr, tiles, hist, N,
+                       bits_for(cand - 1), 32, s);
+            if (ctx->record & RPP_RECORD_COLUMNS) {
+                std::vector<uint32_t> hh(N);
+                res->col_idx[p].resize(N);
+                RPP_CK(cudaMemcpyAsync(hh.data(), key_hi, N * 4, cudaMemcpyDeviceToHost, s));
+                RPP_CK(cudaMemcpyAsync(res->col_idx[p].data(), key_lo, N * 8,
+                                       cudaMemcpyDeviceToHost, s));
+                RPP_CK(cudaStreamSynchronize(s));
+                res->col_diam[p].resize(N);
+                for (uint64_t i = 0; i < N; ++i) res->col_diam[p][i] = bits_to_float(~hh[i]);
+                res->has_cols[p] = true;
+            }
+            RPP_CK(cudaMemsetAsync(status, 0, N, s));
+            RPP_CK(cudaMemsetAsync(&st->napp, 0, 2 * sizeof(unsigned long long), s));
+            const Tuning tu = ctx->tuning_for(n, p);
+            launch_apparent(D, ld, n, p, d_binom, key_hi, key_lo, N, st, status, pivot, pdiam,
+                            tu.group, ctx->sms, s);
+            launch_partition(status, key_hi, key_lo, pivot, pdiam, N, app_tau, app_sigma, left,
+                             st, s);
+            RPP_CK(cudaGetLastError());
+        }
+        RPP_TRY(read_state());
+        const uint64_t napp = hst->napp, nleft = hst->nleft;
+        S.apparent[p] = (int64_t)napp;
+        S.leftover[p] = (int64_t)nleft;
+        // apparent pairs sorted by tau: the second layer of the pair store
+        radix_sort(nullptr, app_tau, app_sigma, nullptr, tmp_lo, tmp_val, tiles, hist, napp,
+                   bits_for(B.at(p + 2, n) - 1), 0, s);
+        RPP_CK(cudaGetLastError());
+        if (ctx->record & RPP_RECORD_APPARENT) {
+            res->app_tau[p].resize(napp);
+            res->app_sigma[p].resize(napp);
+            RPP_CK(cudaMemcpyAsync(res->app_tau[p].data(), app_tau, napp * 8,
+                                   cudaMemcpyDeviceToHost, s));
+            RPP_CK(cudaMemcpyAsync(res->app_sigma[p].data(), app_sigma, napp * 8,
+                                   cudaMemcpyDeviceToHost, s));
+            RPP_CK(cudaStreamSynchronize(s));
+            res->has_app[p] = true;
+        }
+        DimOutput out;
+        if (nleft > 0) {
+            Leftover *hleft;
+            uint64_t *htau, *hsig;
+            RPP_TRY(ws.host(ws.h_left, nleft * sizeof(Leftover), (void **)&hleft));
+            RPP_TRY(ws.host(ws.h_tau, napp * 8, (void **)&htau));
+            RPP_TRY(ws.host(ws.h_sigma, napp * 8, (void **)&hsig));
+            double a = now_ms();
+            RPP_CK(cudaMemcpyAsync(hleft, left, nleft * sizeof(Leftover), cudaMemcpyDeviceToHost, s));
+            RPP_CK(cudaMemcpyAsync(htau, app_tau, napp * 8, cudaMemcpyDeviceToHost, s));
+            RPP_CK(cudaMemcpyAsync(hsig, app_sigma, napp * 8, cudaMemcpyDeviceToHost, s));
+            RPP_CK(cudaStreamSynchronize(s));
+            dev_ms += now_ms() - a;
+            a = now_ms();
+            std::sort(hleft, hleft + nleft,
+                      [](const Leftover &x, const Leftover &y) { return x.index < y.index; });
+            PairStore store;
+            store.app_tau = htau;
+            store.app_sigma = hsig;
+            store.napp = napp;
+            ReduceStats rs;
+            reduce_leftovers(I, p, hleft, (int64_t)nleft, store, out.pairs, rs);
+            S.free_pivot[p] = rs.free_pivot;
+            S.additions[p] = rs.additions;
+            S.store_reads[p] = rs.reads;
+            red_ms += now_ms() - a;
+        }
+        // intervals of dimension p and the deaths that clear dimension p + 1
+        prev_deaths.clear();
+        int vs[RPP_MAX_DIM + 2], vt[RPP_MAX_DIM + 3];
+        for (const HostPair &P : out.pairs) {
+            if (P.tau != NO_PIVOT) prev_deaths.push_back(P.tau);
+            if (P.tau != NO_PIVOT && !(P.death > P.birth)) continue;  // zero length
+            rpp_critical c = {-1, -1, -1, -1};
+            decode_host(B, P.sigma, p, n, vs);
+            youngest_edge(I, vs, p + 1, &c.bu, &c.bv);
+            if (P.tau != NO_PIVOT) {
+                decode_host(B, P.tau, p + 1, n, vt);
+                youngest_edge(I, vt, p + 2, &c.du, &c.dv);
+            }
+            add_interval(res, p, P.birth, P.death, c);
+        }
+        prev_napp = napp;
+    }
+    if (n >= 2 && max_dim >= 1) RPP_CK(cudaStreamSynchronize(s));
+
+    for (int q = 0; q <= max_dim; ++q) {
+        sort_result(res, q);
+        S.intervals[q] = (int64_t)res->iv[q].size();
+    }
+    S.ms_device = dev_ms;
+    S.ms_host_reduce = red_ms;
+    S.ms_host_h0 = h0_ms;
+    S.ms_total = now_ms() - t0;
+    return Status();
+}
+
+}  // namespace rpp

@@ -1,0 +1,116 @@
+// pipeline.h -- device workspaces and the per-instance barcode pipeline.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/rpp.h"
+#include "host.h"
+#include "internal.h"
+
+namespace rpp {
+
+// A grow-only device buffer.
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+// A grow-only pinned host buffer.
+struct HostBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+struct Status {
+    rpp_status code = RPP_OK;
+    std::string msg;
+    bool ok() const { return code == RPP_OK; }
+};
+
+// Everything one in-flight instance needs. A context keeps a pool of these.
+struct Workspace {
+    int device = 0;
+    size_t budget = 0;        // 0 = unbounded
+    size_t device_bytes = 0;  // currently held
+    DevBuf X, Dsrc, D, state, binom, key_hi, key_lo, tmp_hi, tmp_lo, tmp_val, tiles, hist,
+        status, pivot, pdiam, app_tau, app_sigma, left, bitmap, mst, up;
+    HostBuf h_hi, h_lo, h_tau, h_sigma, h_left, h_D, h_state, h_mst, h_up;
+    Binomial binom_host;      // cached table
+    int64_t binom_n = -1;
+    int binom_k = -1;
+    bool binom_on_device = false;
+    std::vector<uint64_t> binom_store;
+    ~Workspace();
+    Status dev(DevBuf &b, size_t bytes, void **out);
+    Status host(HostBuf &b, size_t bytes, void **out);
+};
+
+// Tunables chosen per size bucket by the autotuner (autotune.cpp).
+struct Tuning {
+    int group = 8;  // lanes per column in the apparent-pair pass
+};
+
+struct Context;
+
+// One instance request.
+struct Instance {
+    const float *data = nullptr;
+    rpp_input_kind kind = RPP_INPUT_POINTS;
+    int64_t n = 0;
+    int32_t dim = 0;
+    int32_t max_dim = 1;
+    float threshold = INFINITY;
+    float quantile = 0.0f;  // > 0: threshold by quantile
+};
+
+}  // namespace rpp
+
+// The opaque result handle.
+struct rpp_result {
+    int32_t max_dim = 0;
+    std::vector<rpp_interval> iv[RPP_MAX_DIM + 1];
+    std::vector<rpp_critical> cr[RPP_MAX_DIM + 1];
+    rpp_stats stats{};
+    // recorded intermediate arrays (rpp_context_set_record)
+    bool has_cols[RPP_MAX_DIM + 1] = {};
+    bool has_app[RPP_MAX_DIM + 1] = {};
+    std::vector<float> col_diam[RPP_MAX_DIM + 1];
+    std::vector<uint64_t> col_idx[RPP_MAX_DIM + 1];
+    std::vector<uint64_t> app_sigma[RPP_MAX_DIM + 1];
+    std::vector<uint64_t> app_tau[RPP_MAX_DIM + 1];
+};
+
+struct rpp_context {
+    int device = 0;
+    size_t budget = 0;
+    int sms = 0;
+    int record = 0;  // RPP_RECORD_* flags
+    std::mutex mu;
+    std::vector<rpp::Workspace *> free_ws;
+    std::vector<rpp::Workspace *> all_ws;
+    rpp::Tuning tuning_for(int64_t n, int p);
+    rpp::Workspace *acquire();
+    void release(rpp::Workspace *ws);
+};
+
+namespace rpp {
+
+// Run one instance end to end on `stream` with workspace `ws`.
+Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStream_t stream,
+                    rpp_result *res);
+// Device bytes a workspace holds after running this instance.
+size_t instance_device_bytes(const Instance &in);
+// Validate an instance before any GPU work.
+Status validate_instance(const Instance &in);
+// Fill a binomial table C(v, k), k <= kmax, v <= n (saturating).
+void fill_binomial(int64_t n, int kmax, std::vector<uint64_t> &store, Binomial &B);
+bool is_device_pointer(const void *p);
+// Record a failed status as the thread's last error and return its code.
+rpp_status report(const Status &s);
+
+}  // namespace rpp

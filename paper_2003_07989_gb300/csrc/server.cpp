@@ -1,0 +1,240 @@
+// server.cpp -- serving: requests of point clouds arrive over time and are
+// admitted, as device memory and slots free up, onto slot workers that each own
+// a CUDA stream and a workspace. Admitted requests overlap on the device (one
+// stream per slot) and in their host reductions (one thread per slot).
+//
+// Admission: a request's device footprint is estimated from its simplex counts
+// (the same buffer sizes the pipeline requests). A slot may take the request
+// when the bytes held by the other slots plus the larger of its own held bytes
+// and the estimate stay within the budget; an idle slot holding more than the
+// request needs returns its buffers first. The queue is served first-fit in
+// arrival order; a request passed over too often blocks later ones until it
+// fits, so large requests are not starved.
+#include <chrono>
+#include <cstring>
+#include <condition_variable>
+#include <deque>
+#include <thread>
+#include <unordered_map>
+
+#include "pipeline.h"
+
+using namespace rpp;
+
+namespace {
+
+struct Request {
+    uint64_t ticket = 0;
+    std::vector<float> pts;
+    Instance in;
+    size_t est = 0;
+    int skipped = 0;
+    bool done = false;
+    rpp_result *res = nullptr;
+    Status status;
+};
+
+}  // namespace
+
+struct rpp_server {
+    rpp_context *ctx = nullptr;
+    rpp_server_config cfg{};
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Request *> queue;
+    std::unordered_map<uint64_t, Request *> reqs;
+    std::vector<size_t> held;  // bytes reserved per slot
+    std::vector<std::thread> workers;
+    uint64_t next_ticket = 1;
+    bool stop = false;
+
+    size_t held_others(int k) const {
+        size_t s = 0;
+        for (size_t j = 0; j < held.size(); ++j)
+            if ((int)j != k) s += held[j];
+        return s;
+    }
+    void worker(int k);
+};
+
+void rpp_server::worker(int k) {
+    cudaSetDevice(ctx->device);
+    cudaStream_t s;
+    cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    Workspace *ws = new Workspace();
+    ws->device = ctx->device;
+    const size_t budget = cfg.device_bytes;
+    const int max_skips = 8;
+    for (;;) {
+        Request *r = nullptr;
+        {
+            std::unique_lock<std::mutex> g(mu);
+            for (;;) {
+                if (stop && queue.empty()) break;
+                // first fit in arrival order, with aging of passed-over requests
+                for (auto it = queue.begin(); it != queue.end(); ++it) {
+                    Request *q = *it;
+                    bool fits = budget == 0 || held_others(k) + std::max(held[k], q->est) <= budget;
+                    if (!fits && budget && held_others(k) + q->est <= budget &&
+                        ws->device_bytes > q->est) {
+                        // this slot's cached buffers are in the way: return them
+                        delete ws;
+                        ws = new Workspace();
+                        ws->device = ctx->device;
+                        held[k] = 0;
+                        fits = true;
+                    }
+                    if (fits) {
+                        r = q;
+                        queue.erase(it);
+                        break;
+                    }
+                    if (++q->skipped > max_skips) break;  // nobody may pass it any longer
+                }
+                if (r) break;
+                if (!queue.empty() && held[k] > 0) {
+                    // nothing fits: an idle slot gives its cached buffers back so
+                    // that admission can always make progress
+                    delete ws;
+                    ws = new Workspace();
+                    ws->device = ctx->device;
+                    held[k] = 0;
+                    cv_work.notify_all();
+                    continue;
+                }
+                cv_work.wait(g);
+            }
+            if (!r) break;
+            held[k] = std::max(held[k], r->est);
+        }
+        rpp_result *res = new rpp_result();
+        Status st = run_instance(ctx, *ws, r->in, s, res);
+        {
+            std::lock_guard<std::mutex> g(mu);
+            held[k] = ws->device_bytes;
+            if (st.ok()) r->res = res;
+            else delete res;
+            r->status = st;
+            r->done = true;
+        }
+        cv_done.notify_all();
+        cv_work.notify_all();
+    }
+    delete ws;
+    cudaStreamDestroy(s);
+}
+
+extern "C" {
+
+rpp_status rpp_server_create(rpp_context *ctx, const rpp_server_config *cfg, rpp_server **out) {
+    if (!ctx || !cfg || !out || cfg->max_slots < 1) {
+        set_last_error("rpp_server_create: invalid arguments");
+        return RPP_E_INVALID;
+    }
+    rpp_server *srv = new rpp_server();
+    srv->ctx = ctx;
+    srv->cfg = *cfg;
+    srv->held.assign(cfg->max_slots, 0);
+    for (int k = 0; k < cfg->max_slots; ++k) srv->workers.emplace_back(&rpp_server::worker, srv, k);
+    *out = srv;
+    return RPP_OK;
+}
+
+rpp_status rpp_server_submit(rpp_server *srv, const float *points, int64_t n, int32_t dim,
+                             int32_t max_dim, float threshold, float quantile, uint64_t *ticket) {
+    if (!srv || !points || !ticket) {
+        set_last_error("rpp_server_submit: invalid arguments");
+        return RPP_E_INVALID;
+    }
+    Request *r = new Request();
+    r->in.kind = RPP_INPUT_POINTS;
+    r->in.n = n;
+    r->in.dim = dim;
+    r->in.max_dim = max_dim;
+    r->in.threshold = threshold;
+    r->in.quantile = quantile;
+    r->in.data = points;
+    Status v = validate_instance(r->in);
+    if (!v.ok()) {
+        delete r;
+        return report(v);
+    }
+    r->pts.resize((size_t)n * dim);
+    if (is_device_pointer(points)) {
+        cudaSetDevice(srv->ctx->device);
+        if (cudaMemcpy(r->pts.data(), points, r->pts.size() * 4, cudaMemcpyDeviceToHost) !=
+            cudaSuccess) {
+            delete r;
+            set_last_error("rpp_server_submit: copying the points failed");
+            return RPP_E_CUDA;
+        }
+    } else {
+        std::memcpy(r->pts.data(), points, r->pts.size() * 4);
+    }
+    r->in.data = r->pts.data();
+    r->est = instance_device_bytes(r->in);
+    if (srv->cfg.device_bytes && r->est > srv->cfg.device_bytes) {
+        delete r;
+        set_last_error("rpp_server_submit: request can never fit the server's memory bound");
+        return RPP_E_BUSY;
+    }
+    {
+        std::lock_guard<std::mutex> g(srv->mu);
+        if (srv->stop) {
+            delete r;
+            set_last_error("rpp_server_submit: server is shutting down");
+            return RPP_E_BUSY;
+        }
+        r->ticket = srv->next_ticket++;
+        srv->reqs[r->ticket] = r;
+        srv->queue.push_back(r);
+        *ticket = r->ticket;
+    }
+    srv->cv_work.notify_one();
+    return RPP_OK;
+}
+
+rpp_status rpp_server_poll(rpp_server *srv, uint64_t ticket, int32_t timeout_ms, rpp_result **out) {
+    if (!srv || !out) {
+        set_last_error("rpp_server_poll: invalid arguments");
+        return RPP_E_INVALID;
+    }
+    *out = nullptr;
+    std::unique_lock<std::mutex> g(srv->mu);
+    auto it = srv->reqs.find(ticket);
+    if (it == srv->reqs.end()) {
+        set_last_error("rpp_server_poll: unknown ticket");
+        return RPP_E_INVALID;
+    }
+    Request *r = it->second;
+    if (timeout_ms < 0) {
+        srv->cv_done.wait(g, [&] { return r->done; });
+    } else if (!srv->cv_done.wait_for(g, std::chrono::milliseconds(timeout_ms),
+                                      [&] { return r->done; })) {
+        return RPP_E_TIMEOUT;
+    }
+    srv->reqs.erase(it);
+    g.unlock();
+    rpp_status code = r->status.code;
+    if (code != RPP_OK) set_last_error(r->status.msg);
+    *out = r->res;
+    delete r;
+    return code;
+}
+
+void rpp_server_destroy(rpp_server *srv) {
+    if (!srv) return;
+    {
+        std::lock_guard<std::mutex> g(srv->mu);
+        srv->stop = true;
+    }
+    srv->cv_work.notify_all();
+    for (auto &t : srv->workers) t.join();
+    for (auto &kv : srv->reqs) {
+        rpp_result_free(kv.second->res);
+        delete kv.second;
+    }
+    delete srv;
+}
+
+}  // extern "C"

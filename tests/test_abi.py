@@ -1,0 +1,56 @@
+"""The C-ABI library builds, loads and exports every function include/rpp.h
+declares; host-side argument checks work without a GPU."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "rpp.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = set(re.findall(r"\b(rpp_[a-z_0-9]+)\s*\(", text))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2003_07989_gb300 import build
+    build.build()
+    from paper_2003_07989_gb300 import _native
+    return _native.lib()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for must in ("rpp_barcodes", "rpp_barcodes_batched", "rpp_barcodes_backward",
+                 "rpp_server_submit", "rpp_server_poll", "rpp_result_intervals"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2003_07989_gb300 import _native
+    for name in _declared():
+        assert hasattr(lib, name), name
+    assert set(_declared()) == set(_native.EXPORTED)
+
+
+def test_status_strings(lib):
+    for code in range(7):
+        assert lib.rpp_status_string(code)
+    assert lib.rpp_last_error() is not None
+
+
+def test_argument_errors_without_gpu(lib):
+    from paper_2003_07989_gb300 import _native as N
+    # a NULL out pointer is rejected before any CUDA call
+    assert lib.rpp_context_create(0, 0, None) == N.RPP_E_INVALID
+    h = C.c_void_p()
+    rc = lib.rpp_barcodes(None, None, 0, 10, 3, 1, float("inf"), None, C.byref(h))
+    assert rc == N.RPP_E_INVALID
+    assert b"NULL" in lib.rpp_last_error()
+    assert lib.rpp_result_count(None, 0) == -1
+    assert lib.rpp_result_total(None) == -1
