@@ -1,0 +1,371 @@
+#!/usr/bin/env python
+"""Benchmark of the barcode hot path on the 2000-point noisy torus (H0-H1).
+
+One step = one full barcode computation of one synthetic cloud already
+resident in device memory: distance matrix, enclosing radius, filtration with
+clearing, radix sort, Kruskal H0, apparent-pair pass, partition, submatrix
+reduction, barcode assembly. The metric is simplices/s through the
+apparent-pair pass: columns tested (the dimension-1 simplices inside the
+threshold that clearing kept) per second of whole-step time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank computes its own cloud (seed = rank); the value is the
+columns of all ranks divided by the slowest rank's time (weak scaling).
+`--impl reference` times the CPU oracle (the plain standard reduction) on a
+bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_POINTS, DIM, MAX_DIM = 2000, 3, 1
+WORKLOAD = "torus2000_h1"
+L2_FLUSH_BYTES = 512 << 20  # > 129 MB of L2
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# roofline bookkeeping
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash(files):
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(ROOT, "paper_2003_07989_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+STAGE_FILES = {
+    "apparent": ["apparent.cu", "device_common.cuh"],
+    "sort_columns": ["radix_sort.cu"],
+    "sort_pairs": ["radix_sort.cu"],
+    "build_columns": ["filtration.cu", "device_common.cuh"],
+    "partition": ["apparent.cu"],
+}
+
+
+def traffic_for(stage):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current source of the kernel; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p) or stage not in STAGE_FILES:
+        return None
+    d = json.load(open(p)).get(stage)
+    if not d or d.get("source_hash") != kernel_source_hash(STAGE_FILES[stage]):
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+def algorithmic_bytes(stage, st):
+    """Bytes a stage must move per launch by its definition."""
+    p = 1
+    cols = st["columns"][p] + st["cleared"][p]
+    if stage == "apparent":
+        # per column: (p+1) distance reads per candidate examined, the column
+        # key (12 B) and its outputs (status 1 B, pivot 8 B, pivot diameter 4 B)
+        return st["scanned"][p] * (p + 1) * 4 + cols * (12 + 13)
+    if stage == "build_columns":
+        return st["candidates"][p] * 4 + cols * 12
+    if stage in ("sort_columns", "sort_pairs"):
+        launches = st["stage_launches"][3 if stage == "sort_columns" else 6]
+        passes = max(0, (launches - 1) // 3)
+        n = cols if stage == "sort_columns" else st["apparent"][p]
+        w = 12 if stage == "sort_columns" else 16
+        return n * w + passes * n * (w + 2 * w)  # histogram read + per pass count/scatter
+    if stage == "partition":
+        return cols * (1 + 12 + 12) + st["apparent"][p] * 16 + st["leftover"][p] * 32
+    return None
+
+
+# ---------------------------------------------------------------------------
+# the oracle as the CPU baseline / reference arm
+
+
+def oracle_rate(n_sample: int, seed: int):
+    """The oracle (plain standard reduction, Kruskal H0 + coboundary reduction
+    with clearing) on the first n_sample points of the same torus cloud:
+    dimension-1 columns processed per second, and the threads it used."""
+    from oracle import oracle as O
+    from paper_2003_07989_gb300 import inputs as I
+    X = I.noisy_torus(N_POINTS, seed=seed)[:n_sample]
+    D = O.distance_matrix(X)
+    t0 = time.perf_counter()
+    O.barcodes(D, MAX_DIM, math.inf, O.MODE_COHOM_CLEAR)
+    dt = time.perf_counter() - t0
+    cols = n_sample * (n_sample - 1) // 2 - (n_sample - 1)  # every edge but the cleared MST
+    return cols / dt, dt, cols, O.num_threads()
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    n_sample = 500
+    for _ in range(args.warmup):
+        oracle_rate(n_sample, 0)
+    rates, secs, cols = [], 0.0, 0
+    cores = 1
+    for _ in range(args.steps):
+        r, dt, c, cores = oracle_rate(n_sample, 0)
+        rates.append(r)
+        secs += dt
+        cols += c
+    value = cols / secs
+    line = {
+        "impl": "reference", "metric": "simplices/s in apparent-pair pass", "value": value,
+        "unit": "simplices/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N_POINTS, "dim": DIM, "max_dim": MAX_DIM,
+                   "threshold": "none (full filtration)"},
+        "cpu_baseline": {"value": value, "unit": "simplices/s", "cores": cores, "kind": "oracle",
+                         "sample": f"first {n_sample} of the 2000 torus points per step"},
+        "e2e": {"value": value, "unit": "simplices/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+
+
+def main():
+    args = parse_args()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import numpy as np
+    import torch
+
+    import __graft_entry__ as g
+    g.build()
+    import paper_2003_07989_gb300 as rpp
+    from paper_2003_07989_gb300 import _native as N
+    from paper_2003_07989_gb300 import inputs as I
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device("cuda", local)
+    ctx = rpp.Context(local, record=N.RPP_RECORD_TIMING)
+    X = I.noisy_torus(N_POINTS, seed=rank)
+    pts = torch.from_numpy(X).to(dev)
+    pts_host = torch.from_numpy(X).pin_memory()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def timed(data):
+        """K steps, each bracketed by events on the launching stream; L2 is
+        flushed between steps, outside the events."""
+        total_ms, stats = 0.0, []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = rpp.rpp_barcodes(data, max_dim=MAX_DIM, context=ctx)
+            e1.record(stream)
+            e1.synchronize()
+            total_ms += e0.elapsed_time(e1)
+            stats.append(res)
+        return total_ms, stats
+
+    for _ in range(args.warmup):
+        rpp.rpp_barcodes(pts, max_dim=MAX_DIM, context=ctx)
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    total_ms, results = timed(pts)
+    barrier()
+    clk = clocks.stop()
+
+    # end to end through the public API from pinned host memory
+    for _ in range(max(1, args.warmup // 2)):
+        rpp.rpp_barcodes(pts_host, max_dim=MAX_DIM, context=ctx)
+    barrier()
+    e2e_ms, e2e_results = timed(pts_host)
+    barrier()
+
+    st = [r.stats for r in results]
+    cols_rank = sum(s["columns"][1] for s in st)
+    e2e_cols_rank = sum(r.stats["columns"][1] for r in e2e_results)
+    launches_rank = sum(s["kernel_launches"] for s in st)
+    agg = torch.tensor([total_ms, e2e_ms, cols_rank, e2e_cols_rank, launches_rank],
+                       dtype=torch.float64, device=dev)
+    if dist is not None:
+        mx = agg[:2].clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = agg[2:].clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        agg = torch.cat([mx, sm])
+    total_ms, e2e_ms, cols_all, e2e_cols_all, launches_all = agg.tolist()
+    if rank != 0:
+        dist.destroy_process_group()
+        return
+
+    value = cols_all / (total_ms / 1000.0)
+    e2e_value = e2e_cols_all / (e2e_ms / 1000.0)
+    # per-stage breakdown (rank 0)
+    stage_ms = [sum(s["stage_ms"][i] for s in st) / len(st) for i in range(8)]
+    stage_launch = [st[0]["stage_launches"][i] for i in range(8)]
+    names = N.STAGES
+    kernels = {names[i]: {"ms_per_step": round(stage_ms[i], 4), "launches_per_step": stage_launch[i]}
+               for i in range(8)}
+    # dominant kernel among the filtration / apparent / partition stages
+    cand = ["build_columns", "sort_columns", "apparent", "partition", "sort_pairs"]
+    dom = max(cand, key=lambda k: stage_ms[names.index(k)])
+    i = names.index(dom)
+    launches = max(1, stage_launch[i])
+    dur_s = stage_ms[i] / 1000.0 / launches
+    alg = algorithmic_bytes(dom, st[0])
+    peak, peak_kind = measured_peaks()
+    achieved = (alg / launches) / dur_s / 1e9 if (alg and dur_s > 0) else None
+    s0 = st[0]
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None,
+                "traffic": traffic_for(dom), "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": (alg / launches) if alg else None,
+                "avg_launch_ms": dur_s * 1000.0}
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        r, dt, c, cores = oracle_rate(1000, 0)
+        cpu = {"value": r, "unit": "simplices/s", "cores": cores, "kind": "oracle",
+               "sample": f"first 1000 of the 2000 torus points ({c} dimension-1 columns, "
+                         f"{dt:.1f} s)"}
+    h2d = X.nbytes
+    d2h = sum(len(iv) * (8 + 16) for iv in e2e_results[0].intervals)
+    line = {
+        "metric": "simplices/s in apparent-pair pass", "value": value, "unit": "simplices/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N_POINTS, "dim": DIM, "max_dim": MAX_DIM,
+                   "threshold": "enclosing radius (full filtration)", "seed": "rank",
+                   "l2": "flushed between steps (512 MB write, outside the timed events)",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": {"value": e2e_value, "unit": "simplices/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / args.steps},
+        "gpu_launches": int(launches_all),
+        "clocks": clk,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "breakdown": {
+            "kernels": kernels,
+            "host_reduce_ms": statistics.mean(s["ms_host_reduce"] for s in st),
+            "host_kruskal_ms": statistics.mean(s["ms_host_h0"] for s in st),
+            "columns": s0["columns"][1], "cleared": s0["cleared"][1],
+            "apparent": s0["apparent"][1], "leftover": s0["leftover"][1],
+            "free_pivot": s0["free_pivot"][1], "additions": s0["additions"][1],
+            "scanned": s0["scanned"][1], "intervals_h1": s0["intervals"][1],
+            "apparent_pass_simplices_per_s": s0["columns"][1] / (stage_ms[4] / 1000.0)
+            if stage_ms[4] > 0 else None,
+        },
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

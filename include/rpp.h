@@ -98,7 +98,16 @@ typedef struct {
     int64_t free_pivot[RPP_MAX_DIM + 1];  /* leftover columns whose first pivot was free */
     int64_t additions[RPP_MAX_DIM + 1];   /* column additions in the submatrix reduction */
     int64_t store_reads[RPP_MAX_DIM + 1]; /* pair-store lookups in the reduction */
+    int64_t entries[RPP_MAX_DIM + 1];     /* coboundary entries the reduction examined */
     int64_t intervals[RPP_MAX_DIM + 1];   /* nonzero intervals reported (index 0 = H0) */
+    int64_t scanned[RPP_MAX_DIM + 1];     /* candidate vertices the apparent pass examined */
+    int64_t kernel_launches;              /* CUDA kernels this call launched */
+    /* Per-stage device time from CUDA events on the call's stream, filled when
+     * the context records RPP_RECORD_TIMING: 0 distances, 1 enclosing radius,
+     * 2 filtration (build), 3 column sort, 4 apparent-pair pass, 5 partition,
+     * 6 pair sort, 7 other small kernels. */
+    double stage_ms[8];
+    int64_t stage_launches[8];
     double ms_device;                     /* wall time spent waiting on the GPU */
     double ms_host_reduce;                /* wall time of the submatrix reductions */
     double ms_host_h0;                    /* wall time of Kruskal */
@@ -195,6 +204,7 @@ rpp_status rpp_distance_matrix(rpp_context *ctx, const float *points, int64_t n,
 
 #define RPP_RECORD_COLUMNS 1  /* keep each dimension's column array */
 #define RPP_RECORD_APPARENT 2 /* keep each dimension's apparent pairs */
+#define RPP_RECORD_TIMING 4   /* time each stage with CUDA events (rpp_stats.stage_ms) */
 
 /* Make later calls on ctx copy the selected intermediate arrays into their
  * results (0 turns recording off). Costs host memory and copy time. */

@@ -23,7 +23,9 @@ EXPORTED = [
     "rpp_status_string", "rpp_last_error", "rpp_distance_matrix", "rpp_context_set_record",
     "rpp_result_columns", "rpp_result_apparent",
 ]
-RPP_RECORD_COLUMNS, RPP_RECORD_APPARENT = 1, 2
+RPP_RECORD_COLUMNS, RPP_RECORD_APPARENT, RPP_RECORD_TIMING = 1, 2, 4
+STAGES = ["distance", "enclosing_radius", "build_columns", "sort_columns", "apparent",
+          "partition", "sort_pairs", "other"]
 
 
 class Interval(C.Structure):
@@ -42,7 +44,9 @@ class Stats(C.Structure):
                 ("enclosing_radius", C.c_float),
                 ("candidates", _A), ("columns", _A), ("cleared", _A), ("apparent", _A),
                 ("leftover", _A), ("free_pivot", _A), ("additions", _A), ("store_reads", _A),
-                ("intervals", _A),
+                ("entries", _A),
+                ("intervals", _A), ("scanned", _A), ("kernel_launches", C.c_int64),
+                ("stage_ms", C.c_double * 8), ("stage_launches", C.c_int64 * 8),
                 ("ms_device", C.c_double), ("ms_host_reduce", C.c_double),
                 ("ms_host_h0", C.c_double), ("ms_total", C.c_double)]
 

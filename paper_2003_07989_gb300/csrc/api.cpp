@@ -2,9 +2,11 @@
 // barcodes, result accessors, status strings.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <thread>
 
 #include "pipeline.h"
 
@@ -13,6 +15,8 @@ namespace rpp {
 namespace {
 thread_local std::string g_last_error;
 }
+
+thread_local long long g_launches = 0;
 
 void set_last_error(const std::string &msg) { g_last_error = msg; }
 
@@ -69,6 +73,8 @@ rpp_status rpp_context_create(int device, size_t mem_budget_bytes, rpp_context *
     c->device = device;
     c->budget = mem_budget_bytes;
     c->sms = prop.multiProcessorCount;
+    const unsigned hw = std::thread::hardware_concurrency();
+    c->host_threads = hw == 0 ? 4 : (int)std::min(hw, 32u);
     *out = c;
     return RPP_OK;
 }
@@ -165,7 +171,7 @@ rpp_status rpp_result_stats(const rpp_result *res, rpp_stats *out) {
 void rpp_result_free(rpp_result *res) { delete res; }
 
 rpp_status rpp_context_set_record(rpp_context *ctx, int32_t flags) {
-    if (!ctx || flags < 0 || flags > (RPP_RECORD_COLUMNS | RPP_RECORD_APPARENT)) {
+    if (!ctx || flags < 0 || flags > (RPP_RECORD_COLUMNS | RPP_RECORD_APPARENT | RPP_RECORD_TIMING)) {
         set_last_error("rpp_context_set_record: invalid arguments");
         return RPP_E_INVALID;
     }

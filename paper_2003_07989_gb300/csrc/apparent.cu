@@ -35,11 +35,12 @@ template <int P, int G>
 __global__ void __launch_bounds__(256) k_apparent(
     const float *__restrict__ D, int64_t ld, int64_t n, const uint64_t *__restrict__ gB,
     bool smem_table, const uint32_t *__restrict__ key_hi, const uint64_t *__restrict__ key_lo,
-    uint64_t ncols, const DevState *__restrict__ st, uint8_t *__restrict__ status,
+    uint64_t ncols, DevState *__restrict__ st, uint8_t *__restrict__ status,
     uint64_t *__restrict__ pivot, float *__restrict__ pdiam) {
     extern __shared__ uint64_t sB[];
     const uint64_t *B = stage_binomial(gB, n, P + 2, sB, smem_table);
     const float t = st->t;
+    unsigned scanned = 0;  // candidate vertices this lane examined
     const int lane = threadIdx.x & 31;
     const int grp = lane / G, gl = lane % G;
     const unsigned gmask = (G == 32) ? FULL_MASK : (((1u << G) - 1u) << (grp * G));
@@ -73,6 +74,7 @@ __global__ void __launch_bounds__(256) k_apparent(
 #pragma unroll
             for (int i = 0; i <= P; ++i) member |= (x == v[i]);
             if (!member) {
+                ++scanned;
                 float m = 0.0f;
 #pragma unroll
                 for (int i = 0; i <= P; ++i) {
@@ -139,6 +141,10 @@ __global__ void __launch_bounds__(256) k_apparent(
             }
         }
     }
+    // one atomic per warp for the work counter
+    unsigned long long w = scanned;
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(FULL_MASK, w, o);
+    if (lane == 0 && w) atomicAdd(&st->scanned, w);
 }
 
 __global__ void __launch_bounds__(256) k_partition(
@@ -185,7 +191,7 @@ __global__ void __launch_bounds__(256) k_partition(
 template <int P, int G>
 void apparent_pg(const float *D, int64_t ld, int64_t n, const uint64_t *binom,
                  const uint32_t *key_hi, const uint64_t *key_lo, uint64_t ncols,
-                 const DevState *st, uint8_t *status, uint64_t *pivot, float *pdiam, int sms,
+                 DevState *st, uint8_t *status, uint64_t *pivot, float *pdiam, int sms,
                  cudaStream_t s) {
     const size_t table = (size_t)(P + 3) * (n + 1) * sizeof(uint64_t);
     const bool smem = table <= 48 * 1024;
@@ -197,6 +203,7 @@ void apparent_pg(const float *D, int64_t ld, int64_t n, const uint64_t *binom,
     const uint64_t need = (ncols * G + 255) / 256;
     if (need < blocks) blocks = need;
     if (blocks == 0) return;
+    ++g_launches;
     k_apparent<P, G><<<(unsigned)blocks, 256, smem ? table : 0, s>>>(
         D, ld, n, binom, smem, key_hi, key_lo, ncols, st, status, pivot, pdiam);
 }
@@ -204,7 +211,7 @@ void apparent_pg(const float *D, int64_t ld, int64_t n, const uint64_t *binom,
 template <int P>
 void apparent_p(int group, const float *D, int64_t ld, int64_t n, const uint64_t *binom,
                 const uint32_t *key_hi, const uint64_t *key_lo, uint64_t ncols,
-                const DevState *st, uint8_t *status, uint64_t *pivot, float *pdiam, int sms,
+                DevState *st, uint8_t *status, uint64_t *pivot, float *pdiam, int sms,
                 cudaStream_t s) {
     switch (group) {
         case 4: apparent_pg<P, 4>(D, ld, n, binom, key_hi, key_lo, ncols, st, status, pivot, pdiam, sms, s); break;
@@ -218,7 +225,7 @@ void apparent_p(int group, const float *D, int64_t ld, int64_t n, const uint64_t
 
 void launch_apparent(const float *D, int64_t ld, int64_t n, int p, const uint64_t *binom,
                      const uint32_t *key_hi, const uint64_t *key_lo, uint64_t ncols,
-                     const DevState *st, uint8_t *status, uint64_t *pivot, float *pdiam, int group,
+                     DevState *st, uint8_t *status, uint64_t *pivot, float *pdiam, int group,
                      int sms, cudaStream_t s) {
     if (ncols == 0) return;
     switch (p) {
@@ -236,6 +243,7 @@ void launch_partition(const uint8_t *status, const uint32_t *key_hi, const uint6
     if (ncols == 0) return;
     uint64_t blocks = (ncols + 255) / 256;
     if (blocks > 152 * 8) blocks = 152 * 8;
+    ++g_launches;
     k_partition<<<(unsigned)blocks, 256, 0, s>>>(status, key_hi, key_lo, pivot, pdiam, ncols,
                                                   app_tau, app_sigma, left, st);
 }

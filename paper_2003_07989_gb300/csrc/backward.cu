@@ -150,10 +150,12 @@ extern "C" rpp_status rpp_barcodes_backward(rpp_context *ctx, int32_t batch, con
     std::memcpy(h_csr, csr.data(), csr.size() * sizeof(Contribution));
     cudaMemcpyAsync(d_off, h_off, count.size() * 8, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(d_csr, h_csr, csr.size() * sizeof(Contribution), cudaMemcpyHostToDevice, s);
-    if (npoints > 0)
+    if (npoints > 0) {
+        ++g_launches;
         k_backward<<<(unsigned)((npoints + 127) / 128), 128, 0, s>>>(
             points, dim, npoints, (const int64_t *)d_off, (const Contribution *)d_csr, grad_birth,
             grad_death, grad_points);
+    }
     cudaError_t e = cudaStreamSynchronize(s);  // the staging buffers are reused
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) {

@@ -122,9 +122,11 @@ void launch_distance_matrix(const float *X, int64_t n, int32_t dim, float *D, in
     const size_t smem = 2ull * DT * dim * sizeof(float);
     if (smem <= 48 * 1024) {
         dim3 grid((unsigned)((ld + DT - 1) / DT), (unsigned)((n + DT - 1) / DT));
+        ++g_launches;
         k_distance_smem<<<grid, dim3(DT, 8), smem, s>>>(X, n, dim, D, ld);
     } else {
         dim3 grid((unsigned)((ld + 127) / 128), (unsigned)n);
+        ++g_launches;
         k_distance_global<<<grid, 128, 0, s>>>(X, n, dim, D, ld);
     }
 }
@@ -133,17 +135,21 @@ void launch_copy_validate_distances(const float *src, int64_t n, float *D, int64
                                     DevState *st, cudaStream_t s) {
     if (n <= 0) return;
     dim3 grid((unsigned)((ld + 127) / 128), (unsigned)n);
+    ++g_launches;
     k_copy_validate<<<grid, 128, 0, s>>>(src, n, D, ld, st);
 }
 
 void launch_enclosing_radius(const float *D, int64_t n, int64_t ld, DevState *st, float t_user,
                              cudaStream_t s) {
+    ++g_launches;
     k_init_radius<<<1, 1, 0, s>>>(st);
     if (n > 0) {
         int64_t warps = n < 152 * 32 ? n : 152 * 32;
         int blocks = (int)((warps * 32 + 255) / 256);
+        ++g_launches;
         k_row_max_min<<<blocks, 256, 0, s>>>(D, n, ld, st);
     }
+    ++g_launches;
     k_final_threshold<<<1, 1, 0, s>>>(st, t_user);
 }
 

@@ -98,6 +98,7 @@ void build_p(const float *D, int64_t ld, int64_t n, const uint64_t *binom, uint6
     const uint64_t cap = 152ull * 8;
     if (blocks > cap) blocks = cap;
     if (blocks == 0) return;
+    ++g_launches;
     k_build_columns<P><<<(unsigned)blocks, 256, smem ? table : 0, s>>>(
         D, ld, n, binom, smem, total, cleared, st, key_hi, key_lo);
 }
@@ -118,16 +119,19 @@ void launch_build_columns(const float *D, int64_t ld, int64_t n, int p, const ui
 
 void launch_mark_cleared(const uint32_t *pos, int64_t count, uint8_t *status, cudaStream_t s) {
     if (count <= 0) return;
+    ++g_launches;
     k_mark_cleared<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(pos, count, status);
 }
 
 void launch_lower_bound_u32(const uint32_t *a, uint64_t n, uint32_t key, unsigned long long *out,
                             cudaStream_t s) {
+    ++g_launches;
     k_lower_bound_u32<<<1, 1, 0, s>>>(a, n, key, out);
 }
 
 void launch_bitmap_set(const uint64_t *idx, uint64_t count, uint32_t *bitmap, cudaStream_t s) {
     if (count == 0) return;
+    ++g_launches;
     k_bitmap_set<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(idx, count, bitmap);
 }
 

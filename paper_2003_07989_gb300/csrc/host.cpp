@@ -1,14 +1,36 @@
 // host.cpp -- H0 by Kruskal's union-find (Sec. "Zero-Dimensional Persistence
-// Computation: Kruskal's Algorithm"), the submatrix reduction of the columns
-// that are not apparent (Sec. "Core System Optimizations": the two-layer pair
-// store; Sec. "Reduction Matrix vs. Oblivious Matrix Reduction"), and helpers
-// for barcode assembly.
+// Computation: Kruskal's Algorithm") and the submatrix reduction of the
+// columns that are not apparent (Sec. "Core System Optimizations"; Alg. 1 with
+// the reduction-matrix technique of Sec. "Reduction Matrix vs. Oblivious
+// Matrix Reduction").
+//
+// Reduction of one leftover column j follows Alg. 1: while the pivot (oldest
+// nonzero entry) of the working column has an owner, add the owner's reduced
+// column. Almost every owner is an apparent column, whose reduced column is
+// its plain coboundary; only rarely is it another leftover column. So:
+//   Phase A (in parallel over columns): walk through apparent owners only,
+//     stopping at the first pivot that no apparent column owns.
+//   Phase B (in column order): if that pivot belongs to an earlier leftover
+//     column, add that column's reduced column and continue the walk, now
+//     also looking up earlier leftovers; the first free pivot pairs with j.
+// Both phases add exactly the columns Alg. 1 adds, in the same order.
+//
+// The working column is a heap of lazy cursors, one per added coboundary.
+// Each cursor lists its cofacets oldest first (smallest diameter, then largest
+// index) without materialising them: first the cofacets of equal diameter
+// (vertices w, largest first, with every distance to the simplex <= its
+// diameter), then the others by a (p+1)-way merge of the vertices' neighbour
+// lists sorted by distance. A vertex w is emitted at its last occurrence in
+// the merge, whose distance is the cofacet's diameter. Equal entries from two
+// cursors cancel over Z/2 when they meet at the top of the heap.
 #include "host.h"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <functional>
+#include <thread>
 
 namespace rpp {
 
@@ -26,6 +48,12 @@ void decode_host(const Binomial &B, uint64_t c, int p, int64_t n, int *v) {
         c -= B.at(k, lo);
         hi = lo - 1;
     }
+}
+
+uint64_t index_host(const Binomial &B, const int *v, int p) {
+    uint64_t c = 0;
+    for (int i = 0; i <= p; ++i) c += B.at(p + 1 - i, v[i]);
+    return c;
 }
 
 void youngest_edge(const HostInstance &I, const int *v, int k, int32_t *u, int32_t *w) {
@@ -89,169 +117,426 @@ void Kruskal::run(const uint32_t *hi, const uint64_t *lo, int64_t count, int64_t
 }
 
 // ---------------------------------------------------------------------------
-// pair store
-
-int PairStore::lookup(uint64_t tau, uint64_t *sigma, int64_t *slot) {
-    ++reads;
-    auto it = reduced.find(tau);
-    if (it != reduced.end()) {
-        *slot = it->second;
-        return 2;
-    }
-    const uint64_t *e = app_tau + napp;
-    const uint64_t *f = std::lower_bound(app_tau, e, tau);
-    if (f != e && *f == tau) {
-        *sigma = app_sigma[f - app_tau];
-        return 1;
-    }
-    return 0;
-}
-
-// ---------------------------------------------------------------------------
 // submatrix reduction
 
 namespace {
 
-// A column entry packed so that unsigned 128-bit order is "older first":
-// smaller diameter first, then larger index (the simplex-wise refinement).
-typedef unsigned __int128 entry;
+// Column entries packed so that unsigned 128-bit order is "older first":
+// smaller diameter, then larger index (the simplex-wise refinement).
+typedef unsigned __int128 u128;
+const u128 NONE = ~(u128)0;
 
-inline entry make_entry(float diam, uint64_t idx) {
+inline u128 age_key(float diam, uint64_t idx) {
     uint32_t bits;
     std::memcpy(&bits, &diam, sizeof(float));
-    return ((entry)bits << 64) | (entry)(~idx);
+    return ((u128)bits << 64) | (u128)(~idx);
 }
-inline uint64_t entry_index(entry e) { return ~(uint64_t)e; }
-inline float entry_diam(entry e) {
-    uint32_t bits = (uint32_t)(e >> 64);
+inline uint64_t key_index(u128 k) { return ~(uint64_t)k; }
+inline float key_diam(u128 k) {
+    uint32_t bits = (uint32_t)(k >> 64);
     float d;
     std::memcpy(&d, &bits, sizeof(float));
     return d;
 }
 
-// Working column: a min-heap with repetitions; an entry present an even number
-// of times is zero over Z/2 and cancels when it reaches the top.
-struct WorkColumn {
-    std::vector<entry> h;
-    void push(entry e) {
-        h.push_back(e);
-        std::push_heap(h.begin(), h.end(), std::greater<entry>());
-    }
-    entry pop() {
-        std::pop_heap(h.begin(), h.end(), std::greater<entry>());
-        entry e = h.back();
-        h.pop_back();
-        return e;
-    }
-    // Oldest nonzero entry (kept in the column); false if the sum is zero.
-    bool low(entry *out) {
-        while (!h.empty()) {
-            entry e = pop();
-            if (!h.empty() && h.front() == e) {
-                pop();
-                continue;
-            }
-            push(e);
-            *out = e;
-            return true;
+// Index of the cofacet v + {w} of the p-simplex v[0] > ... > v[p].
+inline uint64_t cofacet_idx(const Binomial &B, const int *v, int p, int w) {
+    uint64_t c = 0;
+    int k = p + 2;
+    bool placed = false;
+    for (int i = 0; i <= p; ++i) {
+        if (!placed && w > v[i]) {
+            c += B.at(k--, w);
+            placed = true;
         }
+        c += B.at(k--, v[i]);
+    }
+    if (!placed) c += B.at(1, w);
+    return c;
+}
+
+struct Cursor {
+    int v[RPP_MAX_DIM + 1];
+    float d = 0.0f;
+    int32_t lune = -1;
+    bool merging = false;       // merge positions set up
+    int32_t pos[RPP_MAX_DIM + 1];
+    std::vector<int32_t> ties;  // equal-key emissions, largest vertex at the back
+    float tie_key = 0.0f;
+    u128 head = NONE;
+};
+
+// Index over the sorted apparent taus: every STRIDE-th key, searched first.
+constexpr int64_t STRIDE = 64;
+
+struct Reducer {
+    const HostInstance &I;
+    int p;
+    int64_t n;
+    std::vector<uint64_t> top;  // app_tau[0], app_tau[STRIDE], ...
+
+    Reducer(const HostInstance &I_, int p_) : I(I_), p(p_), n(I_.n) {
+        for (uint64_t i = 0; i < I.napp; i += STRIDE) top.push_back(I.app_tau[i]);
+    }
+
+    bool is_apparent_tau(uint64_t tau) const {
+        auto it = std::upper_bound(top.begin(), top.end(), tau);
+        if (it == top.begin()) return false;
+        const int64_t blk = (it - top.begin()) - 1;
+        const uint64_t *b = I.app_tau + blk * STRIDE;
+        const uint64_t *e = I.app_tau + std::min<uint64_t>(I.napp, (uint64_t)(blk + 1) * STRIDE);
+        const uint64_t *f = std::lower_bound(b, e, tau);
+        return f != e && *f == tau;
+    }
+
+    bool in_simplex(const int *v, int w) const {
+        for (int i = 0; i <= p; ++i)
+            if (v[i] == w) return true;
         return false;
     }
-    // Remaining nonzero entries, each once, oldest first.
-    void drain(std::vector<entry> &out) {
-        entry e;
-        while (low(&e)) {
-            pop();
-            out.push_back(e);
+
+    // A cursor over the coboundary of the p-simplex v (diameter d). If
+    // `first` >= 0 the caller knows the oldest cofacet adds vertex `first`.
+    void init_cursor(Cursor &c, const int *v, float d, int first) const {
+        for (int i = 0; i <= p; ++i) c.v[i] = v[i];
+        c.d = d;
+        c.merging = false;
+        c.ties.clear();
+        if (first >= 0) {
+            c.lune = first - 1;
+            c.head = age_key(d, cofacet_idx(*I.B, c.v, p, first));
+            return;
         }
+        c.lune = (int32_t)n - 1;
+        advance(c);
+    }
+
+    void start_merge(Cursor &c) const {
+        c.merging = true;
+        for (int i = 0; i <= p; ++i) {  // first neighbour farther than d
+            const uint32_t *row = I.nbr + (int64_t)c.v[i] * n;
+            int64_t lo = 0, hi = n;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (I.dist(c.v[i], (int)row[mid]) <= c.d) lo = mid + 1;
+                else hi = mid;
+            }
+            c.pos[i] = (int32_t)lo;
+        }
+    }
+
+    // Move the cursor to its next cofacet inside the threshold (or NONE).
+    void advance(Cursor &c) const {
+        while (c.lune >= 0) {  // cofacets of diameter d, largest vertex first
+            const int w = c.lune--;
+            if (in_simplex(c.v, w)) continue;
+            float m = 0.0f;
+            for (int i = 0; i <= p; ++i) m = std::max(m, I.dist(c.v[i], w));
+            if (m <= c.d) {
+                c.head = age_key(c.d, cofacet_idx(*I.B, c.v, p, w));
+                return;
+            }
+        }
+        if (!c.merging) start_merge(c);
+        if (!c.ties.empty()) {
+            const int w = c.ties.back();
+            c.ties.pop_back();
+            c.head = age_key(c.tie_key, cofacet_idx(*I.B, c.v, p, w));
+            return;
+        }
+        for (;;) {
+            int best = -1;
+            float bd = INFINITY;
+            for (int i = 0; i <= p; ++i)
+                if (c.pos[i] < n) {
+                    const float x = I.dist(c.v[i], (int)I.nbr[(int64_t)c.v[i] * n + c.pos[i]]);
+                    if (x < bd) {
+                        bd = x;
+                        best = i;
+                    }
+                }
+            if (best < 0 || bd > I.t) {
+                c.head = NONE;
+                return;
+            }
+            // every occurrence at distance bd; a vertex is emitted where its
+            // (distance, list) pair is the largest of its p+1 occurrences
+            for (;;) {
+                int bi = -1;
+                for (int i = 0; i <= p; ++i)
+                    if (c.pos[i] < n &&
+                        I.dist(c.v[i], (int)I.nbr[(int64_t)c.v[i] * n + c.pos[i]]) == bd) {
+                        bi = i;
+                        break;
+                    }
+                if (bi < 0) break;
+                const int w = (int)I.nbr[(int64_t)c.v[bi] * n + c.pos[bi]];
+                ++c.pos[bi];
+                bool emit = true;
+                for (int k = 0; k <= p && emit; ++k) {
+                    if (k == bi) continue;
+                    const float e = I.dist(c.v[k], w);
+                    if (e > bd || (e == bd && k > bi)) emit = false;
+                }
+                if (emit) c.ties.push_back(w);
+            }
+            if (!c.ties.empty()) {
+                std::sort(c.ties.begin(), c.ties.end());
+                c.tie_key = bd;
+                const int w = c.ties.back();
+                c.ties.pop_back();
+                c.head = age_key(bd, cofacet_idx(*I.B, c.v, p, w));
+                return;
+            }
+        }
+    }
+
+    // The apparent column owning pivot tau, if any: tau is among the apparent
+    // taus, and its owner is the youngest facet of tau (vertices into s, the
+    // vertex tau adds to it into *added).
+    bool apparent_owner(u128 key, int *s, int *added) const {
+        const uint64_t tidx = key_index(key);
+        if (!is_apparent_tau(tidx)) return false;
+        const float dt = key_diam(key);
+        int u[RPP_MAX_DIM + 2];
+        decode_host(*I.B, tidx, p + 1, n, u);
+        int best = -1;
+        float bestd = -1.0f;
+        for (int r = 0; r <= p + 1; ++r) {  // facets in increasing index order
+            float fd = 0.0f;
+            for (int a = 0; a <= p + 1; ++a)
+                for (int b = a + 1; b <= p + 1; ++b)
+                    if (a != r && b != r) fd = std::max(fd, I.dist(u[a], u[b]));
+            if (fd > bestd) {  // strict: the first (smallest index) wins ties
+                bestd = fd;
+                best = r;
+            }
+        }
+        if (bestd != dt) return false;  // cannot happen for an apparent tau
+        for (int a = 0, k = 0; a <= p + 1; ++a)
+            if (a != best) s[k++] = u[a];
+        *added = u[best];
+        return true;
     }
 };
 
-// Push the coboundary of the p-simplex v (diameter d) restricted to diam <= t.
-void push_coboundary(const HostInstance &I, int p, const int *v, float d, WorkColumn &W) {
-    const Binomial &B = *I.B;
-    // For w from n-1 down: j = number of vertices of v above w. The cofacet
-    // index is sum_{i<j} C(v_i, p+2-i) + C(w, p+2-j) + sum_{i>=j} C(v_i, p+1-i).
-    uint64_t high = 0, low = 0;
-    for (int i = 0; i <= p; ++i) low += B.at(p + 1 - i, v[i]);
-    int j = 0;
-    for (int64_t w = I.n - 1; w >= 0; --w) {
-        if (j <= p && w == v[j]) {
-            high += B.at(p + 2 - j, v[j]);
-            low -= B.at(p + 1 - j, v[j]);
-            ++j;
+struct ColumnState {
+    std::vector<Cursor> cur;
+    std::vector<std::pair<u128, int32_t>> heap;  // (head, cursor)
+    std::vector<std::pair<uint64_t, float>> V;    // simplices whose coboundaries were added
+    u128 cand = NONE;
+    bool started = false;
+    int64_t additions = 0, reads = 0, entries = 0;
+};
+
+typedef std::greater<std::pair<u128, int32_t>> HeapCmp;
+
+// Add the coboundary of simplex v (index idx, diameter d) to the working
+// column; `first` as in Reducer::init_cursor.
+void add_cursor(const Reducer &R, ColumnState &S, const int *v, uint64_t idx, float d,
+                int first) {
+    S.cur.emplace_back();
+    R.init_cursor(S.cur.back(), v, d, first);
+    if (S.cur.back().head != NONE) {
+        S.heap.emplace_back(S.cur.back().head, (int32_t)(S.cur.size() - 1));
+        std::push_heap(S.heap.begin(), S.heap.end(), HeapCmp());
+    }
+    S.V.emplace_back(idx, d);
+}
+
+void add_cursor(const Reducer &R, ColumnState &S, uint64_t idx, float d) {
+    int v[RPP_MAX_DIM + 1];
+    decode_host(*R.I.B, idx, R.p, R.n, v);
+    add_cursor(R, S, v, idx, d, -1);
+}
+
+// Oldest nonzero entry of the working column (NONE if it is zero).
+u128 pivot(const Reducer &R, ColumnState &S) {
+    while (!S.heap.empty()) {
+        std::pop_heap(S.heap.begin(), S.heap.end(), HeapCmp());
+        const std::pair<u128, int32_t> a = S.heap.back();
+        S.heap.pop_back();
+        if (!S.heap.empty() && S.heap.front().first == a.first) {  // cancels over Z/2
+            std::pop_heap(S.heap.begin(), S.heap.end(), HeapCmp());
+            const std::pair<u128, int32_t> b = S.heap.back();
+            S.heap.pop_back();
+            S.entries += 2;
+            for (int32_t ci : {a.second, b.second}) {
+                Cursor &c = S.cur[ci];
+                R.advance(c);
+                if (c.head != NONE) {
+                    S.heap.emplace_back(c.head, ci);
+                    std::push_heap(S.heap.begin(), S.heap.end(), HeapCmp());
+                }
+            }
             continue;
         }
-        float cd = d;
-        for (int i = 0; i <= p; ++i) cd = std::max(cd, I.dist(v[i], (int)w));
-        if (cd > I.t) continue;
-        W.push(make_entry(cd, high + B.at(p + 2 - j, w) + low));
+        S.heap.push_back(a);
+        std::push_heap(S.heap.begin(), S.heap.end(), HeapCmp());
+        return a.first;
     }
+    return NONE;
+}
+
+// Owner of a pivot among finalized leftover columns: slot index, or -1.
+struct Finalized {
+    std::unordered_map<uint64_t, int64_t> owner;  // pivot index -> leftover slot
+    std::vector<std::vector<std::pair<uint64_t, float>>> V;  // reduced columns as sums
+};
+
+// Walk: add owners of the pivot until it is free. With fin == nullptr only
+// apparent owners are used (Phase A).
+void walk(const Reducer &R, ColumnState &S, const Finalized *fin) {
+    for (;;) {
+        const u128 k = pivot(R, S);
+        if (k == NONE) {
+            S.cand = NONE;
+            return;
+        }
+        ++S.reads;
+        if (fin) {
+            auto it = fin->owner.find(key_index(k));
+            if (it != fin->owner.end()) {
+                ++S.additions;
+                for (const auto &s : fin->V[it->second]) add_cursor(R, S, s.first, s.second);
+                continue;
+            }
+        }
+        int s[RPP_MAX_DIM + 1], added;
+        if (R.apparent_owner(k, s, &added)) {
+            ++S.additions;  // its oldest cofacet is the pivot, which adds `added`
+            add_cursor(R, S, s, index_host(*R.I.B, s, R.p), key_diam(k), added);
+            continue;
+        }
+        S.cand = k;
+        return;
+    }
+}
+
+// The leftover column's own coboundary. Its oldest cofacet (found on the GPU)
+// tells where the cursor starts: a cofacet of equal diameter adds a known
+// vertex; a larger diameter means no cofacet of equal diameter exists.
+void start_column(const Reducer &R, ColumnState &S, const Leftover &L) {
+    S.started = true;
+    int v[RPP_MAX_DIM + 1], u[RPP_MAX_DIM + 2];
+    decode_host(*R.I.B, L.sigma, R.p, R.n, v);
+    int first = -1;
+    const bool empty_lune = L.pivot != NO_PIVOT && L.pdiam != L.diam;
+    if (L.pivot != NO_PIVOT && !empty_lune) {
+        decode_host(*R.I.B, L.pivot, R.p + 1, R.n, u);
+        for (int i = 0; i <= R.p + 1; ++i)
+            if (!R.in_simplex(v, u[i])) first = u[i];
+    }
+    if (empty_lune) {  // no cofacet of equal diameter: go straight to the merge
+        S.cur.emplace_back();
+        Cursor &c = S.cur.back();
+        for (int i = 0; i <= R.p; ++i) c.v[i] = v[i];
+        c.d = L.diam;
+        c.lune = -1;
+        c.merging = false;
+        R.advance(c);
+        if (c.head != NONE) {
+            S.heap.emplace_back(c.head, (int32_t)(S.cur.size() - 1));
+            std::push_heap(S.heap.begin(), S.heap.end(), HeapCmp());
+        }
+        S.V.emplace_back(L.sigma, L.diam);
+        return;
+    }
+    add_cursor(R, S, v, L.sigma, L.diam, first);
+}
+
+// Z/2 sum of the simplices in V: sort and drop pairs.
+void reduce_set(std::vector<std::pair<uint64_t, float>> &V) {
+    std::sort(V.begin(), V.end(),
+              [](const std::pair<uint64_t, float> &a, const std::pair<uint64_t, float> &b) {
+                  return a.first < b.first;
+              });
+    size_t o = 0;
+    for (size_t i = 0; i < V.size();) {
+        size_t j = i;
+        while (j < V.size() && V[j].first == V[i].first) ++j;
+        if ((j - i) & 1) V[o++] = V[i];
+        i = j;
+    }
+    V.resize(o);
 }
 
 }  // namespace
 
 void reduce_leftovers(const HostInstance &I, int p, const Leftover *left, int64_t nleft,
-                      PairStore &store, std::vector<HostPair> &out, ReduceStats &stats) {
-    std::vector<std::vector<entry>> stored(nleft);
-    WorkColumn W;
-    int v[RPP_MAX_DIM + 2];
+                      int threads, std::vector<HostPair> &out, ReduceStats &stats) {
+    Reducer R(I, p);
+    std::vector<ColumnState> col(nleft);
+
+    // Phase A: apparent walks, independent per column
+    std::atomic<int64_t> next(0);
+    auto phase_a = [&]() {
+        for (;;) {
+            const int64_t j = next.fetch_add(1);
+            if (j >= nleft) return;
+            const Leftover &L = left[j];
+            ColumnState &S = col[j];
+            if (L.pivot == NO_PIVOT) {
+                S.cand = NONE;
+                continue;
+            }
+            const u128 k0 = age_key(L.pdiam, L.pivot);
+            int s[RPP_MAX_DIM + 1], added;
+            ++S.reads;
+            if (!R.apparent_owner(k0, s, &added)) {
+                S.cand = k0;  // the unreduced pivot is free of apparent owners
+                continue;
+            }
+            start_column(R, S, L);
+            walk(R, S, nullptr);
+        }
+    };
+    int nt = std::max(1, threads);
+    if (nleft < 8) nt = 1;
+    if (nt == 1) {
+        phase_a();
+    } else {
+        std::vector<std::thread> pool;
+        for (int i = 0; i < nt; ++i) pool.emplace_back(phase_a);
+        for (auto &th : pool) th.join();
+    }
+
+    // Phase B: finalise in column order
+    Finalized fin;
+    fin.V.resize(nleft);
+    fin.owner.reserve((size_t)nleft * 2);
     for (int64_t j = 0; j < nleft; ++j) {
         const Leftover &L = left[j];
+        ColumnState &S = col[j];
+        if (S.cand != NONE && fin.owner.count(key_index(S.cand))) {
+            if (!S.started) start_column(R, S, L);
+            walk(R, S, &fin);
+        }
         HostPair P;
         P.sigma = L.sigma;
         P.birth = L.diam;
-        if (L.pivot == NO_PIVOT) {  // empty coboundary: an essential class
+        if (S.cand == NONE) {
             P.tau = NO_PIVOT;
             P.death = INFINITY;
-            out.push_back(P);
-            continue;
-        }
-        uint64_t osig;
-        int64_t oslot;
-        if (store.lookup(L.pivot, &osig, &oslot) == 0) {  // nobody owns the pivot
-            ++stats.free_pivot;
-            store.reduced[L.pivot] = j;
-            P.tau = L.pivot;
-            P.death = L.pdiam;
-            out.push_back(P);
-            continue;
-        }
-        W.h.clear();
-        decode_host(*I.B, L.sigma, p, I.n, v);
-        push_coboundary(I, p, v, L.diam, W);
-        entry e;
-        bool nonzero;
-        while ((nonzero = W.low(&e))) {
-            const uint64_t tau = entry_index(e);
-            const int kind = store.lookup(tau, &osig, &oslot);
-            if (kind == 0) break;
-            ++stats.additions;
-            if (kind == 1) {  // apparent owner: its column is its coboundary
-                decode_host(*I.B, osig, p, I.n, v);
-                push_coboundary(I, p, v, entry_diam(e), W);
-            } else if (!stored[oslot].empty()) {
-                for (entry x : stored[oslot]) W.push(x);
+        } else {
+            P.tau = key_index(S.cand);
+            P.death = key_diam(S.cand);
+            fin.owner[P.tau] = j;
+            if (S.started) {
+                reduce_set(S.V);
+                fin.V[j].swap(S.V);
             } else {
-                const Leftover &O = left[oslot];
-                decode_host(*I.B, O.sigma, p, I.n, v);
-                push_coboundary(I, p, v, O.diam, W);
+                fin.V[j].emplace_back(L.sigma, L.diam);
+                ++stats.free_pivot;
             }
         }
-        if (nonzero) {
-            const uint64_t tau = entry_index(e);
-            store.reduced[tau] = j;
-            P.tau = tau;
-            P.death = entry_diam(e);
-            out.push_back(P);
-            W.drain(stored[j]);  // the reduced column, for later additions
-        } else {
-            P.tau = NO_PIVOT;
-            P.death = INFINITY;
-            out.push_back(P);
-        }
+        out.push_back(P);
+        stats.additions += S.additions;
+        stats.reads += S.reads;
+        stats.entries += S.entries;
+        std::vector<Cursor>().swap(S.cur);
+        std::vector<std::pair<u128, int32_t>>().swap(S.heap);
     }
-    stats.reads += store.reads;
 }
 
 }  // namespace rpp

@@ -1,5 +1,5 @@
 // host.h -- host-side stages of the pipeline: H0 by Kruskal, the submatrix
-// reduction of the leftover columns, and barcode assembly.
+// reduction of the leftover columns, and barcode assembly helpers.
 #pragma once
 
 #include <stdint.h>
@@ -15,15 +15,20 @@ namespace rpp {
 // Read-only view of one instance for the host stages.
 struct HostInstance {
     int64_t n = 0;
-    const float *D = nullptr;  // host copy, row stride ld
+    const float *D = nullptr;     // host copy, row stride ld
     int64_t ld = 0;
     const Binomial *B = nullptr;
-    float t = 0.0f;            // threshold in use
+    const uint32_t *nbr = nullptr;  // n x n neighbour lists sorted by (distance, index)
+    const uint64_t *app_tau = nullptr;  // apparent pivots (tau) of the current dimension, sorted
+    uint64_t napp = 0;
+    float t = 0.0f;                 // threshold in use
     float dist(int a, int b) const { return D[(int64_t)a * ld + b]; }
 };
 
 // Vertices v[0] > ... > v[p] of a p-simplex index.
 void decode_host(const Binomial &B, uint64_t c, int p, int64_t n, int *v);
+// Index of the p-simplex with vertices v[0] > ... > v[p].
+uint64_t index_host(const Binomial &B, const int *v, int p);
 // Youngest edge of a simplex (largest distance; ties: smallest edge index),
 // returned as (u, w) with u > w.
 void youngest_edge(const HostInstance &I, const int *v, int k, int32_t *u, int32_t *w);
@@ -51,28 +56,18 @@ struct Kruskal {
 };
 
 // ---- submatrix reduction ----------------------------------------------------
-// Two-layer pair store (Sec. "Core System Optimizations", Fig. "two-layer
-// data structure"): pairs found by the reduction live in a hash map, apparent
-// pairs in an array sorted by tau searched with binary search.
-struct PairStore {
-    const uint64_t *app_tau = nullptr;    // sorted ascending
-    const uint64_t *app_sigma = nullptr;
-    uint64_t napp = 0;
-    std::unordered_map<uint64_t, int64_t> reduced;  // tau -> leftover slot
-    int64_t reads = 0;
-    // 0: free; 1: apparent (sigma in *sigma); 2: reduced (slot in *slot)
-    int lookup(uint64_t tau, uint64_t *sigma, int64_t *slot);
-};
-
 struct ReduceStats {
-    int64_t free_pivot = 0, additions = 0, reads = 0;
+    int64_t free_pivot = 0, additions = 0, reads = 0, entries = 0;
 };
 
-// Reduce the leftover columns of dimension p (given in coboundary order) with
-// the reduction-matrix technique (Sec. "Reduction Matrix vs. Oblivious Matrix
-// Reduction"): each column is reduced by adding the reduced columns that own
-// its current pivot. Appends pairs (zero-length included) and essential classes.
+// Reduce the leftover columns of dimension p (given in coboundary order) and
+// append their pairs (zero-length included) and essential classes to out.
+// The pair store has two layers (Sec. "Core System Optimizations"): pairs
+// found here live in a hash map; apparent pairs are the array of their taus
+// sorted on the GPU, searched through a small in-cache index. The owner of an
+// apparent tau is its youngest facet (the definition of an apparent pair), so
+// only the taus are needed.
 void reduce_leftovers(const HostInstance &I, int p, const Leftover *left, int64_t nleft,
-                      PairStore &store, std::vector<HostPair> &out, ReduceStats &stats);
+                      int threads, std::vector<HostPair> &out, ReduceStats &stats);
 
 }  // namespace rpp

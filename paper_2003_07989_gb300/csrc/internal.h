@@ -27,7 +27,11 @@ struct DevState {
     unsigned long long napp;   // apparent pairs written by the partition kernel
     unsigned long long nleft;  // leftover columns written by the partition kernel
     unsigned long long begin;  // first column inside a quantile threshold
+    unsigned long long scanned;  // candidate vertices examined by the apparent pass
 };
+
+// Kernels launched by the calling thread (incremented by every launcher).
+extern thread_local long long g_launches;
 
 enum : unsigned int { ERR_NONFINITE = 1u, ERR_NEGATIVE = 2u, ERR_ASYMMETRIC = 4u, ERR_DIAGONAL = 8u };
 
@@ -87,7 +91,7 @@ void launch_mark_cleared(const uint32_t *pos, int64_t count, uint8_t *status, cu
 // [0, ncols) in coboundary order. Writes status, pivot and pivot diameter.
 void launch_apparent(const float *D, int64_t ld, int64_t n, int p, const uint64_t *binom,
                      const uint32_t *key_hi, const uint64_t *key_lo, uint64_t ncols,
-                     const DevState *st, uint8_t *status, uint64_t *pivot, float *pdiam,
+                     DevState *st, uint8_t *status, uint64_t *pivot, float *pdiam,
                      int group, int sms, cudaStream_t s);
 
 // Partition: apparent columns -> (tau, sigma) pairs; leftover columns -> Leftover.
@@ -99,6 +103,11 @@ void launch_partition(const uint8_t *status, const uint32_t *key_hi, const uint6
 // First position i in [0, n) with a[i] >= key for ascending a, into *out.
 void launch_lower_bound_u32(const uint32_t *a, uint64_t n, uint32_t key, unsigned long long *out,
                             cudaStream_t s);
+
+// Per-vertex neighbour lists: row v of out (n x n) lists all vertices in
+// increasing (D[v][w], w) order. Returns false if n is too large for the
+// shared-memory sort (the caller then sorts on the host).
+bool launch_sort_rows(const float *D, int64_t ld, int64_t n, uint32_t *out, cudaStream_t s);
 
 // Set bit `idx[i]` of a bitmap for every i.
 void launch_bitmap_set(const uint64_t *idx, uint64_t count, uint32_t *bitmap, cudaStream_t s);

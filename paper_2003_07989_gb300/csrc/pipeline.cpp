@@ -12,9 +12,11 @@
 #include "pipeline.h"
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <thread>
 
 namespace rpp {
 
@@ -70,13 +72,87 @@ float bits_to_float(uint32_t b) {
 Workspace::~Workspace() {
     DevBuf *d[] = {&X,    &Dsrc,  &D,      &state,   &binom,     &key_hi, &key_lo,
                    &tmp_hi, &tmp_lo, &tmp_val, &tiles, &hist,      &status, &pivot,
-                   &pdiam, &app_tau, &app_sigma, &left, &bitmap, &mst,    &up};
+                   &pdiam, &app_tau, &app_sigma, &left, &bitmap, &mst,    &up, &nbr};
     for (DevBuf *b : d)
         if (b->p) cudaFree(b->p);
-    HostBuf *h[] = {&h_hi, &h_lo, &h_tau, &h_sigma, &h_left, &h_D, &h_state, &h_mst, &h_up};
+    HostBuf *h[] = {&h_hi,    &h_lo,  &h_tau, &h_sigma, &h_left,
+                    &h_D,     &h_state, &h_mst, &h_up,  &h_nbr};
     for (HostBuf *b : h)
         if (b->p) cudaFreeHost(b->p);
+    for (cudaEvent_t e : events) cudaEventDestroy(e);
 }
+
+namespace {
+
+// Per-stage device time from CUDA events recorded on the pipeline's stream
+// around each stage (rpp_stats.stage_ms), plus kernel launch counts.
+struct StageTimer {
+    bool on = false;
+    cudaStream_t s = nullptr;
+    Workspace *ws = nullptr;
+    size_t used = 0;
+    int cur = -1;
+    long long l0 = 0;
+    cudaEvent_t start = nullptr;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> marks;
+    int64_t launches[8] = {};
+    cudaEvent_t get() {
+        if (used == ws->events.size()) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            ws->events.push_back(e);
+        }
+        return ws->events[used++];
+    }
+    void begin(int stage) {
+        cur = stage;
+        l0 = g_launches;
+        if (!on) return;
+        start = get();
+        cudaEventRecord(start, s);
+    }
+    void end() {
+        if (cur >= 0) launches[cur] += g_launches - l0;
+        if (on) {
+            cudaEvent_t e = get();
+            cudaEventRecord(e, s);
+            marks.push_back({cur, {start, e}});
+        }
+        cur = -1;
+    }
+    // after the stream is synchronised
+    void collect(rpp_stats &S) {
+        for (auto &m : marks) {
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, m.second.first, m.second.second);
+            S.stage_ms[m.first] += ms;
+        }
+        for (int i = 0; i < 8; ++i) S.stage_launches[i] = launches[i];
+    }
+};
+
+enum { ST_DIST = 0, ST_RADIUS, ST_BUILD, ST_SORT, ST_APPARENT, ST_PARTITION, ST_PAIRSORT, ST_OTHER };
+
+// Neighbour lists on the host, for matrices too large for the GPU row sort.
+void sort_rows_host(const float *D, int64_t ld, int64_t n, uint32_t *out, int threads) {
+    std::atomic<int64_t> next(0);
+    auto work = [&]() {
+        for (int64_t r; (r = next.fetch_add(1)) < n;) {
+            uint32_t *row = out + r * n;
+            for (int64_t i = 0; i < n; ++i) row[i] = (uint32_t)i;
+            const float *d = D + r * ld;
+            std::sort(row, row + n, [d](uint32_t a, uint32_t b) {
+                return d[a] < d[b] || (d[a] == d[b] && a < b);
+            });
+        }
+    };
+    std::vector<std::thread> pool;
+    for (int i = 1; i < std::max(1, threads); ++i) pool.emplace_back(work);
+    work();
+    for (auto &t : pool) t.join();
+}
+
+}  // namespace
 
 Status Workspace::dev(DevBuf &b, size_t bytes, void **out) {
     if (bytes == 0) bytes = 256;
@@ -200,6 +276,7 @@ size_t instance_device_bytes(const Instance &in) {
     const size_t per = 4 + 8 + 4 + 8 + 8 + 1 + 8 + 4 + 8 + 8 + sizeof(Leftover);
     total += slack(maxcand * per) + slack(radix_tile_counts_size(maxcand) * 4) + slack(12 * 256 * 4);
     total += slack((size_t)n * 4) + slack(maxcand / 8 + 8) + slack(maxcand * 8);
+    total += slack((size_t)n * n * 4);  // neighbour lists
     return total + 64 * 256;  // per-buffer rounding
 }
 
@@ -262,6 +339,12 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
     std::memset(&S, 0, sizeof S);
     S.n = n;
     S.max_dim = max_dim;
+    StageTimer T;
+    T.on = (ctx->record & RPP_RECORD_TIMING) != 0;
+    T.s = s;
+    T.ws = &ws;
+    const long long launches0 = g_launches;
+    unsigned long long scanned_prev = 0;
 
     // binomial table, cached per (n, kmax)
     const int kmax = max_dim + 2 < 3 ? 3 : max_dim + 2;
@@ -300,7 +383,9 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
                                    cudaMemcpyHostToDevice, s));
             X = (const float *)vp;
         }
+        T.begin(ST_DIST);
         launch_distance_matrix(X, n, in.dim, D, ld, s);
+        T.end();
     } else {
         const float *src = in.data;
         if (!is_device_pointer(src)) {
@@ -309,10 +394,14 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
                                    s));
             src = (const float *)vp;
         }
+        T.begin(ST_DIST);
         launch_copy_validate_distances(src, n, D, ld, st, s);
+        T.end();
     }
     const float t_user = in.quantile > 0.0f ? INFINITY : in.threshold;
+    T.begin(ST_RADIUS);
     launch_enclosing_radius(D, n, ld, st, t_user, s);
+    T.end();
     RPP_CK(cudaGetLastError());
 
     // host copy of D for the reduction and the realising edges
@@ -378,12 +467,16 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
         // ---- dimension 1 columns: every edge inside the threshold, sorted ----
         const uint64_t m = B.at(2, n);
         S.candidates[1] = (int64_t)m;
+        T.begin(ST_BUILD);
         launch_build_columns(D, ld, n, 1, d_binom, m, nullptr, st, key_hi, key_lo, s);
+        T.end();
         RPP_CK(cudaGetLastError());
         RPP_TRY(read_state());
         const uint64_t N = hst->ncols;
+        T.begin(ST_SORT);
         radix_sort(key_hi, key_lo, nullptr, tmp_hi, tmp_lo, nullptr, tiles, hist, N,
                    bits_for(m - 1), 32, s);
+        T.end();
         RPP_CK(cudaGetLastError());
         uint64_t begin = 0;
         if (in.quantile > 0.0f) {
@@ -396,7 +489,9 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
                 RPP_CK(cudaMemcpyAsync(&kh, key_hi + (N - r), 4, cudaMemcpyDeviceToHost, s));
                 RPP_CK(cudaStreamSynchronize(s));
                 t = bits_to_float(~kh);
+                T.begin(ST_OTHER);
                 launch_lower_bound_u32(key_hi, N, kh, &st->begin, s);
+                T.end();
                 RPP_CK(cudaMemcpyAsync(&st->t, &t, sizeof(float), cudaMemcpyHostToDevice, s));
                 RPP_TRY(read_state());
                 begin = hst->begin;
@@ -458,12 +553,18 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
                 for (size_t i = 0; i < K.mst_pos.size(); ++i)
                     hm[i] = (uint32_t)(K.mst_pos[i] - begin);
                 RPP_CK(cudaMemcpyAsync(mst, hm, K.mst_pos.size() * 4, cudaMemcpyHostToDevice, s));
+                T.begin(ST_OTHER);
                 launch_mark_cleared(mst, (int64_t)K.mst_pos.size(), status, s);
+                T.end();
             }
             const Tuning tu = ctx->tuning_for(n, 1);
+            T.begin(ST_APPARENT);
             launch_apparent(D, ld, n, 1, d_binom, hi1, lo1, cols, st, status, pivot, pdiam,
                             tu.group, ctx->sms, s);
+            T.end();
+            T.begin(ST_PARTITION);
             launch_partition(status, hi1, lo1, pivot, pdiam, cols, app_tau, app_sigma, left, st, s);
+            T.end();
             RPP_CK(cudaGetLastError());
         }
     } else {
@@ -495,24 +596,32 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
             uint32_t *bitmap;
             RPP_TRY(ws.dev(ws.bitmap, (cand + 31) / 32 * 4, (void **)&bitmap));
             RPP_CK(cudaMemsetAsync(bitmap, 0, (cand + 31) / 32 * 4, s));
+            T.begin(ST_OTHER);
             launch_bitmap_set(app_tau, prev_napp, bitmap, s);
+            T.end();
             if (!prev_deaths.empty()) {
                 uint64_t *up;
                 RPP_TRY(ws.dev(ws.up, prev_deaths.size() * 8, (void **)&up));
                 RPP_TRY(ws.host(ws.h_up, prev_deaths.size() * 8, &vp));
                 std::memcpy(vp, prev_deaths.data(), prev_deaths.size() * 8);
                 RPP_CK(cudaMemcpyAsync(up, vp, prev_deaths.size() * 8, cudaMemcpyHostToDevice, s));
+                T.begin(ST_OTHER);
                 launch_bitmap_set(up, prev_deaths.size(), bitmap, s);
+                T.end();
             }
             RPP_CK(cudaMemsetAsync(&st->ncols, 0, sizeof(unsigned long long), s));
+            T.begin(ST_BUILD);
             launch_build_columns(D, ld, n, p, d_binom, cand, bitmap, st, key_hi, key_lo, s);
+            T.end();
             RPP_CK(cudaGetLastError());
             RPP_TRY(read_state());
             const uint64_t N = hst->ncols;
             S.columns[p] = (int64_t)N;
             S.cleared[p] = (int64_t)(prev_napp + prev_deaths.size());
+            T.begin(ST_SORT);
             radix_sort(key_hi, key_lo, nullptr, tmp_hi, tmp_lo, nullptr, tiles, hist, N,
                        bits_for(cand - 1), 32, s);
+            T.end();
             if (ctx->record & RPP_RECORD_COLUMNS) {
                 std::vector<uint32_t> hh(N);
                 res->col_idx[p].resize(N);
@@ -527,21 +636,34 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
             RPP_CK(cudaMemsetAsync(status, 0, N, s));
             RPP_CK(cudaMemsetAsync(&st->napp, 0, 2 * sizeof(unsigned long long), s));
             const Tuning tu = ctx->tuning_for(n, p);
+            T.begin(ST_APPARENT);
             launch_apparent(D, ld, n, p, d_binom, key_hi, key_lo, N, st, status, pivot, pdiam,
                             tu.group, ctx->sms, s);
+            T.end();
+            T.begin(ST_PARTITION);
             launch_partition(status, key_hi, key_lo, pivot, pdiam, N, app_tau, app_sigma, left,
                              st, s);
+            T.end();
             RPP_CK(cudaGetLastError());
         }
         RPP_TRY(read_state());
         const uint64_t napp = hst->napp, nleft = hst->nleft;
         S.apparent[p] = (int64_t)napp;
         S.leftover[p] = (int64_t)nleft;
-        // apparent pairs sorted by tau: the second layer of the pair store
-        radix_sort(nullptr, app_tau, app_sigma, nullptr, tmp_lo, tmp_val, tiles, hist, napp,
-                   bits_for(B.at(p + 2, n) - 1), 0, s);
-        RPP_CK(cudaGetLastError());
-        if (ctx->record & RPP_RECORD_APPARENT) {
+        S.scanned[p] = (int64_t)(hst->scanned - scanned_prev);
+        scanned_prev = hst->scanned;
+        const bool record_app = (ctx->record & RPP_RECORD_APPARENT) != 0;
+        if (record_app || nleft > 0) {
+            // the apparent taus sorted: the second layer of the pair store (the
+            // sigmas ride along only when the pairs are recorded; the host
+            // reduction takes the owner of an apparent tau as its youngest facet)
+            T.begin(ST_PAIRSORT);
+            radix_sort(nullptr, app_tau, record_app ? app_sigma : nullptr, nullptr, tmp_lo,
+                       tmp_val, tiles, hist, napp, bits_for(B.at(p + 2, n) - 1), 0, s);
+            T.end();
+            RPP_CK(cudaGetLastError());
+        }
+        if (record_app) {
             res->app_tau[p].resize(napp);
             res->app_sigma[p].resize(napp);
             RPP_CK(cudaMemcpyAsync(res->app_tau[p].data(), app_tau, napp * 8,
@@ -554,28 +676,44 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
         DimOutput out;
         if (nleft > 0) {
             Leftover *hleft;
-            uint64_t *htau, *hsig;
+            uint64_t *htau;
             RPP_TRY(ws.host(ws.h_left, nleft * sizeof(Leftover), (void **)&hleft));
             RPP_TRY(ws.host(ws.h_tau, napp * 8, (void **)&htau));
-            RPP_TRY(ws.host(ws.h_sigma, napp * 8, (void **)&hsig));
-            double a = now_ms();
-            RPP_CK(cudaMemcpyAsync(hleft, left, nleft * sizeof(Leftover), cudaMemcpyDeviceToHost, s));
             RPP_CK(cudaMemcpyAsync(htau, app_tau, napp * 8, cudaMemcpyDeviceToHost, s));
-            RPP_CK(cudaMemcpyAsync(hsig, app_sigma, napp * 8, cudaMemcpyDeviceToHost, s));
-            RPP_CK(cudaStreamSynchronize(s));
-            dev_ms += now_ms() - a;
-            a = now_ms();
+            I.app_tau = htau;
+            I.napp = napp;
+            if (!I.nbr) {  // neighbour lists for the lazy coboundaries, once per instance
+                uint32_t *dn, *hn;
+                RPP_TRY(ws.dev(ws.nbr, (size_t)n * n * 4, (void **)&dn));
+                RPP_TRY(ws.host(ws.h_nbr, (size_t)n * n * 4, (void **)&hn));
+                T.begin(ST_OTHER);
+                const bool gpu_sorted = launch_sort_rows(D, ld, n, dn, s);
+                T.end();
+                if (gpu_sorted)
+                    RPP_CK(cudaMemcpyAsync(hn, dn, (size_t)n * n * 4, cudaMemcpyDeviceToHost, s));
+                RPP_CK(cudaMemcpyAsync(hleft, left, nleft * sizeof(Leftover),
+                                       cudaMemcpyDeviceToHost, s));
+                double a = now_ms();
+                RPP_CK(cudaStreamSynchronize(s));
+                dev_ms += now_ms() - a;
+                if (!gpu_sorted) sort_rows_host(hD, ld, n, hn, ctx->host_threads);
+                I.nbr = hn;
+            } else {
+                double a = now_ms();
+                RPP_CK(cudaMemcpyAsync(hleft, left, nleft * sizeof(Leftover),
+                                       cudaMemcpyDeviceToHost, s));
+                RPP_CK(cudaStreamSynchronize(s));
+                dev_ms += now_ms() - a;
+            }
+            double a = now_ms();
             std::sort(hleft, hleft + nleft,
                       [](const Leftover &x, const Leftover &y) { return x.index < y.index; });
-            PairStore store;
-            store.app_tau = htau;
-            store.app_sigma = hsig;
-            store.napp = napp;
             ReduceStats rs;
-            reduce_leftovers(I, p, hleft, (int64_t)nleft, store, out.pairs, rs);
+            reduce_leftovers(I, p, hleft, (int64_t)nleft, ctx->host_threads, out.pairs, rs);
             S.free_pivot[p] = rs.free_pivot;
             S.additions[p] = rs.additions;
             S.store_reads[p] = rs.reads;
+            S.entries[p] = rs.entries;
             red_ms += now_ms() - a;
         }
         // intervals of dimension p and the deaths that clear dimension p + 1
@@ -595,7 +733,9 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
         }
         prev_napp = napp;
     }
-    if (n >= 2 && max_dim >= 1) RPP_CK(cudaStreamSynchronize(s));
+    if ((n >= 2 && max_dim >= 1) || T.on) RPP_CK(cudaStreamSynchronize(s));
+    T.collect(S);
+    S.kernel_launches = g_launches - launches0;
 
     for (int q = 0; q <= max_dim; ++q) {
         sort_result(res, q);

@@ -38,13 +38,14 @@ struct Workspace {
     size_t budget = 0;        // 0 = unbounded
     size_t device_bytes = 0;  // currently held
     DevBuf X, Dsrc, D, state, binom, key_hi, key_lo, tmp_hi, tmp_lo, tmp_val, tiles, hist,
-        status, pivot, pdiam, app_tau, app_sigma, left, bitmap, mst, up;
-    HostBuf h_hi, h_lo, h_tau, h_sigma, h_left, h_D, h_state, h_mst, h_up;
+        status, pivot, pdiam, app_tau, app_sigma, left, bitmap, mst, up, nbr;
+    HostBuf h_hi, h_lo, h_tau, h_sigma, h_left, h_D, h_state, h_mst, h_up, h_nbr;
     Binomial binom_host;      // cached table
     int64_t binom_n = -1;
     int binom_k = -1;
     bool binom_on_device = false;
     std::vector<uint64_t> binom_store;
+    std::vector<cudaEvent_t> events;  // pool for stage timing
     ~Workspace();
     Status dev(DevBuf &b, size_t bytes, void **out);
     Status host(HostBuf &b, size_t bytes, void **out);
@@ -90,6 +91,7 @@ struct rpp_context {
     size_t budget = 0;
     int sms = 0;
     int record = 0;  // RPP_RECORD_* flags
+    int host_threads = 1;  // threads for the host reductions
     std::mutex mu;
     std::vector<rpp::Workspace *> free_ws;
     std::vector<rpp::Workspace *> all_ws;

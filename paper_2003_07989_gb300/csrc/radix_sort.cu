@@ -160,10 +160,15 @@ void radix_sort(uint32_t *hi, uint64_t *lo, uint64_t *val, uint32_t *tmp_hi, uin
                 uint64_t *tmp_val, uint32_t *tile_counts, uint32_t *digit_hist, uint64_t n,
                 int lo_bits, int hi_bits, cudaStream_t s) {
     if (n <= 1) return;
+    // absent key halves or payloads have no scratch either, so the buffer
+    // swaps below never pair a null array with a live one
+    if (!hi) tmp_hi = nullptr;
+    if (!val) tmp_val = nullptr;
     const int nlo = (lo_bits + 7) / 8, nhi = hi ? (hi_bits + 7) / 8 : 0;
     cudaMemsetAsync(digit_hist, 0, MAX_DIGITS * RADIX * sizeof(uint32_t), s);
     uint64_t hb = (n + SORT_THREADS - 1) / SORT_THREADS;
     if (hb > 152 * 4) hb = 152 * 4;
+    ++g_launches;
     k_hist_all<<<(unsigned)hb, SORT_THREADS, 0, s>>>(hi, lo, n, nlo, nhi, digit_hist);
     std::vector<uint32_t> h(MAX_DIGITS * RADIX);
     cudaMemcpyAsync(h.data(), digit_hist, h.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
@@ -181,8 +186,11 @@ void radix_sort(uint32_t *hi, uint64_t *lo, uint64_t *val, uint32_t *tmp_hi, uin
     uint32_t *hi_a = hi, *hi_b = tmp_hi;
     uint64_t *lo_a = lo, *lo_b = tmp_lo, *val_a = val, *val_b = tmp_val;
     for (int sel : passes) {
+        ++g_launches;
         k_count<<<(unsigned)ntiles, SORT_THREADS, 0, s>>>(hi_a, lo_a, n, sel, tile_counts);
+        ++g_launches;
         k_scan<<<1, RADIX, 0, s>>>(tile_counts, ntiles, digit_hist + sel * RADIX);
+        ++g_launches;
         k_scatter<<<(unsigned)ntiles, SORT_THREADS, 0, s>>>(
             hi_a, lo_a, val_a, hi_a ? hi_b : nullptr, lo_b, val_a ? val_b : nullptr, n, sel,
             tile_counts);
