@@ -200,6 +200,35 @@ int64_t rpp_result_total(const rpp_result *res);
 rpp_status rpp_distance_matrix(rpp_context *ctx, const float *points, int64_t n, int32_t dim,
                                float *out, void *stream);
 
+/* ---- the edge filtration without any device allocation ----
+ *
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot call cudaMalloc: code running inside another runtime's device
+ * memory pool, where all allocations must go through that owner, and
+ * latency-critical loops, where cudaMalloc or cudaFree would synchronise the
+ * device. It computes the dimension-1 columns of the library's filtration
+ * construction without clearing: every edge with diameter <= threshold,
+ * sorted by decreasing diameter, then increasing combinatorial index.
+ *   D          device, n x n float32 row-major distance matrix (symmetric,
+ *              finite, non-negative, zero diagonal, no -0.0; not checked).
+ *   n          1 <= n <= 724.
+ *   threshold  closed threshold t >= 0 (+INFINITY: every edge).
+ *   diam_out, cidx_out  device arrays of `capacity` entries, caller-owned;
+ *              the first *count_out entries are overwritten with the result.
+ *   capacity   must be >= C(n, 2).
+ *   count_out  host, receives the number of edges written.
+ * It allocates nothing: its scratch is one static device array of about
+ * 3.3 MB (up to 262,144 edges) that every GPU loading the library holds until
+ * the process exits. The first call on a device looks up that array's device
+ * address; make that first call before any stream capture. All calls share the
+ * array, so calls that overlap on the GPU (other streams, other threads) race
+ * and must be serialised by the caller. Returns RPP_E_INVALID for n above the
+ * bound, a short capacity, or D not in device memory; RPP_E_CUDA if a CUDA
+ * call fails. Waits for its stream before returning. */
+rpp_status rpp_filtration_edges_noalloc(const float *D, int64_t n, float threshold,
+                                        float *diam_out, uint64_t *cidx_out, int64_t capacity,
+                                        int64_t *count_out, void *stream);
+
 /* ---- recording of intermediate arrays (inspection and parity checks) ---- */
 
 #define RPP_RECORD_COLUMNS 1  /* keep each dimension's column array */

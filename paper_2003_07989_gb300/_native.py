@@ -21,7 +21,7 @@ EXPORTED = [
     "rpp_result_free", "rpp_barcodes_batched", "rpp_barcodes_backward", "rpp_result_total",
     "rpp_server_create", "rpp_server_submit", "rpp_server_poll", "rpp_server_destroy",
     "rpp_status_string", "rpp_last_error", "rpp_distance_matrix", "rpp_context_set_record",
-    "rpp_result_columns", "rpp_result_apparent",
+    "rpp_result_columns", "rpp_result_apparent", "rpp_filtration_edges_noalloc",
 ]
 RPP_RECORD_COLUMNS, RPP_RECORD_APPARENT, RPP_RECORD_TIMING = 1, 2, 4
 STAGES = ["distance", "enclosing_radius", "build_columns", "sort_columns", "apparent",
@@ -113,8 +113,10 @@ def lib():
     L.rpp_result_columns.restype = i64
     L.rpp_result_apparent.argtypes = [vp, i32, u64pp, u64pp]
     L.rpp_result_apparent.restype = i64
+    L.rpp_filtration_edges_noalloc.argtypes = [vp, i64, C.c_float, vp, vp, i64,
+                                               C.POINTER(i64), vp]
     for name in ("rpp_context_create", "rpp_barcodes", "rpp_barcodes_quantile",
-                 "rpp_distance_matrix", "rpp_context_set_record",
+                 "rpp_distance_matrix", "rpp_context_set_record", "rpp_filtration_edges_noalloc",
                  "rpp_result_stats", "rpp_barcodes_batched", "rpp_barcodes_backward",
                  "rpp_server_create", "rpp_server_submit", "rpp_server_poll"):
         getattr(L, name).restype = C.c_int

@@ -84,6 +84,12 @@ void radix_sort(uint32_t *hi, uint64_t *lo, uint64_t *val, uint32_t *tmp_hi, uin
                 uint64_t *tmp_val, uint32_t *tile_counts, uint32_t *digit_hist, uint64_t n,
                 int lo_bits, int hi_bits, cudaStream_t s);
 
+// radix_sort without payload and without any allocation (host_hist: caller
+// buffer of 12 * 256 entries).
+void radix_sort_noalloc(uint32_t *hi, uint64_t *lo, uint32_t *tmp_hi, uint64_t *tmp_lo,
+                        uint32_t *tile_counts, uint32_t *digit_hist, uint32_t *host_hist,
+                        uint64_t n, int lo_bits, int hi_bits, cudaStream_t s);
+
 // Mark columns at the given positions as cleared.
 void launch_mark_cleared(const uint32_t *pos, int64_t count, uint8_t *status, cudaStream_t s);
 

@@ -1,0 +1,154 @@
+// noalloc.cu -- the dimension-1 filtration (edges inside a threshold, sorted in
+// coboundary order) for callers that must not allocate device memory.
+//
+// Some callers cannot call cudaMalloc: code that runs inside another runtime's
+// device memory pool, where every allocation has to go through that owner, and
+// latency-critical loops, where cudaMalloc and cudaFree would implicitly
+// synchronise the device. This entry point takes the caller's input and output
+// buffers and keeps its scratch (counters, binomial table, radix-sort ping-pong
+// buffers and tile histograms) in one static device array of fixed size,
+// declared below. Every GPU that loads the library holds that array until the
+// process exits.
+#include <cmath>
+#include <mutex>
+#include <string>
+
+#include "../../include/rpp.h"
+#include "internal.h"
+
+namespace rpp {
+
+namespace {
+
+constexpr int64_t NA_MAX_EDGES = 1 << 18;  // largest output the scratch can sort
+constexpr int64_t NA_MAX_N = 724;          // C(724, 2) = 261,726 <= NA_MAX_EDGES
+constexpr size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+constexpr size_t OFF_STATE = 0;
+constexpr size_t OFF_BINOM = up256(sizeof(DevState));
+constexpr size_t OFF_HIST = up256(OFF_BINOM + 3 * (NA_MAX_N + 1) * sizeof(uint64_t));
+constexpr size_t OFF_TILES = up256(OFF_HIST + 12 * 256 * sizeof(uint32_t));
+constexpr size_t OFF_TMP_HI = up256(OFF_TILES + ((NA_MAX_EDGES + 2047) / 2048) * 256 * 4);
+constexpr size_t OFF_TMP_LO = up256(OFF_TMP_HI + NA_MAX_EDGES * sizeof(uint32_t));
+constexpr size_t SCRATCH_BYTES = up256(OFF_TMP_LO + NA_MAX_EDGES * sizeof(uint64_t));
+
+// The scratch of rpp_filtration_edges_noalloc (about 3.3 MB per GPU). In host
+// code this name is only a stand-in: its device address comes from
+// cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[SCRATCH_BYTES];
+
+std::mutex g_setup_mu;
+void *g_scratch_addr[256] = {};  // per device, filled by the first call on it
+
+// Zero the counters, set the threshold, and write C(v, k) for k = 0, 1, 2.
+__global__ void k_noalloc_init(DevState *st, float t, uint64_t *binom, int64_t n) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        DevState z = {};
+        z.t = t;
+        *st = z;
+    }
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v <= n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        binom[v] = 1;
+        binom[(n + 1) + v] = (uint64_t)v;
+        binom[2 * (n + 1) + v] = (uint64_t)v * (uint64_t)(v > 0 ? v - 1 : 0) / 2;
+    }
+}
+
+// Sort keys held ~bits(diameter); turn them back into diameters.
+__global__ void k_noalloc_finish(uint32_t *key_hi, uint64_t count) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) key_hi[i] = ~key_hi[i];
+}
+
+int bits_for(uint64_t x) {
+    int b = 0;
+    while (b < 64 && (x >> b)) ++b;
+    return b;
+}
+
+}  // namespace
+
+}  // namespace rpp
+
+using namespace rpp;
+
+extern "C" rpp_status rpp_filtration_edges_noalloc(const float *D, int64_t n, float threshold,
+                                                   float *diam_out, uint64_t *cidx_out,
+                                                   int64_t capacity, int64_t *count_out,
+                                                   void *stream) {
+    if (!D || !diam_out || !cidx_out || !count_out || n < 1 || std::isnan(threshold) ||
+        threshold < 0.0f) {
+        set_last_error("rpp_filtration_edges_noalloc: invalid arguments");
+        return RPP_E_INVALID;
+    }
+    if (n > NA_MAX_N) {
+        set_last_error("rpp_filtration_edges_noalloc: n exceeds the static scratch bound of 724 "
+                       "points (262,144 edges)");
+        return RPP_E_INVALID;
+    }
+    const uint64_t m = (uint64_t)n * (uint64_t)(n - 1) / 2;
+    if (capacity < (int64_t)m) {
+        set_last_error("rpp_filtration_edges_noalloc: output capacity below C(n, 2)");
+        return RPP_E_INVALID;
+    }
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, D) != cudaSuccess ||
+        (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)) {
+        cudaGetLastError();
+        set_last_error("rpp_filtration_edges_noalloc: D must be device memory");
+        return RPP_E_INVALID;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) {
+        set_last_error("rpp_filtration_edges_noalloc: no current CUDA device");
+        return RPP_E_CUDA;
+    }
+    unsigned char *base;
+    {
+        std::lock_guard<std::mutex> g(g_setup_mu);
+        if (!g_scratch_addr[dev]) {
+            void *p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                set_last_error(std::string("rpp_filtration_edges_noalloc: cudaGetSymbolAddress: ") +
+                               cudaGetErrorString(e));
+                return RPP_E_CUDA;
+            }
+            g_scratch_addr[dev] = p;
+        }
+        base = (unsigned char *)g_scratch_addr[dev];
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    DevState *st = (DevState *)(base + OFF_STATE);
+    uint64_t *binom = (uint64_t *)(base + OFF_BINOM);
+    uint32_t *hist = (uint32_t *)(base + OFF_HIST);
+    uint32_t *tiles = (uint32_t *)(base + OFF_TILES);
+    uint32_t *tmp_hi = (uint32_t *)(base + OFF_TMP_HI);
+    uint64_t *tmp_lo = (uint64_t *)(base + OFF_TMP_LO);
+    uint32_t *key_hi = (uint32_t *)diam_out;  // sorted as ~bits(diameter), then converted
+
+    ++g_launches;
+    k_noalloc_init<<<4, 256, 0, s>>>(st, threshold, binom, n);
+    launch_build_columns(D, n, n, 1, binom, m, nullptr, st, key_hi, cidx_out, s);
+    unsigned long long count = 0;
+    cudaMemcpyAsync(&count, &st->ncols, sizeof(count), cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) {
+        uint32_t host_hist[12 * 256];
+        radix_sort_noalloc(key_hi, cidx_out, tmp_hi, tmp_lo, tiles, hist, host_hist, count,
+                           bits_for(m > 0 ? m - 1 : 0), 32, s);
+        if (count > 0) {
+            ++g_launches;
+            k_noalloc_finish<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(key_hi, count);
+        }
+        e = cudaStreamSynchronize(s);
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_last_error(std::string("rpp_filtration_edges_noalloc: ") + cudaGetErrorString(e));
+        return RPP_E_CUDA;
+    }
+    *count_out = (int64_t)count;
+    return RPP_OK;
+}

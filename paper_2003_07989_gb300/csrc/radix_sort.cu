@@ -205,4 +205,49 @@ void radix_sort(uint32_t *hi, uint64_t *lo, uint64_t *val, uint32_t *tmp_hi, uin
     }
 }
 
+// The same sort driven without any allocation: the histogram comes back into
+// the caller's host buffer host_hist (12 * 256 entries), and no payload.
+void radix_sort_noalloc(uint32_t *hi, uint64_t *lo, uint32_t *tmp_hi, uint64_t *tmp_lo,
+                        uint32_t *tile_counts, uint32_t *digit_hist, uint32_t *host_hist,
+                        uint64_t n, int lo_bits, int hi_bits, cudaStream_t s) {
+    if (n <= 1) return;
+    const int nlo = (lo_bits + 7) / 8, nhi = (hi_bits + 7) / 8;
+    cudaMemsetAsync(digit_hist, 0, MAX_DIGITS * RADIX * sizeof(uint32_t), s);
+    uint64_t hb = (n + SORT_THREADS - 1) / SORT_THREADS;
+    if (hb > 152 * 4) hb = 152 * 4;
+    ++g_launches;
+    k_hist_all<<<(unsigned)hb, SORT_THREADS, 0, s>>>(hi, lo, n, nlo, nhi, digit_hist);
+    cudaMemcpyAsync(host_hist, digit_hist, MAX_DIGITS * RADIX * sizeof(uint32_t),
+                    cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    int passes[MAX_DIGITS], np = 0;
+    for (int d = 0; d < MAX_DIGITS; ++d) {
+        if (d < 8 && d >= nlo) continue;
+        if (d >= 8 && d - 8 >= nhi) continue;
+        bool constant = false;
+        for (int b = 0; b < RADIX; ++b)
+            if (host_hist[d * RADIX + b] == n) constant = true;
+        if (!constant) passes[np++] = d;
+    }
+    const uint64_t ntiles = (n + SORT_TILE - 1) / SORT_TILE;
+    uint32_t *hi_a = hi, *hi_b = tmp_hi;
+    uint64_t *lo_a = lo, *lo_b = tmp_lo;
+    for (int k = 0; k < np; ++k) {
+        const int sel = passes[k];
+        ++g_launches;
+        k_count<<<(unsigned)ntiles, SORT_THREADS, 0, s>>>(hi_a, lo_a, n, sel, tile_counts);
+        ++g_launches;
+        k_scan<<<1, RADIX, 0, s>>>(tile_counts, ntiles, digit_hist + sel * RADIX);
+        ++g_launches;
+        k_scatter<<<(unsigned)ntiles, SORT_THREADS, 0, s>>>(hi_a, lo_a, nullptr, hi_b, lo_b,
+                                                            nullptr, n, sel, tile_counts);
+        std::swap(hi_a, hi_b);
+        std::swap(lo_a, lo_b);
+    }
+    if (np & 1) {
+        cudaMemcpyAsync(lo, lo_a, n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(hi, hi_a, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
+    }
+}
+
 }  // namespace rpp
