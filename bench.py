@@ -43,6 +43,9 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=512,
+                    help="requests of the serving section (0 skips it)")
+    ap.add_argument("--serving-slots", type=int, default=8)
     return ap.parse_args()
 
 
@@ -166,6 +169,96 @@ def algorithmic_bytes(stage, st):
     if stage == "partition":
         return cols * (1 + 12 + 12) + st["apparent"][p] * 16 + st["leftover"][p] * 32
     return None
+
+
+# ---------------------------------------------------------------------------
+# serving: plain one-at-a-time path vs the continuous-batching server
+
+
+def _pct(xs, q):
+    xs = sorted(xs)
+    return xs[min(len(xs) - 1, max(0, int(math.ceil(q * len(xs))) - 1))]
+
+
+def serving_bench(rpp, count: int, slots: int):
+    """Barcodes/s at saturation and p50/p99 latency under Poisson arrivals at
+    0.8 x the plain path's sustained rate, for the plain path (the same
+    library, one request at a time, synchronous) and for the server."""
+    import threading
+    from paper_2003_07989_gb300 import inputs as I
+    reqs = I.serving_requests(count, seed=0)
+    for r in reqs[:8]:
+        rpp.rpp_barcodes(r.points, max_dim=1, quantile=r.threshold_quantile)
+    # plain, saturation
+    t0 = time.perf_counter()
+    for r in reqs:
+        rpp.rpp_barcodes(r.points, max_dim=1, quantile=r.threshold_quantile)
+    plain_s = time.perf_counter() - t0
+    plain_rps = count / plain_s
+    lam = 0.8 * plain_rps
+    arrivals = [r.arrival_s for r in I.serving_requests(count, rate_per_s=lam, seed=0)]
+
+    def plain_poisson():
+        lat, start = [], time.perf_counter()
+        for r, a in zip(reqs, arrivals):
+            now = time.perf_counter() - start
+            if now < a:
+                time.sleep(a - now)
+            rpp.rpp_barcodes(r.points, max_dim=1, quantile=r.threshold_quantile)
+            lat.append(time.perf_counter() - start - a)
+        return lat
+
+    def served(arr):
+        srv = rpp.Server(max_slots=slots)
+        done = {}
+        tickets = []
+        lock = threading.Lock()
+        finished = threading.Event()
+
+        def poller():
+            while True:
+                with lock:
+                    todo = [(i, t) for i, t in enumerate(tickets) if i not in done]
+                    all_in = finished.is_set() and len(done) == len(tickets)
+                if all_in:
+                    return
+                progressed = False
+                for i, t in todo:
+                    if srv.poll(t, 0) is not None:
+                        done[i] = time.perf_counter()
+                        progressed = True
+                if not progressed:
+                    time.sleep(0.0002)
+
+        th = threading.Thread(target=poller)
+        start = time.perf_counter()
+        th.start()
+        for r, a in zip(reqs, arr):
+            now = time.perf_counter() - start
+            if now < a:
+                time.sleep(a - now)
+            t = srv.submit(r.points, 1, quantile=r.threshold_quantile)
+            with lock:
+                tickets.append(t)
+        finished.set()
+        th.join()
+        end = max(done.values())
+        srv.close()
+        lat = [done[i] - start - arr[i] for i in range(count)]
+        return lat, end - start
+
+    plain_lat = plain_poisson()
+    _, sat_s = served([0.0] * count)
+    srv_lat, _ = served(arrivals)
+    return {
+        "requests": count, "slots": slots, "poisson_rate_per_s": lam,
+        "plain": {"barcodes_per_s": plain_rps, "p50_ms": 1e3 * _pct(plain_lat, 0.5),
+                  "p99_ms": 1e3 * _pct(plain_lat, 0.99)},
+        "served": {"barcodes_per_s": count / sat_s, "p50_ms": 1e3 * _pct(srv_lat, 0.5),
+                   "p99_ms": 1e3 * _pct(srv_lat, 0.99)},
+        "workload": "serving mix: n uniform in [32, 512], dim uniform in [2, 8], circle/2-sphere/"
+                    "blob, threshold = 0.6 nearest-rank distance quantile, H0-H1, seed 0",
+    }
 
 
 # ---------------------------------------------------------------------------
@@ -334,6 +427,9 @@ def main():
         cpu = {"value": r, "unit": "simplices/s", "cores": cores, "kind": "oracle",
                "sample": f"first 1000 of the 2000 torus points ({c} dimension-1 columns, "
                          f"{dt:.1f} s)"}
+    serving = None
+    if args.serving_requests > 0:
+        serving = serving_bench(rpp, args.serving_requests, args.serving_slots)
     h2d = X.nbytes
     d2h = sum(len(iv) * (8 + 16) for iv in e2e_results[0].intervals)
     line = {
@@ -351,6 +447,7 @@ def main():
         "clocks": clk,
         "roofline": roofline,
         "cpu_baseline": cpu,
+        "serving": serving,
         "breakdown": {
             "kernels": kernels,
             "host_reduce_ms": statistics.mean(s["ms_host_reduce"] for s in st),

@@ -28,11 +28,100 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <condition_variable>
 #include <cstring>
+#include <deque>
 #include <functional>
+#include <memory>
+#include <mutex>
 #include <thread>
 
 namespace rpp {
+
+// ---------------------------------------------------------------------------
+// A persistent pool of host threads shared by every reduction of the process.
+// parallel_for may be called from several threads at once; the caller works
+// on its own job too, so a job always makes progress.
+
+namespace {
+
+class Pool {
+  public:
+    struct Job {
+        std::function<void(int64_t)> fn;
+        int64_t count = 0;
+        std::atomic<int64_t> next{0}, done{0};
+        std::mutex m;
+        std::condition_variable cv;
+    };
+
+    explicit Pool(int workers) {
+        for (int i = 0; i < workers; ++i) th_.emplace_back([this] { loop(); });
+    }
+    ~Pool() {
+        {
+            std::lock_guard<std::mutex> g(mu_);
+            stop_ = true;
+        }
+        cv_.notify_all();
+        for (auto &t : th_) t.join();
+    }
+
+    void parallel_for(int64_t count, const std::function<void(int64_t)> &fn) {
+        auto job = std::make_shared<Job>();
+        job->fn = fn;
+        job->count = count;
+        {
+            std::lock_guard<std::mutex> g(mu_);
+            jobs_.push_back(job);
+        }
+        cv_.notify_all();
+        work(*job);
+        std::unique_lock<std::mutex> g(job->m);
+        job->cv.wait(g, [&] { return job->done.load() == job->count; });
+    }
+
+  private:
+    static void work(Job &j) {
+        for (;;) {
+            const int64_t i = j.next.fetch_add(1);
+            if (i >= j.count) return;
+            j.fn(i);
+            if (j.done.fetch_add(1) + 1 == j.count) {
+                std::lock_guard<std::mutex> g(j.m);
+                j.cv.notify_all();
+            }
+        }
+    }
+    void loop() {
+        for (;;) {
+            std::shared_ptr<Job> job;
+            {
+                std::unique_lock<std::mutex> g(mu_);
+                cv_.wait(g, [&] { return stop_ || !jobs_.empty(); });
+                if (stop_) return;
+                job = jobs_.front();
+                if (job->next.load() >= job->count) {  // exhausted: retire it
+                    jobs_.pop_front();
+                    continue;
+                }
+            }
+            work(*job);
+        }
+    }
+    std::mutex mu_;
+    std::condition_variable cv_;
+    std::deque<std::shared_ptr<Job>> jobs_;
+    std::vector<std::thread> th_;
+    bool stop_ = false;
+};
+
+Pool &pool(int threads) {
+    static Pool p(std::max(0, threads - 1));
+    return p;
+}
+
+}  // namespace
 
 void decode_host(const Binomial &B, uint64_t c, int p, int64_t n, int *v) {
     int hi = (int)n - 1;
@@ -469,36 +558,27 @@ void reduce_leftovers(const HostInstance &I, int p, const Leftover *left, int64_
     std::vector<ColumnState> col(nleft);
 
     // Phase A: apparent walks, independent per column
-    std::atomic<int64_t> next(0);
-    auto phase_a = [&]() {
-        for (;;) {
-            const int64_t j = next.fetch_add(1);
-            if (j >= nleft) return;
-            const Leftover &L = left[j];
-            ColumnState &S = col[j];
-            if (L.pivot == NO_PIVOT) {
-                S.cand = NONE;
-                continue;
-            }
-            const u128 k0 = age_key(L.pdiam, L.pivot);
-            int s[RPP_MAX_DIM + 1], added;
-            ++S.reads;
-            if (!R.apparent_owner(k0, s, &added)) {
-                S.cand = k0;  // the unreduced pivot is free of apparent owners
-                continue;
-            }
-            start_column(R, S, L);
-            walk(R, S, nullptr);
+    auto phase_a_column = [&](int64_t j) {
+        const Leftover &L = left[j];
+        ColumnState &S = col[j];
+        if (L.pivot == NO_PIVOT) {
+            S.cand = NONE;
+            return;
         }
+        const u128 k0 = age_key(L.pdiam, L.pivot);
+        int s[RPP_MAX_DIM + 1], added;
+        ++S.reads;
+        if (!R.apparent_owner(k0, s, &added)) {
+            S.cand = k0;  // the unreduced pivot is free of apparent owners
+            return;
+        }
+        start_column(R, S, L);
+        walk(R, S, nullptr);
     };
-    int nt = std::max(1, threads);
-    if (nleft < 8) nt = 1;
-    if (nt == 1) {
-        phase_a();
+    if (threads <= 1 || nleft < 16) {
+        for (int64_t j = 0; j < nleft; ++j) phase_a_column(j);
     } else {
-        std::vector<std::thread> pool;
-        for (int i = 0; i < nt; ++i) pool.emplace_back(phase_a);
-        for (auto &th : pool) th.join();
+        pool(threads).parallel_for(nleft, phase_a_column);
     }
 
     // Phase B: finalise in column order

@@ -72,25 +72,56 @@ __global__ void __launch_bounds__(SORT_THREADS) k_count(const uint32_t *__restri
     counts[(uint64_t)blockIdx.x * RADIX + threadIdx.x] = sh[threadIdx.x];
 }
 
-// One block: thread d owns digit d. Offsets of (tile, d) = start of digit d
-// among all keys + keys with digit d in earlier tiles.
-__global__ void __launch_bounds__(RADIX) k_scan(uint32_t *__restrict__ counts, uint64_t ntiles,
-                                                const uint32_t *__restrict__ digit_total) {
+// One block of SCAN_PARTS x 256 threads: thread (part, d) owns digit d over a
+// contiguous range of tiles. Offsets of (tile, d) = start of digit d among all
+// keys + keys with digit d in earlier tiles.
+constexpr int SCAN_PARTS = 4;
+
+__global__ void __launch_bounds__(RADIX *SCAN_PARTS) k_scan(uint32_t *__restrict__ counts,
+                                                            uint64_t ntiles,
+                                                            const uint32_t *__restrict__ digit_total) {
     __shared__ uint32_t warp_sums[RADIX / 32];
-    const int d = threadIdx.x, lane = d & 31, w = d >> 5;
-    // exclusive scan of the digit totals across the block
-    uint32_t x = digit_total[d], incl = x;
-    for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(FULL_MASK, incl, o);
-        if (lane >= o) incl += y;
+    __shared__ uint32_t base[RADIX];
+    __shared__ uint32_t part_sum[SCAN_PARTS][RADIX];
+    const int d = threadIdx.x & (RADIX - 1), part = threadIdx.x / RADIX;
+    const int lane = d & 31, w = d >> 5;
+    const uint64_t per = (ntiles + SCAN_PARTS - 1) / SCAN_PARTS;
+    const uint64_t t0 = part * per, t1 = t0 + per < ntiles ? t0 + per : ntiles;
+    // 1. keys with digit d in this part's tiles
+    uint32_t sum = 0;
+    uint64_t t = t0;
+    for (; t + 8 <= t1; t += 8) {
+        uint32_t c[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) c[k] = counts[(t + k) * RADIX + d];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) sum += c[k];
     }
-    if (lane == 31) warp_sums[w] = incl;
+    for (; t < t1; ++t) sum += counts[t * RADIX + d];
+    part_sum[part][d] = sum;
+    // 2. exclusive scan of the digit totals across digits (first 256 threads)
+    uint32_t x = 0, incl = 0;
+    if (part == 0) {
+        x = digit_total[d];
+        incl = x;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(FULL_MASK, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) warp_sums[w] = incl;
+    }
     __syncthreads();
-    uint32_t before = 0;
-    for (int i = 0; i < w; ++i) before += warp_sums[i];
-    uint32_t run = before + incl - x;
-    uint64_t t = 0;
-    for (; t + 8 <= ntiles; t += 8) {
+    if (part == 0) {
+        uint32_t before = 0;
+        for (int i = 0; i < w; ++i) before += warp_sums[i];
+        base[d] = before + incl - x;
+    }
+    __syncthreads();
+    // 3. running offsets over this part's tiles
+    uint32_t run = base[d];
+    for (int q = 0; q < part; ++q) run += part_sum[q][d];
+    t = t0;
+    for (; t + 8 <= t1; t += 8) {
         uint32_t c[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) c[k] = counts[(t + k) * RADIX + d];
@@ -100,7 +131,7 @@ __global__ void __launch_bounds__(RADIX) k_scan(uint32_t *__restrict__ counts, u
             run += c[k];
         }
     }
-    for (; t < ntiles; ++t) {
+    for (; t < t1; ++t) {
         uint32_t c = counts[t * RADIX + d];
         counts[t * RADIX + d] = run;
         run += c;
@@ -189,7 +220,7 @@ void radix_sort(uint32_t *hi, uint64_t *lo, uint64_t *val, uint32_t *tmp_hi, uin
         ++g_launches;
         k_count<<<(unsigned)ntiles, SORT_THREADS, 0, s>>>(hi_a, lo_a, n, sel, tile_counts);
         ++g_launches;
-        k_scan<<<1, RADIX, 0, s>>>(tile_counts, ntiles, digit_hist + sel * RADIX);
+        k_scan<<<1, RADIX * SCAN_PARTS, 0, s>>>(tile_counts, ntiles, digit_hist + sel * RADIX);
         ++g_launches;
         k_scatter<<<(unsigned)ntiles, SORT_THREADS, 0, s>>>(
             hi_a, lo_a, val_a, hi_a ? hi_b : nullptr, lo_b, val_a ? val_b : nullptr, n, sel,
@@ -237,7 +268,7 @@ void radix_sort_noalloc(uint32_t *hi, uint64_t *lo, uint32_t *tmp_hi, uint64_t *
         ++g_launches;
         k_count<<<(unsigned)ntiles, SORT_THREADS, 0, s>>>(hi_a, lo_a, n, sel, tile_counts);
         ++g_launches;
-        k_scan<<<1, RADIX, 0, s>>>(tile_counts, ntiles, digit_hist + sel * RADIX);
+        k_scan<<<1, RADIX * SCAN_PARTS, 0, s>>>(tile_counts, ntiles, digit_hist + sel * RADIX);
         ++g_launches;
         k_scatter<<<(unsigned)ntiles, SORT_THREADS, 0, s>>>(hi_a, lo_a, nullptr, hi_b, lo_b,
                                                             nullptr, n, sel, tile_counts);

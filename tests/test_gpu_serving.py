@@ -1,0 +1,103 @@
+"""Batched and served barcodes: every result is the same alone and in the mix.
+
+Requests are clouds of uneven size (the serving workload's mixture of noisy
+circles, 2-spheres and blobs) with the threshold at the 0.6 nearest-rank
+quantile of their distances. Each batched or served result must equal the
+single-instance result bit for bit, and a sample equals the CPU oracle.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2003_07989_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rpp():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2003_07989_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def requests():
+    return I.serving_requests(40, seed=3, n_range=(32, 220))
+
+
+@pytest.fixture(scope="module")
+def alone(rpp, requests):
+    return [rpp.rpp_barcodes(r.points, max_dim=1, quantile=r.threshold_quantile)
+            for r in requests]
+
+
+def _same(a, b):
+    for q in range(len(a.intervals)):
+        if not (np.array_equal(a.intervals[q], b.intervals[q])
+                and np.array_equal(a.critical[q], b.critical[q])):
+            return False
+    return True
+
+
+def test_alone_matches_oracle(requests, alone):
+    for r, got in list(zip(requests, alone))[:10]:
+        D = O.distance_matrix(r.points)
+        t = O.distance_quantile(D, r.threshold_quantile)
+        ref = O.barcodes(D, 1, t, O.MODE_COHOM_CLEAR)
+        for q in (0, 1):
+            assert np.array_equal(got.intervals[q], ref.barcode(q)), (r.index, q)
+
+
+def test_batched_equals_alone(rpp, requests, alone):
+    got = rpp.rpp_barcodes_batched([r.points for r in requests], max_dim=1,
+                                   quantiles=[r.threshold_quantile for r in requests])
+    assert all(_same(a, b) for a, b in zip(got, alone))
+
+
+def test_batched_device_inputs(rpp, requests, alone):
+    import torch
+    clouds = [torch.from_numpy(r.points).cuda() for r in requests[:12]]
+    got = rpp.rpp_barcodes_batched(clouds, max_dim=1,
+                                   quantiles=[r.threshold_quantile for r in requests[:12]])
+    assert all(_same(a, b) for a, b in zip(got, alone[:12]))
+
+
+@pytest.mark.parametrize("slots,budget_mb", [(4, 0), (8, 64), (2, 24)])
+def test_served_equals_alone(rpp, requests, alone, slots, budget_mb):
+    srv = rpp.Server(max_slots=slots, device_bytes=budget_mb << 20)
+    try:
+        tickets = [srv.submit(r.points, 1, quantile=r.threshold_quantile) for r in requests]
+        for t, a in zip(tickets, alone):
+            assert _same(srv.poll(t), a)
+    finally:
+        srv.close()
+
+
+def test_server_rejects_a_request_that_can_never_fit(rpp):
+    from paper_2003_07989_gb300 import _native as N
+    srv = rpp.Server(max_slots=2, device_bytes=1 << 20)
+    try:
+        with pytest.raises(N.RppError) as e:
+            srv.submit(I.uniform_cube(400, 3, 1), 1)
+        assert e.value.status == N.RPP_E_BUSY
+        small = I.uniform_cube(20, 3, 2)
+        got = srv.poll(srv.submit(small, 1))
+        ref = rpp.rpp_barcodes(small, max_dim=1)
+        assert _same(got, ref)
+    finally:
+        srv.close()
+
+
+def test_server_poll_unknown_ticket(rpp):
+    from paper_2003_07989_gb300 import _native as N
+    srv = rpp.Server(max_slots=1)
+    try:
+        with pytest.raises(N.RppError) as e:
+            srv.poll(12345, 0)
+        assert e.value.status == N.RPP_E_INVALID
+    finally:
+        srv.close()
