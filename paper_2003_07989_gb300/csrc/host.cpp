@@ -13,16 +13,21 @@
 //   Phase B (in column order): if that pivot belongs to an earlier leftover
 //     column, add that column's reduced column and continue the walk, now
 //     also looking up earlier leftovers; the first free pivot pairs with j.
-// Both phases add exactly the columns Alg. 1 adds, in the same order.
+// Both phases add exactly the columns Alg. 1 adds, in the same order. A
+// reduced column is kept as the set V of simplices whose coboundaries it sums.
 //
 // The working column is a heap of lazy cursors, one per added coboundary.
 // Each cursor lists its cofacets oldest first (smallest diameter, then largest
 // index) without materialising them: first the cofacets of equal diameter
 // (vertices w, largest first, with every distance to the simplex <= its
 // diameter), then the others by a (p+1)-way merge of the vertices' neighbour
-// lists sorted by distance. A vertex w is emitted at its last occurrence in
-// the merge, whose distance is the cofacet's diameter. Equal entries from two
-// cursors cancel over Z/2 when they meet at the top of the heap.
+// lists sorted by distance, where a vertex is emitted at its last occurrence,
+// whose distance is the cofacet's diameter.
+//   Dimensions p >= 2: equal entries from two cursors cancel over Z/2 when they
+//     meet at the top of the heap.
+//   Dimension 1 (edges): the parity of a triangle (how many of its edges lie
+//     in V) is read from V's adjacency bits when a cursor reaches it, so even
+//     entries are skipped on the spot and never enter the heap.
 #include "host.h"
 
 #include <algorithm>
@@ -227,6 +232,16 @@ inline float key_diam(u128 k) {
     std::memcpy(&d, &bits, sizeof(float));
     return d;
 }
+inline uint32_t float_bits(float f) {
+    uint32_t b;
+    std::memcpy(&b, &f, sizeof(float));
+    return b;
+}
+inline float bits_float(uint32_t b) {
+    float f;
+    std::memcpy(&f, &b, sizeof(float));
+    return f;
+}
 
 // Index of the cofacet v + {w} of the p-simplex v[0] > ... > v[p].
 inline uint64_t cofacet_idx(const Binomial &B, const int *v, int p, int w) {
@@ -284,6 +299,11 @@ struct Reducer {
         return false;
     }
 
+    int nbr_vertex(int v, int64_t pos) const { return (int)(uint32_t)I.nbr[(int64_t)v * n + pos]; }
+    float nbr_dist(int v, int64_t pos) const {
+        return bits_float((uint32_t)(I.nbr[(int64_t)v * n + pos] >> 32));
+    }
+
     // A cursor over the coboundary of the p-simplex v (diameter d). If
     // `first` >= 0 the caller knows the oldest cofacet adds vertex `first`.
     void init_cursor(Cursor &c, const int *v, float d, int first) const {
@@ -303,14 +323,9 @@ struct Reducer {
     void start_merge(Cursor &c) const {
         c.merging = true;
         for (int i = 0; i <= p; ++i) {  // first neighbour farther than d
-            const uint32_t *row = I.nbr + (int64_t)c.v[i] * n;
-            int64_t lo = 0, hi = n;
-            while (lo < hi) {
-                const int64_t mid = (lo + hi) >> 1;
-                if (I.dist(c.v[i], (int)row[mid]) <= c.d) lo = mid + 1;
-                else hi = mid;
-            }
-            c.pos[i] = (int32_t)lo;
+            const uint64_t *row = I.nbr + (int64_t)c.v[i] * n;
+            const uint64_t lim = ((uint64_t)float_bits(c.d) << 32) | 0xffffffffull;
+            c.pos[i] = (int32_t)(std::upper_bound(row, row + n, lim) - row);
         }
     }
 
@@ -338,7 +353,7 @@ struct Reducer {
             float bd = INFINITY;
             for (int i = 0; i <= p; ++i)
                 if (c.pos[i] < n) {
-                    const float x = I.dist(c.v[i], (int)I.nbr[(int64_t)c.v[i] * n + c.pos[i]]);
+                    const float x = nbr_dist(c.v[i], c.pos[i]);
                     if (x < bd) {
                         bd = x;
                         best = i;
@@ -353,13 +368,12 @@ struct Reducer {
             for (;;) {
                 int bi = -1;
                 for (int i = 0; i <= p; ++i)
-                    if (c.pos[i] < n &&
-                        I.dist(c.v[i], (int)I.nbr[(int64_t)c.v[i] * n + c.pos[i]]) == bd) {
+                    if (c.pos[i] < n && nbr_dist(c.v[i], c.pos[i]) == bd) {
                         bi = i;
                         break;
                     }
                 if (bi < 0) break;
-                const int w = (int)I.nbr[(int64_t)c.v[bi] * n + c.pos[bi]];
+                const int w = nbr_vertex(c.v[bi], c.pos[bi]);
                 ++c.pos[bi];
                 bool emit = true;
                 for (int k = 0; k <= p && emit; ++k) {
@@ -409,6 +423,23 @@ struct Reducer {
     }
 };
 
+// Where a leftover column's own cursor starts, from its oldest cofacet (found
+// on the GPU): a cofacet of equal diameter adds a known vertex (>= 0); a larger
+// diameter means there is no cofacet of equal diameter (EMPTY_LUNE).
+constexpr int EMPTY_LUNE = -2;
+
+int first_vertex(const Reducer &R, const Leftover &L, const int *v) {
+    if (L.pivot == NO_PIVOT) return -1;
+    if (L.pdiam != L.diam) return EMPTY_LUNE;
+    int u[RPP_MAX_DIM + 2];
+    decode_host(*R.I.B, L.pivot, R.p + 1, R.n, u);
+    for (int i = 0; i <= R.p + 1; ++i)
+        if (!R.in_simplex(v, u[i])) return u[i];
+    return -1;
+}
+
+// ---- dimensions p >= 2 -------------------------------------------------------
+
 struct ColumnState {
     std::vector<Cursor> cur;
     std::vector<std::pair<u128, int32_t>> heap;  // (head, cursor)
@@ -421,13 +452,22 @@ struct ColumnState {
 typedef std::greater<std::pair<u128, int32_t>> HeapCmp;
 
 // Add the coboundary of simplex v (index idx, diameter d) to the working
-// column; `first` as in Reducer::init_cursor.
+// column; `first` as in Reducer::init_cursor, or EMPTY_LUNE.
 void add_cursor(const Reducer &R, ColumnState &S, const int *v, uint64_t idx, float d,
                 int first) {
     S.cur.emplace_back();
-    R.init_cursor(S.cur.back(), v, d, first);
-    if (S.cur.back().head != NONE) {
-        S.heap.emplace_back(S.cur.back().head, (int32_t)(S.cur.size() - 1));
+    Cursor &c = S.cur.back();
+    if (first == EMPTY_LUNE) {
+        for (int i = 0; i <= R.p; ++i) c.v[i] = v[i];
+        c.d = d;
+        c.lune = -1;
+        c.merging = false;
+        R.advance(c);
+    } else {
+        R.init_cursor(c, v, d, first);
+    }
+    if (c.head != NONE) {
+        S.heap.emplace_back(c.head, (int32_t)(S.cur.size() - 1));
         std::push_heap(S.heap.begin(), S.heap.end(), HeapCmp());
     }
     S.V.emplace_back(idx, d);
@@ -467,10 +507,10 @@ u128 pivot(const Reducer &R, ColumnState &S) {
     return NONE;
 }
 
-// Owner of a pivot among finalized leftover columns: slot index, or -1.
+// Pivots owned by finalized leftover columns, and those columns as sums.
 struct Finalized {
     std::unordered_map<uint64_t, int64_t> owner;  // pivot index -> leftover slot
-    std::vector<std::vector<std::pair<uint64_t, float>>> V;  // reduced columns as sums
+    std::vector<std::vector<std::pair<uint64_t, float>>> V;
 };
 
 // Walk: add owners of the pivot until it is free. With fin == nullptr only
@@ -502,36 +542,11 @@ void walk(const Reducer &R, ColumnState &S, const Finalized *fin) {
     }
 }
 
-// The leftover column's own coboundary. Its oldest cofacet (found on the GPU)
-// tells where the cursor starts: a cofacet of equal diameter adds a known
-// vertex; a larger diameter means no cofacet of equal diameter exists.
 void start_column(const Reducer &R, ColumnState &S, const Leftover &L) {
     S.started = true;
-    int v[RPP_MAX_DIM + 1], u[RPP_MAX_DIM + 2];
+    int v[RPP_MAX_DIM + 1];
     decode_host(*R.I.B, L.sigma, R.p, R.n, v);
-    int first = -1;
-    const bool empty_lune = L.pivot != NO_PIVOT && L.pdiam != L.diam;
-    if (L.pivot != NO_PIVOT && !empty_lune) {
-        decode_host(*R.I.B, L.pivot, R.p + 1, R.n, u);
-        for (int i = 0; i <= R.p + 1; ++i)
-            if (!R.in_simplex(v, u[i])) first = u[i];
-    }
-    if (empty_lune) {  // no cofacet of equal diameter: go straight to the merge
-        S.cur.emplace_back();
-        Cursor &c = S.cur.back();
-        for (int i = 0; i <= R.p; ++i) c.v[i] = v[i];
-        c.d = L.diam;
-        c.lune = -1;
-        c.merging = false;
-        R.advance(c);
-        if (c.head != NONE) {
-            S.heap.emplace_back(c.head, (int32_t)(S.cur.size() - 1));
-            std::push_heap(S.heap.begin(), S.heap.end(), HeapCmp());
-        }
-        S.V.emplace_back(L.sigma, L.diam);
-        return;
-    }
-    add_cursor(R, S, v, L.sigma, L.diam, first);
+    add_cursor(R, S, v, L.sigma, L.diam, first_vertex(R, L, v));
 }
 
 // Z/2 sum of the simplices in V: sort and drop pairs.
@@ -550,14 +565,11 @@ void reduce_set(std::vector<std::pair<uint64_t, float>> &V) {
     V.resize(o);
 }
 
-}  // namespace
-
-void reduce_leftovers(const HostInstance &I, int p, const Leftover *left, int64_t nleft,
-                      int threads, std::vector<HostPair> &out, ReduceStats &stats) {
+void reduce_general(const HostInstance &I, int p, const Leftover *left, int64_t nleft,
+                    int threads, std::vector<HostPair> &out, ReduceStats &stats) {
     Reducer R(I, p);
     std::vector<ColumnState> col(nleft);
 
-    // Phase A: apparent walks, independent per column
     auto phase_a_column = [&](int64_t j) {
         const Leftover &L = left[j];
         ColumnState &S = col[j];
@@ -581,7 +593,6 @@ void reduce_leftovers(const HostInstance &I, int p, const Leftover *left, int64_
         pool(threads).parallel_for(nleft, phase_a_column);
     }
 
-    // Phase B: finalise in column order
     Finalized fin;
     fin.V.resize(nleft);
     fin.owner.reserve((size_t)nleft * 2);
@@ -617,6 +628,349 @@ void reduce_leftovers(const HostInstance &I, int p, const Leftover *left, int64_
         std::vector<Cursor>().swap(S.cur);
         std::vector<std::pair<u128, int32_t>>().swap(S.heap);
     }
+}
+
+// ---- dimension 1 -------------------------------------------------------------
+//
+// The working column of leftover j is the coboundary of a set V of edges; a
+// triangle is a nonzero entry iff an odd number of its edges lie in V. During
+// an apparent walk V only grows (an apparent edge is added once, when its own
+// pivot is reached, and never leaves), so a triangle's parity can be read from
+// V's adjacency bits whenever a cursor reaches it: the cursor skips it if even.
+// The heap then holds only entries that were nonzero when pushed; one whose
+// parity changed since is dropped when it surfaces. Every nonzero triangle
+// stays reachable: the last of its edges to enter V has a cursor that either
+// has not reached it yet or reached it after its parity last changed. Adding
+// another leftover's column (Phase B) can remove edges from V; the walk then
+// restarts from the new V.
+//
+// Merge part of an edge cursor (x, y) with diameter d: the neighbour rows of x
+// and y beyond distance d are merged; a per-cursor bit set marks vertices met
+// once (the rows' prefixes up to d are marked first), so a vertex is emitted
+// at its second occurrence, whose distance is the triangle's diameter.
+
+struct Cur1 {
+    int32_t x = 0, y = 0;
+    float d = 0.0f;
+    int32_t first = -1;          // known oldest cofacet vertex, emitted before anything else
+    int32_t lune = -1;           // lune vertices <= lune are still to come (-1: done)
+    int32_t pa = -1, pb = -1;    // merge positions (pa < 0: merge not started)
+    int64_t masks = -1;          // arena offset: lune bit set, then seen-once bit set
+    float tie_key = 0.0f;
+    std::vector<int32_t> ties;   // equal-diameter emissions, largest at the back
+    int32_t hw = -1;             // head vertex (-1: no more cofacets)
+    float hd = 0.0f;             // head diameter
+};
+
+struct Walk1 {
+    const HostInstance &I;
+    const Reducer &R;
+    int64_t n;
+    int words;
+    std::vector<int32_t> row_of;  // vertex -> row of V's adjacency bits (-1: none)
+    std::vector<uint64_t> rows;
+    std::vector<uint64_t> arena;  // cursors' bit sets
+    std::vector<Cur1> cur;
+    std::vector<std::pair<u128, int32_t>> heap;
+    std::vector<uint64_t> V;      // edges of V (indices)
+    int64_t additions = 0, reads = 0, entries = 0;
+
+    Walk1(const HostInstance &I_, const Reducer &R_)
+        : I(I_), R(R_), n(I_.n), words((int)((I_.n + 63) / 64)), row_of(I_.n, -1) {}
+
+    static uint64_t edge_index(int x, int y) {
+        return (uint64_t)x * (uint64_t)(x - 1) / 2 + (uint64_t)y;
+    }
+    bool vbit(int a, int b) const {
+        const int32_t r = row_of[a];
+        return r >= 0 && ((rows[(int64_t)r * words + (b >> 6)] >> (b & 63)) & 1ull);
+    }
+    void set_edge(int x, int y) {
+        for (int v : {x, y})
+            if (row_of[v] < 0) {
+                row_of[v] = (int32_t)(rows.size() / words);
+                rows.resize(rows.size() + words, 0);
+            }
+        rows[(int64_t)row_of[x] * words + (y >> 6)] |= 1ull << (y & 63);
+        rows[(int64_t)row_of[y] * words + (x >> 6)] |= 1ull << (x & 63);
+    }
+
+    // One pass over the two distance rows: with Bx = {w : D[x][w] <= d} and
+    // By likewise, the lune (cofacets of diameter d) is Bx & By without x and
+    // y, and the vertices met once in the rows' prefixes up to d are Bx ^ By.
+    void build_masks(Cur1 &c) {
+        c.masks = (int64_t)arena.size();
+        arena.resize(arena.size() + 2 * (size_t)words, 0);
+        uint64_t *lune = arena.data() + c.masks, *seen = lune + words;
+        const float *Dx = I.D + (int64_t)c.x * I.ld, *Dy = I.D + (int64_t)c.y * I.ld;
+        const float d = c.d;
+        for (int k = 0; k < words; ++k) {
+            const int base = k * 64, m = (int)std::min<int64_t>(64, n - base);
+            uint64_t bx = 0, by = 0;
+            for (int j = 0; j < m; ++j) {
+                bx |= (uint64_t)(Dx[base + j] <= d) << j;
+                by |= (uint64_t)(Dy[base + j] <= d) << j;
+            }
+            lune[k] = bx & by;
+            seen[k] = bx ^ by;
+        }
+        lune[c.x >> 6] &= ~(1ull << (c.x & 63));
+        lune[c.y >> 6] &= ~(1ull << (c.y & 63));
+    }
+
+    void start_merge(Cur1 &c) {
+        const uint64_t *rx = I.nbr + (int64_t)c.x * n, *ry = I.nbr + (int64_t)c.y * n;
+        const uint64_t lim = ((uint64_t)float_bits(c.d) << 32) | 0xffffffffull;
+        c.pa = (int32_t)(std::upper_bound(rx, rx + n, lim) - rx);
+        c.pb = (int32_t)(std::upper_bound(ry, ry + n, lim) - ry);
+        if (c.masks < 0) build_masks(c);
+    }
+
+    // Next cofacet of the cursor in age order, whatever its parity.
+    bool raw_next(Cur1 &c) {
+        ++entries;
+        if (c.first >= 0) {  // the oldest cofacet, known in advance
+            c.hw = c.first;
+            c.hd = c.d;
+            c.lune = c.first - 1;
+            c.first = -1;
+            return true;
+        }
+        if (c.lune >= 0) {  // diameter d, largest vertex first
+            if (c.masks < 0) build_masks(c);
+            const uint64_t *lune = arena.data() + c.masks;
+            int k = c.lune >> 6;
+            uint64_t m = lune[k] & (c.lune % 64 == 63 ? ~0ull : ((2ull << (c.lune & 63)) - 1));
+            while (!m && k > 0) m = lune[--k];
+            if (m) {
+                const int w = k * 64 + 63 - __builtin_clzll(m);
+                c.hw = w;
+                c.hd = c.d;
+                c.lune = w - 1;
+                return true;
+            }
+            c.lune = -1;
+        }
+        if (!c.ties.empty()) {
+            c.hw = c.ties.back();
+            c.ties.pop_back();
+            c.hd = c.tie_key;
+            return true;
+        }
+        if (c.pa < 0) start_merge(c);
+        const uint64_t *rx = I.nbr + (int64_t)c.x * n, *ry = I.nbr + (int64_t)c.y * n;
+        uint64_t *sb = arena.data() + c.masks + words;
+        for (;;) {
+            const uint32_t da = c.pa < n ? (uint32_t)(rx[c.pa] >> 32) : 0xffffffffu;
+            const uint32_t db = c.pb < n ? (uint32_t)(ry[c.pb] >> 32) : 0xffffffffu;
+            if (c.pa >= n && c.pb >= n) break;
+            const uint32_t bd = std::min(da, db);
+            if (bits_float(bd) > I.t) break;
+            for (int side = 0; side < 2; ++side) {  // every occurrence at distance bd
+                const uint64_t *row = side ? ry : rx;
+                int32_t &pos = side ? c.pb : c.pa;
+                while (pos < n && (uint32_t)(row[pos] >> 32) == bd) {
+                    const uint32_t w = (uint32_t)row[pos++];
+                    uint64_t &word = sb[w >> 6];
+                    word ^= 1ull << (w & 63);
+                    if (!((word >> (w & 63)) & 1ull)) c.ties.push_back((int32_t)w);  // second time
+                }
+            }
+            if (!c.ties.empty()) {
+                std::sort(c.ties.begin(), c.ties.end());
+                c.tie_key = bits_float(bd);
+                c.hw = c.ties.back();
+                c.ties.pop_back();
+                c.hd = c.tie_key;
+                return true;
+            }
+        }
+        c.hw = -1;
+        return false;
+    }
+
+    bool odd(const Cur1 &c) const { return vbit(c.x, c.hw) == vbit(c.y, c.hw); }
+
+    // Next cofacet with odd parity (hw = -1 if none).
+    void advance(Cur1 &c) {
+        while (raw_next(c))
+            if (odd(c)) return;
+    }
+
+    u128 head_key(const Cur1 &c) const {
+        int v[3] = {c.x, c.y, c.hw};
+        std::sort(v, v + 3, std::greater<int>());
+        return age_key(c.hd, index_host(*I.B, v, 2));
+    }
+
+    void push(int32_t ci) {
+        heap.emplace_back(head_key(cur[ci]), ci);
+        std::push_heap(heap.begin(), heap.end(), HeapCmp());
+    }
+
+    // Cursor of edge (x, y) (x > y); `first` as in Reducer::init_cursor, or
+    // EMPTY_LUNE. The edge's bits must already be set.
+    void add_cursor(int x, int y, float d, int first) {
+        cur.emplace_back();
+        Cur1 &c = cur.back();
+        c.x = x;
+        c.y = y;
+        c.d = d;
+        c.first = first >= 0 ? first : -1;
+        c.lune = first >= 0 ? first - 1 : (first == EMPTY_LUNE ? -1 : (int32_t)n - 1);
+        advance(c);
+        if (c.hw >= 0) push((int32_t)cur.size() - 1);
+    }
+
+    void add_edge(int x, int y, float d, int first) {
+        set_edge(x, y);
+        V.push_back(edge_index(x, y));
+        add_cursor(x, y, d, first);
+    }
+
+    // Restart the walk from the edge set newV (sorted, no repeats).
+    void rebuild(std::vector<uint64_t> newV) {
+        std::fill(row_of.begin(), row_of.end(), -1);
+        rows.clear();
+        arena.clear();
+        cur.clear();
+        heap.clear();
+        V.swap(newV);
+        int v[2];
+        for (uint64_t e : V) {
+            decode_host(*I.B, e, 1, n, v);
+            set_edge(v[0], v[1]);
+        }
+        for (uint64_t e : V) {
+            decode_host(*I.B, e, 1, n, v);
+            add_cursor(v[0], v[1], I.dist(v[0], v[1]), -1);
+        }
+    }
+
+    u128 pivot() {
+        while (!heap.empty()) {
+            const std::pair<u128, int32_t> top = heap.front();
+            Cur1 &c = cur[top.second];
+            if (odd(c)) return top.first;  // still nonzero
+            std::pop_heap(heap.begin(), heap.end(), HeapCmp());
+            heap.pop_back();
+            advance(c);
+            if (c.hw >= 0) push(top.second);
+        }
+        return NONE;
+    }
+
+    // Add owners of the pivot until it is free (fin == nullptr: apparent only).
+    u128 walk(const std::unordered_map<uint64_t, int64_t> *fin,
+              const std::vector<std::vector<uint64_t>> *finV) {
+        for (;;) {
+            const u128 k = pivot();
+            if (k == NONE) return NONE;
+            ++reads;
+            if (fin) {
+                auto it = fin->find(key_index(k));
+                if (it != fin->end()) {
+                    ++additions;
+                    std::vector<uint64_t> a = V, b = (*finV)[it->second], sum;
+                    std::sort(a.begin(), a.end());
+                    std::set_symmetric_difference(a.begin(), a.end(), b.begin(), b.end(),
+                                                  std::back_inserter(sum));
+                    rebuild(std::move(sum));
+                    continue;
+                }
+            }
+            int s[3], added;
+            if (R.apparent_owner(k, s, &added)) {
+                ++additions;  // its oldest cofacet is the pivot, which adds `added`
+                add_edge(s[0], s[1], key_diam(k), added);
+                continue;
+            }
+            return k;
+        }
+    }
+
+    std::vector<uint64_t> edges() const {
+        std::vector<uint64_t> out = V;
+        std::sort(out.begin(), out.end());
+        return out;
+    }
+};
+
+void reduce_p1(const HostInstance &I, const Leftover *left, int64_t nleft, int threads,
+               std::vector<HostPair> &out, ReduceStats &stats) {
+    Reducer R(I, 1);
+    std::vector<u128> cand(nleft, NONE);
+    std::vector<std::vector<uint64_t>> V(nleft);  // reduced columns as edge sets
+    std::vector<char> walked(nleft, 0);
+    std::vector<int64_t> adds(nleft, 0), reads(nleft, 0), entries(nleft, 0);
+
+    auto phase_a = [&](int64_t j) {
+        const Leftover &L = left[j];
+        V[j].push_back(L.sigma);
+        if (L.pivot == NO_PIVOT) return;
+        const u128 k0 = age_key(L.pdiam, L.pivot);
+        int s[3], added;
+        ++reads[j];
+        if (!R.apparent_owner(k0, s, &added)) {
+            cand[j] = k0;  // the unreduced pivot is free of apparent owners
+            return;
+        }
+        Walk1 W(I, R);
+        int v[2];
+        decode_host(*I.B, L.sigma, 1, I.n, v);
+        W.add_edge(v[0], v[1], L.diam, first_vertex(R, L, v));
+        cand[j] = W.walk(nullptr, nullptr);
+        V[j] = W.edges();
+        walked[j] = 1;
+        adds[j] += W.additions;
+        reads[j] += W.reads;
+        entries[j] += W.entries;
+    };
+    if (threads <= 1 || nleft < 16) {
+        for (int64_t j = 0; j < nleft; ++j) phase_a(j);
+    } else {
+        pool(threads).parallel_for(nleft, phase_a);
+    }
+
+    std::unordered_map<uint64_t, int64_t> owner;
+    owner.reserve((size_t)nleft * 2);
+    for (int64_t j = 0; j < nleft; ++j) {
+        const Leftover &L = left[j];
+        if (cand[j] != NONE && owner.count(key_index(cand[j]))) {
+            Walk1 W(I, R);  // resume from the reduced column so far
+            W.rebuild(V[j]);
+            cand[j] = W.walk(&owner, &V);
+            V[j] = W.edges();
+            adds[j] += W.additions;
+            reads[j] += W.reads;
+            entries[j] += W.entries;
+            walked[j] = 1;
+        }
+        HostPair P;
+        P.sigma = L.sigma;
+        P.birth = L.diam;
+        if (cand[j] == NONE) {
+            P.tau = NO_PIVOT;
+            P.death = INFINITY;
+        } else {
+            P.tau = key_index(cand[j]);
+            P.death = key_diam(cand[j]);
+            owner[P.tau] = j;
+            if (!walked[j]) ++stats.free_pivot;
+        }
+        out.push_back(P);
+        stats.additions += adds[j];
+        stats.reads += reads[j];
+        stats.entries += entries[j];
+    }
+}
+
+}  // namespace
+
+void reduce_leftovers(const HostInstance &I, int p, const Leftover *left, int64_t nleft,
+                      int threads, std::vector<HostPair> &out, ReduceStats &stats) {
+    if (p == 1) reduce_p1(I, left, nleft, threads, out, stats);
+    else reduce_general(I, p, left, nleft, threads, out, stats);
 }
 
 }  // namespace rpp

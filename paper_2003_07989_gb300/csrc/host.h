@@ -18,7 +18,7 @@ struct HostInstance {
     const float *D = nullptr;     // host copy, row stride ld
     int64_t ld = 0;
     const Binomial *B = nullptr;
-    const uint32_t *nbr = nullptr;  // n x n neighbour lists sorted by (distance, index)
+    const uint64_t *nbr = nullptr;  // n x n neighbour lists: (bits(distance) << 32) | vertex, sorted
     const uint64_t *app_tau = nullptr;  // apparent pivots (tau) of the current dimension, sorted
     uint64_t napp = 0;
     float t = 0.0f;                 // threshold in use

@@ -111,9 +111,9 @@ void launch_lower_bound_u32(const uint32_t *a, uint64_t n, uint32_t key, unsigne
                             cudaStream_t s);
 
 // Per-vertex neighbour lists: row v of out (n x n) lists all vertices in
-// increasing (D[v][w], w) order. Returns false if n is too large for the
+// increasing (D[v][w], w) order, packed as (bits(D[v][w]) << 32) | w. Returns false if n is too large for the
 // shared-memory sort (the caller then sorts on the host).
-bool launch_sort_rows(const float *D, int64_t ld, int64_t n, uint32_t *out, cudaStream_t s);
+bool launch_sort_rows(const float *D, int64_t ld, int64_t n, uint64_t *out, cudaStream_t s);
 
 // Set bit `idx[i]` of a bitmap for every i.
 void launch_bitmap_set(const uint64_t *idx, uint64_t count, uint32_t *bitmap, cudaStream_t s);

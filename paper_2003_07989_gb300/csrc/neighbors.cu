@@ -2,7 +2,7 @@
 // reduction's lazy coboundary enumeration.
 //
 // Row v of the output lists every vertex w (v itself included) in increasing
-// (D[v][w], w) order. One block sorts one row: the keys (distance bits << 32 |
+// (D[v][w], w) order, each as the key (bits(D[v][w]) << 32) | w. One block sorts one row: the keys (distance bits << 32 |
 // w) are bitonic-sorted in shared memory (distances are non-negative, so
 // their bit patterns order like the values).
 #include "internal.h"
@@ -13,7 +13,7 @@ namespace {
 
 __global__ void __launch_bounds__(512) k_sort_rows(const float *__restrict__ D, int64_t ld,
                                                    int64_t n, int pow2,
-                                                   uint32_t *__restrict__ out) {
+                                                   uint64_t *__restrict__ out) {
     extern __shared__ unsigned long long keys[];
     const int64_t row = blockIdx.x;
     for (int i = threadIdx.x; i < pow2; i += blockDim.x)
@@ -36,12 +36,12 @@ __global__ void __launch_bounds__(512) k_sort_rows(const float *__restrict__ D, 
             __syncthreads();
         }
     }
-    for (int i = threadIdx.x; i < n; i += blockDim.x) out[row * n + i] = (uint32_t)keys[i];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) out[row * n + i] = keys[i];
 }
 
 }  // namespace
 
-bool launch_sort_rows(const float *D, int64_t ld, int64_t n, uint32_t *out, cudaStream_t s) {
+bool launch_sort_rows(const float *D, int64_t ld, int64_t n, uint64_t *out, cudaStream_t s) {
     int pow2 = 1;
     while (pow2 < n) pow2 <<= 1;
     const size_t smem = (size_t)pow2 * 8;

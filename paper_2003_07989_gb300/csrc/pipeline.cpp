@@ -134,16 +134,18 @@ struct StageTimer {
 enum { ST_DIST = 0, ST_RADIUS, ST_BUILD, ST_SORT, ST_APPARENT, ST_PARTITION, ST_PAIRSORT, ST_OTHER };
 
 // Neighbour lists on the host, for matrices too large for the GPU row sort.
-void sort_rows_host(const float *D, int64_t ld, int64_t n, uint32_t *out, int threads) {
+void sort_rows_host(const float *D, int64_t ld, int64_t n, uint64_t *out, int threads) {
     std::atomic<int64_t> next(0);
     auto work = [&]() {
         for (int64_t r; (r = next.fetch_add(1)) < n;) {
-            uint32_t *row = out + r * n;
-            for (int64_t i = 0; i < n; ++i) row[i] = (uint32_t)i;
+            uint64_t *row = out + r * n;
             const float *d = D + r * ld;
-            std::sort(row, row + n, [d](uint32_t a, uint32_t b) {
-                return d[a] < d[b] || (d[a] == d[b] && a < b);
-            });
+            for (int64_t i = 0; i < n; ++i) {
+                uint32_t bits;
+                std::memcpy(&bits, d + i, 4);
+                row[i] = ((uint64_t)bits << 32) | (uint64_t)i;
+            }
+            std::sort(row, row + n);
         }
     };
     std::vector<std::thread> pool;
@@ -276,7 +278,7 @@ size_t instance_device_bytes(const Instance &in) {
     const size_t per = 4 + 8 + 4 + 8 + 8 + 1 + 8 + 4 + 8 + 8 + sizeof(Leftover);
     total += slack(maxcand * per) + slack(radix_tile_counts_size(maxcand) * 4) + slack(12 * 256 * 4);
     total += slack((size_t)n * 4) + slack(maxcand / 8 + 8) + slack(maxcand * 8);
-    total += slack((size_t)n * n * 4);  // neighbour lists
+    total += slack((size_t)n * n * 8);  // neighbour lists
     return total + 64 * 256;  // per-buffer rounding
 }
 
@@ -683,14 +685,14 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
             I.app_tau = htau;
             I.napp = napp;
             if (!I.nbr) {  // neighbour lists for the lazy coboundaries, once per instance
-                uint32_t *dn, *hn;
-                RPP_TRY(ws.dev(ws.nbr, (size_t)n * n * 4, (void **)&dn));
-                RPP_TRY(ws.host(ws.h_nbr, (size_t)n * n * 4, (void **)&hn));
+                uint64_t *dn, *hn;
+                RPP_TRY(ws.dev(ws.nbr, (size_t)n * n * 8, (void **)&dn));
+                RPP_TRY(ws.host(ws.h_nbr, (size_t)n * n * 8, (void **)&hn));
                 T.begin(ST_OTHER);
                 const bool gpu_sorted = launch_sort_rows(D, ld, n, dn, s);
                 T.end();
                 if (gpu_sorted)
-                    RPP_CK(cudaMemcpyAsync(hn, dn, (size_t)n * n * 4, cudaMemcpyDeviceToHost, s));
+                    RPP_CK(cudaMemcpyAsync(hn, dn, (size_t)n * n * 8, cudaMemcpyDeviceToHost, s));
                 RPP_CK(cudaMemcpyAsync(hleft, left, nleft * sizeof(Leftover),
                                        cudaMemcpyDeviceToHost, s));
                 double a = now_ms();
