@@ -40,6 +40,7 @@
 #include <memory>
 #include <mutex>
 #include <thread>
+#include <type_traits>
 
 namespace rpp {
 
@@ -636,86 +637,188 @@ void reduce_general(const HostInstance &I, int p, const Leftover *left, int64_t 
 // triangle is a nonzero entry iff an odd number of its edges lie in V. During
 // an apparent walk V only grows (an apparent edge is added once, when its own
 // pivot is reached, and never leaves), so a triangle's parity can be read from
-// V's adjacency bits whenever a cursor reaches it: the cursor skips it if even.
+// a bit set over edge indices whenever a cursor reaches it: the cursor skips it
+// if even.
 // The heap then holds only entries that were nonzero when pushed; one whose
 // parity changed since is dropped when it surfaces. Every nonzero triangle
 // stays reachable: the last of its edges to enter V has a cursor that either
 // has not reached it yet or reached it after its parity last changed. Adding
 // another leftover's column (Phase B) can remove edges from V; the walk then
-// restarts from the new V.
+// restarts from the new V, each cursor placed just past the cancelled pivot
+// (the sum is zero up to there).
 //
 // Merge part of an edge cursor (x, y) with diameter d: the neighbour rows of x
-// and y beyond distance d are merged; a per-cursor bit set marks vertices met
-// once (the rows' prefixes up to d are marked first), so a vertex is emitted
-// at its second occurrence, whose distance is the triangle's diameter.
+// and y beyond distance d are merged. A vertex w met in x's row at distance e
+// is a cofacet of diameter e exactly when D[y][w] < e (its other occurrence
+// came first); on a tie D[y][w] == e it is taken from y's row, which is merged
+// after x's at each distance. No per-cursor state beyond the two positions.
 
 struct Cur1 {
     int32_t x = 0, y = 0;
+    int32_t hw = -1;             // head vertex (-1: no more cofacets)
+    float hd = 0.0f;             // head diameter
     float d = 0.0f;
     int32_t first = -1;          // known oldest cofacet vertex, emitted before anything else
     int32_t lune = -1;           // lune vertices <= lune are still to come (-1: done)
     int32_t pa = -1, pb = -1;    // merge positions (pa < 0: merge not started)
-    int64_t masks = -1;          // arena offset: lune bit set, then seen-once bit set
+    // The next cofacets in age order, produced in a batch while the cursor's
+    // rows are in cache (their order does not depend on V; parity is read
+    // when each one surfaces).
+    static constexpr int NB = 4;
+    uint8_t bn = 0, bi = 0;      // batch size, next position
+    bool bend = false;           // no cofacets after the batch
+    int32_t bw[NB];
+    float bh[NB];
     float tie_key = 0.0f;
     std::vector<int32_t> ties;   // equal-diameter emissions, largest at the back
-    int32_t hw = -1;             // head vertex (-1: no more cofacets)
-    float hd = 0.0f;             // head diameter
 };
 
+// Heap keys of dimension 1, ordered like age_key. When every triangle index
+// fits in 32 bits the key packs (diameter bits, complemented index) into 64.
+struct Key64 {
+    typedef uint64_t T;
+    static constexpr T NIL = ~(T)0;  // diameter bits of a NaN: never a real key
+    static T make(float d, uint64_t idx) {
+        return ((T)float_bits(d) << 32) | (T)(uint32_t)~(uint32_t)idx;
+    }
+    static u128 wide(T k) {
+        return k == NIL ? NONE : age_key(bits_float((uint32_t)(k >> 32)), (uint32_t)~(uint32_t)k);
+    }
+};
+struct Key128 {
+    typedef u128 T;
+    static constexpr T NIL = ~(T)0;
+    static T make(float d, uint64_t idx) { return age_key(d, idx); }
+    static u128 wide(T k) { return k; }
+};
+
+// 4-ary min-heap of (key, cursor) with a replace-top step (one sift where a
+// pop followed by a push would take two). Four children share a cache line
+// and the tree is half as deep as a binary one.
+template <class T>
+struct MinHeap {
+    typedef std::pair<T, int32_t> E;
+    std::vector<E> h;
+    static bool less(const E &a, const E &b) {
+        return a.first < b.first || (a.first == b.first && a.second < b.second);
+    }
+    bool empty() const { return h.empty(); }
+    const E &top() const { return h[0]; }
+    void clear() { h.clear(); }
+    void push(E e) {
+        size_t i = h.size();
+        h.push_back(e);
+        while (i > 0) {
+            const size_t up = (i - 1) >> 2;
+            if (!less(e, h[up])) break;
+            h[i] = h[up];
+            i = up;
+        }
+        h[i] = e;
+    }
+    void sift_down(E e) {  // place e at the root
+        const size_t m = h.size();
+        size_t i = 0;
+        for (;;) {
+            const size_t c0 = 4 * i + 1;
+            if (c0 >= m) break;
+            size_t c = c0;
+            const size_t ce = std::min(c0 + 4, m);
+            for (size_t k = c0 + 1; k < ce; ++k)
+                if (less(h[k], h[c])) c = k;
+            if (!less(h[c], e)) break;
+            h[i] = h[c];
+            i = c;
+        }
+        h[i] = e;
+    }
+    void replace_top(E e) { sift_down(e); }
+    void pop() {
+        const E last = h.back();
+        h.pop_back();
+        if (!h.empty()) sift_down(last);
+    }
+};
+
+// Monotone priority queue of (64-bit key, cursor): every key pushed is >= the
+// last key taken from the top, which holds for the walk (a new cursor starts
+// at the current pivot, an advanced cursor moves past its previous entry).
+// Bucket i > 0 holds keys whose highest bit differing from `last` is bit
+// i - 1; bucket 0 holds keys equal to `last`. Pushes append; the top is
+// found by redistributing the lowest non-empty bucket, whose elements each
+// move to a strictly lower bucket.
+struct RadixHeap {
+    typedef std::pair<uint64_t, int32_t> E;
+    std::vector<E> b[65];
+    uint64_t last = 0;
+    size_t size = 0;
+    static int bucket(uint64_t k, uint64_t last) {
+        return k == last ? 0 : 64 - __builtin_clzll(k ^ last);
+    }
+    bool empty() const { return size == 0; }
+    void clear() {
+        for (auto &v : b) v.clear();
+        last = 0;
+        size = 0;
+    }
+    void push(E e) {
+        b[bucket(e.first, last)].push_back(e);
+        ++size;
+    }
+    const E &top() {  // requires !empty()
+        if (b[0].empty()) {
+            int i = 1;
+            while (b[i].empty()) ++i;
+            uint64_t m = b[i][0].first;
+            for (const E &e : b[i]) m = std::min(m, e.first);
+            last = m;
+            for (const E &e : b[i]) b[bucket(e.first, last)].push_back(e);
+            b[i].clear();
+        }
+        return b[0].back();
+    }
+    void pop() {  // removes the element top() returned
+        b[0].pop_back();
+        --size;
+    }
+    void replace_top(E e) {
+        pop();
+        push(e);
+    }
+};
+
+template <class K>
 struct Walk1 {
+    typedef typename K::T Key;
     const HostInstance &I;
     const Reducer &R;
     int64_t n;
-    int words;
-    std::vector<int32_t> row_of;  // vertex -> row of V's adjacency bits (-1: none)
-    std::vector<uint64_t> rows;
-    std::vector<uint64_t> arena;  // cursors' bit sets
+    uint64_t *ebits;              // membership in V, one bit per edge index (all clear when idle)
     std::vector<Cur1> cur;
-    std::vector<std::pair<u128, int32_t>> heap;
+    typename std::conditional<std::is_same<Key, uint64_t>::value, RadixHeap, MinHeap<Key>>::type
+        heap;
     std::vector<uint64_t> V;      // edges of V (indices)
     int64_t additions = 0, reads = 0, entries = 0;
 
-    Walk1(const HostInstance &I_, const Reducer &R_)
-        : I(I_), R(R_), n(I_.n), words((int)((I_.n + 63) / 64)), row_of(I_.n, -1) {}
+    // ebits: the calling thread's scratch of C(n, 2) bits, all clear; it is
+    // left clear again when the walk ends.
+    Walk1(const HostInstance &I_, const Reducer &R_, uint64_t *ebits_)
+        : I(I_), R(R_), n(I_.n), ebits(ebits_) {}
+    ~Walk1() { clear_bits(); }
 
     static uint64_t edge_index(int x, int y) {
         return (uint64_t)x * (uint64_t)(x - 1) / 2 + (uint64_t)y;
     }
     bool vbit(int a, int b) const {
-        const int32_t r = row_of[a];
-        return r >= 0 && ((rows[(int64_t)r * words + (b >> 6)] >> (b & 63)) & 1ull);
+        const uint64_t e = a > b ? edge_index(a, b) : edge_index(b, a);
+        return (ebits[e >> 6] >> (e & 63)) & 1ull;
     }
     void set_edge(int x, int y) {
-        for (int v : {x, y})
-            if (row_of[v] < 0) {
-                row_of[v] = (int32_t)(rows.size() / words);
-                rows.resize(rows.size() + words, 0);
-            }
-        rows[(int64_t)row_of[x] * words + (y >> 6)] |= 1ull << (y & 63);
-        rows[(int64_t)row_of[y] * words + (x >> 6)] |= 1ull << (x & 63);
+        const uint64_t e = edge_index(x, y);
+        ebits[e >> 6] |= 1ull << (e & 63);
     }
-
-    // One pass over the two distance rows: with Bx = {w : D[x][w] <= d} and
-    // By likewise, the lune (cofacets of diameter d) is Bx & By without x and
-    // y, and the vertices met once in the rows' prefixes up to d are Bx ^ By.
-    void build_masks(Cur1 &c) {
-        c.masks = (int64_t)arena.size();
-        arena.resize(arena.size() + 2 * (size_t)words, 0);
-        uint64_t *lune = arena.data() + c.masks, *seen = lune + words;
-        const float *Dx = I.D + (int64_t)c.x * I.ld, *Dy = I.D + (int64_t)c.y * I.ld;
-        const float d = c.d;
-        for (int k = 0; k < words; ++k) {
-            const int base = k * 64, m = (int)std::min<int64_t>(64, n - base);
-            uint64_t bx = 0, by = 0;
-            for (int j = 0; j < m; ++j) {
-                bx |= (uint64_t)(Dx[base + j] <= d) << j;
-                by |= (uint64_t)(Dy[base + j] <= d) << j;
-            }
-            lune[k] = bx & by;
-            seen[k] = bx ^ by;
-        }
-        lune[c.x >> 6] &= ~(1ull << (c.x & 63));
-        lune[c.y >> 6] &= ~(1ull << (c.y & 63));
+    void clear_bits() {
+        for (uint64_t e : V) ebits[e >> 6] = 0;
     }
 
     void start_merge(Cur1 &c) {
@@ -723,12 +826,35 @@ struct Walk1 {
         const uint64_t lim = ((uint64_t)float_bits(c.d) << 32) | 0xffffffffull;
         c.pa = (int32_t)(std::upper_bound(rx, rx + n, lim) - rx);
         c.pb = (int32_t)(std::upper_bound(ry, ry + n, lim) - ry);
-        if (c.masks < 0) build_masks(c);
     }
 
     // Next cofacet of the cursor in age order, whatever its parity.
     bool raw_next(Cur1 &c) {
         ++entries;
+        if (c.bi == c.bn) {
+            c.bi = c.bn = 0;
+            while (!c.bend && c.bn < Cur1::NB) {
+                if (!step(c)) {
+                    c.bend = true;
+                    break;
+                }
+                c.bw[c.bn] = c.hw;
+                c.bh[c.bn] = c.hd;
+                ++c.bn;
+            }
+            if (c.bn == 0) {
+                c.hw = -1;
+                return false;
+            }
+        }
+        c.hw = c.bw[c.bi];
+        c.hd = c.bh[c.bi];
+        ++c.bi;
+        return true;
+    }
+
+    // The cofacet after the current one, into (hw, hd); false if none.
+    bool step(Cur1 &c) {
         if (c.first >= 0) {  // the oldest cofacet, known in advance
             c.hw = c.first;
             c.hd = c.d;
@@ -736,20 +862,14 @@ struct Walk1 {
             c.first = -1;
             return true;
         }
-        if (c.lune >= 0) {  // diameter d, largest vertex first
-            if (c.masks < 0) build_masks(c);
-            const uint64_t *lune = arena.data() + c.masks;
-            int k = c.lune >> 6;
-            uint64_t m = lune[k] & (c.lune % 64 == 63 ? ~0ull : ((2ull << (c.lune & 63)) - 1));
-            while (!m && k > 0) m = lune[--k];
-            if (m) {
-                const int w = k * 64 + 63 - __builtin_clzll(m);
+        const float *Dx = I.D + (int64_t)c.x * I.ld, *Dy = I.D + (int64_t)c.y * I.ld;
+        while (c.lune >= 0) {  // diameter d, largest vertex first
+            const int w = c.lune--;
+            if (Dx[w] <= c.d && Dy[w] <= c.d && w != c.x && w != c.y) {
                 c.hw = w;
                 c.hd = c.d;
-                c.lune = w - 1;
                 return true;
             }
-            c.lune = -1;
         }
         if (!c.ties.empty()) {
             c.hw = c.ties.back();
@@ -759,26 +879,30 @@ struct Walk1 {
         }
         if (c.pa < 0) start_merge(c);
         const uint64_t *rx = I.nbr + (int64_t)c.x * n, *ry = I.nbr + (int64_t)c.y * n;
-        uint64_t *sb = arena.data() + c.masks + words;
         for (;;) {
             const uint32_t da = c.pa < n ? (uint32_t)(rx[c.pa] >> 32) : 0xffffffffu;
             const uint32_t db = c.pb < n ? (uint32_t)(ry[c.pb] >> 32) : 0xffffffffu;
             if (c.pa >= n && c.pb >= n) break;
             const uint32_t bd = std::min(da, db);
-            if (bits_float(bd) > I.t) break;
-            for (int side = 0; side < 2; ++side) {  // every occurrence at distance bd
-                const uint64_t *row = side ? ry : rx;
-                int32_t &pos = side ? c.pb : c.pa;
-                while (pos < n && (uint32_t)(row[pos] >> 32) == bd) {
+            const float e = bits_float(bd);
+            if (e > I.t) break;
+            if (da != db) {  // the common case: a lone occurrence at distance e
+                const bool sa = da < db;
+                const uint64_t *row = sa ? rx : ry;
+                int32_t &pos = sa ? c.pa : c.pb;
+                if (pos + 1 >= n || (uint32_t)(row[pos + 1] >> 32) != bd) {
+                    // the other row has nothing left at e, so D[other][w] != e
                     const uint32_t w = (uint32_t)row[pos++];
-                    uint64_t &word = sb[w >> 6];
-                    word ^= 1ull << (w & 63);
-                    if (!((word >> (w & 63)) & 1ull)) c.ties.push_back((int32_t)w);  // second time
+                    if ((sa ? Dy : Dx)[w] < e) {
+                        c.hw = (int32_t)w;
+                        c.hd = e;
+                        return true;
+                    }
+                    continue;
                 }
             }
+            merge_level(c, bd);
             if (!c.ties.empty()) {
-                std::sort(c.ties.begin(), c.ties.end());
-                c.tie_key = bits_float(bd);
                 c.hw = c.ties.back();
                 c.ties.pop_back();
                 c.hd = c.tie_key;
@@ -789,6 +913,63 @@ struct Walk1 {
         return false;
     }
 
+    // Consume every occurrence at distance bits bd in both rows; the cofacets
+    // of diameter bd become the cursor's ties (sorted, largest at the back).
+    void merge_level(Cur1 &c, uint32_t bd) {
+        const uint64_t *rx = I.nbr + (int64_t)c.x * n, *ry = I.nbr + (int64_t)c.y * n;
+        const float *Dx = I.D + (int64_t)c.x * I.ld, *Dy = I.D + (int64_t)c.y * I.ld;
+        const float e = bits_float(bd);
+        while (c.pa < n && (uint32_t)(rx[c.pa] >> 32) == bd) {
+            const uint32_t w = (uint32_t)rx[c.pa++];
+            if (Dy[w] < e) c.ties.push_back((int32_t)w);
+        }
+        while (c.pb < n && (uint32_t)(ry[c.pb] >> 32) == bd) {
+            const uint32_t w = (uint32_t)ry[c.pb++];
+            if (Dx[w] <= e) c.ties.push_back((int32_t)w);
+        }
+        std::sort(c.ties.begin(), c.ties.end());
+        c.tie_key = e;
+    }
+
+    // Colex comparison of the triangle {x, y, w} with the triangle kv[0] >
+    // kv[1] > kv[2]: true if {x, y, w} has the smaller index. For fixed x, y
+    // the sorted tuple never decreases as w grows (also at w = x or w = y), so
+    // the predicate holds on a prefix of w.
+    static bool tri_before(int x, int y, int w, const int *kv) {
+        int a = x, b = y, c = w;  // x > y
+        if (c > a) std::swap(a, c), std::swap(b, c);
+        else if (c > b) std::swap(b, c);
+        if (a != kv[0]) return a < kv[0];
+        if (b != kv[1]) return b < kv[1];
+        return c < kv[2];
+    }
+
+    // Position a fresh cursor so that its next cofacet is the first one younger
+    // than the triangle k = (dk, kv): a column whose entries up to k are known
+    // to be zero need not list them.
+    void seek(Cur1 &c, float dk, const int *kv) {
+        c.first = -1;
+        if (dk < c.d) return;  // every cofacet is younger than k
+        if (dk == c.d) {  // lune vertices w (largest first) with index below k's
+            int lo = -1, hi = (int)n;  // largest w with tri_before(w): in [lo, hi)
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (tri_before(c.x, c.y, mid, kv)) lo = mid;
+                else hi = mid;
+            }
+            c.lune = lo;
+            return;
+        }
+        c.lune = -1;  // the whole lune is older than k
+        const uint64_t *rx = I.nbr + (int64_t)c.x * n, *ry = I.nbr + (int64_t)c.y * n;
+        const uint32_t bd = float_bits(dk);
+        const uint64_t lim = (uint64_t)bd << 32;
+        c.pa = (int32_t)(std::lower_bound(rx, rx + n, lim) - rx);
+        c.pb = (int32_t)(std::lower_bound(ry, ry + n, lim) - ry);
+        merge_level(c, bd);  // cofacets of diameter dk: keep those younger than k
+        while (!c.ties.empty() && !tri_before(c.x, c.y, c.ties.back(), kv)) c.ties.pop_back();
+    }
+
     bool odd(const Cur1 &c) const { return vbit(c.x, c.hw) == vbit(c.y, c.hw); }
 
     // Next cofacet with odd parity (hw = -1 if none).
@@ -797,16 +978,14 @@ struct Walk1 {
             if (odd(c)) return;
     }
 
-    u128 head_key(const Cur1 &c) const {
-        int v[3] = {c.x, c.y, c.hw};
-        std::sort(v, v + 3, std::greater<int>());
-        return age_key(c.hd, index_host(*I.B, v, 2));
+    Key head_key(const Cur1 &c) const {
+        int a = c.x, b = c.y, w = c.hw;  // sort {x, y, w} decreasingly (x > y)
+        if (w > a) std::swap(a, w), std::swap(b, w);
+        else if (w > b) std::swap(b, w);
+        return K::make(c.hd, I.B->at(3, a) + I.B->at(2, b) + (uint64_t)w);
     }
 
-    void push(int32_t ci) {
-        heap.emplace_back(head_key(cur[ci]), ci);
-        std::push_heap(heap.begin(), heap.end(), HeapCmp());
-    }
+    void push(int32_t ci) { heap.push({head_key(cur[ci]), ci}); }
 
     // Cursor of edge (x, y) (x > y); `first` as in Reducer::init_cursor, or
     // EMPTY_LUNE. The edge's bits must already be set.
@@ -828,34 +1007,53 @@ struct Walk1 {
         add_cursor(x, y, d, first);
     }
 
-    // Restart the walk from the edge set newV (sorted, no repeats).
-    void rebuild(std::vector<uint64_t> newV) {
-        std::fill(row_of.begin(), row_of.end(), -1);
-        rows.clear();
-        arena.clear();
+    // Restart the walk from the edge set newV (sorted, no repeats), whose
+    // coboundary is known to vanish up to and including the entry k.
+    void rebuild(std::vector<uint64_t> newV, u128 k) {
+        clear_bits();
         cur.clear();
         heap.clear();
         V.swap(newV);
-        int v[2];
+        int v[2], kv[3];
+        decode_host(*I.B, key_index(k), 2, n, kv);
+        const float dk = key_diam(k);
         for (uint64_t e : V) {
             decode_host(*I.B, e, 1, n, v);
             set_edge(v[0], v[1]);
         }
         for (uint64_t e : V) {
             decode_host(*I.B, e, 1, n, v);
-            add_cursor(v[0], v[1], I.dist(v[0], v[1]), -1);
+            cur.emplace_back();
+            Cur1 &c = cur.back();
+            c.x = v[0];
+            c.y = v[1];
+            c.d = I.dist(v[0], v[1]);
+            c.lune = (int32_t)n - 1;
+            seek(c, dk, kv);
+            advance(c);
+            if (c.hw >= 0) push((int32_t)cur.size() - 1);
         }
+    }
+
+    // Add the reduced column (edge set b, sorted) of the leftover owning the
+    // pivot k of V: the pivot cancels and the walk restarts past it.
+    void add_leftover(const std::vector<uint64_t> &b, u128 k) {
+        ++additions;
+        std::vector<uint64_t> a = V, sum;
+        std::sort(a.begin(), a.end());
+        std::set_symmetric_difference(a.begin(), a.end(), b.begin(), b.end(),
+                                      std::back_inserter(sum));
+        rebuild(std::move(sum), k);
     }
 
     u128 pivot() {
         while (!heap.empty()) {
-            const std::pair<u128, int32_t> top = heap.front();
-            Cur1 &c = cur[top.second];
-            if (odd(c)) return top.first;  // still nonzero
-            std::pop_heap(heap.begin(), heap.end(), HeapCmp());
-            heap.pop_back();
+            const int32_t ci = heap.top().second;
+            Cur1 &c = cur[ci];
+            if (odd(c)) return K::wide(heap.top().first);  // still nonzero
             advance(c);
-            if (c.hw >= 0) push(top.second);
+            if (c.hw >= 0) heap.replace_top({head_key(c), ci});
+            else heap.pop();
         }
         return NONE;
     }
@@ -870,12 +1068,7 @@ struct Walk1 {
             if (fin) {
                 auto it = fin->find(key_index(k));
                 if (it != fin->end()) {
-                    ++additions;
-                    std::vector<uint64_t> a = V, b = (*finV)[it->second], sum;
-                    std::sort(a.begin(), a.end());
-                    std::set_symmetric_difference(a.begin(), a.end(), b.begin(), b.end(),
-                                                  std::back_inserter(sum));
-                    rebuild(std::move(sum));
+                    add_leftover((*finV)[it->second], k);
                     continue;
                 }
             }
@@ -896,6 +1089,15 @@ struct Walk1 {
     }
 };
 
+// A clear bit set of C(n, 2) bits owned by the calling thread.
+uint64_t *edge_scratch(int64_t n) {
+    thread_local std::vector<uint64_t> bits;
+    const size_t words = (size_t)((n * (n - 1) / 2 + 63) / 64);
+    if (bits.size() < words) bits.assign(words, 0);
+    return bits.data();
+}
+
+template <class K>
 void reduce_p1(const HostInstance &I, const Leftover *left, int64_t nleft, int threads,
                std::vector<HostPair> &out, ReduceStats &stats) {
     Reducer R(I, 1);
@@ -915,7 +1117,7 @@ void reduce_p1(const HostInstance &I, const Leftover *left, int64_t nleft, int t
             cand[j] = k0;  // the unreduced pivot is free of apparent owners
             return;
         }
-        Walk1 W(I, R);
+        Walk1<K> W(I, R, edge_scratch(I.n));
         int v[2];
         decode_host(*I.B, L.sigma, 1, I.n, v);
         W.add_edge(v[0], v[1], L.diam, first_vertex(R, L, v));
@@ -936,9 +1138,12 @@ void reduce_p1(const HostInstance &I, const Leftover *left, int64_t nleft, int t
     owner.reserve((size_t)nleft * 2);
     for (int64_t j = 0; j < nleft; ++j) {
         const Leftover &L = left[j];
-        if (cand[j] != NONE && owner.count(key_index(cand[j]))) {
-            Walk1 W(I, R);  // resume from the reduced column so far
-            W.rebuild(V[j]);
+        auto it = cand[j] != NONE ? owner.find(key_index(cand[j])) : owner.end();
+        if (it != owner.end()) {
+            Walk1<K> W(I, R, edge_scratch(I.n));  // resume from the reduced column so far, whose pivot is cand[j]
+            W.V = V[j];
+            ++W.reads;
+            W.add_leftover(V[it->second], cand[j]);
             cand[j] = W.walk(&owner, &V);
             V[j] = W.edges();
             adds[j] += W.additions;
@@ -969,7 +1174,10 @@ void reduce_p1(const HostInstance &I, const Leftover *left, int64_t nleft, int t
 
 void reduce_leftovers(const HostInstance &I, int p, const Leftover *left, int64_t nleft,
                       int threads, std::vector<HostPair> &out, ReduceStats &stats) {
-    if (p == 1) reduce_p1(I, left, nleft, threads, out, stats);
+    if (p == 1 && I.B->at(3, I.n) <= (1ull << 32))  // triangle indices fit in 32 bits
+        reduce_p1<Key64>(I, left, nleft, threads, out, stats);
+    else if (p == 1)
+        reduce_p1<Key128>(I, left, nleft, threads, out, stats);
     else reduce_general(I, p, left, nleft, threads, out, stats);
 }
 
