@@ -189,6 +189,15 @@ def serving_bench(rpp, count: int, slots: int):
     reqs = I.serving_requests(count, seed=0)
     for r in reqs[:8]:
         rpp.rpp_barcodes(r.points, max_dim=1, quantile=r.threshold_quantile)
+    # warm-up of the fused batch path: the autotuner picks each size bucket's
+    # launch shape on first use, outside every timed run below
+    clouds = [r.points for r in reqs]
+    qs = [r.threshold_quantile for r in reqs]
+    rpp.rpp_barcodes_batched(clouds, max_dim=1, quantiles=qs)
+    # batched: all requests in one call (fused launches per size bucket)
+    t0 = time.perf_counter()
+    rpp.rpp_barcodes_batched(clouds, max_dim=1, quantiles=qs)
+    batched_s = time.perf_counter() - t0
     # plain, saturation
     t0 = time.perf_counter()
     for r in reqs:
@@ -209,7 +218,7 @@ def serving_bench(rpp, count: int, slots: int):
         return lat
 
     def served(arr):
-        srv = rpp.Server(max_slots=slots)
+        srv = rpp.Server(max_slots=slots, max_batch=64)
         done = {}
         tickets = []
         lock = threading.Lock()
@@ -255,7 +264,9 @@ def serving_bench(rpp, count: int, slots: int):
         "plain": {"barcodes_per_s": plain_rps, "p50_ms": 1e3 * _pct(plain_lat, 0.5),
                   "p99_ms": 1e3 * _pct(plain_lat, 0.99)},
         "served": {"barcodes_per_s": count / sat_s, "p50_ms": 1e3 * _pct(srv_lat, 0.5),
-                   "p99_ms": 1e3 * _pct(srv_lat, 0.99)},
+                   "p99_ms": 1e3 * _pct(srv_lat, 0.99), "max_batch": 64},
+        "batched": {"barcodes_per_s": count / batched_s,
+                    "note": "one rpp_barcodes_batched call over every request (fused launches)"},
         "workload": "serving mix: n uniform in [32, 512], dim uniform in [2, 8], circle/2-sphere/"
                     "blob, threshold = 0.6 nearest-rank distance quantile, H0-H1, seed 0",
     }

@@ -156,18 +156,42 @@ const rpp_critical *rpp_result_critical(const rpp_result *res, int32_t p);
 rpp_status rpp_result_stats(const rpp_result *res, rpp_stats *out);
 void rpp_result_free(rpp_result *res);
 
-/* Many independent clouds in one call. Clouds are processed together: their
- * distance matrices, filtrations and apparent-pair tests run as shared
- * launches over all clouds, and the host reductions run on a thread pool.
- *   data[i]       points of cloud i (n[i] x dim[i]), device or host.
+/* Many independent clouds in one call (the batched form of the paper's
+ * computation; the paper itself runs one distance matrix at a time).
+ * Clouds of at most 1024 points with max_dim <= 1 run together in one fused
+ * launch per size bucket (64, 128, 256, 512, 1024 points): each block of the
+ * launch takes a whole cloud through its distance matrix, enclosing radius and
+ * threshold, H0 by a minimum spanning forest, and the apparent-pair test of its
+ * edges; the launch is a captured CUDA graph and its shape is chosen per
+ * bucket by the context's autotuner. Host reductions of the clouds with
+ * leftover columns run on the library's host threads. Other clouds (larger,
+ * max_dim >= 2, or a context recording columns or pairs) run one at a time.
+ * Results are identical to rpp_barcodes on each cloud alone.
+ *   data[i]       points of cloud i (n[i] x dim[i] float32, row-major), device
+ *                 or host memory, owned by the caller.
  *   thresholds    per cloud threshold (+INFINITY = full), or NULL for all full.
  *   quantiles     per cloud quantile in (0,1] overriding the threshold, or NULL.
- *   out[i]        result of cloud i.
- * On error no result is returned. */
+ *   stream        CUDA stream for every copy and launch (NULL: legacy stream).
+ *   out[i]        result of cloud i (free each with rpp_result_free).
+ * Errors: RPP_E_INVALID (a cloud's arguments, or non-finite coordinates),
+ * RPP_E_NOMEM, RPP_E_CUDA. On error no result is returned. */
 rpp_status rpp_barcodes_batched(rpp_context *ctx, int32_t batch, const float *const *data,
                                 const int64_t *n, const int32_t *dim, int32_t max_dim,
                                 const float *thresholds, const float *quantiles, void *stream,
                                 rpp_result **out);
+
+/* Batch behaviour of a context. fused = 0 runs every cloud of a batch through
+ * the one-at-a-time pipeline (for comparisons); autotune = 0 keeps the default
+ * launch shape (256 threads, 8 lanes per column) for buckets not yet tuned.
+ * Both default to 1. Errors: RPP_E_INVALID for a NULL context. */
+rpp_status rpp_context_set_batch(rpp_context *ctx, int32_t fused, int32_t autotune);
+
+/* The launch shape the autotuner chose for the bucket of clouds with up to
+ * nmax points (64, 128, 256, 512 or 1024): threads per block and lanes per
+ * column of the apparent-pair test; both 0 if the bucket has not run yet.
+ * Errors: RPP_E_INVALID for a NULL argument. */
+rpp_status rpp_context_batch_tuning(rpp_context *ctx, int32_t nmax, int32_t *threads,
+                                    int32_t *group);
 
 /* Backward of the interval endpoints to the point coordinates.
  * For every finite interval of dimension p >= 0 of result i, with birth edge
@@ -260,7 +284,8 @@ typedef struct {
     int32_t max_slots;          /* requests in flight on the device at once */
     size_t device_bytes;        /* device memory the admitted requests may hold */
     int32_t host_threads;       /* threads for the host reductions (0 = auto) */
-    int32_t max_batch;          /* most requests fused into one launch */
+    int32_t max_batch;          /* most requests one slot takes into one fused batch
+                                   (rpp_barcodes_batched); <= 1: one request per slot */
 } rpp_server_config;
 
 rpp_status rpp_server_create(rpp_context *ctx, const rpp_server_config *cfg, rpp_server **out);

@@ -38,6 +38,19 @@ class Context:
         if record:
             N.check(L.rpp_context_set_record(h, record), "rpp_context_set_record")
 
+    def set_batch(self, fused: bool = True, autotune: bool = True):
+        """rpp_context_set_batch: fused=False runs batched clouds one at a time."""
+        N.check(N.lib().rpp_context_set_batch(self.handle, int(fused), int(autotune)),
+                "rpp_context_set_batch")
+
+    def batch_tuning(self, nmax: int):
+        """(threads, lanes per column) the autotuner chose for a size bucket,
+        (0, 0) if it has not run."""
+        t, g = C.c_int32(), C.c_int32()
+        N.check(N.lib().rpp_context_batch_tuning(self.handle, nmax, C.byref(t), C.byref(g)),
+                "rpp_context_batch_tuning")
+        return t.value, g.value
+
     def close(self):
         if self.handle:
             N.lib().rpp_context_destroy(self.handle)
@@ -199,9 +212,10 @@ class Server:
     """Continuous-batching server (rpp_server_*): submit clouds as they arrive,
     poll for results."""
 
-    def __init__(self, max_slots: int = 8, device_bytes: int = 0, context: Context | None = None):
+    def __init__(self, max_slots: int = 8, device_bytes: int = 0, context: Context | None = None,
+                 max_batch: int = 64):
         self.ctx = context or default_context(0)
-        cfg = N.ServerConfig(max_slots, device_bytes, 0, 0)
+        cfg = N.ServerConfig(max_slots, device_bytes, 0, max_batch)
         h = C.c_void_p()
         N.check(N.lib().rpp_server_create(self.ctx.handle, C.byref(cfg), C.byref(h)),
                 "rpp_server_create")

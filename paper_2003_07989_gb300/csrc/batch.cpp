@@ -1,6 +1,22 @@
-// batch.cpp -- many independent clouds per call, and the size-bucket tuning
-// table used by the apparent-pair pass.
+// batch.cpp -- many independent clouds per call.
+//
+// Clouds of up to BATCH_NMAX points asking for H0 and H1 go through the fused
+// pass of batch.cu: they are grouped into size buckets (64, 128, 256, 512,
+// 1024 points) and each bucket runs in launches of up to `cap` clouds, each
+// launch a captured CUDA graph (control block upload, the fused kernel, and
+// the download of the per-cloud outputs and H0 edges) that is re-instantiated
+// only when a buffer moves. The launch shape of the fused kernel (threads per
+// block, lanes per column of the apparent test) is chosen per bucket by the
+// autotuner the first time the bucket runs in a context: every candidate runs
+// on that launch's clouds and the fastest is kept. Clouds with leftover
+// columns then get their distance rows and sorted neighbour lists (one more
+// launch), and their submatrix reductions run on the host threads, one cloud
+// per thread. Everything else (larger clouds, higher dimensions, recorded
+// intermediate arrays) takes the per-instance pipeline.
+#include <algorithm>
 #include <cmath>
+#include <cstring>
+#include <numeric>
 
 #include "pipeline.h"
 
@@ -12,6 +28,559 @@ rpp::Tuning rpp_context::tuning_for(int64_t n, int p) {
     t.group = n <= 256 ? 4 : 8;
     return t;
 }
+
+namespace rpp {
+
+namespace {
+
+const int BUCKETS[] = {64, 128, 256, 512, BATCH_NMAX};
+constexpr size_t D_SCRATCH_BYTES = 256ull << 20;  // distance matrices of one launch
+constexpr uint64_t LEFT_CAP = 1ull << 20;         // leftover columns of one launch
+
+int bucket_nmax(int64_t n) {
+    for (int b : BUCKETS)
+        if (n <= b) return b;
+    return -1;
+}
+
+int ld_of(int n) { return (n + 3) & ~3; }
+
+// Clouds per launch for a bucket: the distance scratch stays near 256 MB.
+int bucket_cap(int nmax) {
+    const size_t per = (size_t)nmax * ld_of(nmax) * 4;
+    return (int)std::max<size_t>(1, std::min<size_t>(4096, D_SCRATCH_BYTES / per));
+}
+
+int dimcap_of(int dim) {
+    int c = 2;
+    while (c < dim) c <<= 1;
+    return c;
+}
+
+// The device and host buffers of one fused launch of a bucket, sized for its
+// capacity so that the captured graph stays valid from launch to launch.
+struct Bufs {
+    float *pts;
+    BatchCloud *clouds;
+    int32_t *order;
+    BatchCtl *ctl;
+    float *D;
+    uint64_t *mst;
+    BatchOut *outs;
+    Leftover *left;
+    int32_t *lcloud;
+    float *h_pts;
+    BatchCloud *h_clouds;
+    int32_t *h_order;
+    BatchCtl *h_ctl;  // [0] uploaded, [1] downloaded
+    BatchOut *h_outs;
+    uint64_t *h_mst;
+    Leftover *h_left;
+    int32_t *h_lcloud;
+};
+
+uint64_t pow2_ge(uint64_t x) {
+    uint64_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+// Capacities of one fused launch, rounded up to powers of two so that launches
+// of similar batches reuse the same buffers and captured graphs.
+struct Caps {
+    uint64_t clouds = 0, pts = 0, D = 0, mst = 0, left = 0;
+};
+
+Caps caps_of(const std::vector<Instance> &ins, const std::vector<int> &idx) {
+    Caps c;
+    uint64_t pts = 0, D = 0, mst = 0, cols = 0;
+    for (int i : idx) {
+        const uint64_t n = (uint64_t)ins[i].n;
+        pts += n * (uint64_t)ins[i].dim;
+        D += n * (uint64_t)ld_of((int)n);
+        mst += n;
+        cols += n * (n - 1) / 2;
+    }
+    c.clouds = pow2_ge(std::max<size_t>(idx.size(), 16));
+    c.pts = pow2_ge(std::max<uint64_t>(pts, 1024));
+    c.D = pow2_ge(std::max<uint64_t>(D, 1024));
+    c.mst = pow2_ge(std::max<uint64_t>(mst, 1024));
+    // leftover columns are a small share of the columns (the apparent-pair
+    // rate); a launch that finds more runs the overflowing clouds alone
+    c.left = std::min<uint64_t>(LEFT_CAP, pow2_ge(std::max<uint64_t>(cols / 16, 4096)));
+    return c;
+}
+
+// Device bytes a fused launch over these clouds holds (buffers of caps_of,
+// the growth slack of Workspace::dev, and the rows of clouds with leftovers).
+size_t launch_device_bytes(const Caps &c, uint64_t rows) {
+    auto slack = [](size_t b) { return ((b + b / 4) + 255) & ~(size_t)255; };
+    return slack(c.pts * 4) + slack(c.clouds * (sizeof(BatchCloud) + 4 + sizeof(BatchOut) + 8)) +
+           slack(c.D * 4) + slack(c.mst * 8) + slack(c.left * (sizeof(Leftover) + 4)) +
+           slack(rows * 12) + 8 * 256;
+}
+
+Status get_bufs(Workspace &ws, const Caps &c, Bufs &b) {
+    void *p;
+    RPP_TRY(ws.dev(ws.b_pts, c.pts * 4, &p));
+    b.pts = (float *)p;
+    RPP_TRY(ws.dev(ws.b_clouds, c.clouds * sizeof(BatchCloud), &p));
+    b.clouds = (BatchCloud *)p;
+    RPP_TRY(ws.dev(ws.b_order, c.clouds * 4, &p));
+    b.order = (int32_t *)p;
+    RPP_TRY(ws.dev(ws.b_ctl, sizeof(BatchCtl), &p));
+    b.ctl = (BatchCtl *)p;
+    RPP_TRY(ws.dev(ws.b_D, c.D * 4, &p));
+    b.D = (float *)p;
+    RPP_TRY(ws.dev(ws.b_mst, c.mst * 8, &p));
+    b.mst = (uint64_t *)p;
+    RPP_TRY(ws.dev(ws.b_outs, c.clouds * sizeof(BatchOut), &p));
+    b.outs = (BatchOut *)p;
+    RPP_TRY(ws.dev(ws.b_left, c.left * sizeof(Leftover), &p));
+    b.left = (Leftover *)p;
+    RPP_TRY(ws.dev(ws.b_lcloud, c.left * 4, &p));
+    b.lcloud = (int32_t *)p;
+    RPP_TRY(ws.host(ws.hb_pts, c.pts * 4, &p));
+    b.h_pts = (float *)p;
+    RPP_TRY(ws.host(ws.hb_clouds, c.clouds * sizeof(BatchCloud), &p));
+    b.h_clouds = (BatchCloud *)p;
+    RPP_TRY(ws.host(ws.hb_order, c.clouds * 4, &p));
+    b.h_order = (int32_t *)p;
+    RPP_TRY(ws.host(ws.hb_ctl, 2 * sizeof(BatchCtl), &p));
+    b.h_ctl = (BatchCtl *)p;
+    RPP_TRY(ws.host(ws.hb_outs, c.clouds * sizeof(BatchOut), &p));
+    b.h_outs = (BatchOut *)p;
+    RPP_TRY(ws.host(ws.hb_mst, c.mst * 8, &p));
+    b.h_mst = (uint64_t *)p;
+    RPP_TRY(ws.host(ws.hb_left, c.left * sizeof(Leftover), &p));
+    b.h_left = (Leftover *)p;
+    RPP_TRY(ws.host(ws.hb_lcloud, c.left * 4, &p));
+    b.h_lcloud = (int32_t *)p;
+    return Status();
+}
+
+// The fused launch as a CUDA graph: upload the control block, run the fused
+// kernel, download the per-cloud outputs, the control block and the H0 edges.
+Status fused_graph(Workspace &ws, const BatchPlan &plan, const Caps &c, const Bufs &b,
+                   cudaGraphExec_t *out) {
+    const std::vector<uintptr_t> key = {
+        (uintptr_t)plan.nmax,   (uintptr_t)plan.dimcap,  (uintptr_t)plan.cfg.threads,
+        (uintptr_t)plan.cfg.group, (uintptr_t)plan.blocks, (uintptr_t)c.clouds,
+        (uintptr_t)c.mst,       (uintptr_t)c.left,
+        (uintptr_t)b.pts,       (uintptr_t)b.clouds,     (uintptr_t)b.order,
+        (uintptr_t)b.ctl,       (uintptr_t)b.D,          (uintptr_t)b.mst,
+        (uintptr_t)b.outs,      (uintptr_t)b.left,       (uintptr_t)b.lcloud,
+        (uintptr_t)b.h_ctl,     (uintptr_t)b.h_outs,     (uintptr_t)b.h_mst};
+    for (auto &g : ws.graphs)
+        if (g.first == key) {
+            *out = g.second;
+            return Status();
+        }
+    if (ws.graphs.size() >= 16) {  // keep the most recent ones
+        cudaGraphExecDestroy(ws.graphs.front().second);
+        ws.graphs.erase(ws.graphs.begin());
+    }
+    if (!ws.capture_stream) RPP_CK(cudaStreamCreateWithFlags(&ws.capture_stream, cudaStreamNonBlocking));
+    cudaStream_t cs = ws.capture_stream;
+    RPP_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    const long long l0 = g_launches;
+    cudaMemcpyAsync(b.ctl, &b.h_ctl[0], sizeof(BatchCtl), cudaMemcpyHostToDevice, cs);
+    launch_batch_h1(plan, b.pts, b.clouds, b.order, b.ctl, b.D, b.mst, b.outs, b.left, b.lcloud,
+                    c.left, cs);
+    cudaMemcpyAsync(b.h_outs, b.outs, c.clouds * sizeof(BatchOut), cudaMemcpyDeviceToHost, cs);
+    cudaMemcpyAsync(&b.h_ctl[1], b.ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, cs);
+    cudaMemcpyAsync(b.h_mst, b.mst, c.mst * 8, cudaMemcpyDeviceToHost, cs);
+    g_launches = l0;  // nothing ran yet
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cs, &g);
+    if (e != cudaSuccess || !g) {
+        cudaGetLastError();
+        return fail(RPP_E_CUDA, std::string("graph capture of the fused pass failed: ") +
+                                    cudaGetErrorString(e));
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(RPP_E_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    }
+    ws.graphs.emplace_back(key, exec);
+    *out = exec;
+    return Status();
+}
+
+// Autotuner: time every candidate launch shape on this launch's clouds (the
+// inputs are already on the device) and keep the fastest for the bucket.
+Status autotune(rpp_context *ctx, const Bufs &b, const Caps &caps, int nmax, int dimcap,
+                int nclouds, cudaStream_t s, BatchConfig *best) {
+    static const BatchConfig cands[] = {{128, 4}, {128, 8}, {256, 4}, {256, 8},
+                                        {256, 16}, {512, 8}, {512, 16}};
+    cudaEvent_t e0, e1;
+    RPP_CK(cudaEventCreate(&e0));
+    RPP_CK(cudaEventCreate(&e1));
+    float best_ms = INFINITY;
+    for (const BatchConfig &c : cands) {
+        const BatchPlan plan = plan_batch_h1(nmax, dimcap, c, ctx->sms);
+        b.h_ctl[0].queue = 0;
+        b.h_ctl[0].nclouds = nclouds;
+        b.h_ctl[0].left_count = 0;
+        float ms = 0.0f;
+        for (int rep = 0; rep < 2; ++rep) {  // the first run warms the caches
+            cudaMemcpyAsync(b.ctl, &b.h_ctl[0], sizeof(BatchCtl), cudaMemcpyHostToDevice, s);
+            cudaEventRecord(e0, s);
+            launch_batch_h1(plan, b.pts, b.clouds, b.order, b.ctl, b.D, b.mst, b.outs, b.left,
+                            b.lcloud, caps.left, s);
+            cudaEventRecord(e1, s);
+            cudaError_t e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return fail(RPP_E_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+            }
+            cudaEventElapsedTime(&ms, e0, e1);
+        }
+        if (ms < best_ms) {
+            best_ms = ms;
+            *best = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return Status();
+}
+
+// Results of one cloud of a fused launch.
+struct CloudWork {
+    int slot = 0;                  // position in the launch
+    std::vector<Leftover> left;    // its leftover columns
+    int64_t job = -1;              // row job (distance rows and neighbour lists), -1: none
+    bool fallback = false;         // leftover pool overflowed: run it alone
+};
+
+// One fused launch over clouds ins[idx[k]], results into out[idx[k]].
+Status run_launch(rpp_context *ctx, Workspace &ws, const std::vector<Instance> &ins,
+                  const std::vector<int> &idx, int nmax, int dimcap, cudaStream_t s,
+                  rpp_result **out) {
+    const double t0 = now_ms();
+    const long long launches0 = g_launches;
+    const int k = (int)idx.size();
+    const Caps caps = caps_of(ins, idx);
+    Bufs b;
+    RPP_TRY(get_bufs(ws, caps, b));
+
+    // layout and inputs
+    int64_t pt = 0, dd = 0;
+    int32_t ms = 0;
+    std::vector<const float *> dev_src(k, nullptr);
+    bool any_dev = false, any_host = false;
+    for (int j = 0; j < k; ++j) {
+        const Instance &in = ins[idx[j]];
+        BatchCloud &c = b.h_clouds[j];
+        c.n = (int32_t)in.n;
+        c.dim = in.dim;
+        c.ld = ld_of(c.n);
+        c.pt_off = pt;
+        c.d_off = dd;
+        c.mst_off = ms;
+        c.t_user = in.quantile > 0.0f ? INFINITY : in.threshold;
+        c.quantile = in.quantile;
+        c.max_dim = in.max_dim;
+        c.pad = 0;
+        const size_t cnt = (size_t)c.n * c.dim;
+        if (is_device_pointer(in.data)) {
+            dev_src[j] = in.data;
+            any_dev = true;
+        } else {
+            std::memcpy(b.h_pts + pt, in.data, cnt * 4);
+            any_host = true;
+        }
+        pt += (int64_t)cnt;
+        dd += (int64_t)c.n * c.ld;
+        ms += std::max(0, c.n - 1);
+        b.h_order[j] = j;
+    }
+    std::stable_sort(b.h_order, b.h_order + k,
+                     [&](int32_t x, int32_t y) { return b.h_clouds[x].n > b.h_clouds[y].n; });
+    RPP_CK(cudaMemcpyAsync(b.clouds, b.h_clouds, (size_t)k * sizeof(BatchCloud),
+                           cudaMemcpyHostToDevice, s));
+    RPP_CK(cudaMemcpyAsync(b.order, b.h_order, (size_t)k * 4, cudaMemcpyHostToDevice, s));
+    if (any_host) RPP_CK(cudaMemcpyAsync(b.pts, b.h_pts, (size_t)pt * 4, cudaMemcpyHostToDevice, s));
+    if (any_dev) {
+        void *p, *hp;
+        RPP_TRY(ws.dev(ws.b_src, (size_t)k * sizeof(void *), &p));
+        RPP_TRY(ws.host(ws.hb_src, (size_t)k * sizeof(void *), &hp));
+        std::memcpy(hp, dev_src.data(), (size_t)k * sizeof(void *));
+        RPP_CK(cudaMemcpyAsync(p, hp, (size_t)k * sizeof(void *), cudaMemcpyHostToDevice, s));
+        launch_gather_points((const float *const *)p, b.clouds, k, b.pts, s);
+    }
+
+    // launch shape: the bucket's tuned one (tuned now if this is its first run)
+    BatchConfig cfg;
+    bool have = false;
+    {
+        std::lock_guard<std::mutex> g(ctx->tune_mu);
+        auto it = ctx->batch_tuning.find(nmax);
+        if (it != ctx->batch_tuning.end()) {
+            cfg = it->second;
+            have = true;
+        }
+    }
+    if (!have && ctx->autotune) {
+        RPP_TRY(autotune(ctx, b, caps, nmax, dimcap, k, s, &cfg));
+        std::lock_guard<std::mutex> g(ctx->tune_mu);
+        ctx->batch_tuning.emplace(nmax, cfg);
+    }
+    const BatchPlan plan = plan_batch_h1(nmax, dimcap, cfg, ctx->sms);
+    cudaGraphExec_t exec;
+    RPP_TRY(fused_graph(ws, plan, caps, b, &exec));
+    b.h_ctl[0].queue = 0;
+    b.h_ctl[0].nclouds = k;
+    b.h_ctl[0].left_count = 0;
+    RPP_CK(cudaGraphLaunch(exec, s));
+    ++g_launches;  // the fused kernel
+    const double a = now_ms();
+    RPP_CK(cudaStreamSynchronize(s));
+    double dev_ms = now_ms() - a;
+
+    // per-cloud outputs, leftovers grouped by cloud
+    for (int j = 0; j < k; ++j) {
+        const unsigned err = b.h_outs[j].err;
+        if (err & ERR_INTERNAL)
+            return fail(RPP_E_CUDA, "cloud " + std::to_string(idx[j]) +
+                                        ": fused pass: spanning-forest root search exceeded its bound");
+        if (err)
+            return fail(RPP_E_INVALID, "cloud " + std::to_string(idx[j]) +
+                                           ": invalid input: non-finite distance");
+    }
+    const uint64_t found = b.h_ctl[1].left_count, got = std::min(found, caps.left);
+    if (got) {
+        RPP_CK(cudaMemcpyAsync(b.h_left, b.left, got * sizeof(Leftover), cudaMemcpyDeviceToHost, s));
+        RPP_CK(cudaMemcpyAsync(b.h_lcloud, b.lcloud, got * 4, cudaMemcpyDeviceToHost, s));
+        RPP_CK(cudaStreamSynchronize(s));
+    }
+    std::vector<CloudWork> W(k);
+    for (int j = 0; j < k; ++j) W[j].slot = j;
+    for (uint64_t i = 0; i < got; ++i) W[b.h_lcloud[i]].left.push_back(b.h_left[i]);
+    std::vector<int32_t> jobs;
+    std::vector<int64_t> off;
+    int64_t rows = 0;
+    for (int j = 0; j < k; ++j) {
+        if (W[j].left.size() < b.h_outs[j].nleft) {
+            W[j].fallback = true;
+            continue;
+        }
+        if (W[j].left.empty()) continue;
+        W[j].job = (int64_t)jobs.size();
+        jobs.push_back(j);
+        off.push_back(rows);
+        rows += (int64_t)b.h_clouds[j].n * b.h_clouds[j].n;
+    }
+    float *hD = nullptr;
+    uint64_t *hN = nullptr;
+    if (!jobs.empty()) {  // distance rows and neighbour lists of the clouds with leftovers
+        void *p, *hp;
+        const size_t nj = jobs.size();
+        RPP_TRY(ws.dev(ws.b_jobs, nj * 4, &p));
+        int32_t *djobs = (int32_t *)p;
+        RPP_TRY(ws.dev(ws.b_off, nj * 8, &p));
+        int64_t *doff = (int64_t *)p;
+        RPP_TRY(ws.dev(ws.b_Dout, (size_t)rows * 4, &p));
+        float *dD = (float *)p;
+        RPP_TRY(ws.dev(ws.b_nbr, (size_t)rows * 8, &p));
+        uint64_t *dN = (uint64_t *)p;
+        RPP_TRY(ws.host(ws.hb_jobs, nj * 4 + nj * 8, &hp));
+        std::memcpy(hp, jobs.data(), nj * 4);
+        std::memcpy((char *)hp + nj * 4, off.data(), nj * 8);
+        RPP_CK(cudaMemcpyAsync(djobs, hp, nj * 4, cudaMemcpyHostToDevice, s));
+        RPP_CK(cudaMemcpyAsync(doff, (char *)hp + nj * 4, nj * 8, cudaMemcpyHostToDevice, s));
+        launch_batch_rows(b.D, b.clouds, djobs, (int)nj, doff, nmax, dD, dN, s);
+        RPP_CK(cudaGetLastError());
+        RPP_TRY(ws.host(ws.hb_Dout, (size_t)rows * 4, &hp));
+        hD = (float *)hp;
+        RPP_TRY(ws.host(ws.hb_nbr, (size_t)rows * 8, &hp));
+        hN = (uint64_t *)hp;
+        RPP_CK(cudaMemcpyAsync(hD, dD, (size_t)rows * 4, cudaMemcpyDeviceToHost, s));
+        RPP_CK(cudaMemcpyAsync(hN, dN, (size_t)rows * 8, cudaMemcpyDeviceToHost, s));
+        const double a2 = now_ms();
+        RPP_CK(cudaStreamSynchronize(s));
+        dev_ms += now_ms() - a2;
+    }
+    const long long launches = g_launches - launches0;
+
+    // host: H0 from the forest, the submatrix reductions, the barcodes
+    const int inner = (int)jobs.size() >= ctx->host_threads ? 1 : ctx->host_threads;
+    std::vector<rpp_result *> res(k, nullptr);
+    std::vector<std::string> errs(k);
+    parallel_for(ctx->host_threads, k, [&](int64_t jj) {
+        const int j = (int)jj;
+        if (W[j].fallback) return;
+        const BatchCloud &c = b.h_clouds[j];
+        const BatchOut &o = b.h_outs[j];
+        const int n = c.n;
+        rpp_result *r = new rpp_result();
+        r->max_dim = c.max_dim;
+        rpp_stats &S = r->stats;
+        std::memset(&S, 0, sizeof S);
+        S.n = n;
+        S.max_dim = c.max_dim;
+        S.threshold = o.t;
+        S.enclosing_radius = o.R;
+        S.kernel_launches = launches;
+        S.ms_device = dev_ms;
+        std::vector<uint64_t> store;
+        Binomial B;
+        fill_binomial(n, 3, store, B);
+        for (uint32_t q = 0; q < o.nmst; ++q) {  // H0 deaths
+            const uint64_t key = b.h_mst[c.mst_off + q];
+            const float d = bits_to_float((uint32_t)(key >> 32));
+            if (!(d > 0.0f)) continue;  // zero length (duplicate points)
+            int v[2];
+            decode_host(B, key & 0xffffffffull, 1, n, v);
+            rpp_critical cr = {-1, -1, v[0], v[1]};
+            add_interval(r, 0, 0.0f, d, cr);
+        }
+        for (int64_t q = 0; q < (int64_t)n - (int64_t)o.nmst; ++q) {
+            rpp_critical cr = {-1, -1, -1, -1};
+            add_interval(r, 0, 0.0f, INFINITY, cr);
+        }
+        if (n >= 2) {
+            S.candidates[1] = (int64_t)n * (n - 1) / 2;
+            S.cleared[1] = o.nmst;
+            S.columns[1] = (int64_t)o.ncols - o.nmst;
+        }
+        if (c.max_dim >= 1) {
+            S.apparent[1] = (int64_t)o.napp;
+            S.leftover[1] = (int64_t)o.nleft;
+            S.scanned[1] = (int64_t)o.scanned;
+            if (W[j].job >= 0) {
+                const double a3 = now_ms();
+                HostInstance I;
+                I.n = n;
+                I.D = hD + off[W[j].job];
+                I.ld = n;
+                I.B = &B;
+                I.nbr = hN + off[W[j].job];
+                I.app_tau = nullptr;  // apparent pivots are recognised by testing them again
+                I.napp = 0;
+                I.t = o.t;
+                std::vector<Leftover> &L = W[j].left;
+                std::sort(L.begin(), L.end(),
+                          [](const Leftover &x, const Leftover &y) { return x.index < y.index; });
+                std::vector<HostPair> pairs;
+                ReduceStats rs;
+                reduce_leftovers(I, 1, L.data(), (int64_t)L.size(), inner, pairs, rs);
+                S.free_pivot[1] = rs.free_pivot;
+                S.additions[1] = rs.additions;
+                S.store_reads[1] = rs.reads;
+                S.entries[1] = rs.entries;
+                int vs[2], vt[3];
+                for (const HostPair &P : pairs) {
+                    if (P.tau != NO_PIVOT && !(P.death > P.birth)) continue;
+                    rpp_critical cr = {-1, -1, -1, -1};
+                    decode_host(B, P.sigma, 1, n, vs);
+                    youngest_edge(I, vs, 2, &cr.bu, &cr.bv);
+                    if (P.tau != NO_PIVOT) {
+                        decode_host(B, P.tau, 2, n, vt);
+                        youngest_edge(I, vt, 3, &cr.du, &cr.dv);
+                    }
+                    add_interval(r, 1, P.birth, P.death, cr);
+                }
+                S.ms_host_reduce = now_ms() - a3;
+            }
+        }
+        for (int q = 0; q <= c.max_dim; ++q) {
+            sort_result(r, q);
+            S.intervals[q] = (int64_t)r->iv[q].size();
+        }
+        S.ms_total = now_ms() - t0;
+        res[j] = r;
+    });
+    for (int j = 0; j < k; ++j) {
+        if (!W[j].fallback) {
+            out[idx[j]] = res[j];
+            continue;
+        }
+        rpp_result *r = new rpp_result();  // leftover pool overflow: this cloud alone
+        Status st = run_instance(ctx, ws, ins[idx[j]], s, r);
+        if (!st.ok()) {
+            delete r;
+            for (int q = 0; q < k; ++q)
+                if (!W[q].fallback && res[q]) {
+                    delete res[q];
+                    out[idx[q]] = nullptr;
+                }
+            return st;
+        }
+        out[idx[j]] = r;
+    }
+    return Status();
+}
+
+}  // namespace
+
+bool batch_fused_eligible(const rpp_context *ctx, const Instance &in) {
+    return ctx->batch_fused && in.kind == RPP_INPUT_POINTS && in.max_dim <= 1 &&
+           in.n <= BATCH_NMAX && (ctx->record & (RPP_RECORD_COLUMNS | RPP_RECORD_APPARENT)) == 0;
+}
+
+size_t batch_device_bytes(const std::vector<Instance> &ins) {
+    std::vector<int> idx(ins.size());
+    uint64_t rows = 0;
+    for (size_t i = 0; i < ins.size(); ++i) {
+        idx[i] = (int)i;
+        rows += (uint64_t)ins[i].n * (uint64_t)ins[i].n;
+    }
+    return launch_device_bytes(caps_of(ins, idx), rows) + 2 * sizeof(void *) * ins.size();
+}
+
+Status run_batch(rpp_context *ctx, Workspace &ws, const std::vector<Instance> &ins,
+                 cudaStream_t s, rpp_result **out) {
+    RPP_CK(cudaSetDevice(ws.device));
+    std::map<std::pair<int, int>, std::vector<int>> buckets;  // (nmax, dimcap) -> clouds
+    std::vector<int> alone;
+    for (int i = 0; i < (int)ins.size(); ++i) {
+        out[i] = nullptr;
+        if (batch_fused_eligible(ctx, ins[i]))
+            buckets[{bucket_nmax(ins[i].n), dimcap_of(ins[i].dim)}].push_back(i);
+        else
+            alone.push_back(i);
+    }
+    auto cleanup = [&]() {
+        for (size_t i = 0; i < ins.size(); ++i)
+            if (out[i]) {
+                rpp_result_free(out[i]);
+                out[i] = nullptr;
+            }
+    };
+    for (auto &kv : buckets) {
+        const int nmax = kv.first.first, dimcap = kv.first.second;
+        const int cap = bucket_cap(nmax);
+        const std::vector<int> &all = kv.second;
+        for (size_t o = 0; o < all.size(); o += (size_t)cap) {
+            std::vector<int> idx(all.begin() + o, all.begin() + std::min(all.size(), o + cap));
+            Status st = run_launch(ctx, ws, ins, idx, nmax, dimcap, s, out);
+            if (!st.ok()) {
+                cleanup();
+                return st;
+            }
+        }
+    }
+    for (int i : alone) {
+        rpp_result *r = new rpp_result();
+        Status st = run_instance(ctx, ws, ins[i], s, r);
+        if (!st.ok()) {
+            delete r;
+            cleanup();
+            st.msg = "cloud " + std::to_string(i) + ": " + st.msg;
+            return st;
+        }
+        out[i] = r;
+    }
+    return Status();
+}
+
+}  // namespace rpp
 
 extern "C" rpp_status rpp_barcodes_batched(rpp_context *ctx, int32_t batch,
                                            const float *const *data, const int64_t *n,
@@ -38,22 +607,38 @@ extern "C" rpp_status rpp_barcodes_batched(rpp_context *ctx, int32_t batch,
             return report(v);
         }
     }
+    if (batch == 0) return RPP_OK;
     Workspace *ws = ctx->acquire();
-    for (int32_t i = 0; i < batch; ++i) {
-        rpp_result *res = new rpp_result();
-        Status s = run_instance(ctx, *ws, ins[i], (cudaStream_t)stream, res);
-        if (!s.ok()) {
-            delete res;
-            for (int32_t j = 0; j < i; ++j) {
-                rpp_result_free(out[j]);
-                out[j] = nullptr;
-            }
-            ctx->release(ws);
-            s.msg = "cloud " + std::to_string(i) + ": " + s.msg;
-            return report(s);
-        }
-        out[i] = res;
-    }
+    Status s = run_batch(ctx, *ws, ins, (cudaStream_t)stream, out);
     ctx->release(ws);
+    if (!s.ok()) return report(s);
+    return RPP_OK;
+}
+
+extern "C" rpp_status rpp_context_set_batch(rpp_context *ctx, int32_t fused, int32_t autotune) {
+    if (!ctx) {
+        set_last_error("rpp_context_set_batch: ctx is NULL");
+        return RPP_E_INVALID;
+    }
+    ctx->batch_fused = fused != 0;
+    ctx->autotune = autotune != 0;
+    return RPP_OK;
+}
+
+extern "C" rpp_status rpp_context_batch_tuning(rpp_context *ctx, int32_t nmax, int32_t *threads,
+                                               int32_t *group) {
+    if (!ctx || !threads || !group) {
+        set_last_error("rpp_context_batch_tuning: NULL argument");
+        return RPP_E_INVALID;
+    }
+    std::lock_guard<std::mutex> g(ctx->tune_mu);
+    auto it = ctx->batch_tuning.find(nmax);
+    if (it == ctx->batch_tuning.end()) {
+        *threads = 0;
+        *group = 0;
+        return RPP_OK;
+    }
+    *threads = it->second.threads;
+    *group = it->second.group;
     return RPP_OK;
 }

@@ -129,6 +129,14 @@ Pool &pool(int threads) {
 
 }  // namespace
 
+void parallel_for(int threads, int64_t count, const std::function<void(int64_t)> &fn) {
+    if (threads <= 1 || count < 2) {
+        for (int64_t i = 0; i < count; ++i) fn(i);
+        return;
+    }
+    pool(threads).parallel_for(count, fn);
+}
+
 void decode_host(const Binomial &B, uint64_t c, int p, int64_t n, int *v) {
     int hi = (int)n - 1;
     for (int i = 0; i <= p; ++i) {
@@ -397,10 +405,16 @@ struct Reducer {
 
     // The apparent column owning pivot tau, if any: tau is among the apparent
     // taus, and its owner is the youngest facet of tau (vertices into s, the
-    // vertex tau adds to it into *added).
+    // vertex tau adds to it into *added). Without a stored array of taus
+    // (I.app_tau null) the pair is tested again from its definition: tau is
+    // apparent iff its youngest facet s has tau's diameter and tau is the
+    // oldest cofacet of s, i.e. no vertex w above *added lies within tau's
+    // diameter of every vertex of s. (A cleared column never passes: an
+    // apparent pair is a persistence pair, and a cleared simplex is already
+    // paired in the dimension below.)
     bool apparent_owner(u128 key, int *s, int *added) const {
         const uint64_t tidx = key_index(key);
-        if (!is_apparent_tau(tidx)) return false;
+        if (I.app_tau && !is_apparent_tau(tidx)) return false;
         const float dt = key_diam(key);
         int u[RPP_MAX_DIM + 2];
         decode_host(*I.B, tidx, p + 1, n, u);
@@ -416,10 +430,17 @@ struct Reducer {
                 best = r;
             }
         }
-        if (bestd != dt) return false;  // cannot happen for an apparent tau
+        if (bestd != dt) return false;  // cannot happen for a stored apparent tau
         for (int a = 0, k = 0; a <= p + 1; ++a)
             if (a != best) s[k++] = u[a];
         *added = u[best];
+        if (!I.app_tau)
+            for (int w = (int)n - 1; w > *added; --w) {
+                if (in_simplex(s, w)) continue;
+                float m = 0.0f;
+                for (int i = 0; i <= p; ++i) m = std::max(m, I.dist(s[i], w));
+                if (m <= dt) return false;  // an older cofacet of equal diameter
+            }
         return true;
     }
 };

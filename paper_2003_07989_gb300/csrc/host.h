@@ -4,6 +4,7 @@
 
 #include <stdint.h>
 
+#include <functional>
 #include <unordered_map>
 #include <vector>
 
@@ -19,7 +20,9 @@ struct HostInstance {
     int64_t ld = 0;
     const Binomial *B = nullptr;
     const uint64_t *nbr = nullptr;  // n x n neighbour lists: (bits(distance) << 32) | vertex, sorted
-    const uint64_t *app_tau = nullptr;  // apparent pivots (tau) of the current dimension, sorted
+    // apparent pivots (tau) of the current dimension, sorted; null: apparent
+    // pairs are recognised by testing them again
+    const uint64_t *app_tau = nullptr;
     uint64_t napp = 0;
     float t = 0.0f;                 // threshold in use
     float dist(int a, int b) const { return D[(int64_t)a * ld + b]; }
@@ -59,6 +62,10 @@ struct Kruskal {
 struct ReduceStats {
     int64_t free_pivot = 0, additions = 0, reads = 0, entries = 0;
 };
+
+// Run fn(0) .. fn(count - 1) on the library's persistent host threads, the
+// caller included (serially when threads <= 1). Calls may nest.
+void parallel_for(int threads, int64_t count, const std::function<void(int64_t)> &fn);
 
 // Reduce the leftover columns of dimension p (given in coboundary order) and
 // append their pairs (zero-length included) and essential classes to out.

@@ -33,7 +33,13 @@ struct DevState {
 // Kernels launched by the calling thread (incremented by every launcher).
 extern thread_local long long g_launches;
 
-enum : unsigned int { ERR_NONFINITE = 1u, ERR_NEGATIVE = 2u, ERR_ASYMMETRIC = 4u, ERR_DIAGONAL = 8u };
+enum : unsigned int {
+    ERR_NONFINITE = 1u,
+    ERR_NEGATIVE = 2u,
+    ERR_ASYMMETRIC = 4u,
+    ERR_DIAGONAL = 8u,
+    ERR_INTERNAL = 16u  // a kernel's bounded loop ran out (reported, never expected)
+};
 
 // A leftover column handed to the host reduction, with its unreduced pivot
 // (the oldest cofacet inside the threshold) found during the apparent pass.
@@ -117,6 +123,71 @@ bool launch_sort_rows(const float *D, int64_t ld, int64_t n, uint64_t *out, cuda
 
 // Set bit `idx[i]` of a bitmap for every i.
 void launch_bitmap_set(const uint64_t *idx, uint64_t count, uint32_t *bitmap, cudaStream_t s);
+
+// ---- fused batch of small clouds, dimensions 0 and 1 ------------------------
+
+constexpr int BATCH_NMAX = 1024;  // largest cloud of the fused pass
+
+// One cloud of a fused batch.
+struct BatchCloud {
+    int64_t pt_off;   // offset (floats) of its points in the packed point buffer
+    int64_t d_off;    // offset (floats) of its n x ld distance matrix in the scratch
+    int32_t n, dim, ld;
+    int32_t mst_off;  // first of its n - 1 MST slots
+    float t_user;     // threshold (INFINITY: none)
+    float quantile;   // > 0: threshold = the ceil(q C(n,2))-th smallest distance
+    int32_t max_dim;  // 0: H0 only (no apparent-pair test)
+    int32_t pad;
+};
+
+// What the fused pass reports per cloud.
+struct BatchOut {
+    float R, t;                 // enclosing radius, threshold in use
+    uint32_t nmst, err;         // MST edges written (H0 deaths), ERR_* flags
+    unsigned long long ncols;   // edges inside the threshold (MST edges included)
+    unsigned long long napp, nleft, scanned;
+};
+
+// The fused pass: per cloud (one block at a time, clouds taken in `order`)
+// distances, enclosing radius and threshold, the minimum spanning forest
+// inside the threshold (H0, and the clearing set of dimension 1), then, when
+// the cloud asks for dimension 1, the apparent-pair test of every other edge
+// inside the threshold. Leftover columns are appended to `left` (cloud in
+// `left_cloud`) while fewer than left_cap; ctl->left_count counts them all.
+// `group` is the lane-group width of the test.
+struct BatchConfig {
+    int threads = 256, group = 8;
+};
+// Control block of one fused launch (device memory).
+struct BatchCtl {
+    unsigned int queue;               // next position in `order` (0 on entry)
+    int nclouds;                      // clouds in this launch
+    unsigned long long left_count;    // leftover columns found (0 on entry)
+};
+// Launch shape of the fused kernel for clouds of up to nmax points in up to
+// dimcap dimensions; sets the kernel's shared-memory attribute. Call outside
+// stream capture.
+struct BatchPlan {
+    int nmax = 0, dimcap = 0, blocks = 0;
+    size_t smem = 0;
+    BatchConfig cfg;
+};
+BatchPlan plan_batch_h1(int nmax, int dimcap, BatchConfig cfg, int sms);
+void launch_batch_h1(const BatchPlan &plan, const float *pts, const BatchCloud *clouds,
+                     const int32_t *order, BatchCtl *ctl, float *Dbuf, uint64_t *mst_out,
+                     BatchOut *outs, Leftover *left, int32_t *left_cloud, uint64_t left_cap,
+                     cudaStream_t s);
+
+// Rows of selected clouds for the host reduction: for job j (cloud c =
+// jobs[j]) copy its distance matrix to Dout + out_off[j] (stride n) and its
+// sorted neighbour lists (as launch_sort_rows) to nbr + nbr_off[j].
+void launch_batch_rows(const float *Dbuf, const BatchCloud *clouds, const int32_t *jobs, int njobs,
+                       const int64_t *out_off, int nmax, float *Dout, uint64_t *nbr,
+                       cudaStream_t s);
+
+// Gather clouds given by device pointers into the packed point buffer.
+void launch_gather_points(const float *const *src, const BatchCloud *clouds, int nclouds,
+                          float *pts, cudaStream_t s);
 
 // ---- error helpers ---------------------------------------------------------
 void set_last_error(const std::string &msg);

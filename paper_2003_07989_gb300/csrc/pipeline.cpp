@@ -20,8 +20,6 @@
 
 namespace rpp {
 
-namespace {
-
 double now_ms() {
     return std::chrono::duration<double, std::milli>(
                std::chrono::steady_clock::now().time_since_epoch())
@@ -33,23 +31,6 @@ int bits_for(uint64_t x) {  // bits needed to write x (0 for x = 0)
     while (b < 64 && (x >> b)) ++b;
     return b;
 }
-
-#define RPP_CK(call)                                                                  \
-    do {                                                                              \
-        cudaError_t e_ = (call);                                                      \
-        if (e_ != cudaSuccess) {                                                      \
-            Status st_;                                                               \
-            st_.code = RPP_E_CUDA;                                                    \
-            st_.msg = std::string(#call) + ": " + cudaGetErrorString(e_);             \
-            return st_;                                                               \
-        }                                                                             \
-    } while (0)
-
-#define RPP_TRY(expr)             \
-    do {                          \
-        Status s_ = (expr);       \
-        if (!s_.ok()) return s_;  \
-    } while (0)
 
 Status fail(rpp_status code, const std::string &msg) {
     Status s;
@@ -64,8 +45,6 @@ float bits_to_float(uint32_t b) {
     return f;
 }
 
-}  // namespace
-
 // ---------------------------------------------------------------------------
 // workspace
 
@@ -79,6 +58,16 @@ Workspace::~Workspace() {
                     &h_D,     &h_state, &h_mst, &h_up,  &h_nbr};
     for (HostBuf *b : h)
         if (b->p) cudaFreeHost(b->p);
+    DevBuf *bd[] = {&b_pts, &b_clouds, &b_order, &b_ctl, &b_D,   &b_mst,  &b_outs,
+                    &b_left, &b_lcloud, &b_jobs, &b_off, &b_Dout, &b_nbr, &b_src};
+    for (DevBuf *b : bd)
+        if (b->p) cudaFree(b->p);
+    HostBuf *bh[] = {&hb_pts,  &hb_clouds, &hb_order, &hb_ctl, &hb_outs, &hb_mst,  &hb_left,
+                     &hb_lcloud, &hb_jobs, &hb_off,   &hb_Dout, &hb_nbr, &hb_src};
+    for (HostBuf *b : bh)
+        if (b->p) cudaFreeHost(b->p);
+    for (auto &g : graphs) cudaGraphExecDestroy(g.second);
+    if (capture_stream) cudaStreamDestroy(capture_stream);
     for (cudaEvent_t e : events) cudaEventDestroy(e);
 }
 
@@ -291,6 +280,8 @@ struct DimOutput {
     std::vector<HostPair> pairs;  // host-found pairs (zero-length included) and essentials
 };
 
+}  // namespace
+
 void add_interval(rpp_result *res, int q, float b, float d, const rpp_critical &c) {
     rpp_interval iv;
     iv.birth = b;
@@ -320,8 +311,6 @@ void sort_result(rpp_result *res, int q) {
     iv.swap(iv2);
     cr.swap(cr2);
 }
-
-}  // namespace
 
 Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStream_t s,
                     rpp_result *res) {

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -32,6 +33,28 @@ struct Status {
     bool ok() const { return code == RPP_OK; }
 };
 
+#define RPP_CK(call)                                                                  \
+    do {                                                                              \
+        cudaError_t e_ = (call);                                                      \
+        if (e_ != cudaSuccess) {                                                      \
+            ::rpp::Status st_;                                                        \
+            st_.code = RPP_E_CUDA;                                                    \
+            st_.msg = std::string(#call) + ": " + cudaGetErrorString(e_);             \
+            return st_;                                                               \
+        }                                                                             \
+    } while (0)
+
+#define RPP_TRY(expr)                 \
+    do {                              \
+        ::rpp::Status s_ = (expr);    \
+        if (!s_.ok()) return s_;      \
+    } while (0)
+
+double now_ms();
+int bits_for(uint64_t x);  // bits needed to write x (0 for x = 0)
+Status fail(rpp_status code, const std::string &msg);
+float bits_to_float(uint32_t b);
+
 // Everything one in-flight instance needs. A context keeps a pool of these.
 struct Workspace {
     int device = 0;
@@ -46,6 +69,14 @@ struct Workspace {
     bool binom_on_device = false;
     std::vector<uint64_t> binom_store;
     std::vector<cudaEvent_t> events;  // pool for stage timing
+    // the fused batch pass (batch.cpp)
+    DevBuf b_pts, b_clouds, b_order, b_ctl, b_D, b_mst, b_outs, b_left, b_lcloud, b_jobs, b_off,
+        b_Dout, b_nbr, b_src;
+    HostBuf hb_pts, hb_clouds, hb_order, hb_ctl, hb_outs, hb_mst, hb_left, hb_lcloud, hb_jobs,
+        hb_off, hb_Dout, hb_nbr, hb_src;
+    // captured fused launches by (shape, buffer addresses), most recent last
+    std::vector<std::pair<std::vector<uintptr_t>, cudaGraphExec_t>> graphs;
+    cudaStream_t capture_stream = nullptr;
     ~Workspace();
     Status dev(DevBuf &b, size_t bytes, void **out);
     Status host(HostBuf &b, size_t bytes, void **out);
@@ -98,6 +129,11 @@ struct rpp_context {
     rpp::Tuning tuning_for(int64_t n, int p);
     rpp::Workspace *acquire();
     void release(rpp::Workspace *ws);
+    // the fused batch pass: launch shape per size bucket, filled by the autotuner
+    bool batch_fused = true;  // false: every cloud of a batch takes run_instance
+    bool autotune = true;
+    std::mutex tune_mu;
+    std::map<int, rpp::BatchConfig> batch_tuning;  // bucket nmax -> chosen shape
 };
 
 namespace rpp {
@@ -105,6 +141,15 @@ namespace rpp {
 // Run one instance end to end on `stream` with workspace `ws`.
 Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStream_t stream,
                     rpp_result *res);
+// Run validated instances as one batch (fused pass where eligible, batch.cpp);
+// out[i] receives instance i's result. On error no result is left in out.
+Status run_batch(rpp_context *ctx, Workspace &ws, const std::vector<Instance> &ins,
+                 cudaStream_t stream, rpp_result **out);
+// Whether run_batch takes this instance through the fused pass.
+bool batch_fused_eligible(const rpp_context *ctx, const Instance &in);
+// Device bytes a workspace holds after run_batch over these fused-eligible
+// instances (an upper bound).
+size_t batch_device_bytes(const std::vector<Instance> &ins);
 // Device bytes a workspace holds after running this instance.
 size_t instance_device_bytes(const Instance &in);
 // Validate an instance before any GPU work.
@@ -114,5 +159,9 @@ void fill_binomial(int64_t n, int kmax, std::vector<uint64_t> &store, Binomial &
 bool is_device_pointer(const void *p);
 // Record a failed status as the thread's last error and return its code.
 rpp_status report(const Status &s);
+// Append an interval of dimension q with its realising edges.
+void add_interval(rpp_result *res, int q, float b, float d, const rpp_critical &c);
+// Sort the intervals of dimension q by (birth, death, realising edges).
+void sort_result(rpp_result *res, int q);
 
 }  // namespace rpp

@@ -28,6 +28,7 @@ struct Request {
     std::vector<float> pts;
     Instance in;
     size_t est = 0;
+    bool fused = false;  // runs in fused batches (clouds of the fused pass, max_batch > 1)
     int skipped = 0;
     bool done = false;
     rpp_result *res = nullptr;
@@ -65,6 +66,7 @@ void rpp_server::worker(int k) {
     ws->device = ctx->device;
     const size_t budget = cfg.device_bytes;
     const int max_skips = 8;
+    std::vector<Request *> batch;
     for (;;) {
         Request *r = nullptr;
         {
@@ -105,17 +107,67 @@ void rpp_server::worker(int k) {
                 cv_work.wait(g);
             }
             if (!r) break;
-            held[k] = std::max(held[k], r->est);
+            batch.assign(1, r);
+            if (r->fused) {
+                // continuous batching: waiting requests join this launch while
+                // the batch's footprint fits next to the other slots
+                std::vector<Instance> ins(1, r->in);
+                size_t est = r->est;
+                for (auto it = queue.begin();
+                     it != queue.end() && (int)batch.size() < cfg.max_batch;) {
+                    Request *q = *it;
+                    if (!q->fused) {
+                        ++it;
+                        continue;
+                    }
+                    ins.push_back(q->in);
+                    const size_t e = batch_device_bytes(ins);
+                    if (budget == 0 || held_others(k) + std::max(held[k], e) <= budget) {
+                        batch.push_back(q);
+                        est = e;
+                        it = queue.erase(it);
+                    } else {
+                        ins.pop_back();
+                        ++it;
+                    }
+                }
+                held[k] = std::max(held[k], est);
+            } else {
+                held[k] = std::max(held[k], r->est);
+            }
         }
-        rpp_result *res = new rpp_result();
-        Status st = run_instance(ctx, *ws, r->in, s, res);
+        std::vector<rpp_result *> res(batch.size(), nullptr);
+        std::vector<Status> st(batch.size());
+        if (batch.size() > 1 || batch[0]->fused) {
+            std::vector<Instance> ins;
+            for (Request *q : batch) ins.push_back(q->in);
+            Status bs = run_batch(ctx, *ws, ins, s, res.data());
+            if (!bs.ok()) {  // find the failing request: run each one alone
+                for (size_t i = 0; i < batch.size(); ++i) {
+                    res[i] = new rpp_result();
+                    st[i] = run_instance(ctx, *ws, batch[i]->in, s, res[i]);
+                    if (!st[i].ok()) {
+                        delete res[i];
+                        res[i] = nullptr;
+                    }
+                }
+            }
+        } else {
+            res[0] = new rpp_result();
+            st[0] = run_instance(ctx, *ws, batch[0]->in, s, res[0]);
+            if (!st[0].ok()) {
+                delete res[0];
+                res[0] = nullptr;
+            }
+        }
         {
             std::lock_guard<std::mutex> g(mu);
             held[k] = ws->device_bytes;
-            if (st.ok()) r->res = res;
-            else delete res;
-            r->status = st;
-            r->done = true;
+            for (size_t i = 0; i < batch.size(); ++i) {
+                batch[i]->res = res[i];
+                batch[i]->status = st[i];
+                batch[i]->done = true;
+            }
         }
         cv_done.notify_all();
         cv_work.notify_all();
@@ -172,7 +224,8 @@ rpp_status rpp_server_submit(rpp_server *srv, const float *points, int64_t n, in
         std::memcpy(r->pts.data(), points, r->pts.size() * 4);
     }
     r->in.data = r->pts.data();
-    r->est = instance_device_bytes(r->in);
+    r->fused = srv->cfg.max_batch > 1 && batch_fused_eligible(srv->ctx, r->in);
+    r->est = r->fused ? batch_device_bytes({r->in}) : instance_device_bytes(r->in);
     if (srv->cfg.device_bytes && r->est > srv->cfg.device_bytes) {
         delete r;
         set_last_error("rpp_server_submit: request can never fit the server's memory bound");
