@@ -46,7 +46,8 @@ class Stats(C.Structure):
                 ("candidates", _A), ("columns", _A), ("cleared", _A), ("apparent", _A),
                 ("leftover", _A), ("free_pivot", _A), ("additions", _A), ("store_reads", _A),
                 ("entries", _A),
-                ("intervals", _A), ("scanned", _A), ("kernel_launches", C.c_int64),
+                ("intervals", _A), ("scanned", _A), ("sweep_levels", _A),
+                ("kernel_launches", C.c_int64),
                 ("stage_ms", C.c_double * 8), ("stage_launches", C.c_int64 * 8),
                 ("ms_device", C.c_double), ("ms_host_reduce", C.c_double),
                 ("ms_host_h0", C.c_double), ("ms_total", C.c_double)]

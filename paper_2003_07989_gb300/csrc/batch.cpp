@@ -474,6 +474,7 @@ Status run_launch(rpp_context *ctx, Workspace &ws, const std::vector<Instance> &
                 S.additions[1] = rs.additions;
                 S.store_reads[1] = rs.reads;
                 S.entries[1] = rs.entries;
+                S.sweep_levels[1] = rs.levels;
                 int vs[2], vt[3];
                 for (const HostPair &P : pairs) {
                     if (P.tau != NO_PIVOT && !(P.death > P.birth)) continue;

@@ -655,24 +655,31 @@ void reduce_general(const HostInstance &I, int p, const Leftover *left, int64_t 
 // ---- dimension 1 -------------------------------------------------------------
 //
 // The working column of leftover j is the coboundary of a set V of edges; a
-// triangle is a nonzero entry iff an odd number of its edges lie in V. During
-// an apparent walk V only grows (an apparent edge is added once, when its own
-// pivot is reached, and never leaves), so a triangle's parity can be read from
-// a bit set over edge indices whenever a cursor reaches it: the cursor skips it
-// if even.
-// The heap then holds only entries that were nonzero when pushed; one whose
+// triangle is a nonzero entry iff an odd number of its edges lie in V. V is
+// kept as adjacency bits (row a, bit b set iff the edge {a, b} is in V).
+// During an apparent walk V only grows (an apparent edge is added once, when
+// its own pivot is reached; an edge already in V would leave it, and the walk
+// then restarts), so a triangle's parity can be read from the bits whenever a
+// cursor lists it: the cursor skips it if even.
+// The heap then holds only entries that were nonzero when listed; one whose
 // parity changed since is dropped when it surfaces. Every nonzero triangle
-// stays reachable: the last of its edges to enter V has a cursor that either
-// has not reached it yet or reached it after its parity last changed. Adding
-// another leftover's column (Phase B) can remove edges from V; the walk then
-// restarts from the new V, each cursor placed just past the cancelled pivot
-// (the sum is zero up to there).
+// stays reachable: the last of its edges to enter V has a cursor that listed
+// it (or will) after its parity last changed. Adding another leftover's column
+// (Phase B) can remove edges from V; the walk then restarts from the new V,
+// each cursor placed just past the cancelled pivot (the sum is zero up to
+// there).
 //
-// Merge part of an edge cursor (x, y) with diameter d: the neighbour rows of x
-// and y beyond distance d are merged. A vertex w met in x's row at distance e
-// is a cofacet of diameter e exactly when D[y][w] < e (its other occurrence
-// came first); on a tie D[y][w] == e it is taken from y's row, which is merged
-// after x's at each distance. No per-cursor state beyond the two positions.
+// Lune part of an edge cursor (x, y) with diameter d: the vertices w with
+// D[x][w] <= d and D[y][w] <= d, largest first, taken 64 at a time as a bit
+// mask from which the even triangles are masked out (D's rows are read in
+// order; the parity of a word of triangles is two adjacency words).
+// Merge part: the neighbour rows of x and y beyond distance d are merged. A
+// vertex w met in x's row at distance e is a cofacet of diameter e exactly
+// when D[y][w] < e (its other occurrence came first); on a tie D[y][w] == e it
+// is taken from y's row, which is merged after x's at each distance.
+//
+// A walk whose V grows large switches from cursors to a sweep over the
+// triangles themselves, level by level in diameter (see "sweep mode" below).
 
 struct Cur1 {
     int32_t x = 0, y = 0;
@@ -681,6 +688,8 @@ struct Cur1 {
     float d = 0.0f;
     int32_t first = -1;          // known oldest cofacet vertex, emitted before anything else
     int32_t lune = -1;           // lune vertices <= lune are still to come (-1: done)
+    int32_t lw = -1;             // word of lune vertices cached in lm (-1: none)
+    uint64_t lm = 0;
     int32_t pa = -1, pb = -1;    // merge positions (pa < 0: merge not started)
     // The next cofacets in age order, produced in a batch while the cursor's
     // rows are in cache (their order does not depend on V; parity is read
@@ -808,50 +817,89 @@ struct RadixHeap {
     }
 };
 
+uint64_t *plane_scratch(int64_t n);
+
 template <class K>
 struct Walk1 {
     typedef typename K::T Key;
     const HostInstance &I;
     const Reducer &R;
-    int64_t n;
-    uint64_t *ebits;              // membership in V, one bit per edge index (all clear when idle)
+    int64_t n, W;                 // vertices, words per adjacency row
+    uint64_t *adj;                // V as adjacency bits (all clear when idle)
     std::vector<Cur1> cur;
     typename std::conditional<std::is_same<Key, uint64_t>::value, RadixHeap, MinHeap<Key>>::type
         heap;
     std::vector<uint64_t> V;      // edges of V (indices)
-    int64_t additions = 0, reads = 0, entries = 0;
+    int64_t additions = 0, reads = 0, entries = 0, levels = 0;
+    int threads = 1;
 
-    // ebits: the calling thread's scratch of C(n, 2) bits, all clear; it is
-    // left clear again when the walk ends.
-    Walk1(const HostInstance &I_, const Reducer &R_, uint64_t *ebits_)
-        : I(I_), R(R_), n(I_.n), ebits(ebits_) {}
-    ~Walk1() { clear_bits(); }
+    // adj_: the calling thread's scratch of n x ceil(n / 64) words, all
+    // clear; it is left clear again when the walk ends.
+    Walk1(const HostInstance &I_, const Reducer &R_, uint64_t *adj_, int threads_ = 1)
+        : I(I_), R(R_), n(I_.n), W((I_.n + 63) / 64), adj(adj_), threads(threads_) {}
+    ~Walk1() {
+        clear_bits();
+        clear_plane();
+    }
 
     static uint64_t edge_index(int x, int y) {
         return (uint64_t)x * (uint64_t)(x - 1) / 2 + (uint64_t)y;
     }
-    bool vbit(int a, int b) const {
-        const uint64_t e = a > b ? edge_index(a, b) : edge_index(b, a);
-        return (ebits[e >> 6] >> (e & 63)) & 1ull;
+    // Vertices x > y of the edge with index e.
+    static void edge_vertices(uint64_t e, int &x, int &y) {
+        uint64_t a = (uint64_t)((1.0 + std::sqrt(1.0 + 8.0 * (double)e)) / 2.0);
+        while (a * (a - 1) / 2 > e) --a;
+        while ((a + 1) * a / 2 <= e) ++a;
+        x = (int)a;
+        y = (int)(e - a * (a - 1) / 2);
     }
+    bool vbit(int a, int b) const { return (adj[(int64_t)a * W + (b >> 6)] >> (b & 63)) & 1ull; }
     void set_edge(int x, int y) {
-        const uint64_t e = edge_index(x, y);
-        ebits[e >> 6] |= 1ull << (e & 63);
+        adj[(int64_t)x * W + (y >> 6)] |= 1ull << (y & 63);
+        adj[(int64_t)y * W + (x >> 6)] |= 1ull << (x & 63);
     }
     void clear_bits() {
-        for (uint64_t e : V) ebits[e >> 6] = 0;
+        if ((int64_t)V.size() * 8 > n * W) {
+            std::memset(adj, 0, (size_t)(n * W) * sizeof(uint64_t));
+            return;
+        }
+        for (uint64_t e : V) {
+            int x, y;
+            edge_vertices(e, x, y);
+            adj[(int64_t)x * W + (y >> 6)] = 0;
+            adj[(int64_t)y * W + (x >> 6)] = 0;
+        }
     }
 
-    void start_merge(Cur1 &c) {
+    void start_merge(Cur1 &c) const {
         const uint64_t *rx = I.nbr + (int64_t)c.x * n, *ry = I.nbr + (int64_t)c.y * n;
         const uint64_t lim = ((uint64_t)float_bits(c.d) << 32) | 0xffffffffull;
         c.pa = (int32_t)(std::upper_bound(rx, rx + n, lim) - rx);
         c.pb = (int32_t)(std::upper_bound(ry, ry + n, lim) - ry);
     }
 
-    // Next cofacet of the cursor in age order, whatever its parity.
+    // Lune vertices of the cursor in word k: bit i set iff w = 64 k + i is
+    // within c.d of both x and y (x and y themselves excluded).
+    uint64_t lune_word(const Cur1 &c, int64_t k) const {
+        const float *Dx = I.D + (int64_t)c.x * I.ld, *Dy = I.D + (int64_t)c.y * I.ld;
+        const int64_t b = k << 6, e = std::min<int64_t>(b + 64, n);
+        const float d = c.d;
+        uint64_t m = 0;
+        for (int64_t i = b; i < e; ++i)
+            m |= (uint64_t)((Dx[i] <= d) & (Dy[i] <= d)) << (i - b);
+        if ((c.x >> 6) == k) m &= ~(1ull << (c.x & 63));
+        if ((c.y >> 6) == k) m &= ~(1ull << (c.y & 63));
+        return m;
+    }
+
+    // Next cofacet of the cursor in age order: every one of the merge part,
+    // the odd ones of the lune.
     bool raw_next(Cur1 &c) {
         ++entries;
+        return fetch(c);
+    }
+
+    bool fetch(Cur1 &c) const {
         if (c.bi == c.bn) {
             c.bi = c.bn = 0;
             while (!c.bend && c.bn < Cur1::NB) {
@@ -875,7 +923,7 @@ struct Walk1 {
     }
 
     // The cofacet after the current one, into (hw, hd); false if none.
-    bool step(Cur1 &c) {
+    bool step(Cur1 &c) const {
         if (c.first >= 0) {  // the oldest cofacet, known in advance
             c.hw = c.first;
             c.hd = c.d;
@@ -883,14 +931,24 @@ struct Walk1 {
             c.first = -1;
             return true;
         }
-        const float *Dx = I.D + (int64_t)c.x * I.ld, *Dy = I.D + (int64_t)c.y * I.ld;
         while (c.lune >= 0) {  // diameter d, largest vertex first
-            const int w = c.lune--;
-            if (Dx[w] <= c.d && Dy[w] <= c.d && w != c.x && w != c.y) {
+            const int64_t k = c.lune >> 6;
+            if (c.lw != k) {
+                c.lm = lune_word(c, k);
+                c.lw = (int32_t)k;
+            }
+            uint64_t m = c.lm;
+            const int sh = c.lune & 63;
+            if (sh < 63) m &= (2ull << sh) - 1;
+            m &= ~(adj[(int64_t)c.x * W + k] ^ adj[(int64_t)c.y * W + k]);  // odd ones only
+            if (m) {
+                const int w = (int)(k << 6) + 63 - __builtin_clzll(m);
+                c.lune = w - 1;
                 c.hw = w;
                 c.hd = c.d;
                 return true;
             }
+            c.lune = (int32_t)(k << 6) - 1;
         }
         if (!c.ties.empty()) {
             c.hw = c.ties.back();
@@ -900,6 +958,7 @@ struct Walk1 {
         }
         if (c.pa < 0) start_merge(c);
         const uint64_t *rx = I.nbr + (int64_t)c.x * n, *ry = I.nbr + (int64_t)c.y * n;
+        const float *Dx = I.D + (int64_t)c.x * I.ld, *Dy = I.D + (int64_t)c.y * I.ld;
         for (;;) {
             const uint32_t da = c.pa < n ? (uint32_t)(rx[c.pa] >> 32) : 0xffffffffu;
             const uint32_t db = c.pb < n ? (uint32_t)(ry[c.pb] >> 32) : 0xffffffffu;
@@ -936,7 +995,7 @@ struct Walk1 {
 
     // Consume every occurrence at distance bits bd in both rows; the cofacets
     // of diameter bd become the cursor's ties (sorted, largest at the back).
-    void merge_level(Cur1 &c, uint32_t bd) {
+    void merge_level(Cur1 &c, uint32_t bd) const {
         const uint64_t *rx = I.nbr + (int64_t)c.x * n, *ry = I.nbr + (int64_t)c.y * n;
         const float *Dx = I.D + (int64_t)c.x * I.ld, *Dy = I.D + (int64_t)c.y * I.ld;
         const float e = bits_float(bd);
@@ -968,7 +1027,7 @@ struct Walk1 {
     // Position a fresh cursor so that its next cofacet is the first one younger
     // than the triangle k = (dk, kv): a column whose entries up to k are known
     // to be zero need not list them.
-    void seek(Cur1 &c, float dk, const int *kv) {
+    void seek(Cur1 &c, float dk, const int *kv) const {
         c.first = -1;
         if (dk < c.d) return;  // every cofacet is younger than k
         if (dk == c.d) {  // lune vertices w (largest first) with index below k's
@@ -991,6 +1050,7 @@ struct Walk1 {
         while (!c.ties.empty() && !tri_before(c.x, c.y, c.ties.back(), kv)) c.ties.pop_back();
     }
 
+    // Parity of the cursor's head (the cursor's own edge is in V).
     bool odd(const Cur1 &c) const { return vbit(c.x, c.hw) == vbit(c.y, c.hw); }
 
     // Next cofacet with odd parity (hw = -1 if none).
@@ -999,11 +1059,18 @@ struct Walk1 {
             if (odd(c)) return;
     }
 
-    Key head_key(const Cur1 &c) const {
+    static void sort3(const Cur1 &c, int *v) {
         int a = c.x, b = c.y, w = c.hw;  // sort {x, y, w} decreasingly (x > y)
         if (w > a) std::swap(a, w), std::swap(b, w);
         else if (w > b) std::swap(b, w);
-        return K::make(c.hd, I.B->at(3, a) + I.B->at(2, b) + (uint64_t)w);
+        v[0] = a;
+        v[1] = b;
+        v[2] = w;
+    }
+    Key head_key(const Cur1 &c) const {
+        int v[3];
+        sort3(c, v);
+        return K::make(c.hd, I.B->at(3, v[0]) + I.B->at(2, v[1]) + (uint64_t)v[2]);
     }
 
     void push(int32_t ci) { heap.push({head_key(cur[ci]), ci}); }
@@ -1031,24 +1098,29 @@ struct Walk1 {
     // Restart the walk from the edge set newV (sorted, no repeats), whose
     // coboundary is known to vanish up to and including the entry k.
     void rebuild(std::vector<uint64_t> newV, u128 k) {
+        clear_plane();
+        sweep = false;
         clear_bits();
         cur.clear();
         heap.clear();
         V.swap(newV);
-        int v[2], kv[3];
+        for (uint64_t e : V) {
+            int x, y;
+            edge_vertices(e, x, y);
+            set_edge(x, y);
+        }
+        if (can_sweep() && V.size() >= SWEEP_MIN) {
+            enter_sweep(k);
+            return;
+        }
+        int kv[3];
         decode_host(*I.B, key_index(k), 2, n, kv);
         const float dk = key_diam(k);
         for (uint64_t e : V) {
-            decode_host(*I.B, e, 1, n, v);
-            set_edge(v[0], v[1]);
-        }
-        for (uint64_t e : V) {
-            decode_host(*I.B, e, 1, n, v);
             cur.emplace_back();
             Cur1 &c = cur.back();
-            c.x = v[0];
-            c.y = v[1];
-            c.d = I.dist(v[0], v[1]);
+            edge_vertices(e, c.x, c.y);
+            c.d = I.dist(c.x, c.y);
             c.lune = (int32_t)n - 1;
             seek(c, dk, kv);
             advance(c);
@@ -1060,14 +1132,18 @@ struct Walk1 {
     // pivot k of V: the pivot cancels and the walk restarts past it.
     void add_leftover(const std::vector<uint64_t> &b, u128 k) {
         ++additions;
-        std::vector<uint64_t> a = V, sum;
-        std::sort(a.begin(), a.end());
+        if (sweep) {
+            for (uint64_t e : b) toggle_edge(e);
+            return;
+        }
+        std::vector<uint64_t> a = edges(), sum;
         std::set_symmetric_difference(a.begin(), a.end(), b.begin(), b.end(),
                                       std::back_inserter(sum));
         rebuild(std::move(sum), k);
     }
 
     u128 pivot() {
+        if (sweep) return pivot_sweep();
         while (!heap.empty()) {
             const int32_t ci = heap.top().second;
             Cur1 &c = cur[ci];
@@ -1096,24 +1172,326 @@ struct Walk1 {
             int s[3], added;
             if (R.apparent_owner(k, s, &added)) {
                 ++additions;  // its oldest cofacet is the pivot, which adds `added`
-                add_edge(s[0], s[1], key_diam(k), added);
+                if (sweep) {
+                    toggle_edge(edge_index(s[0], s[1]));
+                } else if (vbit(s[0], s[1])) {
+                    // already in V (possible after a leftover's column was
+                    // added): the addition removes it, so restart past k
+                    std::vector<uint64_t> nv = edges(), one{edge_index(s[0], s[1])}, rest;
+                    std::set_symmetric_difference(nv.begin(), nv.end(), one.begin(), one.end(),
+                                                  std::back_inserter(rest));
+                    rebuild(std::move(rest), k);
+                } else {
+                    add_edge(s[0], s[1], key_diam(k), added);
+                    if (can_sweep() && V.size() >= SWEEP_MIN) enter_sweep(k);
+                }
                 continue;
             }
             return k;
         }
     }
 
+    // The edges of V, sorted (an edge listed twice has left V).
     std::vector<uint64_t> edges() const {
         std::vector<uint64_t> out = V;
         std::sort(out.begin(), out.end());
+        size_t o = 0;
+        for (size_t i = 0; i < out.size();) {
+            size_t j = i;
+            while (j < out.size() && out[j] == out[i]) ++j;
+            if ((j - i) & 1) out[o++] = out[i];
+            i = j;
+        }
+        out.resize(o);
         return out;
+    }
+
+    // ---- sweep mode --------------------------------------------------------
+    // Once V holds SWEEP_MIN edges the walk stops listing coboundaries and
+    // sweeps the triangles themselves, in age order, one diameter level at a
+    // time. The triangles of diameter e are the lune triangles {a, b, w} of
+    // the edges {a, b} of length e (w within e of a and of b); a triangle with
+    // several edges of length e belongs to the one with the largest index.
+    // With P[a] the set of vertices within the current level's diameter of a
+    // (kept up to date by setting two bits per edge as the sweep enters its
+    // level), an edge's lune is the word-wise P[a] & P[b], and the parity of
+    // its triangles is adj[a] ^ adj[b] ^ [ab in V]: a level costs a few word
+    // operations per 64 vertices however large V is. Parities are read from
+    // the bits when the sweep gets to a triangle, and every addition changes
+    // only entries at or after the pivot, so additions of any kind (apparent
+    // edges, a leftover's column, an edge that leaves V) are bit flips.
+    static constexpr size_t SWEEP_MIN = 256;
+    static constexpr int64_t SWEEP_NMAX = 8192;  // P and adj: n^2 / 8 bytes each per thread
+    bool sweep = false;
+    uint64_t *P = nullptr;        // n x W bits: w within the level's diameter of a (no self bits)
+    int64_t f1 = 0;               // next edge position in filtration order (level end)
+    float lvl_d = 0.0f;           // diameter of the current level
+    struct LevelEdge {
+        int a, b;                 // a > b
+        uint64_t idx;
+        int wpos;                 // its triangles {a, b, w} with w < wpos are still to come
+        int head;                 // several-edge levels: cached oldest odd triangle (w, -1: none)
+        uint32_t ver;             // version of the cached head
+    };
+    std::vector<LevelEdge> lev;
+    // Levels of several edges: the edges' cached heads in a max-heap by
+    // triangle index (stale entries are skipped by version), the level edges
+    // at each vertex, and the vertices whose edges' heads must be recomputed
+    // (an addition flips only triangles that contain the added edge).
+    std::vector<std::pair<uint64_t, std::pair<int32_t, uint32_t>>> lheap;
+    std::vector<int32_t> inc_start, inc_edge, inc_v, inc_order;
+    static constexpr size_t SMALL_LEVEL = 8;  // up to this many edges: no index, every head recomputed
+    std::vector<int32_t> dirty;
+    std::vector<char> is_dirty;
+
+    bool can_sweep() const { return I.edge_lo != nullptr && n <= SWEEP_NMAX; }
+
+    // Edge at position f of the filtration order (diameter ascending).
+    uint64_t edge_at(int64_t f) const { return I.edge_lo[I.nedges - 1 - f]; }
+    float diam_at(int64_t f) const { return bits_float(~I.edge_hi[I.nedges - 1 - f]); }
+
+    static uint64_t tri_index(const Binomial &B, int a, int b, int w) {
+        int v0 = a, v1 = b, v2 = w;  // a > b
+        if (v2 > v0) std::swap(v0, v2), std::swap(v1, v2);
+        else if (v2 > v1) std::swap(v1, v2);
+        return B.at(3, v0) + B.at(2, v1) + (uint64_t)v2;
+    }
+
+    // Enter the level [f0, f1) of equal diameter starting at f0: set its bits
+    // in P and list its edges with every triangle still to come.
+    void load_level(int64_t f0) {
+        lvl_d = diam_at(f0);
+        f1 = f0;
+        while (f1 < I.nedges && diam_at(f1) == lvl_d) ++f1;
+        lev.clear();
+        for (int64_t f = f0; f < f1; ++f) {
+            LevelEdge E;
+            E.idx = edge_at(f);
+            edge_vertices(E.idx, E.a, E.b);
+            E.wpos = (int)n;
+            E.head = -1;
+            E.ver = 0;
+            P[(int64_t)E.a * W + (E.b >> 6)] |= 1ull << (E.b & 63);
+            P[(int64_t)E.b * W + (E.a >> 6)] |= 1ull << (E.a & 63);
+            lev.push_back(E);
+        }
+        ++levels;
+        if (lev.size() > SMALL_LEVEL) build_level_index();
+    }
+
+    // Several-edge level: the incidence lists, every edge's head, the heap.
+    void build_level_index() {
+        const int m = (int)lev.size();
+        inc_v.clear();
+        for (int i = 0; i < m; ++i) {
+            inc_v.push_back(lev[i].a);
+            inc_v.push_back(lev[i].b);
+        }
+        std::vector<int32_t> &order = inc_order;
+        order.resize(2 * m);
+        for (int i = 0; i < 2 * m; ++i) order[i] = i;
+        std::sort(order.begin(), order.end(),
+                  [&](int32_t x, int32_t y) { return inc_v[x] < inc_v[y]; });
+        inc_start.assign(n + 1, 0);
+        inc_edge.resize(2 * m);
+        for (int i = 0; i < 2 * m; ++i) {
+            inc_edge[i] = order[i] >> 1;
+            ++inc_start[inc_v[order[i]] + 1];
+        }
+        for (int64_t v = 0; v < n; ++v) inc_start[v + 1] += inc_start[v];
+        if ((int64_t)is_dirty.size() < n) is_dirty.assign(n, 0);
+        dirty.clear();
+        lheap.clear();
+        for (int i = 0; i < m; ++i) refresh_head(i);
+    }
+
+    void refresh_head(int i) {
+        LevelEdge &E = lev[i];
+        E.head = level_head(E);
+        ++E.ver;
+        if (E.head >= 0) {
+            lheap.push_back({tri_index(*I.B, E.a, E.b, E.head), {i, E.ver}});
+            std::push_heap(lheap.begin(), lheap.end());
+        }
+    }
+
+    // Does the triangle {a, b, w} of level edge E belong to another edge of
+    // the level (one of its other edges has the same length and a larger
+    // index)?
+    bool taken_by_other(const LevelEdge &E, int w) const {
+        const float e = lvl_d;
+        if (I.dist(E.a, w) == e) {
+            const uint64_t o = E.a > w ? edge_index(E.a, w) : edge_index(w, E.a);
+            if (o > E.idx) return true;
+        }
+        if (I.dist(E.b, w) == e) {
+            const uint64_t o = E.b > w ? edge_index(E.b, w) : edge_index(w, E.b);
+            if (o > E.idx) return true;
+        }
+        return false;
+    }
+
+    // Oldest triangle of edge E still to come that is odd now (w, or -1).
+    int level_head(const LevelEdge &E) const {
+        const uint64_t *Pa = P + (int64_t)E.a * W, *Pb = P + (int64_t)E.b * W;
+        const uint64_t *Aa = adj + (int64_t)E.a * W, *Ab = adj + (int64_t)E.b * W;
+        const uint64_t flip = vbit(E.a, E.b) ? ~0ull : 0ull;
+        const bool shared = lev.size() > 1;
+        int top = E.wpos - 1;
+        while (top >= 0) {
+            const int64_t k = top >> 6;
+            uint64_t m = Pa[k] & Pb[k] & (Aa[k] ^ Ab[k] ^ flip);
+            const int sh = top & 63;
+            if (sh < 63) m &= (2ull << sh) - 1;
+            while (m) {
+                const int w = (int)(k << 6) + 63 - __builtin_clzll(m);
+                if (!shared || !taken_by_other(E, w)) return w;
+                m &= ~(1ull << (w & 63));
+            }
+            top = (int)(k << 6) - 1;
+        }
+        return -1;
+    }
+
+    // Start sweeping just past the entry k (the column is zero up to and
+    // including k); the bits of V are set.
+    void enter_sweep(u128 k) {
+        cur.clear();
+        heap.clear();
+        sweep = true;
+        P = plane_scratch(n);
+        const float dk = key_diam(k);
+        const uint64_t kidx = key_index(k);
+        // P: every edge shorter than dk (the neighbour rows are sorted by distance)
+        const uint32_t bd = float_bits(dk);
+        for (int64_t a = 0; a < n; ++a) {
+            const uint64_t *row = I.nbr + a * n;
+            uint64_t *Pa = P + a * W;
+            for (int64_t i = 0; i < n && (uint32_t)(row[i] >> 32) < bd; ++i) {
+                const int w = (int)(uint32_t)row[i];
+                if (w != a) Pa[w >> 6] |= 1ull << (w & 63);
+            }
+        }
+        // the level of dk (edges are in filtration order, diameter ascending)
+        int64_t lo = 0, hi = I.nedges;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (float_bits(diam_at(mid)) < bd) lo = mid + 1;
+            else hi = mid;
+        }
+        if (lo >= I.nedges || diam_at(lo) != dk) {  // cannot happen: k is a triangle inside the threshold
+            lev.clear();
+            f1 = lo;
+            return;
+        }
+        load_level(lo);
+        int kv[3];
+        decode_host(*I.B, kidx, 2, n, kv);
+        for (LevelEdge &E : lev) {  // triangles of index below k's are still to come
+            int l = -1, h = (int)n;
+            while (h - l > 1) {
+                const int mid = (l + h) >> 1;
+                if (tri_before(E.a, E.b, mid, kv)) l = mid;
+                else h = mid;
+            }
+            E.wpos = l + 1;
+        }
+        if (lev.size() > SMALL_LEVEL) build_level_index();  // heads from the positions just set
+    }
+
+    // Oldest nonzero entry in sweep mode; the sweep moves past it.
+    u128 pivot_sweep() {
+        for (;;) {
+            if (lev.size() == 1) {
+                LevelEdge &E = lev[0];
+                const int w = level_head(E);
+                if (w >= 0) {
+                    E.wpos = w;
+                    return age_key(lvl_d, tri_index(*I.B, E.a, E.b, w));
+                }
+            } else if (lev.size() <= SMALL_LEVEL) {
+                int best = -1, bw = -1;
+                uint64_t bidx = 0;
+                for (int i = 0; i < (int)lev.size(); ++i) {
+                    const int w = level_head(lev[i]);
+                    if (w < 0) continue;
+                    const uint64_t ti = tri_index(*I.B, lev[i].a, lev[i].b, w);
+                    if (best < 0 || ti > bidx) {
+                        best = i;
+                        bw = w;
+                        bidx = ti;
+                    }
+                }
+                if (best >= 0) {
+                    for (int i = 0; i < (int)lev.size(); ++i) {  // index >= bidx has been passed
+                        LevelEdge &E = lev[i];
+                        if (i == best) E.wpos = bw;
+                        else
+                            while (E.wpos > 0 && tri_index(*I.B, E.a, E.b, E.wpos - 1) > bidx)
+                                --E.wpos;
+                    }
+                    return age_key(lvl_d, bidx);
+                }
+            } else {
+                for (int32_t v : dirty) {
+                    is_dirty[v] = 0;
+                    for (int32_t j = inc_start[v]; j < inc_start[v + 1]; ++j) refresh_head(inc_edge[j]);
+                }
+                dirty.clear();
+                while (!lheap.empty()) {
+                    const auto top = lheap.front();
+                    std::pop_heap(lheap.begin(), lheap.end());
+                    lheap.pop_back();
+                    LevelEdge &E = lev[top.second.first];
+                    if (top.second.second != E.ver || E.head < 0) continue;  // stale
+                    E.wpos = E.head;  // taken: its younger triangles are still to come
+                    refresh_head(top.second.first);
+                    return age_key(lvl_d, top.first);
+                }
+            }
+            if (f1 >= I.nedges) {
+                lev.clear();
+                return NONE;
+            }
+            load_level(f1);
+        }
+    }
+
+    // A sweep-mode addition of the edge e: a bit flip.
+    void toggle_edge(uint64_t e) {
+        int x, y;
+        edge_vertices(e, x, y);
+        adj[(int64_t)x * W + (y >> 6)] ^= 1ull << (y & 63);
+        adj[(int64_t)y * W + (x >> 6)] ^= 1ull << (x & 63);
+        V.push_back(e);
+        if (lev.size() > SMALL_LEVEL)
+            for (int v : {x, y})
+                if (!is_dirty[v]) {
+                    is_dirty[v] = 1;
+                    dirty.push_back(v);
+                }
+    }
+
+    void clear_plane() {
+        if (P) std::memset(P, 0, (size_t)(n * W) * sizeof(uint64_t));
+        P = nullptr;
     }
 };
 
-// A clear bit set of C(n, 2) bits owned by the calling thread.
-uint64_t *edge_scratch(int64_t n) {
+// The bits P of a sweep (n rows of ceil(n / 64) words), owned by the calling
+// thread and clear.
+uint64_t *plane_scratch(int64_t n) {
     thread_local std::vector<uint64_t> bits;
-    const size_t words = (size_t)((n * (n - 1) / 2 + 63) / 64);
+    const size_t words = (size_t)(n * ((n + 63) / 64));
+    if (bits.size() < words) bits.assign(words, 0);
+    return bits.data();
+}
+
+// The adjacency bits of a walk (n rows of ceil(n / 64) words), owned by the
+// calling thread and clear.
+uint64_t *adjacency_scratch(int64_t n) {
+    thread_local std::vector<uint64_t> bits;
+    const size_t words = (size_t)(n * ((n + 63) / 64));
     if (bits.size() < words) bits.assign(words, 0);
     return bits.data();
 }
@@ -1125,7 +1503,7 @@ void reduce_p1(const HostInstance &I, const Leftover *left, int64_t nleft, int t
     std::vector<u128> cand(nleft, NONE);
     std::vector<std::vector<uint64_t>> V(nleft);  // reduced columns as edge sets
     std::vector<char> walked(nleft, 0);
-    std::vector<int64_t> adds(nleft, 0), reads(nleft, 0), entries(nleft, 0);
+    std::vector<int64_t> adds(nleft, 0), reads(nleft, 0), entries(nleft, 0), levels(nleft, 0);
 
     auto phase_a = [&](int64_t j) {
         const Leftover &L = left[j];
@@ -1138,7 +1516,7 @@ void reduce_p1(const HostInstance &I, const Leftover *left, int64_t nleft, int t
             cand[j] = k0;  // the unreduced pivot is free of apparent owners
             return;
         }
-        Walk1<K> W(I, R, edge_scratch(I.n));
+        Walk1<K> W(I, R, adjacency_scratch(I.n), threads);
         int v[2];
         decode_host(*I.B, L.sigma, 1, I.n, v);
         W.add_edge(v[0], v[1], L.diam, first_vertex(R, L, v));
@@ -1148,6 +1526,7 @@ void reduce_p1(const HostInstance &I, const Leftover *left, int64_t nleft, int t
         adds[j] += W.additions;
         reads[j] += W.reads;
         entries[j] += W.entries;
+        levels[j] += W.levels;
     };
     if (threads <= 1 || nleft < 16) {
         for (int64_t j = 0; j < nleft; ++j) phase_a(j);
@@ -1161,7 +1540,7 @@ void reduce_p1(const HostInstance &I, const Leftover *left, int64_t nleft, int t
         const Leftover &L = left[j];
         auto it = cand[j] != NONE ? owner.find(key_index(cand[j])) : owner.end();
         if (it != owner.end()) {
-            Walk1<K> W(I, R, edge_scratch(I.n));  // resume from the reduced column so far, whose pivot is cand[j]
+            Walk1<K> W(I, R, adjacency_scratch(I.n), threads);  // resume from the reduced column so far, whose pivot is cand[j]
             W.V = V[j];
             ++W.reads;
             W.add_leftover(V[it->second], cand[j]);
@@ -1170,6 +1549,7 @@ void reduce_p1(const HostInstance &I, const Leftover *left, int64_t nleft, int t
             adds[j] += W.additions;
             reads[j] += W.reads;
             entries[j] += W.entries;
+            levels[j] += W.levels;
             walked[j] = 1;
         }
         HostPair P;
@@ -1188,6 +1568,7 @@ void reduce_p1(const HostInstance &I, const Leftover *left, int64_t nleft, int t
         stats.additions += adds[j];
         stats.reads += reads[j];
         stats.entries += entries[j];
+        stats.levels += levels[j];
     }
 }
 

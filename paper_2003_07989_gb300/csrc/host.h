@@ -24,6 +24,12 @@ struct HostInstance {
     // pairs are recognised by testing them again
     const uint64_t *app_tau = nullptr;
     uint64_t napp = 0;
+    // dimension 1 only (may be null): every edge inside the threshold in
+    // coboundary order (diameter descending, index ascending), as the GPU
+    // sorted them: index and ~bits(diameter)
+    const uint64_t *edge_lo = nullptr;
+    const uint32_t *edge_hi = nullptr;
+    int64_t nedges = 0;
     float t = 0.0f;                 // threshold in use
     float dist(int a, int b) const { return D[(int64_t)a * ld + b]; }
 };
@@ -60,7 +66,7 @@ struct Kruskal {
 
 // ---- submatrix reduction ----------------------------------------------------
 struct ReduceStats {
-    int64_t free_pivot = 0, additions = 0, reads = 0, entries = 0;
+    int64_t free_pivot = 0, additions = 0, reads = 0, entries = 0, levels = 0;
 };
 
 // Run fn(0) .. fn(count - 1) on the library's persistent host threads, the

@@ -55,7 +55,7 @@ Workspace::~Workspace() {
     for (DevBuf *b : d)
         if (b->p) cudaFree(b->p);
     HostBuf *h[] = {&h_hi,    &h_lo,  &h_tau, &h_sigma, &h_left,
-                    &h_D,     &h_state, &h_mst, &h_up,  &h_nbr};
+                    &h_D,     &h_state, &h_mst, &h_up,  &h_nbr, &h_ehi, &h_elo};
     for (HostBuf *b : h)
         if (b->p) cudaFreeHost(b->p);
     DevBuf *bd[] = {&b_pts, &b_clouds, &b_order, &b_ctl, &b_D,   &b_mst,  &b_outs,
@@ -451,6 +451,7 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
 
     Kruskal K;
     K.init(n);
+    uint64_t edges_begin = 0, edges_count = 0;  // dimension-1 columns (MST edges included)
     std::vector<uint64_t> prev_deaths;  // host-found deaths of the previous dimension
     uint64_t prev_napp = 0;
 
@@ -491,6 +492,8 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
         S.threshold = t;
         I.t = t;
         const uint64_t cols = N - begin;
+        edges_begin = begin;
+        edges_count = cols;
 
         // ---- H0: Kruskal on the shortest edges, copied from the tail ----
         {
@@ -673,6 +676,23 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
             RPP_CK(cudaMemcpyAsync(htau, app_tau, napp * 8, cudaMemcpyDeviceToHost, s));
             I.app_tau = htau;
             I.napp = napp;
+            if (p == 1 && edges_count > 0) {  // the sorted edges, for the sweep of long walks
+                uint32_t *he;
+                uint64_t *hl;
+                RPP_TRY(ws.host(ws.h_ehi, edges_count * 4, (void **)&he));
+                RPP_TRY(ws.host(ws.h_elo, edges_count * 8, (void **)&hl));
+                RPP_CK(cudaMemcpyAsync(he, key_hi + edges_begin, edges_count * 4,
+                                       cudaMemcpyDeviceToHost, s));
+                RPP_CK(cudaMemcpyAsync(hl, key_lo + edges_begin, edges_count * 8,
+                                       cudaMemcpyDeviceToHost, s));
+                I.edge_hi = he;
+                I.edge_lo = hl;
+                I.nedges = (int64_t)edges_count;
+            } else {
+                I.edge_hi = nullptr;
+                I.edge_lo = nullptr;
+                I.nedges = 0;
+            }
             if (!I.nbr) {  // neighbour lists for the lazy coboundaries, once per instance
                 uint64_t *dn, *hn;
                 RPP_TRY(ws.dev(ws.nbr, (size_t)n * n * 8, (void **)&dn));
@@ -705,6 +725,7 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
             S.additions[p] = rs.additions;
             S.store_reads[p] = rs.reads;
             S.entries[p] = rs.entries;
+            S.sweep_levels[p] = rs.levels;
             red_ms += now_ms() - a;
         }
         // intervals of dimension p and the deaths that clear dimension p + 1
