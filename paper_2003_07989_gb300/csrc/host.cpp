@@ -1170,7 +1170,7 @@ struct Walk1 {
                 }
             }
             int s[3], added;
-            if (R.apparent_owner(k, s, &added)) {
+            if (sweep ? sweep_owner(s, &added) : R.apparent_owner(k, s, &added)) {
                 ++additions;  // its oldest cofacet is the pivot, which adds `added`
                 if (sweep) {
                     toggle_edge(edge_index(s[0], s[1]));
@@ -1234,6 +1234,7 @@ struct Walk1 {
         uint32_t ver;             // version of the cached head
     };
     std::vector<LevelEdge> lev;
+    int piv_a = -1, piv_b = -1, piv_w = -1;  // the last pivot's triangle
     // Levels of several edges: the edges' cached heads in a max-heap by
     // triangle index (stale entries are skipped by version), the level edges
     // at each vertex, and the vertices whose edges' heads must be recomputed
@@ -1338,6 +1339,15 @@ struct Walk1 {
         const uint64_t flip = vbit(E.a, E.b) ? ~0ull : 0ull;
         const bool shared = lev.size() > 1;
         int top = E.wpos - 1;
+        if (top < 0) return -1;
+        {  // most levels hold no odd triangle: test every word at once first
+            const int64_t kt = top >> 6;
+            const int sh = top & 63;
+            uint64_t any = (Pa[kt] & Pb[kt] & (Aa[kt] ^ Ab[kt] ^ flip)) &
+                           (sh < 63 ? (2ull << sh) - 1 : ~0ull);
+            for (int64_t k = 0; k < kt; ++k) any |= Pa[k] & Pb[k] & (Aa[k] ^ Ab[k] ^ flip);
+            if (!any) return -1;
+        }
         while (top >= 0) {
             const int64_t k = top >> 6;
             uint64_t m = Pa[k] & Pb[k] & (Aa[k] ^ Ab[k] ^ flip);
@@ -1407,6 +1417,7 @@ struct Walk1 {
                 const int w = level_head(E);
                 if (w >= 0) {
                     E.wpos = w;
+                    piv_a = E.a, piv_b = E.b, piv_w = w;
                     return age_key(lvl_d, tri_index(*I.B, E.a, E.b, w));
                 }
             } else if (lev.size() <= SMALL_LEVEL) {
@@ -1423,6 +1434,7 @@ struct Walk1 {
                     }
                 }
                 if (best >= 0) {
+                    piv_a = lev[best].a, piv_b = lev[best].b, piv_w = bw;
                     for (int i = 0; i < (int)lev.size(); ++i) {  // index >= bidx has been passed
                         LevelEdge &E = lev[i];
                         if (i == best) E.wpos = bw;
@@ -1445,6 +1457,7 @@ struct Walk1 {
                     LevelEdge &E = lev[top.second.first];
                     if (top.second.second != E.ver || E.head < 0) continue;  // stale
                     E.wpos = E.head;  // taken: its younger triangles are still to come
+                    piv_a = E.a, piv_b = E.b, piv_w = E.head;
                     refresh_head(top.second.first);
                     return age_key(lvl_d, top.first);
                 }
@@ -1455,6 +1468,36 @@ struct Walk1 {
             }
             load_level(f1);
         }
+    }
+
+    // The apparent column owning the last pivot, if any (as
+    // Reducer::apparent_owner, from the definition): its youngest facet s
+    // (largest diameter, then smallest index) owns it iff the pivot is the
+    // oldest cofacet of s, i.e. the vertex it adds to s is the largest vertex
+    // within the level's diameter of both ends of s, which P gives (s has the
+    // pivot's diameter, the current level's).
+    bool sweep_owner(int *s, int *added) const {
+        int v[3] = {piv_a, piv_b, piv_w};
+        if (v[2] > v[0]) std::swap(v[0], v[2]), std::swap(v[1], v[2]);
+        else if (v[2] > v[1]) std::swap(v[1], v[2]);
+        const float fd[3] = {I.dist(v[1], v[2]), I.dist(v[0], v[2]), I.dist(v[0], v[1])};
+        int r = 0;  // facets in increasing index: without v[0], v[1], v[2]
+        for (int i = 1; i < 3; ++i)
+            if (fd[i] > fd[r]) r = i;
+        if (fd[r] != lvl_d) return false;
+        const int x = r == 0 ? v[1] : v[0], y = r == 2 ? v[1] : v[2];
+        const uint64_t *Px = P + (int64_t)x * W, *Py = P + (int64_t)y * W;
+        for (int64_t k = W - 1; k >= 0; --k) {
+            const uint64_t m = Px[k] & Py[k];
+            if (m) {
+                if ((int)(k << 6) + 63 - __builtin_clzll(m) != v[r]) return false;
+                s[0] = x;
+                s[1] = y;
+                *added = v[r];
+                return true;
+            }
+        }
+        return false;
     }
 
     // A sweep-mode addition of the edge e: a bit flip.
