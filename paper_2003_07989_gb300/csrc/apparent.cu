@@ -49,6 +49,7 @@ __global__ void __launch_bounds__(256) k_apparent(
 
     bool have = false;
     int v[P + 1];
+    const float *row[P + 1];
     float diam = 0.0f, best_d = 0.0f;
     int scan = 0, best_v = -1;
 
@@ -59,6 +60,8 @@ __global__ void __launch_bounds__(256) k_apparent(
                 have = true;
                 diam = __uint_as_float(~key_hi[c]);
                 decode_simplex<P>(key_lo[c], B, n, v);
+#pragma unroll
+                for (int i = 0; i <= P; ++i) row[i] = D + (int64_t)v[i] * ld;
                 scan = (int)n - 1;
                 best_d = __uint_as_float(0x7f800000u);
                 best_v = -1;
@@ -78,7 +81,7 @@ __global__ void __launch_bounds__(256) k_apparent(
                 float m = 0.0f;
 #pragma unroll
                 for (int i = 0; i <= P; ++i) {
-                    dv[i] = D[(int64_t)v[i] * ld + x];
+                    dv[i] = row[i][x];
                     m = fmaxf(m, dv[i]);
                 }
                 ok = m <= diam;
@@ -108,7 +111,7 @@ __global__ void __launch_bounds__(256) k_apparent(
 #pragma unroll
                                 for (int b = a + 1; b <= P; ++b)
                                     if (a != i && b != i)
-                                        fd = fmaxf(fd, D[(int64_t)v[a] * ld + v[b]]);
+                                        fd = fmaxf(fd, row[a][v[b]]);
                             if (fd == diam) apparent = false;
                         }
                     }

@@ -513,7 +513,7 @@ BatchPlan plan_g(int nmax, int dimcap, BatchConfig cfg, int sms) {
     P.dimcap = dimcap;
     P.cfg = cfg;
     P.smem = batch_smem_bytes(nmax, nmax * dimcap);
-    cudaFuncSetAttribute(k_batch_h1<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem);
+    allow_dynamic_smem((const void *)k_batch_h1<G>, P.smem);
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_h1<G>, cfg.threads, P.smem);
     P.blocks = std::max(1, sms * std::max(1, per_sm));
@@ -558,7 +558,7 @@ void launch_batch_rows(const float *Dbuf, const BatchCloud *clouds, const int32_
                        cudaStream_t s) {
     if (njobs <= 0) return;
     const size_t smem = (size_t)pow2_at_least(nmax) * 8;
-    cudaFuncSetAttribute(k_batch_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    allow_dynamic_smem((const void *)k_batch_rows, smem);
     ++g_launches;
     k_batch_rows<<<dim3((unsigned)nmax, (unsigned)njobs), 256, smem, s>>>(Dbuf, clouds, jobs,
                                                                           out_off, Dout, nbr);

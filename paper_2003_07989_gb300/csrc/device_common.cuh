@@ -23,9 +23,25 @@ __device__ __forceinline__ int largest_vertex(const uint64_t *Bk, uint64_t c, in
     return lo;
 }
 
+// Vertices x > y of the edge with index c = C(x, 2) + y: x from the inverse
+// of C(x, 2) = x (x - 1) / 2 through a float square root, then exact integer
+// corrections until C(x, 2) <= c < C(x + 1, 2).
+__device__ __forceinline__ void decode_edge(uint64_t c, int *v) {
+    int x = (int)((1.0f + sqrtf(8.0f * (float)c + 1.0f)) * 0.5f);
+    if (x < 1) x = 1;
+    while ((uint64_t)x * (uint64_t)(x - 1) / 2 > c) --x;
+    while ((uint64_t)(x + 1) * (uint64_t)x / 2 <= c) ++x;
+    v[0] = x;
+    v[1] = (int)(c - (uint64_t)x * (uint64_t)(x - 1) / 2);
+}
+
 // Decode a dimension-P index into vertices v[0] > v[1] > ... > v[P].
 template <int P>
 __device__ __forceinline__ void decode_simplex(uint64_t c, const uint64_t *B, int64_t n, int *v) {
+    if constexpr (P == 1) {
+        decode_edge(c, v);
+        return;
+    }
     int hi = (int)n - 1;
 #pragma unroll
     for (int i = 0; i <= P; ++i) {

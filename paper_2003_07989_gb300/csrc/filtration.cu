@@ -92,8 +92,7 @@ void build_p(const float *D, int64_t ld, int64_t n, const uint64_t *binom, uint6
              cudaStream_t s) {
     const size_t table = (size_t)(P + 2) * (n + 1) * sizeof(uint64_t);
     const bool smem = table <= 160 * 1024;
-    if (smem) cudaFuncSetAttribute(k_build_columns<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)table);
+    if (smem) allow_dynamic_smem((const void *)k_build_columns<P>, table);
     uint64_t blocks = (total + 255) / 256;
     const uint64_t cap = 152ull * 8;
     if (blocks > cap) blocks = cap;

@@ -1224,7 +1224,12 @@ struct Walk1 {
     static constexpr int64_t SWEEP_NMAX = 8192;  // P and adj: n^2 / 8 bytes each per thread
     bool sweep = false;
     uint64_t *P = nullptr;        // n x W bits: w within the level's diameter of a (no self bits)
-    int64_t f1 = 0;               // next edge position in filtration order (level end)
+    int64_t f1 = 0;               // array source: next edge position in filtration order
+    // Row source (no edge array): the neighbour rows merged by a min-heap of
+    // (distance bits, vertex a) over each row's entries w < a, so every edge
+    // comes once; rpos[a] is the next entry of row a.
+    std::vector<std::pair<uint32_t, int32_t>> rheap;
+    std::vector<int32_t> rpos;
     float lvl_d = 0.0f;           // diameter of the current level
     struct LevelEdge {
         int a, b;                 // a > b
@@ -1245,7 +1250,7 @@ struct Walk1 {
     std::vector<int32_t> dirty;
     std::vector<char> is_dirty;
 
-    bool can_sweep() const { return I.edge_lo != nullptr && n <= SWEEP_NMAX; }
+    bool can_sweep() const { return n <= SWEEP_NMAX; }
 
     // Edge at position f of the filtration order (diameter ascending).
     uint64_t edge_at(int64_t f) const { return I.edge_lo[I.nedges - 1 - f]; }
@@ -1258,26 +1263,63 @@ struct Walk1 {
         return B.at(3, v0) + B.at(2, v1) + (uint64_t)v2;
     }
 
-    // Enter the level [f0, f1) of equal diameter starting at f0: set its bits
-    // in P and list its edges with every triangle still to come.
-    void load_level(int64_t f0) {
-        lvl_d = diam_at(f0);
-        f1 = f0;
-        while (f1 < I.nedges && diam_at(f1) == lvl_d) ++f1;
+    void level_edge(int a, int b) {  // a > b
+        LevelEdge E;
+        E.a = a;
+        E.b = b;
+        E.idx = edge_index(a, b);
+        E.wpos = (int)n;
+        E.head = -1;
+        E.ver = 0;
+        P[(int64_t)a * W + (b >> 6)] |= 1ull << (b & 63);
+        P[(int64_t)b * W + (a >> 6)] |= 1ull << (a & 63);
+        lev.push_back(E);
+    }
+
+    // Row source: move row a to its next entry w < a inside the threshold
+    // and queue it (a row with none left leaves the heap).
+    void row_push(int a) {
+        const uint64_t *row = I.nbr + (int64_t)a * n;
+        int32_t &i = rpos[a];
+        while (i < n && (int)(uint32_t)row[i] >= a) ++i;
+        if (i >= n) return;
+        const uint32_t db = (uint32_t)(row[i] >> 32);
+        if (bits_float(db) > I.t) return;
+        rheap.push_back({db, a});
+        std::push_heap(rheap.begin(), rheap.end(), std::greater<std::pair<uint32_t, int32_t>>());
+    }
+
+    // Enter the next level of equal diameter: set its bits in P and list its
+    // edges with every triangle still to come; false when no edge is left.
+    bool next_level() {
         lev.clear();
-        for (int64_t f = f0; f < f1; ++f) {
-            LevelEdge E;
-            E.idx = edge_at(f);
-            edge_vertices(E.idx, E.a, E.b);
-            E.wpos = (int)n;
-            E.head = -1;
-            E.ver = 0;
-            P[(int64_t)E.a * W + (E.b >> 6)] |= 1ull << (E.b & 63);
-            P[(int64_t)E.b * W + (E.a >> 6)] |= 1ull << (E.a & 63);
-            lev.push_back(E);
+        if (I.edge_lo) {
+            if (f1 >= I.nedges) return false;
+            const int64_t f0 = f1;
+            lvl_d = diam_at(f0);
+            while (f1 < I.nedges && diam_at(f1) == lvl_d) ++f1;
+            for (int64_t f = f0; f < f1; ++f) {
+                int a, b;
+                edge_vertices(edge_at(f), a, b);
+                level_edge(a, b);
+            }
+        } else {
+            if (rheap.empty()) return false;
+            const uint32_t db = rheap.front().first;
+            lvl_d = bits_float(db);
+            while (!rheap.empty() && rheap.front().first == db) {
+                std::pop_heap(rheap.begin(), rheap.end(),
+                              std::greater<std::pair<uint32_t, int32_t>>());
+                const int a = rheap.back().second;
+                rheap.pop_back();
+                level_edge(a, (int)(uint32_t)I.nbr[(int64_t)a * n + rpos[a]]);
+                ++rpos[a];
+                row_push(a);
+            }
         }
         ++levels;
         if (lev.size() > SMALL_LEVEL) build_level_index();
+        return true;
     }
 
     // Several-edge level: the incidence lists, every edge's head, the heap.
@@ -1382,19 +1424,29 @@ struct Walk1 {
                 if (w != a) Pa[w >> 6] |= 1ull << (w & 63);
             }
         }
-        // the level of dk (edges are in filtration order, diameter ascending)
-        int64_t lo = 0, hi = I.nedges;
-        while (lo < hi) {
-            const int64_t mid = (lo + hi) >> 1;
-            if (float_bits(diam_at(mid)) < bd) lo = mid + 1;
-            else hi = mid;
-        }
-        if (lo >= I.nedges || diam_at(lo) != dk) {  // cannot happen: k is a triangle inside the threshold
-            lev.clear();
+        // position the level source at the first edge of length dk
+        if (I.edge_lo) {  // edges in filtration order, diameter ascending
+            int64_t lo = 0, hi = I.nedges;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (float_bits(diam_at(mid)) < bd) lo = mid + 1;
+                else hi = mid;
+            }
             f1 = lo;
+        } else {
+            rheap.clear();
+            rpos.assign(n, 0);
+            const uint64_t lim = (uint64_t)bd << 32;
+            for (int64_t a = 0; a < n; ++a) {
+                const uint64_t *row = I.nbr + a * n;
+                rpos[a] = (int32_t)(std::lower_bound(row, row + n, lim) - row);
+                row_push((int)a);
+            }
+        }
+        if (!next_level() || lvl_d != dk) {  // cannot happen: k is a triangle inside the threshold
+            lev.clear();
             return;
         }
-        load_level(lo);
         int kv[3];
         decode_host(*I.B, kidx, 2, n, kv);
         for (LevelEdge &E : lev) {  // triangles of index below k's are still to come
@@ -1462,11 +1514,7 @@ struct Walk1 {
                     return age_key(lvl_d, top.first);
                 }
             }
-            if (f1 >= I.nedges) {
-                lev.clear();
-                return NONE;
-            }
-            load_level(f1);
+            if (!next_level()) return NONE;
         }
     }
 

@@ -189,6 +189,12 @@ void launch_batch_rows(const float *Dbuf, const BatchCloud *clouds, const int32_
 void launch_gather_points(const float *const *src, const BatchCloud *clouds, int nclouds,
                           float *pts, cudaStream_t s);
 
+// Allow kernel fn at least `bytes` of dynamic shared memory on the current
+// device. The attribute belongs to the kernel, not to a launch, so callers on
+// several threads must only ever raise it: a per-(device, kernel) maximum
+// under a lock. Returns the error of cudaFuncSetAttribute, if any.
+cudaError_t allow_dynamic_smem(const void *fn, size_t bytes);
+
 // ---- error helpers ---------------------------------------------------------
 void set_last_error(const std::string &msg);
 

@@ -46,7 +46,7 @@ bool launch_sort_rows(const float *D, int64_t ld, int64_t n, uint64_t *out, cuda
     while (pow2 < n) pow2 <<= 1;
     const size_t smem = (size_t)pow2 * 8;
     if (smem > 200 * 1024) return false;
-    cudaFuncSetAttribute(k_sort_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    allow_dynamic_smem((const void *)k_sort_rows, smem);
     ++g_launches;
     k_sort_rows<<<(unsigned)n, 512, smem, s>>>(D, ld, n, pow2, out);
     return true;

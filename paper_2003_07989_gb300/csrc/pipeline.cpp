@@ -16,6 +16,8 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <thread>
 
 namespace rpp {
@@ -213,6 +215,20 @@ void fill_binomial(int64_t n, int kmax, std::vector<uint64_t> &store, Binomial &
     B.n = n;
     B.kmax = kmax;
     B.host = store.data();
+}
+
+cudaError_t allow_dynamic_smem(const void *fn, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void *>, size_t> allowed;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> g(mu);
+    size_t &a = allowed[{dev, fn}];
+    if (bytes <= a) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) a = bytes;
+    return e;
 }
 
 bool is_device_pointer(const void *p) {

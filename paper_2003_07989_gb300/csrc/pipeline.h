@@ -39,7 +39,8 @@ struct Status {
         if (e_ != cudaSuccess) {                                                      \
             ::rpp::Status st_;                                                        \
             st_.code = RPP_E_CUDA;                                                    \
-            st_.msg = std::string(#call) + ": " + cudaGetErrorString(e_);             \
+            st_.msg = std::string(#call) + ": " + cudaGetErrorString(e_) + " (" +     \
+                      ::rpp::source_name(__FILE__) + ":" + std::to_string(__LINE__) + ")"; \
             return st_;                                                               \
         }                                                                             \
     } while (0)
@@ -51,6 +52,13 @@ struct Status {
     } while (0)
 
 double now_ms();
+// The file name of a source path (for error messages).
+inline const char *source_name(const char *path) {
+    const char *b = path;
+    for (const char *p = path; *p; ++p)
+        if (*p == '/') b = p + 1;
+    return b;
+}
 int bits_for(uint64_t x);  // bits needed to write x (0 for x = 0)
 Status fail(rpp_status code, const std::string &msg);
 float bits_to_float(uint32_t b);
