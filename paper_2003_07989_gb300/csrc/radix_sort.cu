@@ -7,8 +7,10 @@
 // least significant upwards, so each pass must be stable. One histogram kernel
 // first counts every digit position at once; passes whose digit is the same
 // for every key are skipped. Each remaining pass is reduce-then-scan:
-//   count   : per 2048-key tile, a 256-bin histogram of the pass's digit;
-//   scan    : one block turns the tile histograms into global offsets;
+//   count   : per 2048-key tile, a 256-bin histogram of the pass's digit,
+//             stored digit-major (all tiles of digit 0, then digit 1, ...);
+//   scan    : one block per digit: the digit's start among all keys (from the
+//             up-front histogram) plus an exclusive scan over the tiles;
 //   scatter : each tile ranks its keys stably (warp match + per-warp counts in
 //             tile order) and writes them to their final positions.
 #include <cuda_runtime.h>
@@ -69,72 +71,52 @@ __global__ void __launch_bounds__(SORT_THREADS) k_count(const uint32_t *__restri
         if (i < n) atomicAdd(&sh[digit_of(hi, lo, i, sel)], 1u);
     }
     __syncthreads();
-    counts[(uint64_t)blockIdx.x * RADIX + threadIdx.x] = sh[threadIdx.x];
+    counts[(uint64_t)threadIdx.x * gridDim.x + blockIdx.x] = sh[threadIdx.x];  // digit-major
 }
 
-// One block of SCAN_PARTS x 256 threads: thread (part, d) owns digit d over a
-// contiguous range of tiles. Offsets of (tile, d) = start of digit d among all
-// keys + keys with digit d in earlier tiles.
-constexpr int SCAN_PARTS = 4;
+// Block d owns digit d: offsets of (tile, d) = keys with a smaller digit (an
+// exclusive scan of the digit totals, redone by every block) + keys with
+// digit d in earlier tiles (an exclusive scan over this digit's tile counts).
+constexpr int SCAN_THREADS = 256;
 
-__global__ void __launch_bounds__(RADIX *SCAN_PARTS) k_scan(uint32_t *__restrict__ counts,
-                                                            uint64_t ntiles,
-                                                            const uint32_t *__restrict__ digit_total) {
-    __shared__ uint32_t warp_sums[RADIX / 32];
-    __shared__ uint32_t base[RADIX];
-    __shared__ uint32_t part_sum[SCAN_PARTS][RADIX];
-    const int d = threadIdx.x & (RADIX - 1), part = threadIdx.x / RADIX;
-    const int lane = d & 31, w = d >> 5;
-    const uint64_t per = (ntiles + SCAN_PARTS - 1) / SCAN_PARTS;
-    const uint64_t t0 = part * per, t1 = t0 + per < ntiles ? t0 + per : ntiles;
-    // 1. keys with digit d in this part's tiles
-    uint32_t sum = 0;
-    uint64_t t = t0;
-    for (; t + 8 <= t1; t += 8) {
-        uint32_t c[8];
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_digit(uint32_t *__restrict__ counts,
+                                                             uint64_t ntiles,
+                                                             const uint32_t *__restrict__ digit_total) {
+    __shared__ uint32_t warp_sums[SCAN_THREADS / 32];
+    __shared__ uint32_t carry;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int d = blockIdx.x;
+    // 1. start of digit d: sum of the totals of digits below d
+    uint32_t x = tid < d ? digit_total[tid] : 0u;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) c[k] = counts[(t + k) * RADIX + d];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) sum += c[k];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(FULL_MASK, x, o);
+    if (lane == 0) warp_sums[w] = x;
+    __syncthreads();
+    if (tid == 0) {
+        uint32_t b = 0;
+        for (int i = 0; i < SCAN_THREADS / 32; ++i) b += warp_sums[i];
+        carry = b;
     }
-    for (; t < t1; ++t) sum += counts[t * RADIX + d];
-    part_sum[part][d] = sum;
-    // 2. exclusive scan of the digit totals across digits (first 256 threads)
-    uint32_t x = 0, incl = 0;
-    if (part == 0) {
-        x = digit_total[d];
-        incl = x;
+    __syncthreads();
+    // 2. running exclusive scan over the tiles, SCAN_THREADS tiles per round
+    uint32_t *row = counts + (uint64_t)d * ntiles;
+    for (uint64_t t0 = 0; t0 < ntiles; t0 += SCAN_THREADS) {
+        const uint64_t t = t0 + tid;
+        const uint32_t c = t < ntiles ? row[t] : 0u;
+        uint32_t incl = c;
+#pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(FULL_MASK, incl, o);
+            const uint32_t y = __shfl_up_sync(FULL_MASK, incl, o);
             if (lane >= o) incl += y;
         }
+        __syncthreads();  // carry and warp_sums of the previous round are read
         if (lane == 31) warp_sums[w] = incl;
-    }
-    __syncthreads();
-    if (part == 0) {
-        uint32_t before = 0;
+        __syncthreads();
+        uint32_t before = carry;
         for (int i = 0; i < w; ++i) before += warp_sums[i];
-        base[d] = before + incl - x;
-    }
-    __syncthreads();
-    // 3. running offsets over this part's tiles
-    uint32_t run = base[d];
-    for (int q = 0; q < part; ++q) run += part_sum[q][d];
-    t = t0;
-    for (; t + 8 <= t1; t += 8) {
-        uint32_t c[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) c[k] = counts[(t + k) * RADIX + d];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            counts[(t + k) * RADIX + d] = run;
-            run += c[k];
-        }
-    }
-    for (; t < t1; ++t) {
-        uint32_t c = counts[t * RADIX + d];
-        counts[t * RADIX + d] = run;
-        run += c;
+        if (t < ntiles) row[t] = before + incl - c;
+        __syncthreads();
+        if (tid == SCAN_THREADS - 1) carry = before + incl;
     }
 }
 
@@ -147,7 +129,7 @@ __global__ void __launch_bounds__(SORT_THREADS) k_scatter(
     __shared__ uint32_t s_run[RADIX];
     __shared__ uint32_t s_warp[WARPS][RADIX];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    s_run[tid] = offsets[(uint64_t)blockIdx.x * RADIX + tid];
+    s_run[tid] = offsets[(uint64_t)tid * gridDim.x + blockIdx.x];
     const uint64_t base = (uint64_t)blockIdx.x * SORT_TILE;
     for (int j = 0; j < SORT_ITEMS; ++j) {
         const uint64_t i = base + (uint64_t)j * SORT_THREADS + tid;
@@ -220,7 +202,7 @@ void radix_sort(uint32_t *hi, uint64_t *lo, uint64_t *val, uint32_t *tmp_hi, uin
         ++g_launches;
         k_count<<<(unsigned)ntiles, SORT_THREADS, 0, s>>>(hi_a, lo_a, n, sel, tile_counts);
         ++g_launches;
-        k_scan<<<1, RADIX * SCAN_PARTS, 0, s>>>(tile_counts, ntiles, digit_hist + sel * RADIX);
+        k_scan_digit<<<RADIX, SCAN_THREADS, 0, s>>>(tile_counts, ntiles, digit_hist + sel * RADIX);
         ++g_launches;
         k_scatter<<<(unsigned)ntiles, SORT_THREADS, 0, s>>>(
             hi_a, lo_a, val_a, hi_a ? hi_b : nullptr, lo_b, val_a ? val_b : nullptr, n, sel,
@@ -268,7 +250,7 @@ void radix_sort_noalloc(uint32_t *hi, uint64_t *lo, uint32_t *tmp_hi, uint64_t *
         ++g_launches;
         k_count<<<(unsigned)ntiles, SORT_THREADS, 0, s>>>(hi_a, lo_a, n, sel, tile_counts);
         ++g_launches;
-        k_scan<<<1, RADIX * SCAN_PARTS, 0, s>>>(tile_counts, ntiles, digit_hist + sel * RADIX);
+        k_scan_digit<<<RADIX, SCAN_THREADS, 0, s>>>(tile_counts, ntiles, digit_hist + sel * RADIX);
         ++g_launches;
         k_scatter<<<(unsigned)ntiles, SORT_THREADS, 0, s>>>(hi_a, lo_a, nullptr, hi_b, lo_b,
                                                             nullptr, n, sel, tile_counts);

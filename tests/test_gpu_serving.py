@@ -101,3 +101,19 @@ def test_server_poll_unknown_ticket(rpp):
         assert e.value.status == N.RPP_E_INVALID
     finally:
         srv.close()
+
+
+def test_served_mixed_buckets_under_load(rpp):
+    # many slots launching clouds of every size bucket (32 .. 1024 points, up
+    # to 12 dimensions) at once: per-kernel launch limits are shared by all
+    # slots, and each result must still equal its single-instance result
+    reqs = I.serving_requests(160, seed=11, n_range=(32, 1024), dim_range=(2, 12))
+    alone = [rpp.rpp_barcodes(r.points, max_dim=1, quantile=r.threshold_quantile)
+             for r in reqs]
+    srv = rpp.Server(max_slots=8, max_batch=16)
+    try:
+        tickets = [srv.submit(r.points, 1, quantile=r.threshold_quantile) for r in reqs]
+        for t, a in zip(tickets, alone):
+            assert _same(srv.poll(t), a)
+    finally:
+        srv.close()
