@@ -46,6 +46,8 @@ def parse_args():
     ap.add_argument("--serving-requests", type=int, default=512,
                     help="requests of the serving section (0 skips it)")
     ap.add_argument("--serving-slots", type=int, default=8)
+    ap.add_argument("--no-census", action="store_true",
+                    help="skip the apparent-pair census of random edge orders")
     return ap.parse_args()
 
 
@@ -273,6 +275,35 @@ def serving_bench(rpp, count: int, slots: int):
 
 
 # ---------------------------------------------------------------------------
+# apparent-pair census of random edge orders (the paper's apparent-rate experiment)
+
+
+def census_bench(rpp, torch, dev, ctx):
+    """Dimension-1 apparent fraction of uniformly random total orders of the
+    C(n,2) edges (the paper's random permutations of 1..C(n,2)), full
+    filtration, one sample per n; beside the paper's value at 10,000 points
+    (the average of ten samples) and the theorem's upper bound (n-2)/n."""
+    from paper_2003_07989_gb300 import inputs as I
+    out = []
+    for n in (1000, 4000, 10000):
+        D = torch.from_numpy(I.rank_distances(n, seed=0)).to(dev)
+        rpp.rpp_apparent_census(D, kind="distances", context=ctx)  # warm-up (allocations)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        st = rpp.rpp_apparent_census(D, kind="distances", context=ctx)
+        wall = time.perf_counter() - t0
+        frac = st["apparent"][1] / st["candidates"][1]
+        out.append({"n": n, "edges": st["candidates"][1], "apparent": st["apparent"][1],
+                    "fraction": frac, "upper_bound": (n - 2) / n,
+                    "apparent_pass_ms": st["stage_ms"][4], "wall_ms": 1e3 * wall,
+                    "edges_per_s": st["candidates"][1] / wall})
+        del D
+    return {"samples": out, "paper_fraction_at_10000": 0.991127743,
+            "workload": "random total order of the edges (distinct float32 values), seed 0, "
+                        "dimension 1, full filtration, no reduction"}
+
+
+# ---------------------------------------------------------------------------
 # the oracle as the CPU baseline / reference arm
 
 
@@ -441,6 +472,7 @@ def main():
     serving = None
     if args.serving_requests > 0:
         serving = serving_bench(rpp, args.serving_requests, args.serving_slots)
+    census = None if args.no_census else census_bench(rpp, torch, dev, ctx)
     h2d = X.nbytes
     d2h = sum(len(iv) * (8 + 16) for iv in e2e_results[0].intervals)
     line = {
@@ -459,6 +491,7 @@ def main():
         "roofline": roofline,
         "cpu_baseline": cpu,
         "serving": serving,
+        "apparent_census": census,
         "breakdown": {
             "kernels": kernels,
             "host_reduce_ms": statistics.mean(s["ms_host_reduce"] for s in st),

@@ -147,6 +147,20 @@ rpp_status rpp_barcodes_quantile(rpp_context *ctx, const float *data, rpp_input_
                                  int64_t n, int32_t dim, int32_t max_dim, float quantile,
                                  void *stream, rpp_result **out);
 
+/* Apparent-pair census of dimension 1 (Sec. "Experiments on the Apparent
+ * Pairs Rate" and its figure of the apparent fraction): on the full
+ * filtration (every edge: neither a threshold nor the enclosing radius cuts
+ * it) the edges are built and sorted, Kruskal's merging edges are cleared,
+ * and the apparent-pair pass (Alg. 3) tests every other edge; the submatrix
+ * reduction does not run. On success *out (caller-owned) holds
+ * candidates[1] = C(n,2) edges, cleared[1] (merging edges), apparent[1] and
+ * leftover[1] (cleared + apparent + leftover = C(n,2)) and the stage times;
+ * the apparent fraction of the paper's figure is apparent[1] / C(n,2).
+ * data, kind, n, dim and stream as in rpp_barcodes.
+ * Errors: RPP_E_INVALID, RPP_E_OVERFLOW, RPP_E_NOMEM, RPP_E_CUDA. */
+rpp_status rpp_apparent_census(rpp_context *ctx, const float *data, rpp_input_kind kind,
+                               int64_t n, int32_t dim, void *stream, rpp_stats *out);
+
 /* Number of intervals of dimension p (0 <= p <= max_dim) in a result. */
 int64_t rpp_result_count(const rpp_result *res, int32_t p);
 /* Intervals of dimension p, host memory owned by the result, sorted by

@@ -12,11 +12,12 @@ The build step is ``paper_2003_07989_gb300.build.build()``. Importing the
 binding functions raises if the library was not built.
 """
 from ._native import RppError
-from .api import (Barcodes, Context, Server, default_context, rpp_barcodes,
-                  rpp_barcodes_batched, rpp_distance_matrix)
+from .api import (Barcodes, Context, Server, default_context, rpp_apparent_census,
+                  rpp_barcodes, rpp_barcodes_batched, rpp_distance_matrix)
 
-__all__ = ["Barcodes", "Context", "RppError", "Server", "default_context", "rpp_barcodes",
-           "rpp_barcodes_batched", "rpp_distance_matrix", "rips_persistence", "total_persistence"]
+__all__ = ["Barcodes", "Context", "RppError", "Server", "default_context", "rpp_apparent_census",
+           "rpp_barcodes", "rpp_barcodes_batched", "rpp_distance_matrix", "rips_persistence",
+           "total_persistence"]
 
 
 def __getattr__(name):

@@ -22,7 +22,7 @@ EXPORTED = [
     "rpp_server_create", "rpp_server_submit", "rpp_server_poll", "rpp_server_destroy",
     "rpp_status_string", "rpp_last_error", "rpp_distance_matrix", "rpp_context_set_record",
     "rpp_result_columns", "rpp_result_apparent", "rpp_filtration_edges_noalloc",
-    "rpp_context_set_batch", "rpp_context_batch_tuning",
+    "rpp_context_set_batch", "rpp_context_batch_tuning", "rpp_apparent_census",
 ]
 RPP_RECORD_COLUMNS, RPP_RECORD_APPARENT, RPP_RECORD_TIMING = 1, 2, 4
 STAGES = ["distance", "enclosing_radius", "build_columns", "sort_columns", "apparent",
@@ -83,6 +83,7 @@ def lib():
     L.rpp_barcodes.argtypes = [vp, vp, C.c_int, i64, i32, i32, C.c_float, vp, C.POINTER(vp)]
     L.rpp_barcodes_quantile.argtypes = [vp, vp, C.c_int, i64, i32, i32, C.c_float, vp,
                                         C.POINTER(vp)]
+    L.rpp_apparent_census.argtypes = [vp, vp, C.c_int, i64, i32, vp, C.POINTER(Stats)]
     L.rpp_result_count.argtypes = [vp, i32]
     L.rpp_result_count.restype = i64
     L.rpp_result_total.argtypes = [vp]

@@ -178,6 +178,24 @@ def rpp_barcodes(data, max_dim: int = 1, threshold: float = math.inf, kind: str 
     return _take_result(h.value)
 
 
+def rpp_apparent_census(data, kind: str = "points", stream=None,
+                        context: Context | None = None) -> dict:
+    """Dimension-1 apparent-pair census of the full filtration (no threshold,
+    no enclosing-radius cut): the apparent-pair pass without the reduction.
+    Returns the call's counters; the apparent fraction is
+    stats["apparent"][1] / stats["candidates"][1]."""
+    ptr, keep, is_cuda, dev = _as_input(data)
+    ctx = context or default_context(dev or 0)
+    kd = N.RPP_INPUT_POINTS if kind == "points" else N.RPP_INPUT_DISTANCES
+    n = int(keep.shape[0])
+    dim = int(keep.shape[1]) if kd == N.RPP_INPUT_POINTS else 0
+    st = N.Stats()
+    N.check(N.lib().rpp_apparent_census(ctx.handle, ptr, kd, n, dim,
+                                        _stream_ptr(stream, is_cuda), C.byref(st)),
+            "rpp_apparent_census")
+    return _stats_dict(st)
+
+
 def rpp_distance_matrix(points, stream=None, context: Context | None = None) -> np.ndarray:
     """The library's float32 distance matrix of a point cloud (host copy)."""
     ptr, keep, is_cuda, dev = _as_input(points)

@@ -137,6 +137,28 @@ rpp_status rpp_barcodes_quantile(rpp_context *ctx, const float *data, rpp_input_
     return run_one(ctx, in, stream, out);
 }
 
+rpp_status rpp_apparent_census(rpp_context *ctx, const float *data, rpp_input_kind kind,
+                               int64_t n, int32_t dim, void *stream, rpp_stats *out) {
+    if (!out) {
+        set_last_error("out is NULL");
+        return RPP_E_INVALID;
+    }
+    Instance in;
+    in.data = data;
+    in.kind = kind;
+    in.n = n;
+    in.dim = dim;
+    in.max_dim = 1;
+    in.threshold = INFINITY;
+    in.census = true;
+    rpp_result *res = nullptr;
+    const rpp_status st = run_one(ctx, in, stream, &res);
+    if (st != RPP_OK) return st;
+    *out = res->stats;
+    delete res;
+    return RPP_OK;
+}
+
 int64_t rpp_result_count(const rpp_result *res, int32_t p) {
     if (!res || p < 0 || p > res->max_dim) return -1;
     return (int64_t)res->iv[p].size();

@@ -410,6 +410,10 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
     launch_enclosing_radius(D, n, ld, st, t_user, s);
     T.end();
     RPP_CK(cudaGetLastError());
+    if (in.census) {  // every edge: neither a threshold nor the enclosing radius
+        static const float inf = INFINITY;
+        RPP_CK(cudaMemcpyAsync(&st->t, &inf, sizeof(float), cudaMemcpyHostToDevice, s));
+    }
 
     // host copy of D for the reduction and the realising edges
     RPP_TRY(ws.host(ws.h_D, (size_t)n * ld * sizeof(float), &vp));
@@ -662,6 +666,15 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
         S.leftover[p] = (int64_t)nleft;
         S.scanned[p] = (int64_t)(hst->scanned - scanned_prev);
         scanned_prev = hst->scanned;
+        if (in.census) {  // the census ends with the apparent-pair pass
+            RPP_CK(cudaStreamSynchronize(s));
+            T.collect(S);
+            S.kernel_launches = g_launches - launches0;
+            S.ms_device = dev_ms;
+            S.ms_host_h0 = h0_ms;
+            S.ms_total = now_ms() - t0;
+            return Status();
+        }
         const bool record_app = (ctx->record & RPP_RECORD_APPARENT) != 0;
         if (record_app || nleft > 0) {
             // the apparent taus sorted: the second layer of the pair store (the

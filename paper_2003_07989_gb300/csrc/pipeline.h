@@ -106,6 +106,9 @@ struct Instance {
     int32_t max_dim = 1;
     float threshold = INFINITY;
     float quantile = 0.0f;  // > 0: threshold by quantile
+    // apparent-pair census: dimension 1 of the full filtration (no threshold,
+    // no enclosing-radius cut), stopping after the apparent-pair pass
+    bool census = false;
 };
 
 }  // namespace rpp

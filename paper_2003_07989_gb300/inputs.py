@@ -234,6 +234,24 @@ def permutation_distances(n: int, seed: int = 0) -> np.ndarray:
     return D
 
 
+def rank_distances(n: int, seed: int = 0) -> np.ndarray:
+    """A uniformly random total order of the C(n,2) edges, as distinct float32
+    values at any n: the edge of rank r (1-based) gets the float whose bit
+    pattern is that of 1.0 plus r, so values increase with rank and no two are
+    equal (integers would tie in float32 beyond 2^24). Symmetric, zero
+    diagonal. The ranks are those of permutation_distances."""
+    m = n * (n - 1) // 2
+    u = uniform01(stream_seed(seed, 31), m)
+    rank = np.empty(m, dtype=np.int64)
+    rank[np.argsort(u, kind="stable")] = np.arange(1, m + 1, dtype=np.int64)
+    vals = (np.int64(0x3F800000) + rank).astype(np.uint32).view(np.float32)
+    D = np.zeros((n, n), dtype=np.float32)
+    iu = np.triu_indices(n, 1)
+    D[iu] = vals
+    D.T[iu] = vals
+    return D
+
+
 def decreasing_lex_distances(n: int) -> np.ndarray:
     """Edge (a, b), a > b, gets C(n,2) - (its rank in lexicographic order of the
     decreasing vertex pair); the construction of Sec. "The Upper Bound Under

@@ -87,3 +87,30 @@ def test_fullsize_apparent_sample(rpp):
     # within the upper bound of the theorem on apparent pairs
     assert len(app) <= math.comb(n - 1, 2)
     assert got.stats["apparent"][1] + got.stats["leftover"][1] == got.stats["columns"][1]
+
+
+def test_sphere192_served_beside_a_stream_of_small_requests(rpp):
+    # The 192 points on S^3 (H0-H2) go in as one large request under a device
+    # memory bound, among small requests of the serving mix that keep
+    # arriving; the large one is admitted when memory allows, and every result
+    # equals its stored or single-instance value.
+    from paper_2003_07989_gb300 import inputs as I
+    g = np.load(os.path.join(GOLDEN, "sphere192.npz"))
+    X = np.ascontiguousarray(g["points"])
+    small = I.serving_requests(48, seed=5, n_range=(32, 200))
+    alone = [rpp.rpp_barcodes(r.points, max_dim=1, quantile=r.threshold_quantile)
+             for r in small]
+    srv = rpp.Server(max_slots=4, device_bytes=320 << 20, max_batch=8)
+    try:
+        first = [srv.submit(r.points, 1, quantile=r.threshold_quantile) for r in small[:24]]
+        big = srv.submit(X, 2)
+        rest = [srv.submit(r.points, 1, quantile=r.threshold_quantile) for r in small[24:]]
+        got = srv.poll(big)
+        for q in range(3):
+            assert np.array_equal(got.intervals[q], g[f"H{q}"]), q
+        for t, a in zip(first + rest, alone):
+            r = srv.poll(t)
+            for q in (0, 1):
+                assert np.array_equal(r.intervals[q], a.intervals[q])
+    finally:
+        srv.close()
