@@ -817,15 +817,17 @@ struct RadixHeap {
     }
 };
 
-uint64_t *plane_scratch(int64_t n);
-
 template <class K>
 struct Walk1 {
     typedef typename K::T Key;
     const HostInstance &I;
     const Reducer &R;
-    int64_t n, W;                 // vertices, words per adjacency row
-    uint64_t *adj;                // V as adjacency bits (all clear when idle)
+    int64_t n, W, S;              // vertices, words per bit row, words per vertex
+    // Per vertex a, S = 2W words: the sweep's bits P[a] (words 0..W-1), then
+    // V's adjacency bits of a (words W..2W-1); next to each other, so that a
+    // level reads two contiguous stretches. All clear when idle.
+    uint64_t *rows;
+    uint64_t *adj;                // rows + W: V as adjacency bits
     std::vector<Cur1> cur;
     typename std::conditional<std::is_same<Key, uint64_t>::value, RadixHeap, MinHeap<Key>>::type
         heap;
@@ -833,10 +835,11 @@ struct Walk1 {
     int64_t additions = 0, reads = 0, entries = 0, levels = 0;
     int threads = 1;
 
-    // adj_: the calling thread's scratch of n x ceil(n / 64) words, all
+    // rows_: the calling thread's scratch of n x 2 ceil(n / 64) words, all
     // clear; it is left clear again when the walk ends.
-    Walk1(const HostInstance &I_, const Reducer &R_, uint64_t *adj_, int threads_ = 1)
-        : I(I_), R(R_), n(I_.n), W((I_.n + 63) / 64), adj(adj_), threads(threads_) {}
+    Walk1(const HostInstance &I_, const Reducer &R_, uint64_t *rows_, int threads_ = 1)
+        : I(I_), R(R_), n(I_.n), W((I_.n + 63) / 64), S(2 * ((I_.n + 63) / 64)), rows(rows_),
+          adj(rows_ + (I_.n + 63) / 64), threads(threads_) {}
     ~Walk1() {
         clear_bits();
         clear_plane();
@@ -853,21 +856,22 @@ struct Walk1 {
         x = (int)a;
         y = (int)(e - a * (a - 1) / 2);
     }
-    bool vbit(int a, int b) const { return (adj[(int64_t)a * W + (b >> 6)] >> (b & 63)) & 1ull; }
+    bool vbit(int a, int b) const { return (adj[(int64_t)a * S + (b >> 6)] >> (b & 63)) & 1ull; }
     void set_edge(int x, int y) {
-        adj[(int64_t)x * W + (y >> 6)] |= 1ull << (y & 63);
-        adj[(int64_t)y * W + (x >> 6)] |= 1ull << (x & 63);
+        adj[(int64_t)x * S + (y >> 6)] |= 1ull << (y & 63);
+        adj[(int64_t)y * S + (x >> 6)] |= 1ull << (x & 63);
     }
     void clear_bits() {
         if ((int64_t)V.size() * 8 > n * W) {
-            std::memset(adj, 0, (size_t)(n * W) * sizeof(uint64_t));
+            for (int64_t a = 0; a < n; ++a)
+                std::memset(adj + a * S, 0, (size_t)W * sizeof(uint64_t));
             return;
         }
         for (uint64_t e : V) {
             int x, y;
             edge_vertices(e, x, y);
-            adj[(int64_t)x * W + (y >> 6)] = 0;
-            adj[(int64_t)y * W + (x >> 6)] = 0;
+            adj[(int64_t)x * S + (y >> 6)] = 0;
+            adj[(int64_t)y * S + (x >> 6)] = 0;
         }
     }
 
@@ -940,7 +944,7 @@ struct Walk1 {
             uint64_t m = c.lm;
             const int sh = c.lune & 63;
             if (sh < 63) m &= (2ull << sh) - 1;
-            m &= ~(adj[(int64_t)c.x * W + k] ^ adj[(int64_t)c.y * W + k]);  // odd ones only
+            m &= ~(adj[(int64_t)c.x * S + k] ^ adj[(int64_t)c.y * S + k]);  // odd ones only
             if (m) {
                 const int w = (int)(k << 6) + 63 - __builtin_clzll(m);
                 c.lune = w - 1;
@@ -1221,6 +1225,7 @@ struct Walk1 {
     // only entries at or after the pivot, so additions of any kind (apparent
     // edges, a leftover's column, an edge that leaves V) are bit flips.
     static constexpr size_t SWEEP_MIN = 256;
+    static constexpr int64_t PREFETCH_AHEAD = 2;  // levels
     static constexpr int64_t SWEEP_NMAX = 8192;  // P and adj: n^2 / 8 bytes each per thread
     bool sweep = false;
     uint64_t *P = nullptr;        // n x W bits: w within the level's diameter of a (no self bits)
@@ -1240,6 +1245,9 @@ struct Walk1 {
     };
     std::vector<LevelEdge> lev;
     int piv_a = -1, piv_b = -1, piv_w = -1;  // the last pivot's triangle
+    // Degree of each vertex in V: a level edge with no edge of V at either
+    // end has only even triangles (all three of its edges are outside V).
+    std::vector<int32_t> deg;
     // Levels of several edges: the edges' cached heads in a max-heap by
     // triangle index (stale entries are skipped by version), the level edges
     // at each vertex, and the vertices whose edges' heads must be recomputed
@@ -1271,8 +1279,8 @@ struct Walk1 {
         E.wpos = (int)n;
         E.head = -1;
         E.ver = 0;
-        P[(int64_t)a * W + (b >> 6)] |= 1ull << (b & 63);
-        P[(int64_t)b * W + (a >> 6)] |= 1ull << (a & 63);
+        P[(int64_t)a * S + (b >> 6)] |= 1ull << (b & 63);
+        P[(int64_t)b * S + (a >> 6)] |= 1ull << (a & 63);
         lev.push_back(E);
     }
 
@@ -1302,6 +1310,16 @@ struct Walk1 {
                 int a, b;
                 edge_vertices(edge_at(f), a, b);
                 level_edge(a, b);
+            }
+            // the sweep is bound by the latency of the bit rows: ask for the
+            // rows of an edge a few levels ahead
+            if (f1 + PREFETCH_AHEAD < I.nedges) {
+                int a, b;
+                edge_vertices(edge_at(f1 + PREFETCH_AHEAD), a, b);
+                for (int64_t k = 0; k < S; k += 8) {
+                    __builtin_prefetch(rows + (int64_t)a * S + k);
+                    __builtin_prefetch(rows + (int64_t)b * S + k);
+                }
             }
         } else {
             if (rheap.empty()) return false;
@@ -1376,8 +1394,9 @@ struct Walk1 {
 
     // Oldest triangle of edge E still to come that is odd now (w, or -1).
     int level_head(const LevelEdge &E) const {
-        const uint64_t *Pa = P + (int64_t)E.a * W, *Pb = P + (int64_t)E.b * W;
-        const uint64_t *Aa = adj + (int64_t)E.a * W, *Ab = adj + (int64_t)E.b * W;
+        if (deg[E.a] == 0 && deg[E.b] == 0) return -1;
+        const uint64_t *Pa = P + (int64_t)E.a * S, *Pb = P + (int64_t)E.b * S;
+        const uint64_t *Aa = adj + (int64_t)E.a * S, *Ab = adj + (int64_t)E.b * S;
         const uint64_t flip = vbit(E.a, E.b) ? ~0ull : 0ull;
         const bool shared = lev.size() > 1;
         int top = E.wpos - 1;
@@ -1411,14 +1430,21 @@ struct Walk1 {
         cur.clear();
         heap.clear();
         sweep = true;
-        P = plane_scratch(n);
+        P = rows;
+        deg.assign(n, 0);
+        for (uint64_t e : V) {  // V has no repeats here (heap mode or a rebuilt set)
+            int x, y;
+            edge_vertices(e, x, y);
+            ++deg[x];
+            ++deg[y];
+        }
         const float dk = key_diam(k);
         const uint64_t kidx = key_index(k);
         // P: every edge shorter than dk (the neighbour rows are sorted by distance)
         const uint32_t bd = float_bits(dk);
         for (int64_t a = 0; a < n; ++a) {
             const uint64_t *row = I.nbr + a * n;
-            uint64_t *Pa = P + a * W;
+            uint64_t *Pa = P + a * S;
             for (int64_t i = 0; i < n && (uint32_t)(row[i] >> 32) < bd; ++i) {
                 const int w = (int)(uint32_t)row[i];
                 if (w != a) Pa[w >> 6] |= 1ull << (w & 63);
@@ -1534,7 +1560,7 @@ struct Walk1 {
             if (fd[i] > fd[r]) r = i;
         if (fd[r] != lvl_d) return false;
         const int x = r == 0 ? v[1] : v[0], y = r == 2 ? v[1] : v[2];
-        const uint64_t *Px = P + (int64_t)x * W, *Py = P + (int64_t)y * W;
+        const uint64_t *Px = P + (int64_t)x * S, *Py = P + (int64_t)y * S;
         for (int64_t k = W - 1; k >= 0; --k) {
             const uint64_t m = Px[k] & Py[k];
             if (m) {
@@ -1552,8 +1578,11 @@ struct Walk1 {
     void toggle_edge(uint64_t e) {
         int x, y;
         edge_vertices(e, x, y);
-        adj[(int64_t)x * W + (y >> 6)] ^= 1ull << (y & 63);
-        adj[(int64_t)y * W + (x >> 6)] ^= 1ull << (x & 63);
+        const int32_t d = vbit(x, y) ? -1 : 1;  // leaves V, or enters it
+        deg[x] += d;
+        deg[y] += d;
+        adj[(int64_t)x * S + (y >> 6)] ^= 1ull << (y & 63);
+        adj[(int64_t)y * S + (x >> 6)] ^= 1ull << (x & 63);
         V.push_back(e);
         if (lev.size() > SMALL_LEVEL)
             for (int v : {x, y})
@@ -1564,25 +1593,18 @@ struct Walk1 {
     }
 
     void clear_plane() {
-        if (P) std::memset(P, 0, (size_t)(n * W) * sizeof(uint64_t));
+        if (P)
+            for (int64_t a = 0; a < n; ++a) std::memset(P + a * S, 0, (size_t)W * sizeof(uint64_t));
         P = nullptr;
     }
 };
 
-// The bits P of a sweep (n rows of ceil(n / 64) words), owned by the calling
-// thread and clear.
-uint64_t *plane_scratch(int64_t n) {
-    thread_local std::vector<uint64_t> bits;
-    const size_t words = (size_t)(n * ((n + 63) / 64));
-    if (bits.size() < words) bits.assign(words, 0);
-    return bits.data();
-}
 
-// The adjacency bits of a walk (n rows of ceil(n / 64) words), owned by the
+// The bit rows of a walk (n rows of 2 ceil(n / 64) words), owned by the
 // calling thread and clear.
 uint64_t *adjacency_scratch(int64_t n) {
     thread_local std::vector<uint64_t> bits;
-    const size_t words = (size_t)(n * ((n + 63) / 64));
+    const size_t words = (size_t)(n * 2 * ((n + 63) / 64));
     if (bits.size() < words) bits.assign(words, 0);
     return bits.data();
 }
