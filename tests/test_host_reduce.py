@@ -1,0 +1,94 @@
+"""The library's host reduction (csrc/host.cpp) on the CPU, against the oracle.
+
+tests/host_reduce_harness.cpp prepares what the GPU stages would hand over
+(sorted edges, Kruskal clearing, apparent pairs by definition, leftovers with
+their unreduced pivots, neighbour rows) and runs the dimension-1 submatrix
+reduction; its H1 intervals must be the oracle's, bit for bit. The cases make
+the reduction walk long enough to sweep diameter levels (the long-lived H1
+classes of tori), with and without a threshold below the enclosing radius,
+with many equal distances, with the levels taken from the sorted edges or
+from the neighbour rows, and with apparent pivots looked up or tested again.
+"""
+import math
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2003_07989_gb300 import inputs as I
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(ROOT, "paper_2003_07989_gb300", "csrc")
+
+
+def _cuda_include():
+    for d in (os.environ.get("CUDA_HOME"), "/usr/local/cuda"):
+        if d and os.path.exists(os.path.join(d, "include", "cuda_runtime.h")):
+            return os.path.join(d, "include")
+    return None
+
+
+@pytest.fixture(scope="module")
+def harness(tmp_path_factory):
+    cxx = shutil.which("g++")
+    inc = _cuda_include()
+    if not cxx or not inc:
+        pytest.skip("needs g++ and the CUDA headers")
+    exe = str(tmp_path_factory.mktemp("hr") / "host_reduce_harness")
+    cmd = [cxx, "-O2", "-std=c++17", "-ffp-contract=off", "-I", CSRC, "-I", inc,
+           "-I", os.path.join(ROOT, "include"), os.path.join(HERE, "host_reduce_harness.cpp"),
+           os.path.join(CSRC, "host.cpp"), "-o", exe, "-lpthread"]
+    subprocess.run(cmd, check=True)
+    return exe
+
+
+def _run(exe, D, t, threads, flags, tmp):
+    D = np.ascontiguousarray(D, dtype=np.float32)
+    dpath, opath = str(tmp / "D.f32"), str(tmp / "out.f32")
+    D.tofile(dpath)
+    r = subprocess.run([exe, dpath, str(len(D)), repr(float(t)), str(threads), str(flags), opath],
+                       capture_output=True, text=True, check=True)
+    iv = np.fromfile(opath, dtype=np.float32).reshape(-1, 2)
+    iv = iv[np.lexsort((iv[:, 1], iv[:, 0]))]
+    levels = int(r.stdout.split("levels ")[1].split()[0])
+    return iv, levels
+
+
+def _quantized(D, scale):
+    Dq = (np.round(D.astype(np.float64) * scale) / scale).astype(np.float32)
+    np.fill_diagonal(Dq, 0.0)
+    return Dq
+
+
+CASES = {
+    "torus500": lambda: (O.distance_matrix(I.noisy_torus(500, seed=1)), math.inf),
+    "torus420_t": lambda: (O.distance_matrix(I.noisy_torus(420, seed=2)), 0.8),
+    "torus450_ties": lambda: (_quantized(O.distance_matrix(I.noisy_torus(450, seed=5)), 16.0),
+                              math.inf),
+    "cube300": lambda: (O.distance_matrix(I.uniform_cube(300, 3, seed=3)), math.inf),
+    "circle400_q": lambda: (O.distance_matrix(I.circle_cloud(400, 1.0, 0.05, 3, 7)), None),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+@pytest.mark.parametrize("flags", [0, 3])
+def test_host_reduction_equals_oracle(harness, tmp_path, name, flags):
+    D, t = CASES[name]()
+    if t is None:  # the serving workload's 0.6 nearest-rank quantile threshold
+        t = O.distance_quantile(D, 0.6)
+    got, levels = _run(harness, D, t, 4, flags, tmp_path)
+    ref = O.barcodes(D, 1, t, O.MODE_COHOM_CLEAR).barcode(1)
+    assert got.shape == ref.shape and np.array_equal(got, ref), name
+    if name in ("torus500", "torus450_ties"):
+        assert levels > 0, "the long walks should sweep"
+
+
+def test_host_reduction_threads_agree(harness, tmp_path):
+    D = O.distance_matrix(I.noisy_torus(360, seed=9))
+    a, _ = _run(harness, D, math.inf, 1, 0, tmp_path)
+    b, _ = _run(harness, D, math.inf, 8, 1, tmp_path)
+    assert np.array_equal(a, b)
