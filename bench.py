@@ -43,7 +43,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--serving-requests", type=int, default=512,
+    ap.add_argument("--serving-requests", type=int, default=4096,
                     help="requests of the serving section (0 skips it)")
     ap.add_argument("--serving-slots", type=int, default=8)
     ap.add_argument("--no-census", action="store_true",
@@ -275,6 +275,33 @@ def serving_bench(rpp, count: int, slots: int):
 
 
 # ---------------------------------------------------------------------------
+# differentiation: total H1 persistence of a batch of noisy circles, backward
+
+
+def backward_bench(rpp, torch, dev, reps: int = 10):
+    """Forward (batched barcodes) + backward (gradients to the points) of the
+    total H1 persistence of 256 noisy planar circles of 128 points."""
+    import numpy as np
+    from paper_2003_07989_gb300 import inputs as I
+    X = torch.from_numpy(np.ascontiguousarray(I.noisy_circles(256, 128, seed=0))).to(dev)
+    for _ in range(2):
+        pts = X.clone().requires_grad_(True)
+        rpp.total_persistence(pts, 1).backward()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        pts = X.clone().requires_grad_(True)
+        loss = rpp.total_persistence(pts, 1)
+        loss.backward()
+    torch.cuda.synchronize(dev)
+    dt = (time.perf_counter() - t0) / reps
+    return {"clouds": 256, "points": 128, "ms_per_batch": 1e3 * dt,
+            "clouds_per_s": 256 / dt, "loss": float(loss.detach()),
+            "workload": "256 noisy planar circles of 128 points (radius U[0.5,2], sigma 0.05), "
+                        "loss = total H1 persistence, forward + backward to the points"}
+
+
+# ---------------------------------------------------------------------------
 # apparent-pair census of random edge orders (the paper's apparent-rate experiment)
 
 
@@ -473,6 +500,7 @@ def main():
     if args.serving_requests > 0:
         serving = serving_bench(rpp, args.serving_requests, args.serving_slots)
     census = None if args.no_census else census_bench(rpp, torch, dev, ctx)
+    backward = backward_bench(rpp, torch, dev)
     h2d = X.nbytes
     d2h = sum(len(iv) * (8 + 16) for iv in e2e_results[0].intervals)
     line = {
@@ -492,6 +520,7 @@ def main():
         "cpu_baseline": cpu,
         "serving": serving,
         "apparent_census": census,
+        "differentiation": backward,
         "breakdown": {
             "kernels": kernels,
             "host_reduce_ms": statistics.mean(s["ms_host_reduce"] for s in st),

@@ -12,13 +12,16 @@
 //      decreasing order (Alg. 5); the facets before sigma drop a vertex
 //      w > w*. sigma is apparent iff none of them has diam == diam(sigma)
 //      (condition 2; Proposition "apparent-support").
-// The paper runs one thread per column. Here a group of G lanes owns a column
-// and tests G candidate vertices w = scan, scan-1, ..., scan-G+1 per step: the
-// G reads D[v_i][w] of each row are contiguous, so every step is a coalesced
-// load of (p+1) short row segments (the rows are L2-resident). A warp ballot
-// picks the lowest qualifying lane, i.e. the largest w. Groups of one warp
-// advance independently: a group that finishes takes its next column in the
-// same iteration, so no lane idles while a neighbour scans a long column.
+// The kernel is bound by the latency of its L1/L2 loads, so it is compiled
+// for eight 256-thread blocks per SM (32 registers a thread) to keep more
+// warps in flight. The paper runs one thread per column. Here a group of G
+// lanes owns a column and tests G candidate vertices w = scan, scan-1, ...,
+// scan-G+1 per step: the G reads D[v_i][w] of each row are contiguous, so
+// every step is a coalesced load of (p+1) short row segments (the rows are
+// L2-resident). A warp ballot picks the lowest qualifying lane, i.e. the
+// largest w. Groups of one warp advance independently: a group that finishes
+// takes its next column in the same iteration, so no lane idles while a
+// neighbour scans a long column.
 // While scanning, each lane also tracks its oldest cofacet inside the
 // threshold (smallest diameter, then largest vertex); for a column with no
 // equal-diameter cofacet the scan covers every vertex, and the group reduces
@@ -32,7 +35,7 @@ namespace rpp {
 namespace {
 
 template <int P, int G>
-__global__ void __launch_bounds__(256) k_apparent(
+__global__ void __launch_bounds__(256, 8) k_apparent(
     const float *__restrict__ D, int64_t ld, int64_t n, const uint64_t *__restrict__ gB,
     bool smem_table, const uint32_t *__restrict__ key_hi, const uint64_t *__restrict__ key_lo,
     uint64_t ncols, DevState *__restrict__ st, uint8_t *__restrict__ status,
