@@ -59,6 +59,17 @@ __global__ void __launch_bounds__(256) k_build_columns(const float *__restrict__
     }
 }
 
+// The vertices (a << 16) | b, a > b, of edge indices (n <= 65535).
+__global__ void k_edge_pairs(const uint64_t *__restrict__ lo, uint64_t count,
+                             uint32_t *__restrict__ out) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+        int v[2];
+        decode_edge(lo[i], v);
+        out[i] = ((uint32_t)v[0] << 16) | (uint32_t)v[1];
+    }
+}
+
 __global__ void k_mark_cleared(const uint32_t *__restrict__ pos, int64_t count,
                                uint8_t *__restrict__ status) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -114,6 +125,14 @@ void launch_build_columns(const float *D, int64_t ld, int64_t n, int p, const ui
         case 4: build_p<4>(D, ld, n, binom, total, cleared, st, key_hi, key_lo, s); break;
         default: break;
     }
+}
+
+void launch_edge_pairs(const uint64_t *lo, uint64_t count, uint32_t *out, cudaStream_t s) {
+    if (count == 0) return;
+    uint64_t blocks = (count + 255) / 256;
+    if (blocks > 152ull * 8) blocks = 152ull * 8;
+    ++g_launches;
+    k_edge_pairs<<<(unsigned)blocks, 256, 0, s>>>(lo, count, out);
 }
 
 void launch_mark_cleared(const uint32_t *pos, int64_t count, uint8_t *status, cudaStream_t s) {

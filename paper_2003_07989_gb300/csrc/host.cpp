@@ -1261,7 +1261,11 @@ struct Walk1 {
     bool can_sweep() const { return n <= SWEEP_NMAX; }
 
     // Edge at position f of the filtration order (diameter ascending).
-    uint64_t edge_at(int64_t f) const { return I.edge_lo[I.nedges - 1 - f]; }
+    void edge_at(int64_t f, int &a, int &b) const {
+        const uint32_t ab = I.edge_ab[I.nedges - 1 - f];
+        a = (int)(ab >> 16);
+        b = (int)(ab & 0xffffu);
+    }
     float diam_at(int64_t f) const { return bits_float(~I.edge_hi[I.nedges - 1 - f]); }
 
     static uint64_t tri_index(const Binomial &B, int a, int b, int w) {
@@ -1301,21 +1305,21 @@ struct Walk1 {
     // edges with every triangle still to come; false when no edge is left.
     bool next_level() {
         lev.clear();
-        if (I.edge_lo) {
+        if (I.edge_ab) {
             if (f1 >= I.nedges) return false;
             const int64_t f0 = f1;
             lvl_d = diam_at(f0);
             while (f1 < I.nedges && diam_at(f1) == lvl_d) ++f1;
             for (int64_t f = f0; f < f1; ++f) {
                 int a, b;
-                edge_vertices(edge_at(f), a, b);
+                edge_at(f, a, b);
                 level_edge(a, b);
             }
             // the sweep is bound by the latency of the bit rows: ask for the
             // rows of an edge a few levels ahead
             if (f1 + PREFETCH_AHEAD < I.nedges) {
                 int a, b;
-                edge_vertices(edge_at(f1 + PREFETCH_AHEAD), a, b);
+                edge_at(f1 + PREFETCH_AHEAD, a, b);
                 for (int64_t k = 0; k < S; k += 8) {
                     __builtin_prefetch(rows + (int64_t)a * S + k);
                     __builtin_prefetch(rows + (int64_t)b * S + k);
@@ -1451,7 +1455,7 @@ struct Walk1 {
             }
         }
         // position the level source at the first edge of length dk
-        if (I.edge_lo) {  // edges in filtration order, diameter ascending
+        if (I.edge_ab) {  // edges in filtration order, diameter ascending
             int64_t lo = 0, hi = I.nedges;
             while (lo < hi) {
                 const int64_t mid = (lo + hi) >> 1;

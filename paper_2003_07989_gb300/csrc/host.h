@@ -24,10 +24,11 @@ struct HostInstance {
     // pairs are recognised by testing them again
     const uint64_t *app_tau = nullptr;
     uint64_t napp = 0;
-    // dimension 1 only (may be null): every edge inside the threshold in
-    // coboundary order (diameter descending, index ascending), as the GPU
-    // sorted them: index and ~bits(diameter)
-    const uint64_t *edge_lo = nullptr;
+    // dimension 1 only (may be null; n <= 65535): every edge inside the
+    // threshold in coboundary order (diameter descending, index ascending), as
+    // the GPU sorted them: its vertices packed as (a << 16) | b, a > b, and
+    // ~bits(diameter)
+    const uint32_t *edge_ab = nullptr;
     const uint32_t *edge_hi = nullptr;
     int64_t nedges = 0;
     float t = 0.0f;                 // threshold in use

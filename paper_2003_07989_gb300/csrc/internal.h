@@ -96,6 +96,9 @@ void radix_sort_noalloc(uint32_t *hi, uint64_t *lo, uint32_t *tmp_hi, uint64_t *
                         uint32_t *tile_counts, uint32_t *digit_hist, uint32_t *host_hist,
                         uint64_t n, int lo_bits, int hi_bits, cudaStream_t s);
 
+// The vertices of edge indices, packed (a << 16) | b with a > b (n <= 65535).
+void launch_edge_pairs(const uint64_t *lo, uint64_t count, uint32_t *out, cudaStream_t s);
+
 // Mark columns at the given positions as cleared.
 void launch_mark_cleared(const uint32_t *pos, int64_t count, uint8_t *status, cudaStream_t s);
 

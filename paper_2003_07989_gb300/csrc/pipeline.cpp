@@ -57,7 +57,7 @@ Workspace::~Workspace() {
     for (DevBuf *b : d)
         if (b->p) cudaFree(b->p);
     HostBuf *h[] = {&h_hi,    &h_lo,  &h_tau, &h_sigma, &h_left,
-                    &h_D,     &h_state, &h_mst, &h_up,  &h_nbr, &h_ehi, &h_elo};
+                    &h_D,     &h_state, &h_mst, &h_up,  &h_nbr, &h_ehi, &h_eab};
     for (HostBuf *b : h)
         if (b->p) cudaFreeHost(b->p);
     DevBuf *bd[] = {&b_pts, &b_clouds, &b_order, &b_ctl, &b_D,   &b_mst,  &b_outs,
@@ -705,21 +705,24 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
             RPP_CK(cudaMemcpyAsync(htau, app_tau, napp * 8, cudaMemcpyDeviceToHost, s));
             I.app_tau = htau;
             I.napp = napp;
-            if (p == 1 && edges_count > 0) {  // the sorted edges, for the sweep of long walks
-                uint32_t *he;
-                uint64_t *hl;
+            if (p == 1 && edges_count > 0 && n <= 65535) {
+                // the sorted edges as vertex pairs, for the sweep of long walks
+                // (tmp_hi is free once the pair sort has run)
+                uint32_t *he, *hab;
                 RPP_TRY(ws.host(ws.h_ehi, edges_count * 4, (void **)&he));
-                RPP_TRY(ws.host(ws.h_elo, edges_count * 8, (void **)&hl));
+                RPP_TRY(ws.host(ws.h_eab, edges_count * 4, (void **)&hab));
+                T.begin(ST_OTHER);
+                launch_edge_pairs(key_lo + edges_begin, edges_count, tmp_hi, s);
+                T.end();
                 RPP_CK(cudaMemcpyAsync(he, key_hi + edges_begin, edges_count * 4,
                                        cudaMemcpyDeviceToHost, s));
-                RPP_CK(cudaMemcpyAsync(hl, key_lo + edges_begin, edges_count * 8,
-                                       cudaMemcpyDeviceToHost, s));
+                RPP_CK(cudaMemcpyAsync(hab, tmp_hi, edges_count * 4, cudaMemcpyDeviceToHost, s));
                 I.edge_hi = he;
-                I.edge_lo = hl;
+                I.edge_ab = hab;
                 I.nedges = (int64_t)edges_count;
             } else {
                 I.edge_hi = nullptr;
-                I.edge_lo = nullptr;
+                I.edge_ab = nullptr;
                 I.nedges = 0;
             }
             if (!I.nbr) {  // neighbour lists for the lazy coboundaries, once per instance

@@ -139,10 +139,9 @@ int main(int argc, char **argv) {
         for (int i = 0; i < n; ++i) row[i] = ((uint64_t)fbits(D[(size_t)r * ld + i]) << 32) | (uint64_t)i;
         std::sort(row, row + n);
     }
-    std::vector<uint64_t> elo(ne);
-    std::vector<uint32_t> ehi(ne);
+    std::vector<uint32_t> eab(ne), ehi(ne);
     for (int64_t k = 0; k < ne; ++k) {
-        elo[k] = E[k].idx;
+        eab[k] = ((uint32_t)E[k].x << 16) | (uint32_t)E[k].y;
         ehi[k] = ~fbits(E[k].d);
     }
     HostInstance I;
@@ -153,7 +152,7 @@ int main(int argc, char **argv) {
     I.nbr = nbr.data();
     I.t = t;
     if (!(flags & 1)) {
-        I.edge_lo = elo.data();
+        I.edge_ab = eab.data();
         I.edge_hi = ehi.data();
         I.nedges = ne;
     }
