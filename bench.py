@@ -48,6 +48,8 @@ def parse_args():
     ap.add_argument("--serving-slots", type=int, default=8)
     ap.add_argument("--no-census", action="store_true",
                     help="skip the apparent-pair census of random edge orders")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="only the torus steps: no serving, census or differentiation section")
     return ap.parse_args()
 
 
@@ -497,10 +499,10 @@ def main():
                "sample": f"first 1000 of the 2000 torus points ({c} dimension-1 columns, "
                          f"{dt:.1f} s)"}
     serving = None
-    if args.serving_requests > 0:
+    if args.serving_requests > 0 and not args.no_extras:
         serving = serving_bench(rpp, args.serving_requests, args.serving_slots)
-    census = None if args.no_census else census_bench(rpp, torch, dev, ctx)
-    backward = backward_bench(rpp, torch, dev)
+    census = None if (args.no_census or args.no_extras) else census_bench(rpp, torch, dev, ctx)
+    backward = None if args.no_extras else backward_bench(rpp, torch, dev)
     h2d = X.nbytes
     d2h = sum(len(iv) * (8 + 16) for iv in e2e_results[0].intervals)
     line = {
