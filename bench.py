@@ -351,6 +351,28 @@ def oracle_rate(n_sample: int, seed: int):
     return cols / dt, dt, cols, O.num_threads()
 
 
+def over_ranks(dist, slowest, summed, device):
+    """The job's figures from every rank's: the maximum of `slowest` (times:
+    the slowest rank bounds the job) and the sum of `summed` (work done)."""
+    import torch
+    mx = torch.tensor(slowest, dtype=torch.float64, device=device)
+    sm = torch.tensor(summed, dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return mx.tolist(), sm.tolist()
+
+
+def bench_config(world: int) -> dict:
+    """The workload both arms report (the oracle computes the same barcodes of
+    the full filtration; the library cuts it at the enclosing radius, which
+    leaves every nonzero interval unchanged)."""
+    return {"workload": WORKLOAD, "n": N_POINTS, "dim": DIM, "max_dim": MAX_DIM,
+            "threshold": "none (full filtration)", "seed": "rank",
+            "l2": "flushed between steps (512 MB write, outside the timed events)",
+            "parallelism": f"replicas x{world}"}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -370,8 +392,7 @@ def run_reference(args, rank, world):
         "unit": "simplices/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000.0 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": N_POINTS, "dim": DIM, "max_dim": MAX_DIM,
-                   "threshold": "none (full filtration)"},
+        "config": bench_config(world),
         "cpu_baseline": {"value": value, "unit": "simplices/s", "cores": cores, "kind": "oracle",
                          "sample": f"first {n_sample} of the 2000 torus points per step"},
         "e2e": {"value": value, "unit": "simplices/s", "h2d_bytes_per_step": 0,
@@ -454,15 +475,8 @@ def main():
     cols_rank = sum(s["columns"][1] for s in st)
     e2e_cols_rank = sum(r.stats["columns"][1] for r in e2e_results)
     launches_rank = sum(s["kernel_launches"] for s in st)
-    agg = torch.tensor([total_ms, e2e_ms, cols_rank, e2e_cols_rank, launches_rank],
-                       dtype=torch.float64, device=dev)
-    if dist is not None:
-        mx = agg[:2].clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = agg[2:].clone()
-        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        agg = torch.cat([mx, sm])
-    total_ms, e2e_ms, cols_all, e2e_cols_all, launches_all = agg.tolist()
+    (total_ms, e2e_ms), (cols_all, e2e_cols_all, launches_all) = over_ranks(
+        dist, [total_ms, e2e_ms], [cols_rank, e2e_cols_rank, launches_rank], dev)
     if rank != 0:
         dist.destroy_process_group()
         return
@@ -510,10 +524,7 @@ def main():
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": N_POINTS, "dim": DIM, "max_dim": MAX_DIM,
-                   "threshold": "enclosing radius (full filtration)", "seed": "rank",
-                   "l2": "flushed between steps (512 MB write, outside the timed events)",
-                   "parallelism": f"replicas x{world}"},
+        "config": bench_config(world),
         "e2e": {"value": e2e_value, "unit": "simplices/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / args.steps},
         "gpu_launches": int(launches_all),

@@ -70,12 +70,6 @@ __global__ void k_edge_pairs(const uint64_t *__restrict__ lo, uint64_t count,
     }
 }
 
-__global__ void k_mark_cleared(const uint32_t *__restrict__ pos, int64_t count,
-                               uint8_t *__restrict__ status) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < count) status[pos[i]] = COL_CLEARED;
-}
-
 __global__ void k_bitmap_set(const uint64_t *__restrict__ idx, uint64_t count,
                              uint32_t *__restrict__ bitmap) {
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -133,12 +127,6 @@ void launch_edge_pairs(const uint64_t *lo, uint64_t count, uint32_t *out, cudaSt
     if (blocks > 152ull * 8) blocks = 152ull * 8;
     ++g_launches;
     k_edge_pairs<<<(unsigned)blocks, 256, 0, s>>>(lo, count, out);
-}
-
-void launch_mark_cleared(const uint32_t *pos, int64_t count, uint8_t *status, cudaStream_t s) {
-    if (count <= 0) return;
-    ++g_launches;
-    k_mark_cleared<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(pos, count, status);
 }
 
 void launch_lower_bound_u32(const uint32_t *a, uint64_t n, uint32_t key, unsigned long long *out,

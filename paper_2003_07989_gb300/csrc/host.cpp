@@ -1,8 +1,6 @@
-// host.cpp -- H0 by Kruskal's union-find (Sec. "Zero-Dimensional Persistence
-// Computation: Kruskal's Algorithm") and the submatrix reduction of the
-// columns that are not apparent (Sec. "Core System Optimizations"; Alg. 1 with
-// the reduction-matrix technique of Sec. "Reduction Matrix vs. Oblivious
-// Matrix Reduction").
+// host.cpp -- the submatrix reduction of the columns that are not apparent
+// (Sec. "Core System Optimizations"; Alg. 1 with the reduction-matrix
+// technique of Sec. "Reduction Matrix vs. Oblivious Matrix Reduction").
 //
 // Reduction of one leftover column j follows Alg. 1: while the pivot (oldest
 // nonzero entry) of the working column has an owner, add the owner's reduced
@@ -175,48 +173,6 @@ void youngest_edge(const HostInstance &I, const int *v, int k, int32_t *u, int32
                 *w = y;
             }
         }
-}
-
-// ---------------------------------------------------------------------------
-// Kruskal
-
-void Kruskal::init(int64_t n) {
-    parent.resize(n);
-    size_.assign(n, 1);
-    for (int64_t i = 0; i < n; ++i) parent[i] = (int32_t)i;
-    components = n;
-    deaths.clear();
-    mst_pos.clear();
-}
-
-int32_t Kruskal::find(int32_t x) {
-    while (parent[x] != x) {
-        parent[x] = parent[parent[x]];
-        x = parent[x];
-    }
-    return x;
-}
-
-void Kruskal::run(const uint32_t *hi, const uint64_t *lo, int64_t count, int64_t pos0,
-                  const Binomial &B, int64_t n) {
-    int v[2];
-    for (int64_t k = 0; k < count && components > 1; ++k) {
-        decode_host(B, lo[k], 1, n, v);
-        int32_t a = find(v[0]), b = find(v[1]);
-        if (a == b) continue;
-        if (size_[a] < size_[b]) std::swap(a, b);
-        parent[b] = a;
-        size_[a] += size_[b];
-        --components;
-        HostPair P;
-        P.sigma = 0;
-        P.tau = lo[k];
-        P.birth = 0.0f;
-        uint32_t bits = ~hi[k];
-        std::memcpy(&P.death, &bits, sizeof(float));
-        deaths.push_back(P);
-        mst_pos.push_back((uint32_t)(pos0 - k));
-    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1693,7 +1649,12 @@ void reduce_p1(const HostInstance &I, const Leftover *left, int64_t nleft, int t
 
 void reduce_leftovers(const HostInstance &I, int p, const Leftover *left, int64_t nleft,
                       int threads, std::vector<HostPair> &out, ReduceStats &stats) {
-    if (p == 1 && I.B->at(3, I.n) <= (1ull << 32))  // triangle indices fit in 32 bits
+#ifdef RPP_WIDE_KEYS_ONLY  // tests build the 128-bit key path for small inputs too
+    const bool narrow = false;
+#else
+    const bool narrow = I.B->at(3, I.n) <= (1ull << 32);
+#endif
+    if (p == 1 && narrow)  // triangle indices fit in 32 bits
         reduce_p1<Key64>(I, left, nleft, threads, out, stats);
     else if (p == 1)
         reduce_p1<Key128>(I, left, nleft, threads, out, stats);

@@ -1,5 +1,5 @@
-// host.h -- host-side stages of the pipeline: H0 by Kruskal, the submatrix
-// reduction of the leftover columns, and barcode assembly helpers.
+// host.h -- host-side stages of the pipeline: the submatrix reduction of the
+// leftover columns, and barcode assembly helpers.
 #pragma once
 
 #include <stdint.h>
@@ -47,22 +47,6 @@ void youngest_edge(const HostInstance &I, const int *v, int k, int32_t *u, int32
 struct HostPair {
     uint64_t sigma, tau;
     float birth, death;
-};
-
-// ---- H0 -------------------------------------------------------------------
-// Union-find over edges given in filtration order (increasing diameter, then
-// decreasing index). Keeps state across chunks of edges.
-struct Kruskal {
-    std::vector<int32_t> parent, size_;
-    int64_t components = 0;
-    std::vector<HostPair> deaths;     // (vertex index in sigma, edge in tau)
-    std::vector<uint32_t> mst_pos;    // positions (in the edge array) of merging edges
-    void init(int64_t n);
-    int32_t find(int32_t x);
-    // Process edges e[k] for k = 0..count-1 in this order; pos0 - k is the
-    // position of e[k] in the coboundary-ordered edge array.
-    void run(const uint32_t *hi, const uint64_t *lo, int64_t count, int64_t pos0,
-             const Binomial &B, int64_t n);
 };
 
 // ---- submatrix reduction ----------------------------------------------------

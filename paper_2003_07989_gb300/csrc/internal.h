@@ -96,11 +96,24 @@ void radix_sort_noalloc(uint32_t *hi, uint64_t *lo, uint32_t *tmp_hi, uint64_t *
                         uint32_t *tile_counts, uint32_t *digit_hist, uint32_t *host_hist,
                         uint64_t n, int lo_bits, int hi_bits, cudaStream_t s);
 
+// H0 of one instance on the device: the minimum spanning forest of the edges
+// inside st->t under the filtration's order of edges (Boruvka, a fixed number
+// of rounds, no host round trip). mst receives the forest's keys
+// (bits(d) << 32) | ~index, *nmst their count; comp, parent, next: n ints,
+// best: n keys, flags: 64 words of scratch. A root search beyond its bound
+// sets ERR_INTERNAL.
+void launch_h0_forest(const float *D, int64_t ld, int64_t n, DevState *st, int32_t *comp,
+                      int32_t *parent, int32_t *next, unsigned long long *best,
+                      unsigned long long *mst, unsigned *nmst, unsigned *flags, cudaStream_t s);
+// Mark the forest's columns cleared in the sorted dimension-1 array (ncols
+// columns, ascending (key_hi, key_lo)); pos[i] receives the position of edge i.
+void launch_h0_clear(const unsigned long long *mst, const unsigned *nmst, int64_t n,
+                     const uint32_t *key_hi, const uint64_t *key_lo, uint64_t ncols,
+                     uint8_t *status, uint32_t *pos, cudaStream_t s);
+
 // The vertices of edge indices, packed (a << 16) | b with a > b (n <= 65535).
 void launch_edge_pairs(const uint64_t *lo, uint64_t count, uint32_t *out, cudaStream_t s);
 
-// Mark columns at the given positions as cleared.
-void launch_mark_cleared(const uint32_t *pos, int64_t count, uint8_t *status, cudaStream_t s);
 
 // Apparent-pair pass (Alg. 3 with the Apparent Pairs Lemma) over the columns
 // [0, ncols) in coboundary order. Writes status, pivot and pivot diameter.

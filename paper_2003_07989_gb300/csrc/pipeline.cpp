@@ -2,9 +2,9 @@
 // dimension p the filtration with clearing, the apparent-pair pass, the
 // partition and the submatrix reduction (the flow of Fig. "framework" (b)).
 //
-// Host <-> device crossings, as in the paper's hybrid design:
-//   * after the dimension-1 filtration is sorted, its shortest edges go to the
-//     host for Kruskal; the merging edges come back as cleared columns;
+// Host <-> device crossings (the paper's hybrid design, with H0 moved to the
+// device: the minimum spanning forest is found by Boruvka rounds on the GPU
+// and its edges are marked cleared there; only its n - 1 keys come back):
 //   * after the partition of dimension p, the leftover columns and the apparent
 //     pairs (sorted by tau) go to the host for the submatrix reduction;
 //   * the deaths the host found return to the device as the clearing bitmap of
@@ -53,7 +53,7 @@ float bits_to_float(uint32_t b) {
 Workspace::~Workspace() {
     DevBuf *d[] = {&X,    &Dsrc,  &D,      &state,   &binom,     &key_hi, &key_lo,
                    &tmp_hi, &tmp_lo, &tmp_val, &tiles, &hist,      &status, &pivot,
-                   &pdiam, &app_tau, &app_sigma, &left, &bitmap, &mst,    &up, &nbr};
+                   &pdiam, &app_tau, &app_sigma, &left, &bitmap, &mst,    &up, &nbr, &h0};
     for (DevBuf *b : d)
         if (b->p) cudaFree(b->p);
     HostBuf *h[] = {&h_hi,    &h_lo,  &h_tau, &h_sigma, &h_left,
@@ -284,6 +284,7 @@ size_t instance_device_bytes(const Instance &in) {
     total += slack(maxcand * per) + slack(radix_tile_counts_size(maxcand) * 4) + slack(12 * 256 * 4);
     total += slack((size_t)n * 4) + slack(maxcand / 8 + 8) + slack(maxcand * 8);
     total += slack((size_t)n * n * 8);  // neighbour lists
+    total += slack(512 + (size_t)n * 32);  // the H0 forest
     return total + 64 * 256;  // per-buffer rounding
 }
 
@@ -423,7 +424,7 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
     // buffers sized for the largest dimension
     uint64_t maxcand = 0;
     for (int p = 1; p <= std::max(1, max_dim); ++p) maxcand = std::max(maxcand, B.at(p + 1, n));
-    uint32_t *key_hi, *tmp_hi, *tiles, *hist, *mst;
+    uint32_t *key_hi, *tmp_hi, *tiles, *hist;
     uint64_t *key_lo, *tmp_lo, *tmp_val, *pivot, *app_tau, *app_sigma;
     uint8_t *status;
     float *pdiam;
@@ -441,7 +442,6 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
     RPP_TRY(ws.dev(ws.app_tau, maxcand * 8, (void **)&app_tau));
     RPP_TRY(ws.dev(ws.app_sigma, maxcand * 8, (void **)&app_sigma));
     RPP_TRY(ws.dev(ws.left, maxcand * sizeof(Leftover), (void **)&left));
-    RPP_TRY(ws.dev(ws.mst, (size_t)n * 4, (void **)&mst));
 
     auto read_state = [&]() -> Status {
         double a = now_ms();
@@ -469,8 +469,27 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
     I.ld = ld;
     I.B = &B;
 
-    Kruskal K;
-    K.init(n);
+    // H0 on the device: forest edges (keys (bits(d) << 32) | ~index), their
+    // count, and their positions among the dimension-1 columns
+    unsigned long long *h0_mst = nullptr, *h0_best = nullptr;
+    unsigned *h0_count = nullptr, *h0_flags = nullptr;
+    uint32_t *h0_pos = nullptr;
+    int32_t *h0_comp = nullptr, *h0_parent = nullptr, *h0_next = nullptr;
+    unsigned char *h0_host = nullptr;  // pinned: count (16 B), keys, positions
+    if (n >= 2) {
+        unsigned char *q;
+        const size_t nb = (size_t)n;
+        RPP_TRY(ws.dev(ws.h0, 512 + nb * (3 * 4 + 8 + 8 + 4), (void **)&q));
+        RPP_TRY(ws.host(ws.h_mst, 16 + nb * (8 + 4), (void **)&h0_host));
+        h0_comp = (int32_t *)q;
+        h0_parent = h0_comp + nb;
+        h0_next = h0_parent + nb;
+        h0_best = (unsigned long long *)(q + ((nb * 12 + 15) & ~(size_t)15));
+        h0_mst = h0_best + nb;
+        h0_pos = (uint32_t *)(h0_mst + nb);
+        h0_count = (unsigned *)(h0_pos + nb);
+        h0_flags = h0_count + 1;  // 64 words
+    }
     uint64_t edges_begin = 0, edges_count = 0;  // dimension-1 columns (MST edges included)
     std::vector<uint64_t> prev_deaths;  // host-found deaths of the previous dimension
     uint64_t prev_napp = 0;
@@ -515,40 +534,39 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
         edges_begin = begin;
         edges_count = cols;
 
-        // ---- H0: Kruskal on the shortest edges, copied from the tail ----
-        {
-            uint64_t done = 0, chunk = std::min<uint64_t>(cols, 1ull << 16);
-            while (K.components > 1 && done < cols) {
-                const uint64_t cnt = std::min<uint64_t>(chunk, cols - done);
-                const uint64_t first = N - done - cnt;  // array position of the chunk start
-                RPP_TRY(ws.host(ws.h_hi, cnt * 4, &vp));
-                uint32_t *hhi = (uint32_t *)vp;
-                RPP_TRY(ws.host(ws.h_lo, cnt * 8, &vp));
-                uint64_t *hlo = (uint64_t *)vp;
-                double a = now_ms();
-                RPP_CK(cudaMemcpyAsync(hhi, key_hi + first, cnt * 4, cudaMemcpyDeviceToHost, s));
-                RPP_CK(cudaMemcpyAsync(hlo, key_lo + first, cnt * 8, cudaMemcpyDeviceToHost, s));
-                RPP_CK(cudaStreamSynchronize(s));
-                dev_ms += now_ms() - a;
-                a = now_ms();
-                std::reverse(hhi, hhi + cnt);
-                std::reverse(hlo, hlo + cnt);
-                K.run(hhi, hlo, (int64_t)cnt, (int64_t)(first + cnt - 1), B, n);
-                h0_ms += now_ms() - a;
-                done += cnt;
-                chunk *= 4;
-            }
+        // ---- H0: the minimum spanning forest inside t, on the device ----
+        const double a0 = now_ms();
+        T.begin(ST_OTHER);
+        launch_h0_forest(D, ld, n, st, h0_comp, h0_parent, h0_next, h0_best, h0_mst, h0_count,
+                         h0_flags, s);
+        T.end();
+        RPP_CK(cudaGetLastError());
+        const uint32_t *hi1 = key_hi + begin;
+        const uint64_t *lo1 = key_lo + begin;
+        const bool dim1 = max_dim >= 1 && cols > 0;
+        if (dim1) {  // its edges are the cleared dimension-1 columns
+            RPP_CK(cudaMemsetAsync(status, 0, cols, s));
+            T.begin(ST_OTHER);
+            launch_h0_clear(h0_mst, h0_count, n, hi1, lo1, cols, status, h0_pos, s);
+            T.end();
+            RPP_CK(cudaGetLastError());
         }
-        S.cleared[1] = (int64_t)K.mst_pos.size();
-        S.columns[1] = (int64_t)cols - S.cleared[1];
+        RPP_CK(cudaMemcpyAsync(h0_host, h0_count, 4, cudaMemcpyDeviceToHost, s));
+        RPP_CK(cudaMemcpyAsync(h0_host + 16, h0_mst, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
+        if (dim1)
+            RPP_CK(cudaMemcpyAsync(h0_host + 16 + (size_t)n * 8, h0_pos, (size_t)n * 4,
+                                   cudaMemcpyDeviceToHost, s));
+        h0_ms += now_ms() - a0;
         if ((ctx->record & RPP_RECORD_COLUMNS) && max_dim >= 1) {
             std::vector<uint32_t> hh(cols);
             std::vector<uint64_t> ll(cols);
             RPP_CK(cudaMemcpyAsync(hh.data(), key_hi + begin, cols * 4, cudaMemcpyDeviceToHost, s));
             RPP_CK(cudaMemcpyAsync(ll.data(), key_lo + begin, cols * 8, cudaMemcpyDeviceToHost, s));
             RPP_CK(cudaStreamSynchronize(s));
+            const unsigned nm = *(const unsigned *)h0_host;
+            const uint32_t *pos = (const uint32_t *)(h0_host + 16 + (size_t)n * 8);
             std::vector<char> cl(cols, 0);
-            for (uint32_t pos : K.mst_pos) cl[pos - begin] = 1;
+            for (unsigned i = 0; i < nm && cols > 0; ++i) cl[pos[i]] = 1;
             for (uint64_t i = 0; i < cols; ++i)
                 if (!cl[i]) {
                     res->col_diam[1].push_back(bits_to_float(~hh[i]));
@@ -557,20 +575,7 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
             res->has_cols[1] = true;
         }
 
-        if (max_dim >= 1 && cols > 0) {
-            const uint32_t *hi1 = key_hi + begin;
-            const uint64_t *lo1 = key_lo + begin;
-            RPP_CK(cudaMemsetAsync(status, 0, cols, s));
-            if (!K.mst_pos.empty()) {
-                RPP_TRY(ws.host(ws.h_mst, K.mst_pos.size() * 4, &vp));
-                uint32_t *hm = (uint32_t *)vp;
-                for (size_t i = 0; i < K.mst_pos.size(); ++i)
-                    hm[i] = (uint32_t)(K.mst_pos[i] - begin);
-                RPP_CK(cudaMemcpyAsync(mst, hm, K.mst_pos.size() * 4, cudaMemcpyHostToDevice, s));
-                T.begin(ST_OTHER);
-                launch_mark_cleared(mst, (int64_t)K.mst_pos.size(), status, s);
-                T.end();
-            }
+        if (dim1) {
             const Tuning tu = ctx->tuning_for(n, 1);
             T.begin(ST_APPARENT);
             launch_apparent(D, ld, n, 1, d_binom, hi1, lo1, cols, st, status, pivot, pdiam,
@@ -586,16 +591,27 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
         I.t = t;
     }
 
-    // H0 intervals
+    // H0 intervals: one death per forest edge, one essential class per component
     {
-        int v[2];
-        for (const HostPair &P : K.deaths) {
-            if (!(P.death > 0.0f)) continue;  // zero-length (duplicate points)
-            decode_host(B, P.tau, 1, n, v);
-            rpp_critical c = {-1, -1, v[0], v[1]};
-            add_interval(res, 0, 0.0f, P.death, c);
+        unsigned nm = 0;
+        if (n >= 2) {
+            RPP_TRY(read_state());  // the forest's copies are in
+            if (hst->err & ERR_INTERNAL)
+                return fail(RPP_E_CUDA, "H0 forest: a root search exceeded its bound");
+            nm = *(const unsigned *)h0_host;
+            const unsigned long long *keys = (const unsigned long long *)(h0_host + 16);
+            int v[2];
+            for (unsigned i = 0; i < nm; ++i) {
+                const float d = bits_to_float((uint32_t)(keys[i] >> 32));
+                if (!(d > 0.0f)) continue;  // zero-length (duplicate points)
+                decode_host(B, (uint64_t)(~(uint32_t)keys[i]), 1, n, v);
+                rpp_critical c = {-1, -1, v[0], v[1]};
+                add_interval(res, 0, 0.0f, d, c);
+            }
+            S.cleared[1] = (int64_t)nm;
+            S.columns[1] = (int64_t)edges_count - S.cleared[1];
         }
-        for (int64_t i = 0; i < K.components; ++i) {
+        for (int64_t i = 0; i < n - (int64_t)nm; ++i) {
             rpp_critical c = {-1, -1, -1, -1};
             add_interval(res, 0, 0.0f, INFINITY, c);
         }

@@ -69,7 +69,7 @@ struct Workspace {
     size_t budget = 0;        // 0 = unbounded
     size_t device_bytes = 0;  // currently held
     DevBuf X, Dsrc, D, state, binom, key_hi, key_lo, tmp_hi, tmp_lo, tmp_val, tiles, hist,
-        status, pivot, pdiam, app_tau, app_sigma, left, bitmap, mst, up, nbr;
+        status, pivot, pdiam, app_tau, app_sigma, left, bitmap, mst, up, nbr, h0;
     HostBuf h_hi, h_lo, h_tau, h_sigma, h_left, h_D, h_state, h_mst, h_up, h_nbr, h_ehi, h_eab;
     Binomial binom_host;      // cached table
     int64_t binom_n = -1;

@@ -32,18 +32,28 @@ def _cuda_include():
     return None
 
 
-@pytest.fixture(scope="module")
-def harness(tmp_path_factory):
+def _build(tmp_path_factory, name, extra):
     cxx = shutil.which("g++")
     inc = _cuda_include()
     if not cxx or not inc:
         pytest.skip("needs g++ and the CUDA headers")
-    exe = str(tmp_path_factory.mktemp("hr") / "host_reduce_harness")
-    cmd = [cxx, "-O2", "-std=c++17", "-ffp-contract=off", "-I", CSRC, "-I", inc,
+    exe = str(tmp_path_factory.mktemp("hr") / name)
+    cmd = [cxx, "-O2", "-std=c++17", "-ffp-contract=off", *extra, "-I", CSRC, "-I", inc,
            "-I", os.path.join(ROOT, "include"), os.path.join(HERE, "host_reduce_harness.cpp"),
            os.path.join(CSRC, "host.cpp"), "-o", exe, "-lpthread"]
     subprocess.run(cmd, check=True)
     return exe
+
+
+@pytest.fixture(scope="module")
+def harness(tmp_path_factory):
+    return _build(tmp_path_factory, "host_reduce_harness", [])
+
+
+@pytest.fixture(scope="module")
+def harness_wide(tmp_path_factory):
+    # the 128-bit heap keys that inputs of more than 2953 points take
+    return _build(tmp_path_factory, "host_reduce_harness_wide", ["-DRPP_WIDE_KEYS_ONLY"])
 
 
 def _run(exe, D, t, threads, flags, tmp):
@@ -85,6 +95,17 @@ def test_host_reduction_equals_oracle(harness, tmp_path, name, flags):
     assert got.shape == ref.shape and np.array_equal(got, ref), name
     if name in ("torus500", "torus450_ties"):
         assert levels > 0, "the long walks should sweep"
+
+
+@pytest.mark.parametrize("name", ["torus500", "torus450_ties", "circle400_q"])
+def test_host_reduction_wide_keys_equal_oracle(harness_wide, tmp_path, name):
+    D, t = CASES[name]()
+    if t is None:
+        t = O.distance_quantile(D, 0.6)
+    for flags in (0, 3):
+        got, _ = _run(harness_wide, D, t, 4, flags, tmp_path)
+        ref = O.barcodes(D, 1, t, O.MODE_COHOM_CLEAR).barcode(1)
+        assert got.shape == ref.shape and np.array_equal(got, ref), (name, flags)
 
 
 def test_host_reduction_threads_agree(harness, tmp_path):
