@@ -35,6 +35,7 @@ class Context:
         N.check(L.rpp_context_create(device, mem_budget, C.byref(h)), "rpp_context_create")
         self.handle = h
         self.device = device
+        self.record = record
         if record:
             N.check(L.rpp_context_set_record(h, record), "rpp_context_set_record")
 
@@ -74,12 +75,20 @@ def default_context(device: int = 0) -> Context:
 class Barcodes:
     """Per dimension q: intervals[q] float32 [k, 2] (birth, death; death = inf
     for essential classes) sorted by (birth, death), and critical[q] int32 [k, 4]
-    (bu, bv, du, dv): the youngest edge of the birth and of the death simplex."""
+    (bu, bv, du, dv): the youngest edge of the birth and of the death simplex.
+    stats: the call's counters and stage times (a dict, built on first use)."""
     intervals: list = field(default_factory=list)
     critical: list = field(default_factory=list)
-    stats: dict = field(default_factory=dict)
     columns: dict = field(default_factory=dict)   # p -> (diam, cidx) when recorded
     apparent: dict = field(default_factory=dict)  # p -> (sigma, tau) when recorded
+    _raw_stats: object = None
+    _stats: dict = None
+
+    @property
+    def stats(self) -> dict:
+        if self._stats is None:
+            self._stats = _stats_dict(self._raw_stats) if self._raw_stats is not None else {}
+        return self._stats
 
     def __getitem__(self, q):
         return self.intervals[q]
@@ -93,7 +102,9 @@ def _stats_dict(s: N.Stats) -> dict:
     return out
 
 
-def _take_result(h, with_stats=True) -> Barcodes:
+def _take_result(h, with_stats=True, recorded=True) -> Barcodes:
+    """Copy a result out of the library (and free it); `recorded`: also look
+    for recorded columns and apparent pairs."""
     L = N.lib()
     try:
         b = Barcodes()
@@ -112,8 +123,8 @@ def _take_result(h, with_stats=True) -> Barcodes:
                 b.intervals.append(np.zeros((0, 2), np.float32))
                 b.critical.append(np.zeros((0, 4), np.int32))
         if with_stats:
-            b.stats = _stats_dict(st)
-        for p in range(1, st.max_dim + 1):
+            b._raw_stats = st
+        for p in range(1, st.max_dim + 1 if recorded else 1):
             dp, ip = C.POINTER(C.c_float)(), C.POINTER(C.c_uint64)()
             m = L.rpp_result_columns(h, p, C.byref(dp), C.byref(ip))
             if m >= 0:
@@ -223,7 +234,8 @@ def rpp_barcodes_batched(clouds, max_dim: int = 1, thresholds=None, quantiles=No
     s = _stream_ptr(stream, any(cu for _, _, cu, _ in items))
     N.check(N.lib().rpp_barcodes_batched(ctx.handle, B, ptrs, ns, dims, max_dim, th, qs, s, outs),
             "rpp_barcodes_batched")
-    return [_take_result(outs[i]) for i in range(B)]
+    rec = (ctx.record & (N.RPP_RECORD_COLUMNS | N.RPP_RECORD_APPARENT)) != 0
+    return [_take_result(outs[i], recorded=rec) for i in range(B)]
 
 
 class Server:

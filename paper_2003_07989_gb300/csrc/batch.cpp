@@ -69,6 +69,7 @@ struct Bufs {
     BatchOut *outs;
     Leftover *left;
     int32_t *lcloud;
+    uint16_t *app_w;  // per cloud and edge: the vertex of its apparent pair, or 0xFFFF
     float *h_pts;
     BatchCloud *h_clouds;
     int32_t *h_order;
@@ -88,7 +89,7 @@ uint64_t pow2_ge(uint64_t x) {
 // Capacities of one fused launch, rounded up to powers of two so that launches
 // of similar batches reuse the same buffers and captured graphs.
 struct Caps {
-    uint64_t clouds = 0, pts = 0, D = 0, mst = 0, left = 0;
+    uint64_t clouds = 0, pts = 0, D = 0, mst = 0, left = 0, aw = 0;
 };
 
 Caps caps_of(const std::vector<Instance> &ins, const std::vector<int> &idx) {
@@ -105,6 +106,7 @@ Caps caps_of(const std::vector<Instance> &ins, const std::vector<int> &idx) {
     c.pts = pow2_ge(std::max<uint64_t>(pts, 1024));
     c.D = pow2_ge(std::max<uint64_t>(D, 1024));
     c.mst = pow2_ge(std::max<uint64_t>(mst, 1024));
+    c.aw = pow2_ge(std::max<uint64_t>(cols, 1024));
     // leftover columns are a small share of the columns (the apparent-pair
     // rate); a launch that finds more runs the overflowing clouds alone
     c.left = std::min<uint64_t>(LEFT_CAP, pow2_ge(std::max<uint64_t>(cols / 16, 4096)));
@@ -117,7 +119,7 @@ size_t launch_device_bytes(const Caps &c, uint64_t rows) {
     auto slack = [](size_t b) { return ((b + b / 4) + 255) & ~(size_t)255; };
     return slack(c.pts * 4) + slack(c.clouds * (sizeof(BatchCloud) + 4 + sizeof(BatchOut) + 8)) +
            slack(c.D * 4) + slack(c.mst * 8) + slack(c.left * (sizeof(Leftover) + 4)) +
-           slack(rows * 12) + 8 * 256;
+           slack(c.aw * 2) + slack(rows * 12) + slack(rows) + 8 * 256;
 }
 
 Status get_bufs(Workspace &ws, const Caps &c, Bufs &b) {
@@ -140,6 +142,8 @@ Status get_bufs(Workspace &ws, const Caps &c, Bufs &b) {
     b.left = (Leftover *)p;
     RPP_TRY(ws.dev(ws.b_lcloud, c.left * 4, &p));
     b.lcloud = (int32_t *)p;
+    RPP_TRY(ws.dev(ws.b_aw, c.aw * 2, &p));
+    b.app_w = (uint16_t *)p;
     RPP_TRY(ws.host(ws.hb_pts, c.pts * 4, &p));
     b.h_pts = (float *)p;
     RPP_TRY(ws.host(ws.hb_clouds, c.clouds * sizeof(BatchCloud), &p));
@@ -170,6 +174,7 @@ Status fused_graph(Workspace &ws, const BatchPlan &plan, const Caps &c, const Bu
         (uintptr_t)b.pts,       (uintptr_t)b.clouds,     (uintptr_t)b.order,
         (uintptr_t)b.ctl,       (uintptr_t)b.D,          (uintptr_t)b.mst,
         (uintptr_t)b.outs,      (uintptr_t)b.left,       (uintptr_t)b.lcloud,
+        (uintptr_t)b.app_w,     (uintptr_t)c.aw,
         (uintptr_t)b.h_ctl,     (uintptr_t)b.h_outs,     (uintptr_t)b.h_mst};
     for (auto &g : ws.graphs)
         if (g.first == key) {
@@ -186,7 +191,7 @@ Status fused_graph(Workspace &ws, const BatchPlan &plan, const Caps &c, const Bu
     const long long l0 = g_launches;
     cudaMemcpyAsync(b.ctl, &b.h_ctl[0], sizeof(BatchCtl), cudaMemcpyHostToDevice, cs);
     launch_batch_h1(plan, b.pts, b.clouds, b.order, b.ctl, b.D, b.mst, b.outs, b.left, b.lcloud,
-                    c.left, cs);
+                    c.left, b.app_w, cs);
     cudaMemcpyAsync(b.h_outs, b.outs, c.clouds * sizeof(BatchOut), cudaMemcpyDeviceToHost, cs);
     cudaMemcpyAsync(&b.h_ctl[1], b.ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, cs);
     cudaMemcpyAsync(b.h_mst, b.mst, c.mst * 8, cudaMemcpyDeviceToHost, cs);
@@ -230,7 +235,7 @@ Status autotune(rpp_context *ctx, const Bufs &b, const Caps &caps, int nmax, int
             cudaMemcpyAsync(b.ctl, &b.h_ctl[0], sizeof(BatchCtl), cudaMemcpyHostToDevice, s);
             cudaEventRecord(e0, s);
             launch_batch_h1(plan, b.pts, b.clouds, b.order, b.ctl, b.D, b.mst, b.outs, b.left,
-                            b.lcloud, caps.left, s);
+                            b.lcloud, caps.left, b.app_w, s);
             cudaEventRecord(e1, s);
             cudaError_t e = cudaStreamSynchronize(s);
             if (e != cudaSuccess) {
@@ -270,7 +275,7 @@ Status run_launch(rpp_context *ctx, Workspace &ws, const std::vector<Instance> &
     RPP_TRY(get_bufs(ws, caps, b));
 
     // layout and inputs
-    int64_t pt = 0, dd = 0;
+    int64_t pt = 0, dd = 0, aw = 0;
     int32_t ms = 0;
     std::vector<const float *> dev_src(k, nullptr);
     bool any_dev = false, any_host = false;
@@ -287,6 +292,7 @@ Status run_launch(rpp_context *ctx, Workspace &ws, const std::vector<Instance> &
         c.quantile = in.quantile;
         c.max_dim = in.max_dim;
         c.pad = 0;
+        c.aw_off = aw;
         const size_t cnt = (size_t)c.n * c.dim;
         if (is_device_pointer(in.data)) {
             dev_src[j] = in.data;
@@ -297,6 +303,7 @@ Status run_launch(rpp_context *ctx, Workspace &ws, const std::vector<Instance> &
         }
         pt += (int64_t)cnt;
         dd += (int64_t)c.n * c.ld;
+        aw += (int64_t)c.n * (c.n - 1) / 2;
         ms += std::max(0, c.n - 1);
         b.h_order[j] = j;
     }
@@ -363,8 +370,8 @@ Status run_launch(rpp_context *ctx, Workspace &ws, const std::vector<Instance> &
     for (int j = 0; j < k; ++j) W[j].slot = j;
     for (uint64_t i = 0; i < got; ++i) W[b.h_lcloud[i]].left.push_back(b.h_left[i]);
     std::vector<int32_t> jobs;
-    std::vector<int64_t> off;
-    int64_t rows = 0;
+    std::vector<int64_t> off, aoff;  // per job: rows (n^2) and edges (C(n,2)) before it
+    int64_t rows = 0, edges = 0;
     for (int j = 0; j < k; ++j) {
         if (W[j].left.size() < b.h_outs[j].nleft) {
             W[j].fallback = true;
@@ -374,27 +381,33 @@ Status run_launch(rpp_context *ctx, Workspace &ws, const std::vector<Instance> &
         W[j].job = (int64_t)jobs.size();
         jobs.push_back(j);
         off.push_back(rows);
+        aoff.push_back(edges);
         rows += (int64_t)b.h_clouds[j].n * b.h_clouds[j].n;
+        edges += (int64_t)b.h_clouds[j].n * (b.h_clouds[j].n - 1) / 2;
     }
     float *hD = nullptr;
     uint64_t *hN = nullptr;
+    uint16_t *hA = nullptr;
     if (!jobs.empty()) {  // distance rows and neighbour lists of the clouds with leftovers
         void *p, *hp;
         const size_t nj = jobs.size();
         RPP_TRY(ws.dev(ws.b_jobs, nj * 4, &p));
         int32_t *djobs = (int32_t *)p;
-        RPP_TRY(ws.dev(ws.b_off, nj * 8, &p));
+        RPP_TRY(ws.dev(ws.b_off, 2 * nj * 8, &p));
         int64_t *doff = (int64_t *)p;
         RPP_TRY(ws.dev(ws.b_Dout, (size_t)rows * 4, &p));
         float *dD = (float *)p;
         RPP_TRY(ws.dev(ws.b_nbr, (size_t)rows * 8, &p));
         uint64_t *dN = (uint64_t *)p;
-        RPP_TRY(ws.host(ws.hb_jobs, nj * 4 + nj * 8, &hp));
+        RPP_TRY(ws.dev(ws.b_awout, (size_t)std::max<int64_t>(edges, 1) * 2, &p));
+        uint16_t *dA = (uint16_t *)p;
+        RPP_TRY(ws.host(ws.hb_jobs, nj * 4 + 2 * nj * 8, &hp));
         std::memcpy(hp, jobs.data(), nj * 4);
         std::memcpy((char *)hp + nj * 4, off.data(), nj * 8);
+        std::memcpy((char *)hp + nj * 4 + nj * 8, aoff.data(), nj * 8);
         RPP_CK(cudaMemcpyAsync(djobs, hp, nj * 4, cudaMemcpyHostToDevice, s));
-        RPP_CK(cudaMemcpyAsync(doff, (char *)hp + nj * 4, nj * 8, cudaMemcpyHostToDevice, s));
-        launch_batch_rows(b.D, b.clouds, djobs, (int)nj, doff, nmax, dD, dN, s);
+        RPP_CK(cudaMemcpyAsync(doff, (char *)hp + nj * 4, 2 * nj * 8, cudaMemcpyHostToDevice, s));
+        launch_batch_rows(b.D, b.clouds, djobs, (int)nj, doff, nmax, dD, dN, b.app_w, dA, s);
         RPP_CK(cudaGetLastError());
         RPP_TRY(ws.host(ws.hb_Dout, (size_t)rows * 4, &hp));
         hD = (float *)hp;
@@ -402,6 +415,9 @@ Status run_launch(rpp_context *ctx, Workspace &ws, const std::vector<Instance> &
         hN = (uint64_t *)hp;
         RPP_CK(cudaMemcpyAsync(hD, dD, (size_t)rows * 4, cudaMemcpyDeviceToHost, s));
         RPP_CK(cudaMemcpyAsync(hN, dN, (size_t)rows * 8, cudaMemcpyDeviceToHost, s));
+        RPP_TRY(ws.host(ws.hb_awout, (size_t)std::max<int64_t>(edges, 1) * 2, &hp));
+        hA = (uint16_t *)hp;
+        RPP_CK(cudaMemcpyAsync(hA, dA, (size_t)edges * 2, cudaMemcpyDeviceToHost, s));
         const double a2 = now_ms();
         RPP_CK(cudaStreamSynchronize(s));
         dev_ms += now_ms() - a2;
@@ -412,8 +428,16 @@ Status run_launch(rpp_context *ctx, Workspace &ws, const std::vector<Instance> &
     const int inner = (int)jobs.size() >= ctx->host_threads ? 1 : ctx->host_threads;
     std::vector<rpp_result *> res(k, nullptr);
     std::vector<std::string> errs(k);
+    // the heaviest reductions first (most leftover columns, then most
+    // points), so that the threads do not wait on one long cloud at the end
+    std::vector<int> sched(k);
+    for (int j = 0; j < k; ++j) sched[j] = j;
+    std::stable_sort(sched.begin(), sched.end(), [&](int x, int y) {
+        if (W[x].left.size() != W[y].left.size()) return W[x].left.size() > W[y].left.size();
+        return b.h_clouds[x].n > b.h_clouds[y].n;
+    });
     parallel_for(ctx->host_threads, k, [&](int64_t jj) {
-        const int j = (int)jj;
+        const int j = sched[jj];
         if (W[j].fallback) return;
         const BatchCloud &c = b.h_clouds[j];
         const BatchOut &o = b.h_outs[j];
@@ -461,8 +485,9 @@ Status run_launch(rpp_context *ctx, Workspace &ws, const std::vector<Instance> &
                 I.ld = n;
                 I.B = &B;
                 I.nbr = hN + off[W[j].job];
-                I.app_tau = nullptr;  // apparent pivots are recognised by testing them again
+                I.app_tau = nullptr;  // no sorted taus: the apparent vertex of each edge instead
                 I.napp = 0;
+                I.app_w = hA + aoff[W[j].job];  // the apparent pairs found on the GPU
                 I.t = o.t;
                 std::vector<Leftover> &L = W[j].left;
                 std::sort(L.begin(), L.end(),

@@ -95,7 +95,8 @@ __global__ void __launch_bounds__(512) k_batch_h1(
     const float *__restrict__ pts, const BatchCloud *__restrict__ clouds,
     const int32_t *__restrict__ order, BatchCtl *ctl, int nmax, int points_floats,
     float *__restrict__ Dbuf, uint64_t *__restrict__ mst_out, BatchOut *__restrict__ outs,
-    Leftover *__restrict__ left, int32_t *__restrict__ left_cloud, uint64_t left_cap) {
+    Leftover *__restrict__ left, int32_t *__restrict__ left_cloud, uint64_t left_cap,
+    uint16_t *__restrict__ app_w) {
     const int nclouds = ctl->nclouds;
     unsigned int *queue = &ctl->queue;
     unsigned long long *left_count = &ctl->left_count;
@@ -320,6 +321,7 @@ __global__ void __launch_bounds__(512) k_batch_h1(
             bool have = false;
             int u = 0, w = 0, scan = 0, best_v = -1;
             float diam = 0.0f, best_d = 0.0f;
+            uint16_t *aw = app_w + C.aw_off;
             for (;;) {
                 while (!have && e < m) {
                     edge_decode(e, &u, &w);
@@ -332,6 +334,7 @@ __global__ void __launch_bounds__(512) k_batch_h1(
                             else hi = mid;
                         }
                         if (lo < nm && S.mst[lo] == e) {
+                            if (gl == 0) aw[e] = 0xFFFFu;
                             e += ngroups;
                             continue;
                         }
@@ -340,6 +343,7 @@ __global__ void __launch_bounds__(512) k_batch_h1(
                         best_d = __uint_as_float(0x7f800000u);
                         best_v = -1;
                     } else {
+                        if (gl == 0) aw[e] = 0xFFFFu;
                         e += ngroups;
                     }
                 }
@@ -372,6 +376,7 @@ __global__ void __launch_bounds__(512) k_batch_h1(
                             bool apparent = true;
                             if (u > x && dw == diam) apparent = false;  // facet {w, x}
                             if (w > x && du == diam) apparent = false;  // facet {u, x}
+                            aw[e] = apparent ? (uint16_t)x : (uint16_t)0xFFFFu;
                             if (apparent) {
                                 ++napp;
                             } else {
@@ -397,6 +402,7 @@ __global__ void __launch_bounds__(512) k_batch_h1(
                         }
                         if (gl == 0) {
                             emit = true;
+                            aw[e] = 0xFFFFu;
                             if (best_v >= 0) {
                                 const int x2 = best_v;
                                 const int a = max(u, x2), c = min(w, x2);
@@ -458,14 +464,22 @@ __global__ void __launch_bounds__(512) k_batch_h1(
 __global__ void __launch_bounds__(512) k_batch_rows(const float *__restrict__ Dbuf,
                                                     const BatchCloud *__restrict__ clouds,
                                                     const int32_t *__restrict__ jobs,
-                                                    const int64_t *__restrict__ out_off,
+                                                    const int64_t *__restrict__ out_off, int njobs,
                                                     float *__restrict__ Dout,
-                                                    uint64_t *__restrict__ nbr) {
+                                                    uint64_t *__restrict__ nbr,
+                                                    const uint16_t *__restrict__ app_w,
+                                                    uint16_t *__restrict__ aw_out) {
     extern __shared__ unsigned long long keys[];
     const int j = blockIdx.y;
     const BatchCloud C = clouds[jobs[j]];
     const int n = C.n, row = blockIdx.x;
     if (row >= n) return;
+    {  // this row's edges {row, w}, w < row: indices C(row, 2) .. C(row, 2) + row - 1
+        const int64_t e0 = (int64_t)row * (row - 1) / 2;
+        const uint16_t *src = app_w + C.aw_off + e0;
+        uint16_t *dst = aw_out + out_off[njobs + j] + e0;
+        for (int i = threadIdx.x; i < row; i += blockDim.x) dst[i] = src[i];
+    }
     const int p2 = pow2_at_least(n);
     const float *src = Dbuf + C.d_off + (int64_t)row * C.ld;
     float *drow = Dout + out_off[j] + (int64_t)row * n;
@@ -523,11 +537,11 @@ BatchPlan plan_g(int nmax, int dimcap, BatchConfig cfg, int sms) {
 template <int G>
 void launch_g(const BatchPlan &P, const float *pts, const BatchCloud *clouds, const int32_t *order,
               BatchCtl *ctl, float *Dbuf, uint64_t *mst_out, BatchOut *outs, Leftover *left,
-              int32_t *left_cloud, uint64_t left_cap, cudaStream_t s) {
+              int32_t *left_cloud, uint64_t left_cap, uint16_t *app_w, cudaStream_t s) {
     ++g_launches;
     k_batch_h1<G><<<P.blocks, P.cfg.threads, P.smem, s>>>(pts, clouds, order, ctl, P.nmax,
                                                           P.nmax * P.dimcap, Dbuf, mst_out, outs,
-                                                          left, left_cloud, left_cap);
+                                                          left, left_cloud, left_cap, app_w);
 }
 
 }  // namespace
@@ -544,24 +558,24 @@ BatchPlan plan_batch_h1(int nmax, int dimcap, BatchConfig cfg, int sms) {
 void launch_batch_h1(const BatchPlan &P, const float *pts, const BatchCloud *clouds,
                      const int32_t *order, BatchCtl *ctl, float *Dbuf, uint64_t *mst_out,
                      BatchOut *outs, Leftover *left, int32_t *left_cloud, uint64_t left_cap,
-                     cudaStream_t s) {
+                     uint16_t *app_w, cudaStream_t s) {
     switch (P.cfg.group) {
-        case 4: launch_g<4>(P, pts, clouds, order, ctl, Dbuf, mst_out, outs, left, left_cloud, left_cap, s); break;
-        case 16: launch_g<16>(P, pts, clouds, order, ctl, Dbuf, mst_out, outs, left, left_cloud, left_cap, s); break;
-        case 32: launch_g<32>(P, pts, clouds, order, ctl, Dbuf, mst_out, outs, left, left_cloud, left_cap, s); break;
-        default: launch_g<8>(P, pts, clouds, order, ctl, Dbuf, mst_out, outs, left, left_cloud, left_cap, s);
+        case 4: launch_g<4>(P, pts, clouds, order, ctl, Dbuf, mst_out, outs, left, left_cloud, left_cap, app_w, s); break;
+        case 16: launch_g<16>(P, pts, clouds, order, ctl, Dbuf, mst_out, outs, left, left_cloud, left_cap, app_w, s); break;
+        case 32: launch_g<32>(P, pts, clouds, order, ctl, Dbuf, mst_out, outs, left, left_cloud, left_cap, app_w, s); break;
+        default: launch_g<8>(P, pts, clouds, order, ctl, Dbuf, mst_out, outs, left, left_cloud, left_cap, app_w, s);
     }
 }
 
 void launch_batch_rows(const float *Dbuf, const BatchCloud *clouds, const int32_t *jobs, int njobs,
                        const int64_t *out_off, int nmax, float *Dout, uint64_t *nbr,
-                       cudaStream_t s) {
+                       const uint16_t *app_w, uint16_t *aw_out, cudaStream_t s) {
     if (njobs <= 0) return;
     const size_t smem = (size_t)pow2_at_least(nmax) * 8;
     allow_dynamic_smem((const void *)k_batch_rows, smem);
     ++g_launches;
-    k_batch_rows<<<dim3((unsigned)nmax, (unsigned)njobs), 256, smem, s>>>(Dbuf, clouds, jobs,
-                                                                          out_off, Dout, nbr);
+    k_batch_rows<<<dim3((unsigned)nmax, (unsigned)njobs), 256, smem, s>>>(
+        Dbuf, clouds, jobs, out_off, njobs, Dout, nbr, app_w, aw_out);
 }
 
 void launch_gather_points(const float *const *src, const BatchCloud *clouds, int nclouds,

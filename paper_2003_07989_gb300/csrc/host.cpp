@@ -361,8 +361,9 @@ struct Reducer {
 
     // The apparent column owning pivot tau, if any: tau is among the apparent
     // taus, and its owner is the youngest facet of tau (vertices into s, the
-    // vertex tau adds to it into *added). Without a stored array of taus
-    // (I.app_tau null) the pair is tested again from its definition: tau is
+    // vertex tau adds to it into *added). Given each edge's apparent vertex
+    // (I.app_w), s owns tau iff that vertex is *added. Without either (I.app_tau
+    // and I.app_w null) the pair is tested again from its definition: tau is
     // apparent iff its youngest facet s has tau's diameter and tau is the
     // oldest cofacet of s, i.e. no vertex w above *added lies within tau's
     // diameter of every vertex of s. (A cleared column never passes: an
@@ -390,6 +391,8 @@ struct Reducer {
         for (int a = 0, k = 0; a <= p + 1; ++a)
             if (a != best) s[k++] = u[a];
         *added = u[best];
+        if (I.app_w && p == 1)  // s is apparent with tau iff tau adds its recorded vertex
+            return I.app_w[(uint64_t)s[0] * (uint64_t)(s[0] - 1) / 2 + (uint64_t)s[1]] == *added;
         if (!I.app_tau)
             for (int w = (int)n - 1; w > *added; --w) {
                 if (in_simplex(s, w)) continue;

@@ -24,6 +24,9 @@ struct HostInstance {
     // pairs are recognised by testing them again
     const uint64_t *app_tau = nullptr;
     uint64_t napp = 0;
+    // dimension 1, instead of app_tau (may be null): for every edge index, the
+    // vertex its apparent pair adds to it, 0xFFFF if it has none
+    const uint16_t *app_w = nullptr;
     // dimension 1 only (may be null; n <= 65535): every edge inside the
     // threshold in coboundary order (diameter descending, index ascending), as
     // the GPU sorted them: its vertices packed as (a << 16) | b, a > b, and

@@ -154,6 +154,7 @@ struct BatchCloud {
     float quantile;   // > 0: threshold = the ceil(q C(n,2))-th smallest distance
     int32_t max_dim;  // 0: H0 only (no apparent-pair test)
     int32_t pad;
+    int64_t aw_off;   // offset of its C(n,2) entries in the apparent-vertex buffer
 };
 
 // What the fused pass reports per cloud.
@@ -189,17 +190,22 @@ struct BatchPlan {
     BatchConfig cfg;
 };
 BatchPlan plan_batch_h1(int nmax, int dimcap, BatchConfig cfg, int sms);
+// app_w: per cloud (from aw_off), for every edge index e < C(n,2), the vertex
+// that the edge's apparent pair adds to it, or 0xFFFF if the edge is not the
+// first simplex of an apparent pair (outside the threshold, cleared, leftover).
 void launch_batch_h1(const BatchPlan &plan, const float *pts, const BatchCloud *clouds,
                      const int32_t *order, BatchCtl *ctl, float *Dbuf, uint64_t *mst_out,
                      BatchOut *outs, Leftover *left, int32_t *left_cloud, uint64_t left_cap,
-                     cudaStream_t s);
+                     uint16_t *app_w, cudaStream_t s);
 
 // Rows of selected clouds for the host reduction: for job j (cloud c =
-// jobs[j]) copy its distance matrix to Dout + out_off[j] (stride n) and its
-// sorted neighbour lists (as launch_sort_rows) to nbr + nbr_off[j].
+// jobs[j]) copy its distance matrix to Dout + out_off[j] (stride n), its
+// sorted neighbour lists (as launch_sort_rows) to nbr + out_off[j], and its
+// apparent vertices (app_w from the cloud's aw_off) to aw_out +
+// out_off[njobs + j].
 void launch_batch_rows(const float *Dbuf, const BatchCloud *clouds, const int32_t *jobs, int njobs,
                        const int64_t *out_off, int nmax, float *Dout, uint64_t *nbr,
-                       cudaStream_t s);
+                       const uint16_t *app_w, uint16_t *aw_out, cudaStream_t s);
 
 // Gather clouds given by device pointers into the packed point buffer.
 void launch_gather_points(const float *const *src, const BatchCloud *clouds, int nclouds,

@@ -78,8 +78,10 @@ struct Workspace {
     std::vector<uint64_t> binom_store;
     std::vector<cudaEvent_t> events;  // pool for stage timing
     // the fused batch pass (batch.cpp)
+    DevBuf b_aw, b_awout;
     DevBuf b_pts, b_clouds, b_order, b_ctl, b_D, b_mst, b_outs, b_left, b_lcloud, b_jobs, b_off,
         b_Dout, b_nbr, b_src;
+    HostBuf hb_awout;
     HostBuf hb_pts, hb_clouds, hb_order, hb_ctl, hb_outs, hb_mst, hb_left, hb_lcloud, hb_jobs,
         hb_off, hb_Dout, hb_nbr, hb_src;
     // captured fused launches by (shape, buffer addresses), most recent last
