@@ -5,14 +5,17 @@
 // Reduction of one leftover column j follows Alg. 1: while the pivot (oldest
 // nonzero entry) of the working column has an owner, add the owner's reduced
 // column. Almost every owner is an apparent column, whose reduced column is
-// its plain coboundary; only rarely is it another leftover column. So:
-//   Phase A (in parallel over columns): walk through apparent owners only,
-//     stopping at the first pivot that no apparent column owns.
-//   Phase B (in column order): if that pivot belongs to an earlier leftover
-//     column, add that column's reduced column and continue the walk, now
-//     also looking up earlier leftovers; the first free pivot pairs with j.
-// Both phases add exactly the columns Alg. 1 adds, in the same order. A
-// reduced column is kept as the set V of simplices whose coboundaries it sums.
+// its plain coboundary; only rarely is it another leftover column.
+//   Dimension 1: every leftover column walks in its own thread, through
+//     apparent owners and through earlier leftover columns once these are
+//     finished; a pivot that no finished column owns is kept only when every
+//     unfinished earlier column has moved past it (see Ledger).
+//   Dimensions p >= 2: Phase A (in parallel over columns) walks through
+//     apparent owners only, stopping at the first pivot that no apparent
+//     column owns; Phase B (in column order) adds earlier leftover columns
+//     where that pivot belongs to one and continues the walk.
+// Both add exactly the columns Alg. 1 adds, in the same order. A reduced
+// column is kept as the set V of simplices whose coboundaries it sums.
 //
 // The working column is a heap of lazy cursors, one per added coboundary.
 // Each cursor lists its cofacets oldest first (smallest diameter, then largest
@@ -30,6 +33,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <cmath>
 #include <condition_variable>
 #include <cstring>
@@ -624,7 +628,7 @@ void reduce_general(const HostInstance &I, int p, const Leftover *left, int64_t 
 // parity changed since is dropped when it surfaces. Every nonzero triangle
 // stays reachable: the last of its edges to enter V has a cursor that listed
 // it (or will) after its parity last changed. Adding another leftover's column
-// (Phase B) can remove edges from V; the walk then restarts from the new V,
+// can remove edges from V; the walk then restarts from the new V,
 // each cursor placed just past the cancelled pivot (the sum is zero up to
 // there).
 //
@@ -773,6 +777,71 @@ struct RadixHeap {
     void replace_top(E e) {
         pop();
         push(e);
+    }
+};
+
+// Pivots of the leftover columns of dimension 1 reduced so far, shared by
+// the columns that are reduced in parallel. Column j adds column i < j once
+// i is finished, and keeps a pivot that no finished column owns only when
+// every unfinished column before it has moved past that pivot: pivots only
+// move forward (an addition cancels the pivot and brings younger entries
+// only), so none of those columns can end there. The additions are then
+// those of Alg. 1 in column order, whatever the interleaving, and the lowest
+// unfinished column never waits. Columns must be started in increasing order
+// and each finished by the thread that started it.
+template <class K>
+struct Ledger {
+    std::mutex m;
+    std::condition_variable cv;
+    std::unordered_map<uint64_t, int64_t> owner;  // pivot index -> finished column
+    std::vector<std::vector<uint64_t>> &V;        // reduced columns, final once finished
+    std::vector<char> done;
+    int64_t low = 0;                              // columns below are finished
+    // Per column, a lower bound of its current pivot as a 64-bit key: exact
+    // for 64-bit keys, the diameter bits alone for 128-bit ones.
+    std::unique_ptr<std::atomic<uint64_t>[]> front;
+
+    Ledger(std::vector<std::vector<uint64_t>> &V_, int64_t ncols)
+        : V(V_), done(ncols, 0), front(new std::atomic<uint64_t>[ncols]) {
+        owner.reserve((size_t)ncols * 2);
+        for (int64_t j = 0; j < ncols; ++j) front[j].store(0, std::memory_order_relaxed);
+    }
+    static uint64_t lower(u128 k) {
+        if (k == NONE) return ~0ull;
+        if (std::is_same<typename K::T, uint64_t>::value) return (uint64_t)K::make(key_diam(k), key_index(k));
+        return (uint64_t)float_bits(key_diam(k)) << 32;
+    }
+    static uint64_t upper(u128 k) {
+        if (std::is_same<typename K::T, uint64_t>::value) return (uint64_t)K::make(key_diam(k), key_index(k));
+        return ((uint64_t)float_bits(key_diam(k)) << 32) | 0xffffffffull;
+    }
+    void advance(int64_t j, u128 k) { front[j].store(lower(k), std::memory_order_relaxed); }
+
+    // The finished column that owns pivot k of column j, or -1 when k is
+    // free for j; waits while an unfinished earlier column may still end at k.
+    int64_t query(int64_t j, u128 k) {
+        const uint64_t ub = upper(k);
+        std::unique_lock<std::mutex> g(m);
+        for (int round = 0;; ++round) {
+            auto it = owner.find(key_index(k));
+            if (it != owner.end()) return it->second;
+            while (low < j && done[low]) ++low;
+            bool blocked = false;
+            for (int64_t i = low; i < j && !blocked; ++i)
+                blocked = !done[i] && front[i].load(std::memory_order_relaxed) <= ub;
+            if (!blocked) return -1;
+            // earlier columns move their pivots without notice: look again soon
+            cv.wait_for(g, std::chrono::microseconds(round < 64 ? 10 : 100));
+        }
+    }
+    // Column j is finished with pivot k (NONE: a zero column); V[j] is final.
+    void finish(int64_t j, u128 k) {
+        {
+            std::lock_guard<std::mutex> g(m);
+            if (k != NONE) owner[key_index(k)] = j;
+            done[j] = 1;
+        }
+        cv.notify_all();
     }
 };
 
@@ -1118,20 +1187,14 @@ struct Walk1 {
         return NONE;
     }
 
-    // Add owners of the pivot until it is free (fin == nullptr: apparent only).
-    u128 walk(const std::unordered_map<uint64_t, int64_t> *fin,
-              const std::vector<std::vector<uint64_t>> *finV) {
+    // Add owners of the pivot until it is free; led: the finished leftover
+    // columns, j: this column's position among them.
+    u128 walk(Ledger<K> &led, int64_t j) {
         for (;;) {
             const u128 k = pivot();
             if (k == NONE) return NONE;
             ++reads;
-            if (fin) {
-                auto it = fin->find(key_index(k));
-                if (it != fin->end()) {
-                    add_leftover((*finV)[it->second], k);
-                    continue;
-                }
-            }
+            led.advance(j, k);
             int s[3], added;
             if (sweep ? sweep_owner(s, &added) : R.apparent_owner(k, s, &added)) {
                 ++additions;  // its oldest cofacet is the pivot, which adds `added`
@@ -1148,6 +1211,11 @@ struct Walk1 {
                     add_edge(s[0], s[1], key_diam(k), added);
                     if (can_sweep() && V.size() >= SWEEP_MIN) enter_sweep(k);
                 }
+                continue;
+            }
+            const int64_t i = led.query(j, k);  // a pivot has one owner at most
+            if (i >= 0) {
+                add_leftover(led.V[i], k);
                 continue;
             }
             return k;
@@ -1576,68 +1644,61 @@ template <class K>
 void reduce_p1(const HostInstance &I, const Leftover *left, int64_t nleft, int threads,
                std::vector<HostPair> &out, ReduceStats &stats) {
     Reducer R(I, 1);
-    std::vector<u128> cand(nleft, NONE);
+    std::vector<u128> piv(nleft, NONE);
     std::vector<std::vector<uint64_t>> V(nleft);  // reduced columns as edge sets
     std::vector<char> walked(nleft, 0);
     std::vector<int64_t> adds(nleft, 0), reads(nleft, 0), entries(nleft, 0), levels(nleft, 0);
+    Ledger<K> led(V, nleft);
+    for (int64_t j = 0; j < nleft; ++j)
+        if (left[j].pivot != NO_PIVOT) led.advance(j, age_key(left[j].pdiam, left[j].pivot));
 
-    auto phase_a = [&](int64_t j) {
+    auto column = [&](int64_t j) {
         const Leftover &L = left[j];
         V[j].push_back(L.sigma);
-        if (L.pivot == NO_PIVOT) return;
+        if (L.pivot == NO_PIVOT) {
+            led.finish(j, NONE);
+            return;
+        }
         const u128 k0 = age_key(L.pdiam, L.pivot);
         int s[3], added;
         ++reads[j];
-        if (!R.apparent_owner(k0, s, &added)) {
-            cand[j] = k0;  // the unreduced pivot is free of apparent owners
+        if (!R.apparent_owner(k0, s, &added) && led.query(j, k0) < 0) {
+            piv[j] = k0;  // the unreduced pivot is free
+            led.finish(j, k0);
             return;
         }
         Walk1<K> W(I, R, adjacency_scratch(I.n), threads);
         int v[2];
         decode_host(*I.B, L.sigma, 1, I.n, v);
         W.add_edge(v[0], v[1], L.diam, first_vertex(R, L, v));
-        cand[j] = W.walk(nullptr, nullptr);
+        const u128 k = W.walk(led, j);
         V[j] = W.edges();
+        piv[j] = k;
         walked[j] = 1;
-        adds[j] += W.additions;
+        adds[j] = W.additions;
         reads[j] += W.reads;
-        entries[j] += W.entries;
-        levels[j] += W.levels;
+        entries[j] = W.entries;
+        levels[j] = W.levels;
+        led.finish(j, k);
     };
+    // columns start in increasing order (the pool hands out indices in order)
     if (threads <= 1 || nleft < 16) {
-        for (int64_t j = 0; j < nleft; ++j) phase_a(j);
+        for (int64_t j = 0; j < nleft; ++j) column(j);
     } else {
-        pool(threads).parallel_for(nleft, phase_a);
+        pool(threads).parallel_for(nleft, column);
     }
 
-    std::unordered_map<uint64_t, int64_t> owner;
-    owner.reserve((size_t)nleft * 2);
     for (int64_t j = 0; j < nleft; ++j) {
         const Leftover &L = left[j];
-        auto it = cand[j] != NONE ? owner.find(key_index(cand[j])) : owner.end();
-        if (it != owner.end()) {
-            Walk1<K> W(I, R, adjacency_scratch(I.n), threads);  // resume from the reduced column so far, whose pivot is cand[j]
-            W.V = V[j];
-            ++W.reads;
-            W.add_leftover(V[it->second], cand[j]);
-            cand[j] = W.walk(&owner, &V);
-            V[j] = W.edges();
-            adds[j] += W.additions;
-            reads[j] += W.reads;
-            entries[j] += W.entries;
-            levels[j] += W.levels;
-            walked[j] = 1;
-        }
         HostPair P;
         P.sigma = L.sigma;
         P.birth = L.diam;
-        if (cand[j] == NONE) {
+        if (piv[j] == NONE) {
             P.tau = NO_PIVOT;
             P.death = INFINITY;
         } else {
-            P.tau = key_index(cand[j]);
-            P.death = key_diam(cand[j]);
-            owner[P.tau] = j;
+            P.tau = key_index(piv[j]);
+            P.death = key_diam(piv[j]);
             if (!walked[j]) ++stats.free_pivot;
         }
         out.push_back(P);

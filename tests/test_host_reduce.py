@@ -113,3 +113,24 @@ def test_host_reduction_threads_agree(harness, tmp_path):
     a, _ = _run(harness, D, math.inf, 1, 0, tmp_path)
     b, _ = _run(harness, D, math.inf, 8, 1, tmp_path)
     assert np.array_equal(a, b)
+
+
+PARALLEL_CASES = {
+    # random edge orders and integer ties: many leftover columns whose walks
+    # meet one another's pivots
+    "perm160": lambda: (I.permutation_distances(160, seed=4), math.inf),
+    "int140": lambda: (I.integer_distances(140, levels=6, seed=2), math.inf),
+    "torus450_ties": CASES["torus450_ties"],
+}
+
+
+@pytest.mark.parametrize("name", sorted(PARALLEL_CASES))
+def test_host_reduction_parallel_columns_equal_oracle(harness, harness_wide, tmp_path, name):
+    """Leftover columns reduced concurrently (each waiting only for earlier
+    columns that may still end at its pivot) give the oracle's barcode on
+    every run, with 64- and 128-bit keys."""
+    D, t = PARALLEL_CASES[name]()
+    ref = O.barcodes(D, 1, t, O.MODE_COHOM_CLEAR).barcode(1)
+    for exe, threads in ((harness, 8), (harness, 3), (harness_wide, 8), (harness, 8)):
+        got, _ = _run(exe, D, t, threads, 0, tmp_path)
+        assert got.shape == ref.shape and np.array_equal(got, ref), (name, threads)
