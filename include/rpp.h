@@ -171,6 +171,25 @@ const rpp_critical *rpp_result_critical(const rpp_result *res, int32_t p);
 rpp_status rpp_result_stats(const rpp_result *res, rpp_stats *out);
 void rpp_result_free(rpp_result *res);
 
+/* The same accessors over many results at once (e.g. the out[] of
+ * rpp_barcodes_batched), so that a caller pays one call per array rather
+ * than one per result.
+ *   rpp_results_gather: the dimension-p intervals and realising edges of
+ *     results[0..count-1], result after result, into caller-owned host
+ *     arrays. offsets[0..count] (caller-owned) receives where each result's
+ *     entries start (offsets[count] = total); a result without dimension p
+ *     contributes none. With intervals and critical both NULL only offsets
+ *     are written, to size the arrays; otherwise each non-NULL array must
+ *     hold offsets[count] entries.
+ *   rpp_results_stats: out[i] = the counters of results[i].
+ *   rpp_results_free: rpp_result_free of every non-NULL entry.
+ * Errors: RPP_E_INVALID for a NULL array, a NULL result, count < 0 or p
+ * outside [0, RPP_MAX_DIM]; nothing is written then. */
+rpp_status rpp_results_gather(const rpp_result *const *results, int32_t count, int32_t p,
+                              int64_t *offsets, rpp_interval *intervals, rpp_critical *critical);
+rpp_status rpp_results_stats(const rpp_result *const *results, int32_t count, rpp_stats *out);
+void rpp_results_free(rpp_result *const *results, int32_t count);
+
 /* Many independent clouds in one call (the batched form of the paper's
  * computation; the paper itself runs one distance matrix at a time).
  * Clouds of at most 1024 points with max_dim <= 1 run together in one fused

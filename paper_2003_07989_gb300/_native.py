@@ -23,6 +23,7 @@ EXPORTED = [
     "rpp_status_string", "rpp_last_error", "rpp_distance_matrix", "rpp_context_set_record",
     "rpp_result_columns", "rpp_result_apparent", "rpp_filtration_edges_noalloc",
     "rpp_context_set_batch", "rpp_context_batch_tuning", "rpp_apparent_census",
+    "rpp_results_gather", "rpp_results_stats", "rpp_results_free",
 ]
 RPP_RECORD_COLUMNS, RPP_RECORD_APPARENT, RPP_RECORD_TIMING = 1, 2, 4
 STAGES = ["distance", "enclosing_radius", "build_columns", "sort_columns", "apparent",
@@ -119,12 +120,17 @@ def lib():
     L.rpp_filtration_edges_noalloc.argtypes = [vp, i64, C.c_float, vp, vp, i64,
                                                C.POINTER(i64), vp]
     L.rpp_context_set_batch.argtypes = [vp, i32, i32]
+    L.rpp_results_gather.argtypes = [C.POINTER(vp), i32, i32, vp, vp, vp]
+    L.rpp_results_stats.argtypes = [C.POINTER(vp), i32, C.POINTER(Stats)]
+    L.rpp_results_free.argtypes = [C.POINTER(vp), i32]
+    L.rpp_results_free.restype = None
     L.rpp_context_batch_tuning.argtypes = [vp, i32, C.POINTER(i32), C.POINTER(i32)]
     for name in ("rpp_context_set_batch", "rpp_context_batch_tuning",
                  "rpp_context_create", "rpp_barcodes", "rpp_barcodes_quantile",
                  "rpp_distance_matrix", "rpp_context_set_record", "rpp_filtration_edges_noalloc",
                  "rpp_result_stats", "rpp_barcodes_batched", "rpp_barcodes_backward",
-                 "rpp_server_create", "rpp_server_submit", "rpp_server_poll"):
+                 "rpp_server_create", "rpp_server_submit", "rpp_server_poll",
+                 "rpp_results_gather", "rpp_results_stats"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L

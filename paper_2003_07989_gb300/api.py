@@ -102,9 +102,8 @@ def _stats_dict(s: N.Stats) -> dict:
     return out
 
 
-def _take_result(h, with_stats=True, recorded=True) -> Barcodes:
-    """Copy a result out of the library (and free it); `recorded`: also look
-    for recorded columns and apparent pairs."""
+def _take_result(h, with_stats=True) -> Barcodes:
+    """Copy a result out of the library (and free it)."""
     L = N.lib()
     try:
         b = Barcodes()
@@ -124,7 +123,7 @@ def _take_result(h, with_stats=True, recorded=True) -> Barcodes:
                 b.critical.append(np.zeros((0, 4), np.int32))
         if with_stats:
             b._raw_stats = st
-        for p in range(1, st.max_dim + 1 if recorded else 1):
+        for p in range(1, st.max_dim + 1):
             dp, ip = C.POINTER(C.c_float)(), C.POINTER(C.c_uint64)()
             m = L.rpp_result_columns(h, p, C.byref(dp), C.byref(ip))
             if m >= 0:
@@ -142,6 +141,42 @@ def _take_result(h, with_stats=True, recorded=True) -> Barcodes:
     finally:
         L.rpp_result_free(h)
     return b
+
+
+def _take_results(handles) -> list:
+    """Copy many results out of the library in a few calls (rpp_results_*) and
+    free them; the per-result arrays are views of one array per dimension."""
+    L = N.lib()
+    B = len(handles)
+    arr = (C.c_void_p * B)(*handles)
+    try:
+        stats = (N.Stats * B)()
+        N.check(L.rpp_results_stats(arr, B, stats), "rpp_results_stats")
+        top = max((s.max_dim for s in stats), default=-1)
+        per_dim = []
+        for q in range(top + 1):
+            offs = np.zeros(B + 1, np.int64)
+            N.check(L.rpp_results_gather(arr, B, q, offs.ctypes.data, None, None),
+                    "rpp_results_gather")
+            tot = int(offs[-1])
+            iv = np.empty((tot, 2), np.float32)
+            cr = np.empty((tot, 4), np.int32)
+            N.check(L.rpp_results_gather(arr, B, q, offs.ctypes.data, iv.ctypes.data,
+                                         cr.ctypes.data), "rpp_results_gather")
+            o = offs.tolist()
+            per_dim.append(([iv[o[i]:o[i + 1]] for i in range(B)],
+                            [cr[o[i]:o[i + 1]] for i in range(B)]))
+        out = []
+        for i in range(B):
+            b = Barcodes()
+            b._raw_stats = stats[i]
+            for q in range(stats[i].max_dim + 1):
+                b.intervals.append(per_dim[q][0][i])
+                b.critical.append(per_dim[q][1][i])
+            out.append(b)
+    finally:
+        L.rpp_results_free(arr, B)
+    return out
 
 
 def _as_input(data):
@@ -234,8 +269,9 @@ def rpp_barcodes_batched(clouds, max_dim: int = 1, thresholds=None, quantiles=No
     s = _stream_ptr(stream, any(cu for _, _, cu, _ in items))
     N.check(N.lib().rpp_barcodes_batched(ctx.handle, B, ptrs, ns, dims, max_dim, th, qs, s, outs),
             "rpp_barcodes_batched")
-    rec = (ctx.record & (N.RPP_RECORD_COLUMNS | N.RPP_RECORD_APPARENT)) != 0
-    return [_take_result(outs[i], recorded=rec) for i in range(B)]
+    if ctx.record & (N.RPP_RECORD_COLUMNS | N.RPP_RECORD_APPARENT):
+        return [_take_result(outs[i]) for i in range(B)]
+    return _take_results([outs[i] for i in range(B)])
 
 
 class Server:

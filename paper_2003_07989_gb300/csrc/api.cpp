@@ -192,6 +192,50 @@ rpp_status rpp_result_stats(const rpp_result *res, rpp_stats *out) {
 
 void rpp_result_free(rpp_result *res) { delete res; }
 
+rpp_status rpp_results_gather(const rpp_result *const *results, int32_t count, int32_t p,
+                              int64_t *offsets, rpp_interval *intervals, rpp_critical *critical) {
+    if (count < 0 || (count > 0 && !results) || !offsets || p < 0 || p > RPP_MAX_DIM) {
+        set_last_error("rpp_results_gather: invalid arguments");
+        return RPP_E_INVALID;
+    }
+    for (int32_t i = 0; i < count; ++i)
+        if (!results[i]) {
+            set_last_error("rpp_results_gather: result " + std::to_string(i) + " is NULL");
+            return RPP_E_INVALID;
+        }
+    int64_t at = 0;
+    for (int32_t i = 0; i < count; ++i) {
+        offsets[i] = at;
+        const rpp_result *r = results[i];
+        if (p > r->max_dim) continue;
+        const size_t m = r->iv[p].size();
+        if (intervals && m) std::memcpy(intervals + at, r->iv[p].data(), m * sizeof(rpp_interval));
+        if (critical && m) std::memcpy(critical + at, r->cr[p].data(), m * sizeof(rpp_critical));
+        at += (int64_t)m;
+    }
+    offsets[count] = at;
+    return RPP_OK;
+}
+
+rpp_status rpp_results_stats(const rpp_result *const *results, int32_t count, rpp_stats *out) {
+    if (count < 0 || (count > 0 && (!results || !out))) {
+        set_last_error("rpp_results_stats: invalid arguments");
+        return RPP_E_INVALID;
+    }
+    for (int32_t i = 0; i < count; ++i)
+        if (!results[i]) {
+            set_last_error("rpp_results_stats: result " + std::to_string(i) + " is NULL");
+            return RPP_E_INVALID;
+        }
+    for (int32_t i = 0; i < count; ++i) out[i] = results[i]->stats;
+    return RPP_OK;
+}
+
+void rpp_results_free(rpp_result *const *results, int32_t count) {
+    if (!results) return;
+    for (int32_t i = 0; i < count; ++i) delete results[i];
+}
+
 rpp_status rpp_context_set_record(rpp_context *ctx, int32_t flags) {
     if (!ctx || flags < 0 || flags > (RPP_RECORD_COLUMNS | RPP_RECORD_APPARENT | RPP_RECORD_TIMING)) {
         set_last_error("rpp_context_set_record: invalid arguments");

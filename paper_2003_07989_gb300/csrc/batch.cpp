@@ -17,6 +17,7 @@
 #include <cmath>
 #include <cstring>
 #include <numeric>
+#include <thread>
 
 #include "pipeline.h"
 
@@ -263,15 +264,32 @@ struct CloudWork {
     bool fallback = false;         // leftover pool overflowed: run it alone
 };
 
-// One fused launch over clouds ins[idx[k]], results into out[idx[k]].
-Status run_launch(rpp_context *ctx, Workspace &ws, const std::vector<Instance> &ins,
-                  const std::vector<int> &idx, int nmax, int dimcap, cudaStream_t s,
-                  rpp_result **out) {
-    const double t0 = now_ms();
+// One fused launch over clouds ins[idx[k]]: what its host half needs.
+struct Launch {
+    std::vector<int> idx;
+    double t0 = 0.0;
+    long long launches = 0;
+    double dev_ms = 0.0;
+    Bufs b{};
+    std::vector<CloudWork> W;
+    std::vector<int64_t> off, aoff;  // per row job: rows (n^2) and edges (C(n,2)) before it
+    float *hD = nullptr;             // per job: distance rows, neighbour lists, apparent vertices
+    uint64_t *hN = nullptr;
+    uint16_t *hA = nullptr;
+};
+
+// Device half of a fused launch: the pass itself, then the distance rows,
+// neighbour lists and apparent vertices of every cloud with leftovers, copied
+// into ws's host buffers (which stay in use until the host half is done).
+Status launch_device(rpp_context *ctx, Workspace &ws, const std::vector<Instance> &ins,
+                     const std::vector<int> &idx, int nmax, int dimcap, cudaStream_t s,
+                     Launch &L) {
+    L.idx = idx;
+    L.t0 = now_ms();
     const long long launches0 = g_launches;
     const int k = (int)idx.size();
     const Caps caps = caps_of(ins, idx);
-    Bufs b;
+    Bufs &b = L.b;
     RPP_TRY(get_bufs(ws, caps, b));
 
     // layout and inputs
@@ -366,11 +384,14 @@ Status run_launch(rpp_context *ctx, Workspace &ws, const std::vector<Instance> &
         RPP_CK(cudaMemcpyAsync(b.h_lcloud, b.lcloud, got * 4, cudaMemcpyDeviceToHost, s));
         RPP_CK(cudaStreamSynchronize(s));
     }
-    std::vector<CloudWork> W(k);
+    std::vector<CloudWork> &W = L.W;
+    W.assign(k, CloudWork());
     for (int j = 0; j < k; ++j) W[j].slot = j;
     for (uint64_t i = 0; i < got; ++i) W[b.h_lcloud[i]].left.push_back(b.h_left[i]);
     std::vector<int32_t> jobs;
-    std::vector<int64_t> off, aoff;  // per job: rows (n^2) and edges (C(n,2)) before it
+    std::vector<int64_t> &off = L.off, &aoff = L.aoff;
+    off.clear();
+    aoff.clear();
     int64_t rows = 0, edges = 0;
     for (int j = 0; j < k; ++j) {
         if (W[j].left.size() < b.h_outs[j].nleft) {
@@ -385,9 +406,12 @@ Status run_launch(rpp_context *ctx, Workspace &ws, const std::vector<Instance> &
         rows += (int64_t)b.h_clouds[j].n * b.h_clouds[j].n;
         edges += (int64_t)b.h_clouds[j].n * (b.h_clouds[j].n - 1) / 2;
     }
-    float *hD = nullptr;
-    uint64_t *hN = nullptr;
-    uint16_t *hA = nullptr;
+    float *&hD = L.hD;
+    uint64_t *&hN = L.hN;
+    uint16_t *&hA = L.hA;
+    hD = nullptr;
+    hN = nullptr;
+    hA = nullptr;
     if (!jobs.empty()) {  // distance rows and neighbour lists of the clouds with leftovers
         void *p, *hp;
         const size_t nj = jobs.size();
@@ -422,12 +446,28 @@ Status run_launch(rpp_context *ctx, Workspace &ws, const std::vector<Instance> &
         RPP_CK(cudaStreamSynchronize(s));
         dev_ms += now_ms() - a2;
     }
-    const long long launches = g_launches - launches0;
+    L.launches = g_launches - launches0;
+    L.dev_ms = dev_ms;
+    return Status();
+}
 
-    // host: H0 from the forest, the submatrix reductions, the barcodes
-    const int inner = (int)jobs.size() >= ctx->host_threads ? 1 : ctx->host_threads;
+// Host half of a fused launch: H0 from the forest, the submatrix reductions
+// and the barcodes; results into out[idx[k]]. Clouds whose leftover columns
+// overflowed the pool are appended to `alone` (run by themselves later).
+Status launch_host(rpp_context *ctx, const std::vector<Instance> &ins, Launch &L,
+                   rpp_result **out, std::vector<int> &alone) {
+    const std::vector<int> &idx = L.idx;
+    const int k = (int)idx.size();
+    const Bufs &b = L.b;
+    std::vector<CloudWork> &W = L.W;
+    const std::vector<int64_t> &off = L.off, &aoff = L.aoff;
+    const float *hD = L.hD;
+    const uint64_t *hN = L.hN;
+    const uint16_t *hA = L.hA;
+    const double t0 = L.t0, dev_ms = L.dev_ms;
+    const long long launches = L.launches;
+    const int inner = (int)off.size() >= ctx->host_threads ? 1 : ctx->host_threads;
     std::vector<rpp_result *> res(k, nullptr);
-    std::vector<std::string> errs(k);
     // the heaviest reductions first (most leftover columns, then most
     // points), so that the threads do not wait on one long cloud at the end
     std::vector<int> sched(k);
@@ -523,22 +563,8 @@ Status run_launch(rpp_context *ctx, Workspace &ws, const std::vector<Instance> &
         res[j] = r;
     });
     for (int j = 0; j < k; ++j) {
-        if (!W[j].fallback) {
-            out[idx[j]] = res[j];
-            continue;
-        }
-        rpp_result *r = new rpp_result();  // leftover pool overflow: this cloud alone
-        Status st = run_instance(ctx, ws, ins[idx[j]], s, r);
-        if (!st.ok()) {
-            delete r;
-            for (int q = 0; q < k; ++q)
-                if (!W[q].fallback && res[q]) {
-                    delete res[q];
-                    out[idx[q]] = nullptr;
-                }
-            return st;
-        }
-        out[idx[j]] = r;
+        if (W[j].fallback) alone.push_back(idx[j]);
+        else out[idx[j]] = res[j];
     }
     return Status();
 }
@@ -561,7 +587,7 @@ size_t batch_device_bytes(const std::vector<Instance> &ins) {
 }
 
 Status run_batch(rpp_context *ctx, Workspace &ws, const std::vector<Instance> &ins,
-                 cudaStream_t s, rpp_result **out) {
+                 cudaStream_t s, rpp_result **out, Workspace *ws2) {
     RPP_CK(cudaSetDevice(ws.device));
     std::map<std::pair<int, int>, std::vector<int>> buckets;  // (nmax, dimcap) -> clouds
     std::vector<int> alone;
@@ -579,22 +605,64 @@ Status run_batch(rpp_context *ctx, Workspace &ws, const std::vector<Instance> &i
                 out[i] = nullptr;
             }
     };
+    struct Planned {
+        std::vector<int> idx;
+        int nmax, dimcap;
+    };
+    std::vector<Planned> plan;
     for (auto &kv : buckets) {
-        const int nmax = kv.first.first, dimcap = kv.first.second;
-        const int cap = bucket_cap(nmax);
+        const int cap = bucket_cap(kv.first.first);
         const std::vector<int> &all = kv.second;
-        for (size_t o = 0; o < all.size(); o += (size_t)cap) {
-            std::vector<int> idx(all.begin() + o, all.begin() + std::min(all.size(), o + cap));
-            Status st = run_launch(ctx, ws, ins, idx, nmax, dimcap, s, out);
-            if (!st.ok()) {
-                cleanup();
-                return st;
-            }
-        }
+        for (size_t o = 0; o < all.size(); o += (size_t)cap)
+            plan.push_back({std::vector<int>(all.begin() + o,
+                                             all.begin() + std::min(all.size(), o + cap)),
+                            kv.first.first, kv.first.second});
     }
+    // With a second workspace the device half of launch i + 1 runs (from this
+    // thread, on the stream) while the host threads finish launch i; each
+    // launch's buffers belong to one workspace until its host half is done.
+    Launch L[2];
+    Workspace *wsp[2] = {&ws, ws2 ? ws2 : &ws};
+    const bool overlap = ws2 && ws2 != &ws && plan.size() > 1;
+    std::vector<int> overflow;
+    Status st;
+    if (!plan.empty())
+        st = launch_device(ctx, ws, ins, plan[0].idx, plan[0].nmax, plan[0].dimcap, s, L[0]);
+    for (size_t i = 0; st.ok() && i < plan.size(); ++i) {
+        Launch &cur = L[i & 1];
+        const bool more = i + 1 < plan.size();
+        Workspace &wn = *wsp[overlap ? (i + 1) & 1 : 0];
+        if (!overlap) {
+            st = launch_host(ctx, ins, cur, out, overflow);
+            if (st.ok() && more)
+                st = launch_device(ctx, wn, ins, plan[i + 1].idx, plan[i + 1].nmax,
+                                   plan[i + 1].dimcap, s, L[(i + 1) & 1]);
+            continue;
+        }
+        Status hs;
+        std::thread host([&] {
+            try {
+                hs = launch_host(ctx, ins, cur, out, overflow);
+            } catch (const std::exception &e) {
+                hs = fail(RPP_E_NOMEM, std::string("batched host reduction: ") + e.what());
+            }
+        });
+        if (more)
+            st = launch_device(ctx, wn, ins, plan[i + 1].idx, plan[i + 1].nmax, plan[i + 1].dimcap,
+                               s, L[(i + 1) & 1]);
+        host.join();
+        if (st.ok()) st = hs;
+    }
+    if (!st.ok()) {
+        cleanup();
+        return st;
+    }
+    // clouds run alone: not fusable, or their leftover columns overflowed the pool
+    std::sort(overflow.begin(), overflow.end());
+    alone.insert(alone.end(), overflow.begin(), overflow.end());
     for (int i : alone) {
         rpp_result *r = new rpp_result();
-        Status st = run_instance(ctx, ws, ins[i], s, r);
+        st = run_instance(ctx, ws, ins[i], s, r);
         if (!st.ok()) {
             delete r;
             cleanup();
@@ -635,7 +703,11 @@ extern "C" rpp_status rpp_barcodes_batched(rpp_context *ctx, int32_t batch,
     }
     if (batch == 0) return RPP_OK;
     Workspace *ws = ctx->acquire();
-    Status s = run_batch(ctx, *ws, ins, (cudaStream_t)stream, out);
+    // a second workspace lets launches overlap (not under a memory budget,
+    // which holds per workspace)
+    Workspace *ws2 = ctx->budget == 0 ? ctx->acquire() : nullptr;
+    Status s = run_batch(ctx, *ws, ins, (cudaStream_t)stream, out, ws2);
+    if (ws2) ctx->release(ws2);
     ctx->release(ws);
     if (!s.ok()) return report(s);
     return RPP_OK;

@@ -242,6 +242,114 @@ struct Cursor {
 // Index over the sorted apparent taus: every STRIDE-th key, searched first.
 constexpr int64_t STRIDE = 64;
 
+// The edges {a, b} (a > b) of diameter in [from, threshold] in coboundary
+// order (diameter descending, index ascending), packed as the GPU path hands
+// them over: ab = (a << 16) | b and hi = ~bits(diameter), at position
+// m - 1 - f for filtration position f. One 64-bit key per edge,
+// (bits(diameter) - bits(from), ~a, ~b) with a and b in w bits each, orders
+// the edges into filtration order (diameter ascending; on ties the index
+// descends with (a, b)). The keys are partitioned once into up to 2048
+// buckets by their top varying bits; a bucket is sorted only when a sweep
+// first reaches it, so a short sweep pays for little more than the partition.
+struct EdgeList {
+    float from = 0.0f;
+    int w = 1, sh = 0;
+    uint64_t vmax = 1, kmin = 0, kmax = 0;
+    uint32_t base = 0;
+    int64_t m = 0;
+    mutable std::vector<uint64_t> key;  // partitioned; a bucket's range sorted once done
+    std::vector<int64_t> bstart;        // bucket i: positions [bstart[i], bstart[i + 1])
+    mutable std::vector<uint32_t> ab, hi;
+    std::unique_ptr<std::atomic<uint8_t>[]> done;
+    mutable std::mutex mu;
+
+    int nbuckets() const { return (int)bstart.size() - 1; }
+    int bucket_of(uint64_t k) const { return (int)((k >> sh) - (kmin >> sh)); }
+
+    // Sort bucket i and fill its positions of ab and hi (once).
+    void ensure(int i) const {
+        if (done[i].load(std::memory_order_acquire)) return;
+        std::lock_guard<std::mutex> g(mu);
+        if (done[i].load(std::memory_order_relaxed)) return;
+        std::sort(key.begin() + bstart[i], key.begin() + bstart[i + 1]);
+        for (int64_t f = bstart[i]; f < bstart[i + 1]; ++f) {
+            const uint64_t k = key[f];
+            const uint32_t a = (uint32_t)(vmax - ((k >> w) & vmax));
+            const uint32_t b = (uint32_t)(vmax - (k & vmax));
+            ab[m - 1 - f] = (a << 16) | b;
+            hi[m - 1 - f] = ~((uint32_t)(k >> (2 * w)) + base);
+        }
+        done[i].store(1, std::memory_order_release);
+    }
+
+    // Filtration position of the first edge of diameter bits >= bd, and its
+    // bucket (its bucket sorted).
+    int64_t first_at(uint32_t bd, int *bucket) const {
+        *bucket = 0;
+        if (m == 0) return 0;
+        const uint64_t kb = bd <= base ? 0 : (uint64_t)(bd - base) << (2 * w);
+        if (kb > kmax) {
+            *bucket = nbuckets() - 1;
+            return m;
+        }
+        const int i = kb <= kmin ? 0 : bucket_of(kb);
+        ensure(i);
+        *bucket = i;
+        return std::lower_bound(key.begin() + bstart[i], key.begin() + bstart[i + 1], kb) -
+               key.begin();
+    }
+};
+
+void sort_edges(const HostInstance &I, float from, EdgeList &out) {
+    const int64_t n = I.n;
+    int w = 1;
+    while ((int64_t(1) << w) < n) ++w;
+    const uint64_t vmax = (uint64_t(1) << w) - 1;
+    const uint32_t base = float_bits(from);
+    std::vector<uint64_t> key;
+    key.reserve((size_t)(n * (n - 1) / 2));
+    for (int64_t a = 1; a < n; ++a) {
+        const float *Da = I.D + a * I.ld;
+        const uint64_t ka = (vmax - (uint64_t)a) << w;
+        for (int64_t b = 0; b < a; ++b) {
+            const float d = Da[b];
+            if (d >= from && d <= I.t)
+                key.push_back(((uint64_t)(float_bits(d) - base) << (2 * w)) | ka |
+                              (vmax - (uint64_t)b));
+        }
+    }
+    const int64_t m = (int64_t)key.size();
+    uint64_t kmin = ~0ull, kmax = 0;
+    for (uint64_t k : key) {
+        kmin = std::min(kmin, k);
+        kmax = std::max(kmax, k);
+    }
+    int sh = 0;
+    if (m > 1) {
+        const int hb = 63 - __builtin_clzll(kmin ^ kmax);  // top bit in which keys differ
+        sh = std::max(0, hb + 1 - 11);
+    }
+    out.from = from;
+    out.w = w;
+    out.sh = sh;
+    out.vmax = vmax;
+    out.kmin = m ? kmin : 0;
+    out.kmax = m ? kmax : 0;
+    out.base = base;
+    out.m = m;
+    const int nb = m ? (int)((kmax >> sh) - (kmin >> sh)) + 1 : 1;
+    out.bstart.assign(nb + 1, 0);
+    for (uint64_t k : key) ++out.bstart[out.bucket_of(k) + 1];
+    for (int i = 0; i < nb; ++i) out.bstart[i + 1] += out.bstart[i];
+    std::vector<int64_t> at(out.bstart.begin(), out.bstart.end() - 1);
+    out.key.resize(m);
+    for (uint64_t k : key) out.key[at[out.bucket_of(k)]++] = k;
+    out.ab.resize(m);
+    out.hi.resize(m);
+    out.done.reset(new std::atomic<uint8_t>[nb]);
+    for (int i = 0; i < nb; ++i) out.done[i].store(0, std::memory_order_relaxed);
+}
+
 struct Reducer {
     const HostInstance &I;
     int p;
@@ -266,6 +374,21 @@ struct Reducer {
         for (int i = 0; i <= p; ++i)
             if (v[i] == w) return true;
         return false;
+    }
+
+    // Dimension 1, the instance without the GPU's sorted edges: the edges of
+    // diameter >= from sorted here for all walks of the reduction; when a
+    // walk starts below the first sweep's level, all of them (twice at most).
+    mutable std::mutex edges_mu;
+    mutable std::shared_ptr<const EdgeList> own_edges;
+    std::shared_ptr<const EdgeList> level_edges(float from) const {
+        std::lock_guard<std::mutex> g(edges_mu);
+        if (!own_edges || own_edges->from > from) {
+            auto e = std::make_shared<EdgeList>();
+            sort_edges(I, own_edges ? 0.0f : from, *e);
+            own_edges = e;
+        }
+        return own_edges;
     }
 
     int nbr_vertex(int v, int64_t pos) const { return (int)(uint32_t)I.nbr[(int64_t)v * n + pos]; }
@@ -1256,12 +1379,15 @@ struct Walk1 {
     static constexpr int64_t SWEEP_NMAX = 8192;  // P and adj: n^2 / 8 bytes each per thread
     bool sweep = false;
     uint64_t *P = nullptr;        // n x W bits: w within the level's diameter of a (no self bits)
-    int64_t f1 = 0;               // array source: next edge position in filtration order
-    // Row source (no edge array): the neighbour rows merged by a min-heap of
-    // (distance bits, vertex a) over each row's entries w < a, so every edge
-    // comes once; rpos[a] is the next entry of row a.
-    std::vector<std::pair<uint32_t, int32_t>> rheap;
-    std::vector<int32_t> rpos;
+    // The levels: the edges inside the threshold in coboundary order (those
+    // of diameter >= the sweep's first level at least), f1 the next position
+    // in filtration order.
+    const uint32_t *eab = nullptr, *ehi = nullptr;
+    int64_t ne = 0;
+    std::shared_ptr<const EdgeList> elist;  // the arrays, when sorted on the host
+    int ebucket = 0;              // host-sorted: the bucket of the last position asked for
+    int64_t eready = 0;           // positions below are sorted (from the sweep's start on)
+    int64_t f1 = 0;
     float lvl_d = 0.0f;           // diameter of the current level
     struct LevelEdge {
         int a, b;                 // a > b
@@ -1288,12 +1414,20 @@ struct Walk1 {
     bool can_sweep() const { return n <= SWEEP_NMAX; }
 
     // Edge at position f of the filtration order (diameter ascending).
+    // Host-sorted edges: sort the bucket of position f if the sweep has not
+    // been there yet (the sweep only moves forward).
+    void need(int64_t f) {
+        if (f < eready) return;
+        while (elist->bstart[ebucket + 1] <= f) ++ebucket;
+        elist->ensure(ebucket);
+        eready = elist->bstart[ebucket + 1];
+    }
     void edge_at(int64_t f, int &a, int &b) const {
-        const uint32_t ab = I.edge_ab[I.nedges - 1 - f];
+        const uint32_t ab = eab[ne - 1 - f];
         a = (int)(ab >> 16);
         b = (int)(ab & 0xffffu);
     }
-    float diam_at(int64_t f) const { return bits_float(~I.edge_hi[I.nedges - 1 - f]); }
+    float diam_at(int64_t f) const { return bits_float(~ehi[ne - 1 - f]); }
 
     static uint64_t tri_index(const Binomial &B, int a, int b, int w) {
         int v0 = a, v1 = b, v2 = w;  // a > b
@@ -1315,55 +1449,30 @@ struct Walk1 {
         lev.push_back(E);
     }
 
-    // Row source: move row a to its next entry w < a inside the threshold
-    // and queue it (a row with none left leaves the heap).
-    void row_push(int a) {
-        const uint64_t *row = I.nbr + (int64_t)a * n;
-        int32_t &i = rpos[a];
-        while (i < n && (int)(uint32_t)row[i] >= a) ++i;
-        if (i >= n) return;
-        const uint32_t db = (uint32_t)(row[i] >> 32);
-        if (bits_float(db) > I.t) return;
-        rheap.push_back({db, a});
-        std::push_heap(rheap.begin(), rheap.end(), std::greater<std::pair<uint32_t, int32_t>>());
-    }
-
     // Enter the next level of equal diameter: set its bits in P and list its
     // edges with every triangle still to come; false when no edge is left.
     bool next_level() {
         lev.clear();
-        if (I.edge_ab) {
-            if (f1 >= I.nedges) return false;
-            const int64_t f0 = f1;
-            lvl_d = diam_at(f0);
-            while (f1 < I.nedges && diam_at(f1) == lvl_d) ++f1;
-            for (int64_t f = f0; f < f1; ++f) {
-                int a, b;
-                edge_at(f, a, b);
-                level_edge(a, b);
-            }
-            // the sweep is bound by the latency of the bit rows: ask for the
-            // rows of an edge a few levels ahead
-            if (f1 + PREFETCH_AHEAD < I.nedges) {
-                int a, b;
-                edge_at(f1 + PREFETCH_AHEAD, a, b);
-                for (int64_t k = 0; k < S; k += 8) {
-                    __builtin_prefetch(rows + (int64_t)a * S + k);
-                    __builtin_prefetch(rows + (int64_t)b * S + k);
-                }
-            }
-        } else {
-            if (rheap.empty()) return false;
-            const uint32_t db = rheap.front().first;
-            lvl_d = bits_float(db);
-            while (!rheap.empty() && rheap.front().first == db) {
-                std::pop_heap(rheap.begin(), rheap.end(),
-                              std::greater<std::pair<uint32_t, int32_t>>());
-                const int a = rheap.back().second;
-                rheap.pop_back();
-                level_edge(a, (int)(uint32_t)I.nbr[(int64_t)a * n + rpos[a]]);
-                ++rpos[a];
-                row_push(a);
+        if (f1 >= ne) return false;
+        const int64_t f0 = f1;
+        need(f0);
+        lvl_d = diam_at(f0);
+        while (f1 + 1 < ne && (need(f1 + 1), diam_at(f1 + 1) == lvl_d)) ++f1;
+        ++f1;
+        for (int64_t f = f0; f < f1; ++f) {
+            int a, b;
+            edge_at(f, a, b);
+            level_edge(a, b);
+        }
+        // the sweep is bound by the latency of the bit rows: ask for the rows
+        // of an edge a few levels ahead
+        if (f1 + PREFETCH_AHEAD < ne) {
+            int a, b;
+            need(f1 + PREFETCH_AHEAD);
+            edge_at(f1 + PREFETCH_AHEAD, a, b);
+            for (int64_t k = 0; k < S; k += 8) {
+                __builtin_prefetch(rows + (int64_t)a * S + k);
+                __builtin_prefetch(rows + (int64_t)b * S + k);
             }
         }
         ++levels;
@@ -1482,8 +1591,11 @@ struct Walk1 {
             }
         }
         // position the level source at the first edge of length dk
-        if (I.edge_ab) {  // edges in filtration order, diameter ascending
-            int64_t lo = 0, hi = I.nedges;
+        if (I.edge_ab) {
+            eab = I.edge_ab;
+            ehi = I.edge_hi;
+            ne = eready = I.nedges;
+            int64_t lo = 0, hi = ne;  // filtration order, diameter ascending
             while (lo < hi) {
                 const int64_t mid = (lo + hi) >> 1;
                 if (float_bits(diam_at(mid)) < bd) lo = mid + 1;
@@ -1491,14 +1603,12 @@ struct Walk1 {
             }
             f1 = lo;
         } else {
-            rheap.clear();
-            rpos.assign(n, 0);
-            const uint64_t lim = (uint64_t)bd << 32;
-            for (int64_t a = 0; a < n; ++a) {
-                const uint64_t *row = I.nbr + a * n;
-                rpos[a] = (int32_t)(std::lower_bound(row, row + n, lim) - row);
-                row_push((int)a);
-            }
+            elist = R.level_edges(dk);
+            eab = elist->ab.data();
+            ehi = elist->hi.data();
+            ne = elist->m;
+            f1 = elist->first_at(bd, &ebucket);
+            eready = f1 < ne ? elist->bstart[ebucket + 1] : ne;
         }
         if (!next_level() || lvl_d != dk) {  // cannot happen: k is a triangle inside the threshold
             lev.clear();

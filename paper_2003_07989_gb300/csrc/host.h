@@ -27,10 +27,10 @@ struct HostInstance {
     // dimension 1, instead of app_tau (may be null): for every edge index, the
     // vertex its apparent pair adds to it, 0xFFFF if it has none
     const uint16_t *app_w = nullptr;
-    // dimension 1 only (may be null; n <= 65535): every edge inside the
-    // threshold in coboundary order (diameter descending, index ascending), as
-    // the GPU sorted them: its vertices packed as (a << 16) | b, a > b, and
-    // ~bits(diameter)
+    // dimension 1 only (n <= 65535): every edge inside the threshold in
+    // coboundary order (diameter descending, index ascending), as the GPU
+    // sorted them: its vertices packed as (a << 16) | b, a > b, and
+    // ~bits(diameter); null: the reduction sorts them itself if a walk sweeps
     const uint32_t *edge_ab = nullptr;
     const uint32_t *edge_hi = nullptr;
     int64_t nedges = 0;

@@ -156,8 +156,10 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
                     rpp_result *res);
 // Run validated instances as one batch (fused pass where eligible, batch.cpp);
 // out[i] receives instance i's result. On error no result is left in out.
+// ws2 (optional, another workspace of the context): fused launches overlap,
+// the device work of one with the host reductions of the one before.
 Status run_batch(rpp_context *ctx, Workspace &ws, const std::vector<Instance> &ins,
-                 cudaStream_t stream, rpp_result **out);
+                 cudaStream_t stream, rpp_result **out, Workspace *ws2 = nullptr);
 // Whether run_batch takes this instance through the fused pass.
 bool batch_fused_eligible(const rpp_context *ctx, const Instance &in);
 // Device bytes a workspace holds after run_batch over these fused-eligible

@@ -9,7 +9,7 @@
 //
 //   host_reduce_harness D.f32 n t threads flags out.f32
 //     t        threshold (inf: the enclosing radius, as the library does)
-//     flags    bit 0: no sorted edge array (levels from the neighbour rows)
+//     flags    bit 0: no sorted edge array (the reduction sorts the edges itself)
 //              bit 1: no apparent array (apparent pivots tested again)
 //   out.f32    (birth, death) float32 pairs of the nonzero H1 intervals
 #include <algorithm>

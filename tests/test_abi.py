@@ -54,3 +54,23 @@ def test_argument_errors_without_gpu(lib):
     assert b"NULL" in lib.rpp_last_error()
     assert lib.rpp_result_count(None, 0) == -1
     assert lib.rpp_result_total(None) == -1
+
+
+def test_results_accessors_reject_bad_arguments(lib):
+    from paper_2003_07989_gb300 import _native as N
+    offs = (C.c_int64 * 3)()
+    two = (C.c_void_p * 2)(None, None)
+    # NULL entries, a NULL offsets array, a dimension out of range
+    assert lib.rpp_results_gather(two, 2, 1, C.addressof(offs), None, None) == N.RPP_E_INVALID
+    assert b"NULL" in lib.rpp_last_error()
+    assert lib.rpp_results_gather(two, 0, 1, None, None, None) == N.RPP_E_INVALID
+    assert lib.rpp_results_gather(two, 0, N.RPP_MAX_DIM + 1, C.addressof(offs), None,
+                                  None) == N.RPP_E_INVALID
+    assert lib.rpp_results_gather(two, -1, 0, C.addressof(offs), None, None) == N.RPP_E_INVALID
+    stats = (N.Stats * 2)()
+    assert lib.rpp_results_stats(two, 2, stats) == N.RPP_E_INVALID
+    # an empty set is fine: offsets[0] = 0
+    offs[0] = 7
+    assert lib.rpp_results_gather(two, 0, 0, C.addressof(offs), None, None) == N.RPP_OK
+    assert offs[0] == 0
+    lib.rpp_results_free(two, 2)  # NULL entries are skipped

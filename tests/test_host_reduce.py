@@ -6,8 +6,9 @@ their unreduced pivots, neighbour rows) and runs the dimension-1 submatrix
 reduction; its H1 intervals must be the oracle's, bit for bit. The cases make
 the reduction walk long enough to sweep diameter levels (the long-lived H1
 classes of tori), with and without a threshold below the enclosing radius,
-with many equal distances, with the levels taken from the sorted edges or
-from the neighbour rows, and with apparent pivots looked up or tested again.
+with many equal distances, with the levels taken from the sorted edges handed
+over or from the reduction's own sort of the edges, and with apparent pivots
+looked up or tested again.
 """
 import math
 import os
@@ -131,6 +132,9 @@ def test_host_reduction_parallel_columns_equal_oracle(harness, harness_wide, tmp
     every run, with 64- and 128-bit keys."""
     D, t = PARALLEL_CASES[name]()
     ref = O.barcodes(D, 1, t, O.MODE_COHOM_CLEAR).barcode(1)
-    for exe, threads in ((harness, 8), (harness, 3), (harness_wide, 8), (harness, 8)):
-        got, _ = _run(exe, D, t, threads, 0, tmp_path)
-        assert got.shape == ref.shape and np.array_equal(got, ref), (name, threads)
+    # flags 1: the edges are sorted by the reduction itself, a bucket at a
+    # time, by whichever walk reaches it first
+    for exe, threads, flags in ((harness, 8, 0), (harness, 3, 1), (harness_wide, 8, 1),
+                                (harness, 8, 1)):
+        got, _ = _run(exe, D, t, threads, flags, tmp_path)
+        assert got.shape == ref.shape and np.array_equal(got, ref), (name, threads, flags)
