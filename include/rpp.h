@@ -19,8 +19,9 @@
  *   - submatrix reduction of the leftover columns on the host with the
  *     two-layer pair store (hash map over the sorted apparent array) and the
  *     reduction-matrix technique (Sec. "Reduction Matrix vs. Oblivious Matrix
- *     Reduction"); H0 by Kruskal's union-find (Sec. "Zero-Dimensional
- *     Persistence Computation").
+ *     Reduction"); H0 from the minimum spanning forest (Sec. "Zero-Dimensional
+ *     Persistence Computation"; Kruskal's forest, built here by Boruvka's
+ *     rounds on the GPU).
  *
  * Conventions common to every entry point:
  *   - Every call returns an rpp_status and never aborts the process. Invalid
@@ -28,7 +29,11 @@
  *     returns a thread-local message describing the last failure.
  *   - Input buffers are owned by the caller; the library never frees them.
  *     A data pointer may be device memory or host memory (pageable or pinned);
- *     the library asks the CUDA runtime which one it is.
+ *     the library asks the CUDA runtime which one it is. A buffer must hold
+ *     the floats its sizes declare (n * dim points or n * n distances): the
+ *     library cannot check its extent, and a shorter buffer is read past its
+ *     end (on systems where the GPU reads host memory directly, a device
+ *     memory fault).
  *   - Results are owned by the library and freed with rpp_result_free.
  *   - All GPU work of a call runs on the given CUDA stream (cudaStream_t passed
  *     as void*; NULL means the legacy default stream). A call returns after its
@@ -55,7 +60,8 @@ typedef enum {
     RPP_OK = 0,
     RPP_E_INVALID = 1,   /* bad argument or input (non-finite, negative, asymmetric ...) */
     RPP_E_NOMEM = 2,     /* device or host allocation failed, or the budget is exceeded */
-    RPP_E_OVERFLOW = 3,  /* C(n, max_dim + 2) does not fit the 63-bit index */
+    RPP_E_OVERFLOW = 3,  /* an index does not fit: C(n, max_dim + 2) the 63-bit simplex
+                            index, or C(n, 2) the 32-bit edge index (n > 92682) */
     RPP_E_CUDA = 4,      /* a CUDA runtime call failed (message in rpp_last_error) */
     RPP_E_TIMEOUT = 5,   /* a bounded wait ran out (poll deadline, device wait limit) */
     RPP_E_BUSY = 6       /* admission refused: no slot or memory free right now */
@@ -111,7 +117,7 @@ typedef struct {
     int64_t stage_launches[8];
     double ms_device;                     /* wall time spent waiting on the GPU */
     double ms_host_reduce;                /* wall time of the submatrix reductions */
-    double ms_host_h0;                    /* wall time of Kruskal */
+    double ms_host_h0;                    /* wall time of the H0 stage (forest, intervals) */
     double ms_total;
 } rpp_stats;
 
@@ -126,7 +132,7 @@ void rpp_context_destroy(rpp_context *ctx);
 /* Barcodes of dimensions 0..max_dim of Rips_t.
  *   data       points (n x dim) or distances (n x n), float32, device or host.
  *   kind       RPP_INPUT_POINTS or RPP_INPUT_DISTANCES (dim ignored).
- *   n          number of points, n >= 1.
+ *   n          number of points, 1 <= n <= 92682 (C(n, 2) < 2^32).
  *   max_dim    0 <= max_dim <= RPP_MAX_DIM.
  *   threshold  closed threshold t >= 0; +INFINITY means the full filtration.
  *              The enclosing radius R bounds the work: min(t, R) is used,

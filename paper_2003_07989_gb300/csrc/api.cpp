@@ -87,13 +87,17 @@ void rpp_context_destroy(rpp_context *ctx) {
 }
 
 static rpp_status run_one(rpp_context *ctx, const Instance &in, void *stream, rpp_result **out) {
-    if (!ctx || !out) {
-        set_last_error("ctx or out is NULL");
+    if (!out) {
+        set_last_error("out is NULL");
         return RPP_E_INVALID;
     }
     *out = nullptr;
-    Status v = validate_instance(in);
+    Status v = validate_instance(in);  // before the context: argument checks need no device
     if (!v.ok()) return report(v);
+    if (!ctx) {
+        set_last_error("ctx is NULL");
+        return RPP_E_INVALID;
+    }
     Workspace *ws = ctx->acquire();
     rpp_result *res = new rpp_result();
     Status s = run_instance(ctx, *ws, in, (cudaStream_t)stream, res);

@@ -12,9 +12,10 @@
 // them without reading anything back; a round after one that hooked nothing
 // returns at once (flags[r] records whether round r hooked). A round:
 //   reset : best[c] = none for every vertex (only roots are used);
-//   min   : one warp per vertex u scans its row for the lightest edge to
-//           another component and folds it into best[comp[u]] (64-bit
-//           atomicMin of the key (bits(d) << 32) | ~index);
+//   min   : warps scan the rows in chunks for each vertex u's lightest edge
+//           to another component and fold it into best[comp[u]] (64-bit
+//           atomicMin of the key (bits(d) << 32) | ~index; the index fits
+//           32 bits since C(n, 2) < 2^32);
 //   hook  : each root with an edge hooks onto the other endpoint's root; when
 //           two roots picked the same edge, the smaller one stays a root, and
 //           that edge is recorded once;
@@ -52,27 +53,47 @@ __global__ void k_h0_reset(unsigned long long *__restrict__ best, int64_t n,
     if (v < n) best[v] = ~0ull;
 }
 
+// A task is one chunk of H0_CHUNK entries of one row, taken by one warp: each
+// lane loads its H0_CHUNK / 32 entries (and their components) before testing
+// any, so the loads of a chunk are in flight together; many chunks per row
+// keep the SMs busy however few rows there are.
+constexpr int H0_CHUNK = 256;
+
 __global__ void __launch_bounds__(256) k_h0_min(const float *__restrict__ D, int64_t ld, int64_t n,
                                                 const DevState *__restrict__ st,
                                                 const int32_t *__restrict__ comp,
                                                 unsigned long long *__restrict__ best,
                                                 const unsigned *__restrict__ flags, int r) {
     if (h0_idle(flags, r)) return;
+    constexpr int PER = H0_CHUNK / 32;
     const float t = st->t;
     const int lane = threadIdx.x & 31;
+    const int64_t chunks = (n + H0_CHUNK - 1) / H0_CHUNK;
+    const int64_t tasks = n * chunks;
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += warps) {
+    for (int64_t task = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; task < tasks;
+         task += warps) {
+        const int64_t u = task / chunks;
+        const int64_t w0 = (task - u * chunks) * H0_CHUNK + lane;
         const int32_t cu = comp[u];
         const float *row = D + u * ld;
+        float d[PER];
+        int32_t cw[PER];
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            const int64_t w = w0 + 32 * i;
+            d[i] = w < n ? row[w] : 0.0f;
+            cw[i] = w < n ? comp[w] : cu;
+        }
         unsigned long long bk = ~0ull;
-        for (int64_t w = lane; w < n; w += 32) {
-            if (w == u || comp[w] == cu) continue;
-            const float d = row[w];
-            if (!(d <= t)) continue;
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            const int64_t w = w0 + 32 * i;
+            if (cw[i] == cu || !(d[i] <= t)) continue;  // also w == u and w >= n
             const uint64_t e = u > w ? (uint64_t)u * (uint64_t)(u - 1) / 2 + (uint64_t)w
                                      : (uint64_t)w * (uint64_t)(w - 1) / 2 + (uint64_t)u;
             const unsigned long long key =
-                ((unsigned long long)__float_as_uint(d) << 32) | (unsigned long long)(~(uint32_t)e);
+                ((unsigned long long)__float_as_uint(d[i]) << 32) | (unsigned long long)(~(uint32_t)e);
             bk = key < bk ? key : bk;
         }
 #pragma unroll
@@ -158,7 +179,8 @@ void launch_h0_forest(const float *D, int64_t ld, int64_t n, DevState *st, int32
     ++g_launches;
     k_h0_init<<<blocks_for(std::max<int64_t>(n, rounds), 256), 256, 0, s>>>(comp, n, nmst, flags,
                                                                           rounds);
-    int64_t warps = n;
+    const int64_t tasks = n * ((n + H0_CHUNK - 1) / H0_CHUNK);  // one warp each
+    int64_t warps = tasks;
     if (warps > 152 * 64) warps = 152 * 64;
     const unsigned min_blocks = (unsigned)((warps * 32 + 255) / 256);
     for (int r = 0; r < rounds; ++r) {

@@ -260,6 +260,9 @@ Status validate_instance(const Instance &in) {
     fill_binomial(in.n, in.max_dim + 2, store, B);
     if (B.at(in.max_dim + 2, in.n) == ~0ull)
         return fail(RPP_E_OVERFLOW, "C(n, max_dim + 2) does not fit the 63-bit index");
+    // H0's forest keys hold 32-bit edge indices (for max_dim = 0 too)
+    if ((uint64_t)in.n * (uint64_t)(in.n - 1) / 2 >= (1ull << 32))
+        return fail(RPP_E_OVERFLOW, "C(n, 2) does not fit the 32-bit edge index (n > 92682)");
     for (int p = 1; p <= in.max_dim; ++p)
         if (B.at(p + 1, in.n) >= (1ull << 32))
             return fail(RPP_E_NOMEM, "more than 2^32 candidate simplices in one dimension");

@@ -53,6 +53,14 @@ def test_argument_errors_without_gpu(lib):
     assert rc == N.RPP_E_INVALID
     assert b"NULL" in lib.rpp_last_error()
     assert lib.rpp_result_count(None, 0) == -1
+    # C(n, 2) >= 2^32 from n = 92683 on: refused by the argument checks, which
+    # need no context and read no input
+    tiny = (C.c_float * 4)()
+    for n_pts, want, msg in ((92683, N.RPP_E_OVERFLOW, b"92682"), (0, N.RPP_E_INVALID, b"n must")):
+        rc = lib.rpp_barcodes(None, C.addressof(tiny), N.RPP_INPUT_DISTANCES, n_pts, 0, 0,
+                              float("inf"), None, C.byref(h))
+        assert rc == want and not h.value
+        assert msg in lib.rpp_last_error()
     assert lib.rpp_result_total(None) == -1
 
 
