@@ -228,20 +228,15 @@ def serving_bench(rpp, count: int, slots: int):
         lock = threading.Lock()
         finished = threading.Event()
 
-        def poller():
+        def poller():  # results in completion order (rpp_server_next), timed on return
             while True:
                 with lock:
-                    todo = [(i, t) for i, t in enumerate(tickets) if i not in done]
                     all_in = finished.is_set() and len(done) == len(tickets)
                 if all_in:
                     return
-                progressed = False
-                for i, t in todo:
-                    if srv.poll(t, 0) is not None:
-                        done[i] = time.perf_counter()
-                        progressed = True
-                if not progressed:
-                    time.sleep(0.0002)
+                got = srv.next(20)
+                if got is not None:
+                    done[got[0]] = time.perf_counter()
 
         th = threading.Thread(target=poller)
         start = time.perf_counter()
@@ -257,7 +252,7 @@ def serving_bench(rpp, count: int, slots: int):
         th.join()
         end = max(done.values())
         srv.close()
-        lat = [done[i] - start - arr[i] for i in range(count)]
+        lat = [done[tickets[i]] - start - arr[i] for i in range(count)]
         return lat, end - start
 
     plain_lat = plain_poisson()

@@ -337,6 +337,14 @@ rpp_status rpp_server_submit(rpp_server *srv, const float *points, int64_t n, in
 /* Wait up to timeout_ms (< 0: forever) for a request; RPP_E_TIMEOUT if not done. */
 rpp_status rpp_server_poll(rpp_server *srv, uint64_t ticket, int32_t timeout_ms,
                            rpp_result **out);
+/* The next finished request in completion order (a completion queue): its
+ * ticket into *ticket and its result into *out, as rpp_server_poll would give
+ * for that ticket (a request already taken by rpp_server_poll is skipped).
+ * Waits up to timeout_ms (< 0: with no bound) for one to finish; returns
+ * RPP_E_TIMEOUT if none did. With every submitted request already taken and
+ * timeout_ms < 0 it waits for the next submission's completion. */
+rpp_status rpp_server_next(rpp_server *srv, int32_t timeout_ms, uint64_t *ticket,
+                           rpp_result **out);
 /* Drain every outstanding request and stop the worker threads. */
 void rpp_server_destroy(rpp_server *srv);
 

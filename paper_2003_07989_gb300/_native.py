@@ -23,7 +23,7 @@ EXPORTED = [
     "rpp_status_string", "rpp_last_error", "rpp_distance_matrix", "rpp_context_set_record",
     "rpp_result_columns", "rpp_result_apparent", "rpp_filtration_edges_noalloc",
     "rpp_context_set_batch", "rpp_context_batch_tuning", "rpp_apparent_census",
-    "rpp_results_gather", "rpp_results_stats", "rpp_results_free",
+    "rpp_results_gather", "rpp_results_stats", "rpp_results_free", "rpp_server_next",
 ]
 RPP_RECORD_COLUMNS, RPP_RECORD_APPARENT, RPP_RECORD_TIMING = 1, 2, 4
 STAGES = ["distance", "enclosing_radius", "build_columns", "sort_columns", "apparent",
@@ -104,6 +104,7 @@ def lib():
     L.rpp_server_submit.argtypes = [vp, vp, i64, i32, i32, C.c_float, C.c_float,
                                     C.POINTER(C.c_uint64)]
     L.rpp_server_poll.argtypes = [vp, C.c_uint64, i32, C.POINTER(vp)]
+    L.rpp_server_next.argtypes = [vp, i32, C.POINTER(C.c_uint64), C.POINTER(vp)]
     L.rpp_server_destroy.argtypes = [vp]
     L.rpp_server_destroy.restype = None
     L.rpp_status_string.argtypes = [C.c_int]
@@ -130,7 +131,7 @@ def lib():
                  "rpp_distance_matrix", "rpp_context_set_record", "rpp_filtration_edges_noalloc",
                  "rpp_result_stats", "rpp_barcodes_batched", "rpp_barcodes_backward",
                  "rpp_server_create", "rpp_server_submit", "rpp_server_poll",
-                 "rpp_results_gather", "rpp_results_stats"):
+                 "rpp_results_gather", "rpp_results_stats", "rpp_server_next"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L

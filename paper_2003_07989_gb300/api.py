@@ -306,6 +306,16 @@ class Server:
         N.check(rc, "rpp_server_poll")
         return _take_result(h.value)
 
+    def next(self, timeout_ms: int = -1):
+        """(ticket, Barcodes) of the next finished request in completion order
+        (rpp_server_next); None if none finished within timeout_ms."""
+        t, h = C.c_uint64(), C.c_void_p()
+        rc = N.lib().rpp_server_next(self.handle, timeout_ms, C.byref(t), C.byref(h))
+        if rc == N.RPP_E_TIMEOUT:
+            return None
+        N.check(rc, "rpp_server_next")
+        return int(t.value), _take_result(h.value)
+
     def close(self):
         if self.handle:
             N.lib().rpp_server_destroy(self.handle)

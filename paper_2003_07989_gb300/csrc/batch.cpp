@@ -576,6 +576,10 @@ bool batch_fused_eligible(const rpp_context *ctx, const Instance &in) {
            in.n <= BATCH_NMAX && (ctx->record & (RPP_RECORD_COLUMNS | RPP_RECORD_APPARENT)) == 0;
 }
 
+int64_t batch_bucket(const Instance &in) {
+    return ((int64_t)bucket_nmax(in.n) << 32) | (int64_t)dimcap_of(in.dim);
+}
+
 size_t batch_device_bytes(const std::vector<Instance> &ins) {
     std::vector<int> idx(ins.size());
     uint64_t rows = 0;

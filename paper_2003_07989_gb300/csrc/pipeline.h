@@ -162,6 +162,9 @@ Status run_batch(rpp_context *ctx, Workspace &ws, const std::vector<Instance> &i
                  cudaStream_t stream, rpp_result **out, Workspace *ws2 = nullptr);
 // Whether run_batch takes this instance through the fused pass.
 bool batch_fused_eligible(const rpp_context *ctx, const Instance &in);
+// The fused launch an eligible instance joins (size bucket and dimension
+// capacity): instances of one bucket share a launch.
+int64_t batch_bucket(const Instance &in);
 // Device bytes a workspace holds after run_batch over these fused-eligible
 // instances (an upper bound).
 size_t batch_device_bytes(const std::vector<Instance> &ins);

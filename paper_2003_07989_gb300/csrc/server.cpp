@@ -44,6 +44,7 @@ struct rpp_server {
     std::condition_variable cv_work, cv_done;
     std::deque<Request *> queue;
     std::unordered_map<uint64_t, Request *> reqs;
+    std::deque<uint64_t> finished;  // tickets in completion order (rpp_server_next)
     std::vector<size_t> held;  // bytes reserved per slot
     std::vector<std::thread> workers;
     uint64_t next_ticket = 1;
@@ -109,14 +110,16 @@ void rpp_server::worker(int k) {
             if (!r) break;
             batch.assign(1, r);
             if (r->fused) {
-                // continuous batching: waiting requests join this launch while
-                // the batch's footprint fits next to the other slots
+                // continuous batching: waiting requests of the same size bucket
+                // join this launch (one fused launch per batch) while the
+                // batch's footprint fits next to the other slots
                 std::vector<Instance> ins(1, r->in);
                 size_t est = r->est;
+                const int64_t bucket = batch_bucket(r->in);
                 for (auto it = queue.begin();
                      it != queue.end() && (int)batch.size() < cfg.max_batch;) {
                     Request *q = *it;
-                    if (!q->fused) {
+                    if (!q->fused || batch_bucket(q->in) != bucket) {
                         ++it;
                         continue;
                     }
@@ -167,6 +170,15 @@ void rpp_server::worker(int k) {
                 batch[i]->res = res[i];
                 batch[i]->status = st[i];
                 batch[i]->done = true;
+                finished.push_back(batch[i]->ticket);
+            }
+            // tickets taken by rpp_server_poll stay queued until skipped:
+            // drop them now and then so that a poll-only user stays bounded
+            if (finished.size() > 4096 && finished.size() > 2 * reqs.size()) {
+                std::deque<uint64_t> keep;
+                for (uint64_t t : finished)
+                    if (reqs.count(t)) keep.push_back(t);
+                finished.swap(keep);
             }
         }
         cv_done.notify_all();
@@ -268,6 +280,42 @@ rpp_status rpp_server_poll(rpp_server *srv, uint64_t ticket, int32_t timeout_ms,
     }
     srv->reqs.erase(it);
     g.unlock();
+    rpp_status code = r->status.code;
+    if (code != RPP_OK) set_last_error(r->status.msg);
+    *out = r->res;
+    delete r;
+    return code;
+}
+
+rpp_status rpp_server_next(rpp_server *srv, int32_t timeout_ms, uint64_t *ticket,
+                           rpp_result **out) {
+    if (!srv || !ticket || !out) {
+        set_last_error("rpp_server_next: invalid arguments");
+        return RPP_E_INVALID;
+    }
+    *out = nullptr;
+    *ticket = 0;
+    std::unique_lock<std::mutex> g(srv->mu);
+    Request *r = nullptr;
+    auto ready = [&] {  // the oldest finished request not yet taken by rpp_server_poll
+        while (!srv->finished.empty()) {
+            auto it = srv->reqs.find(srv->finished.front());
+            srv->finished.pop_front();
+            if (it != srv->reqs.end()) {
+                r = it->second;
+                srv->reqs.erase(it);
+                return true;
+            }
+        }
+        return false;
+    };
+    if (timeout_ms < 0) {
+        srv->cv_done.wait(g, ready);
+    } else if (!srv->cv_done.wait_for(g, std::chrono::milliseconds(timeout_ms), ready)) {
+        return RPP_E_TIMEOUT;
+    }
+    g.unlock();
+    *ticket = r->ticket;
     rpp_status code = r->status.code;
     if (code != RPP_OK) set_last_error(r->status.msg);
     *out = r->res;

@@ -117,3 +117,30 @@ def test_served_mixed_buckets_under_load(rpp):
             assert _same(srv.poll(t), a)
     finally:
         srv.close()
+
+
+def test_server_completion_queue(rpp, requests, alone):
+    """rpp_server_next hands every finished request back once, in completion
+    order, with the same result as alone; one taken by rpp_server_poll first is
+    skipped, and an empty queue times out."""
+    from paper_2003_07989_gb300 import _native as N
+    srv = rpp.Server(max_slots=4, max_batch=16)
+    try:
+        assert srv.next(0) is None
+        tickets = [srv.submit(r.points, 1, quantile=r.threshold_quantile) for r in requests]
+        first = srv.poll(tickets[0])  # taken here, so next() must skip it
+        assert _same(first, alone[0])
+        seen = {}
+        while len(seen) < len(tickets) - 1:
+            got = srv.next(60000)
+            assert got is not None
+            t, res = got
+            assert t not in seen and t != tickets[0]
+            seen[t] = res
+        assert srv.next(0) is None
+        for i, t in enumerate(tickets[1:], start=1):
+            assert _same(seen[t], alone[i]), i
+        with pytest.raises(N.RppError):
+            srv.poll(tickets[1], 0)  # already handed out by next()
+    finally:
+        srv.close()
