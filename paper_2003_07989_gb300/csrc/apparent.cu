@@ -15,11 +15,12 @@
 // The kernel is bound by the latency of its L1/L2 loads, so it is compiled
 // for eight 256-thread blocks per SM (32 registers a thread) to keep more
 // warps in flight. The paper runs one thread per column. Here a group of G
-// lanes owns a column and tests G candidate vertices w = scan, scan-1, ...,
-// scan-G+1 per step: the G reads D[v_i][w] of each row are contiguous, so
-// every step is a coalesced load of (p+1) short row segments (the rows are
-// L2-resident). A warp ballot picks the lowest qualifying lane, i.e. the
-// largest w. Groups of one warp advance independently: a group that finishes
+// lanes owns a column and tests U blocks of G candidate vertices per step,
+// lane l taking w = scan - l - u G for u < U: the reads D[v_i][w] of a block
+// are contiguous, so a step is U coalesced loads of (p+1) short row segments
+// (the rows are L2-resident), all in flight before any test, and one warp
+// ballot per block picks the largest qualifying w (first block, lowest
+// lane). Groups of one warp advance independently: a group that finishes
 // takes its next column in the same iteration, so no lane idles while a
 // neighbour scans a long column.
 // While scanning, each lane also tracks its oldest cofacet inside the
@@ -34,7 +35,7 @@ namespace rpp {
 
 namespace {
 
-template <int P, int G>
+template <int P, int G, int U>
 __global__ void __launch_bounds__(256, 8) k_apparent(
     const float *__restrict__ D, int64_t ld, int64_t n, const uint64_t *__restrict__ gB,
     bool smem_table, const uint32_t *__restrict__ key_hi, const uint64_t *__restrict__ key_lo,
@@ -43,7 +44,9 @@ __global__ void __launch_bounds__(256, 8) k_apparent(
     extern __shared__ uint64_t sB[];
     const uint64_t *B = stage_binomial(gB, n, P + 2, sB, smem_table);
     const float t = st->t;
-    unsigned scanned = 0;  // candidate vertices this lane examined
+    // candidate vertices a sequential scan examines before its exit (the
+    // algorithmic count, independent of the lanes' and blocks' over-reads)
+    unsigned long long scanned = 0;
     const int lane = threadIdx.x & 31;
     const int grp = lane / G, gl = lane % G;
     const unsigned gmask = (G == 32) ? FULL_MASK : (((1u << G) - 1u) << (grp * G));
@@ -72,35 +75,55 @@ __global__ void __launch_bounds__(256, 8) k_apparent(
         }
         if (!__any_sync(FULL_MASK, have)) break;
 
-        bool ok = false;
-        float dv[P + 1];
-        const int x = scan - gl;
-        if (have && x >= 0) {
-            bool member = false;
+        // U blocks of G candidates per step: lane gl tests scan - gl - u G
+        bool ok[U];
+        float dv[U][P + 1];
 #pragma unroll
-            for (int i = 0; i <= P; ++i) member |= (x == v[i]);
-            if (!member) {
-                ++scanned;
-                float m = 0.0f;
+        for (int u = 0; u < U; ++u) {
+            ok[u] = false;
+            const int x = scan - gl - u * G;
+            if (have && x >= 0) {
+                bool member = false;
 #pragma unroll
-                for (int i = 0; i <= P; ++i) {
-                    dv[i] = row[i][x];
-                    m = fmaxf(m, dv[i]);
-                }
-                ok = m <= diam;
-                const float cd = fmaxf(m, diam);
-                if (cd <= t && cd < best_d) {
-                    best_d = cd;
-                    best_v = x;
+                for (int i = 0; i <= P; ++i) member |= (x == v[i]);
+                if (!member) {
+                    float m = 0.0f;
+#pragma unroll
+                    for (int i = 0; i <= P; ++i) {
+                        dv[u][i] = row[i][x];
+                        m = fmaxf(m, dv[u][i]);
+                    }
+                    ok[u] = m <= diam;
+                    const float cd = fmaxf(m, diam);
+                    if (cd <= t && cd < best_d) {
+                        best_d = cd;
+                        best_v = x;
+                    }
                 }
             }
         }
-        const unsigned ball = __ballot_sync(FULL_MASK, ok);
+        unsigned gb[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) gb[u] = (__ballot_sync(FULL_MASK, ok[u]) & gmask) >> (grp * G);
         if (have) {
-            const unsigned gb = (ball & gmask) >> (grp * G);
-            if (gb) {
-                const int first = __ffs(gb) - 1;  // lowest lane = largest vertex
+            int first = -1, fu = 0;  // the largest qualifying vertex: first block, lowest lane
+#pragma unroll
+            for (int u = U - 1; u >= 0; --u)
+                if (gb[u]) {
+                    first = __ffs(gb[u]) - 1;
+                    fu = u;
+                }
+            if (first >= 0) {
                 if (gl == first) {
+                    const int x = scan - gl - fu * G;
+                    float dx[P + 1];
+#pragma unroll
+                    for (int i = 0; i <= P; ++i) {
+                        dx[i] = dv[0][i];
+#pragma unroll
+                        for (int u = 1; u < U; ++u)
+                            if (fu == u) dx[i] = dv[u][i];
+                    }
                     bool apparent = true;
 #pragma unroll
                     for (int i = 0; i <= P; ++i) {
@@ -108,7 +131,7 @@ __global__ void __launch_bounds__(256, 8) k_apparent(
                             float fd = 0.0f;
 #pragma unroll
                             for (int k = 0; k <= P; ++k)
-                                if (k != i) fd = fmaxf(fd, dv[k]);
+                                if (k != i) fd = fmaxf(fd, dx[k]);
 #pragma unroll
                             for (int a = 0; a <= P; ++a)
 #pragma unroll
@@ -121,10 +144,14 @@ __global__ void __launch_bounds__(256, 8) k_apparent(
                     status[c] = apparent ? COL_APPARENT : COL_LEFTOVER;
                     pivot[c] = cofacet_index<P>(v, x, B, n);
                     pdiam[c] = diam;
+                    int above = 0;  // vertices of sigma above x
+#pragma unroll
+                    for (int i = 0; i <= P; ++i) above += v[i] > x;
+                    scanned += (unsigned long long)(n - x - above);
                 }
                 have = false;
                 c += ngroups;
-            } else if (scan - G < 0) {
+            } else if (scan - U * G < 0) {
                 // every vertex seen, none of equal diameter: reduce the oldest cofacet
 #pragma unroll
                 for (int o = G / 2; o > 0; o >>= 1) {
@@ -139,11 +166,12 @@ __global__ void __launch_bounds__(256, 8) k_apparent(
                     status[c] = COL_LEFTOVER;
                     pivot[c] = best_v >= 0 ? cofacet_index<P>(v, best_v, B, n) : NO_PIVOT;
                     pdiam[c] = best_d;
+                    scanned += (unsigned long long)(n - (P + 1));
                 }
                 have = false;
                 c += ngroups;
             } else {
-                scan -= G;
+                scan -= U * G;
             }
         }
     }
@@ -194,7 +222,7 @@ __global__ void __launch_bounds__(256) k_partition(
     }
 }
 
-template <int P, int G>
+template <int P, int G, int U>
 void apparent_pg(const float *D, int64_t ld, int64_t n, const uint64_t *binom,
                  const uint32_t *key_hi, const uint64_t *key_lo, uint64_t ncols,
                  DevState *st, uint8_t *status, uint64_t *pivot, float *pdiam, int sms,
@@ -202,7 +230,7 @@ void apparent_pg(const float *D, int64_t ld, int64_t n, const uint64_t *binom,
     const size_t table = (size_t)(P + 3) * (n + 1) * sizeof(uint64_t);
     const bool smem = table <= 48 * 1024;
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apparent<P, G>, 256,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apparent<P, G, U>, 256,
                                                   smem ? table : 0);
     if (per_sm < 1) per_sm = 1;
     uint64_t blocks = (uint64_t)sms * per_sm;
@@ -210,20 +238,25 @@ void apparent_pg(const float *D, int64_t ld, int64_t n, const uint64_t *binom,
     if (need < blocks) blocks = need;
     if (blocks == 0) return;
     ++g_launches;
-    k_apparent<P, G><<<(unsigned)blocks, 256, smem ? table : 0, s>>>(
+    k_apparent<P, G, U><<<(unsigned)blocks, 256, smem ? table : 0, s>>>(
         D, ld, n, binom, smem, key_hi, key_lo, ncols, st, status, pivot, pdiam);
 }
 
+// group: lanes per column G (4, 8, 16, 32) for one candidate block per step,
+// or 10 G + U for U blocks (42, 44, 82).
 template <int P>
 void apparent_p(int group, const float *D, int64_t ld, int64_t n, const uint64_t *binom,
                 const uint32_t *key_hi, const uint64_t *key_lo, uint64_t ncols,
                 DevState *st, uint8_t *status, uint64_t *pivot, float *pdiam, int sms,
                 cudaStream_t s) {
     switch (group) {
-        case 4: apparent_pg<P, 4>(D, ld, n, binom, key_hi, key_lo, ncols, st, status, pivot, pdiam, sms, s); break;
-        case 16: apparent_pg<P, 16>(D, ld, n, binom, key_hi, key_lo, ncols, st, status, pivot, pdiam, sms, s); break;
-        case 32: apparent_pg<P, 32>(D, ld, n, binom, key_hi, key_lo, ncols, st, status, pivot, pdiam, sms, s); break;
-        default: apparent_pg<P, 8>(D, ld, n, binom, key_hi, key_lo, ncols, st, status, pivot, pdiam, sms, s); break;
+        case 4: apparent_pg<P, 4, 1>(D, ld, n, binom, key_hi, key_lo, ncols, st, status, pivot, pdiam, sms, s); break;
+        case 16: apparent_pg<P, 16, 1>(D, ld, n, binom, key_hi, key_lo, ncols, st, status, pivot, pdiam, sms, s); break;
+        case 32: apparent_pg<P, 32, 1>(D, ld, n, binom, key_hi, key_lo, ncols, st, status, pivot, pdiam, sms, s); break;
+        case 42: apparent_pg<P, 4, 2>(D, ld, n, binom, key_hi, key_lo, ncols, st, status, pivot, pdiam, sms, s); break;
+        case 82: apparent_pg<P, 8, 2>(D, ld, n, binom, key_hi, key_lo, ncols, st, status, pivot, pdiam, sms, s); break;
+        case 44: apparent_pg<P, 4, 4>(D, ld, n, binom, key_hi, key_lo, ncols, st, status, pivot, pdiam, sms, s); break;
+        default: apparent_pg<P, 8, 1>(D, ld, n, binom, key_hi, key_lo, ncols, st, status, pivot, pdiam, sms, s); break;
     }
 }
 

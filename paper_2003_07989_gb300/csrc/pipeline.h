@@ -94,7 +94,7 @@ struct Workspace {
 
 // Tunables chosen per size bucket by the autotuner (autotune.cpp).
 struct Tuning {
-    int group = 8;  // lanes per column in the apparent-pair pass
+    int group = 44;  // apparent-pair pass shape: G lanes per column, or 10 G + U for U blocks a step
 };
 
 struct Context;
