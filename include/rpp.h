@@ -106,7 +106,8 @@ typedef struct {
     int64_t store_reads[RPP_MAX_DIM + 1]; /* pair-store lookups in the reduction */
     int64_t entries[RPP_MAX_DIM + 1];     /* coboundary entries the reduction examined */
     int64_t intervals[RPP_MAX_DIM + 1];   /* nonzero intervals reported (index 0 = H0) */
-    int64_t scanned[RPP_MAX_DIM + 1];     /* candidate vertices the apparent pass examined */
+    int64_t scanned[RPP_MAX_DIM + 1];     /* candidate vertices a sequential apparent test
+                                             examines up to its exit, summed over columns */
     int64_t sweep_levels[RPP_MAX_DIM + 1]; /* diameter levels swept by long dimension-1 walks */
     int64_t kernel_launches;              /* CUDA kernels this call launched */
     /* Per-stage device time from CUDA events on the call's stream, filled when

@@ -353,7 +353,6 @@ __global__ void __launch_bounds__(512) k_batch_h1(
                 float du = 0.0f, dw = 0.0f;
                 const int x = scan - gl;
                 if (have && x >= 0 && x != u && x != w) {
-                    ++scanned;
                     du = D[u * ld + x];
                     dw = D[w * ld + x];
                     const float mx = fmaxf(du, dw);
@@ -372,6 +371,8 @@ __global__ void __launch_bounds__(512) k_batch_h1(
                     if (gb) {
                         const int first = __ffs(gb) - 1;  // lowest lane: largest vertex
                         if (gl == first) {
+                            // candidates a sequential scan examines up to x
+                            scanned += (unsigned long long)(n - x - (u > x) - (w > x));
                             // facets of tau = {u, w, x} before sigma drop a vertex above x
                             bool apparent = true;
                             if (u > x && dw == diam) apparent = false;  // facet {w, x}
@@ -401,6 +402,7 @@ __global__ void __launch_bounds__(512) k_batch_h1(
                             }
                         }
                         if (gl == 0) {
+                            scanned += (unsigned long long)(n - 2);
                             emit = true;
                             aw[e] = 0xFFFFu;
                             if (best_v >= 0) {

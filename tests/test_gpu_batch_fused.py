@@ -18,9 +18,10 @@ from paper_2003_07989_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 STAT_KEYS = ("threshold", "enclosing_radius")
-# "scanned" (candidate vertices examined) depends on the lanes per column, a
-# launch shape the autotuner picks, so it is a work counter and not compared
-STAT_LISTS = ("candidates", "columns", "cleared", "apparent", "leftover", "intervals")
+# "scanned" counts the candidates a sequential apparent test examines up to its
+# exit, whatever launch shape ran it, so both paths must agree on it too
+STAT_LISTS = ("candidates", "columns", "cleared", "apparent", "leftover", "intervals",
+              "scanned")
 
 
 @pytest.fixture(scope="module")
