@@ -44,6 +44,8 @@
 #include <thread>
 #include <type_traits>
 
+static_assert(__BYTE_ORDER__ == __ORDER_LITTLE_ENDIAN__, "lune_word packs bytes little-endian");
+
 namespace rpp {
 
 // ---------------------------------------------------------------------------
@@ -248,30 +250,31 @@ constexpr int64_t STRIDE = 64;
 // m - 1 - f for filtration position f. One 64-bit key per edge,
 // (bits(diameter) - bits(from), ~a, ~b) with a and b in w bits each, orders
 // the edges into filtration order (diameter ascending; on ties the index
-// descends with (a, b)). The keys are partitioned once into up to 2048
-// buckets by their top varying bits; a bucket is sorted only when a sweep
-// first reaches it, so a short sweep pays for little more than the partition.
+// descends with (a, b)). The keys are written straight into up to 2048
+// buckets by their top bits (two passes over the distance rows: count, then
+// place); a bucket is sorted only when a sweep first reaches it, so a short
+// sweep pays for little more than the partition.
 struct EdgeList {
     float from = 0.0f;
     int w = 1, sh = 0;
-    uint64_t vmax = 1, kmin = 0, kmax = 0;
+    uint64_t vmax = 1, kmax = 0;  // kmax: no key exceeds it
     uint32_t base = 0;
     int64_t m = 0;
-    mutable std::vector<uint64_t> key;  // partitioned; a bucket's range sorted once done
-    std::vector<int64_t> bstart;        // bucket i: positions [bstart[i], bstart[i + 1])
-    mutable std::vector<uint32_t> ab, hi;
+    mutable std::unique_ptr<uint64_t[]> key;  // by bucket; a bucket sorted once done
+    std::vector<int64_t> bstart;              // bucket i: positions [bstart[i], bstart[i + 1])
+    mutable std::unique_ptr<uint32_t[]> ab, hi;
     std::unique_ptr<std::atomic<uint8_t>[]> done;
     mutable std::mutex mu;
 
     int nbuckets() const { return (int)bstart.size() - 1; }
-    int bucket_of(uint64_t k) const { return (int)((k >> sh) - (kmin >> sh)); }
+    int bucket_of(uint64_t k) const { return (int)(k >> sh); }
 
     // Sort bucket i and fill its positions of ab and hi (once).
     void ensure(int i) const {
         if (done[i].load(std::memory_order_acquire)) return;
         std::lock_guard<std::mutex> g(mu);
         if (done[i].load(std::memory_order_relaxed)) return;
-        std::sort(key.begin() + bstart[i], key.begin() + bstart[i + 1]);
+        std::sort(key.get() + bstart[i], key.get() + bstart[i + 1]);
         for (int64_t f = bstart[i]; f < bstart[i + 1]; ++f) {
             const uint64_t k = key[f];
             const uint32_t a = (uint32_t)(vmax - ((k >> w) & vmax));
@@ -292,11 +295,10 @@ struct EdgeList {
             *bucket = nbuckets() - 1;
             return m;
         }
-        const int i = kb <= kmin ? 0 : bucket_of(kb);
+        const int i = bucket_of(kb);
         ensure(i);
         *bucket = i;
-        return std::lower_bound(key.begin() + bstart[i], key.begin() + bstart[i + 1], kb) -
-               key.begin();
+        return std::lower_bound(key.get() + bstart[i], key.get() + bstart[i + 1], kb) - key.get();
     }
 };
 
@@ -306,46 +308,46 @@ void sort_edges(const HostInstance &I, float from, EdgeList &out) {
     while ((int64_t(1) << w) < n) ++w;
     const uint64_t vmax = (uint64_t(1) << w) - 1;
     const uint32_t base = float_bits(from);
-    std::vector<uint64_t> key;
-    key.reserve((size_t)(n * (n - 1) / 2));
-    for (int64_t a = 1; a < n; ++a) {
-        const float *Da = I.D + a * I.ld;
-        const uint64_t ka = (vmax - (uint64_t)a) << w;
-        for (int64_t b = 0; b < a; ++b) {
-            const float d = Da[b];
-            if (d >= from && d <= I.t)
-                key.push_back(((uint64_t)(float_bits(d) - base) << (2 * w)) | ka |
-                              (vmax - (uint64_t)b));
-        }
-    }
-    const int64_t m = (int64_t)key.size();
-    uint64_t kmin = ~0ull, kmax = 0;
-    for (uint64_t k : key) {
-        kmin = std::min(kmin, k);
-        kmax = std::max(kmax, k);
-    }
-    int sh = 0;
-    if (m > 1) {
-        const int hb = 63 - __builtin_clzll(kmin ^ kmax);  // top bit in which keys differ
-        sh = std::max(0, hb + 1 - 11);
-    }
+    const float t = I.t;
+    // every key is at most kmax: the bucket shift follows from the range alone
+    const uint64_t kmax = t >= from ? ((uint64_t)(float_bits(t) - base) << (2 * w)) |
+                                          ((uint64_t(1) << (2 * w)) - 1)
+                                    : 0;
+    const int top = kmax ? 64 - __builtin_clzll(kmax) : 0;
+    const int sh = std::max(0, top - 11);
     out.from = from;
     out.w = w;
     out.sh = sh;
     out.vmax = vmax;
-    out.kmin = m ? kmin : 0;
-    out.kmax = m ? kmax : 0;
+    out.kmax = kmax;
     out.base = base;
+    const int nb = (int)(kmax >> sh) + 1;
+    auto key_of = [&](int64_t a, int64_t b, float d) {
+        return ((uint64_t)(float_bits(d) - base) << (2 * w)) | ((vmax - (uint64_t)a) << w) |
+               (vmax - (uint64_t)b);
+    };
+    std::vector<int64_t> &bs = out.bstart;
+    bs.assign(nb + 1, 0);
+    for (int64_t a = 1; a < n; ++a) {
+        const float *Da = I.D + a * I.ld;
+        for (int64_t b = 0; b < a; ++b)
+            if (Da[b] >= from && Da[b] <= t) ++bs[out.bucket_of(key_of(a, b, Da[b])) + 1];
+    }
+    for (int i = 0; i < nb; ++i) bs[i + 1] += bs[i];
+    const int64_t m = bs[nb];
     out.m = m;
-    const int nb = m ? (int)((kmax >> sh) - (kmin >> sh)) + 1 : 1;
-    out.bstart.assign(nb + 1, 0);
-    for (uint64_t k : key) ++out.bstart[out.bucket_of(k) + 1];
-    for (int i = 0; i < nb; ++i) out.bstart[i + 1] += out.bstart[i];
-    std::vector<int64_t> at(out.bstart.begin(), out.bstart.end() - 1);
-    out.key.resize(m);
-    for (uint64_t k : key) out.key[at[out.bucket_of(k)]++] = k;
-    out.ab.resize(m);
-    out.hi.resize(m);
+    out.key.reset(new uint64_t[m > 0 ? m : 1]);
+    std::vector<int64_t> at(bs.begin(), bs.end() - 1);
+    for (int64_t a = 1; a < n; ++a) {
+        const float *Da = I.D + a * I.ld;
+        for (int64_t b = 0; b < a; ++b)
+            if (Da[b] >= from && Da[b] <= t) {
+                const uint64_t k = key_of(a, b, Da[b]);
+                out.key[at[out.bucket_of(k)]++] = k;
+            }
+    }
+    out.ab.reset(new uint32_t[m > 0 ? m : 1]);
+    out.hi.reset(new uint32_t[m > 0 ? m : 1]);
     out.done.reset(new std::atomic<uint8_t>[nb]);
     for (int i = 0; i < nb; ++i) out.done[i].store(0, std::memory_order_relaxed);
 }
@@ -1040,8 +1042,23 @@ struct Walk1 {
         const int64_t b = k << 6, e = std::min<int64_t>(b + 64, n);
         const float d = c.d;
         uint64_t m = 0;
-        for (int64_t i = b; i < e; ++i)
-            m |= (uint64_t)((Dx[i] <= d) & (Dy[i] <= d)) << (i - b);
+        if (e - b == 64) {
+            // one flag byte per vertex (a loop the compiler vectorises), then
+            // eight 0/1 bytes at a time into eight bits: the product with
+            // sum_i 2^(56 - 7 i) gathers byte i into bit 56 + i, and every other
+            // partial product falls below bit 56 without carrying into it or
+            // beyond bit 63
+            uint8_t f[64];
+            for (int i = 0; i < 64; ++i) f[i] = (uint8_t)((Dx[b + i] <= d) & (Dy[b + i] <= d));
+            for (int j = 0; j < 8; ++j) {
+                uint64_t x;
+                std::memcpy(&x, f + 8 * j, 8);  // little-endian: byte i at bits 8i..8i+7
+                m |= ((x * 0x0102040810204080ull) >> 56) << (8 * j);
+            }
+        } else {
+            for (int64_t i = b; i < e; ++i)
+                m |= (uint64_t)((Dx[i] <= d) & (Dy[i] <= d)) << (i - b);
+        }
         if ((c.x >> 6) == k) m &= ~(1ull << (c.x & 63));
         if ((c.y >> 6) == k) m &= ~(1ull << (c.y & 63));
         return m;
@@ -1385,7 +1402,7 @@ struct Walk1 {
     const uint32_t *eab = nullptr, *ehi = nullptr;
     int64_t ne = 0;
     std::shared_ptr<const EdgeList> elist;  // the arrays, when sorted on the host
-    int ebucket = 0;              // host-sorted: the bucket of the last position asked for
+    int ebucket = 0;              // host-sorted: the last bucket sorted for this sweep
     int64_t eready = 0;           // positions below are sorted (from the sweep's start on)
     int64_t f1 = 0;
     float lvl_d = 0.0f;           // diameter of the current level
@@ -1414,13 +1431,15 @@ struct Walk1 {
     bool can_sweep() const { return n <= SWEEP_NMAX; }
 
     // Edge at position f of the filtration order (diameter ascending).
-    // Host-sorted edges: sort the bucket of position f if the sweep has not
-    // been there yet (the sweep only moves forward).
+    // Host-sorted edges: sort every bucket from the last one sorted up to the
+    // one holding position f (the sweep only moves forward, and positions
+    // below eready are sorted from the sweep's start on).
     void need(int64_t f) {
-        if (f < eready) return;
-        while (elist->bstart[ebucket + 1] <= f) ++ebucket;
-        elist->ensure(ebucket);
-        eready = elist->bstart[ebucket + 1];
+        while (f >= eready) {
+            ++ebucket;
+            elist->ensure(ebucket);
+            eready = elist->bstart[ebucket + 1];
+        }
     }
     void edge_at(int64_t f, int &a, int &b) const {
         const uint32_t ab = eab[ne - 1 - f];
@@ -1604,8 +1623,8 @@ struct Walk1 {
             f1 = lo;
         } else {
             elist = R.level_edges(dk);
-            eab = elist->ab.data();
-            ehi = elist->hi.data();
+            eab = elist->ab.get();
+            ehi = elist->hi.get();
             ne = elist->m;
             f1 = elist->first_at(bd, &ebucket);
             eready = f1 < ne ? elist->bstart[ebucket + 1] : ne;

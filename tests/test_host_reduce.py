@@ -57,6 +57,20 @@ def harness_wide(tmp_path_factory):
     return _build(tmp_path_factory, "host_reduce_harness_wide", ["-DRPP_WIDE_KEYS_ONLY"])
 
 
+def _run_full(exe, D, t, threads, flags, tmp):
+    """(sorted H1 intervals, levels swept, additions) of one harness run."""
+    D = np.ascontiguousarray(D, dtype=np.float32)
+    dpath, opath = str(tmp / "D.f32"), str(tmp / "out.f32")
+    D.tofile(dpath)
+    r = subprocess.run([exe, dpath, str(len(D)), repr(float(t)), str(threads), str(flags), opath],
+                       capture_output=True, text=True, check=True)
+    iv = np.fromfile(opath, dtype=np.float32).reshape(-1, 2)
+    iv = iv[np.lexsort((iv[:, 1], iv[:, 0]))]
+    levels = int(r.stdout.split("levels ")[1].split()[0])
+    additions = int(r.stdout.split("additions ")[1].split()[0])
+    return iv, levels, additions
+
+
 def _run(exe, D, t, threads, flags, tmp):
     D = np.ascontiguousarray(D, dtype=np.float32)
     dpath, opath = str(tmp / "D.f32"), str(tmp / "out.f32")
@@ -138,3 +152,21 @@ def test_host_reduction_parallel_columns_equal_oracle(harness, harness_wide, tmp
                                 (harness, 8, 1)):
         got, _ = _run(exe, D, t, threads, flags, tmp_path)
         assert got.shape == ref.shape and np.array_equal(got, ref), (name, threads, flags)
+
+
+@pytest.mark.parametrize("index", [29, 136, 3, 52])
+def test_host_sorted_levels_add_what_the_sorted_array_adds(harness, tmp_path, index):
+    """Serving clouds (circles whose H1 class outlives the 0.6-quantile
+    threshold sweep long walks): with the reduction sorting the edges itself,
+    a bucket at a time as its sweeps reach them, it makes exactly the
+    additions it makes over a sorted edge array handed over, and the barcode
+    is the oracle's. Clouds 29 and 136 have buckets of one or two edges that
+    the sweep's look-ahead crosses."""
+    r = I.serving_requests(4096, seed=0)[index]
+    D = O.distance_matrix(r.points)
+    t = O.distance_quantile(D, r.threshold_quantile)
+    ref = O.barcodes(D, 1, t, O.MODE_COHOM_CLEAR).barcode(1)
+    given, lv0, add0 = _run_full(harness, D, t, 1, 0, tmp_path)
+    own, lv1, add1 = _run_full(harness, D, t, 1, 1, tmp_path)
+    assert np.array_equal(given, ref) and np.array_equal(own, ref)
+    assert (lv1, add1) == (lv0, add0)
