@@ -170,3 +170,27 @@ def test_host_sorted_levels_add_what_the_sorted_array_adds(harness, tmp_path, in
     own, lv1, add1 = _run_full(harness, D, t, 1, 1, tmp_path)
     assert np.array_equal(given, ref) and np.array_equal(own, ref)
     assert (lv1, add1) == (lv0, add0)
+
+
+@pytest.fixture(scope="module")
+def harness_sanitized(tmp_path_factory):
+    # AddressSanitizer and UndefinedBehaviorSanitizer, every report fatal
+    flags = ["-O1", "-g", "-fsanitize=address,undefined", "-fno-sanitize-recover=undefined"]
+    try:
+        return _build(tmp_path_factory, "host_reduce_harness_asan", flags)
+    except subprocess.CalledProcessError:
+        pytest.skip("the compiler cannot build with the sanitizers here")
+
+
+@pytest.mark.parametrize("name,flags,threads", [("perm160", 1, 4), ("circle400_q", 3, 4),
+                                                ("torus450_ties", 1, 1)])
+def test_host_reduction_under_sanitizers(harness_sanitized, tmp_path, name, flags, threads):
+    """No out-of-bounds access, use after free or undefined behaviour in the
+    host reduction (concurrent columns, host-sorted level buckets, apparent
+    pivots tested again), and still the oracle's barcode."""
+    D, t = {**CASES, **PARALLEL_CASES}[name]()
+    if t is None:
+        t = O.distance_quantile(D, 0.6)
+    got, _ = _run(harness_sanitized, D, t, threads, flags, tmp_path)
+    ref = O.barcodes(D, 1, t, O.MODE_COHOM_CLEAR).barcode(1)
+    assert np.array_equal(got, ref), name
