@@ -454,7 +454,7 @@ Status launch_device(rpp_context *ctx, Workspace &ws, const std::vector<Instance
 // Host half of a fused launch: H0 from the forest, the submatrix reductions
 // and the barcodes; results into out[idx[k]]. Clouds whose leftover columns
 // overflowed the pool are appended to `alone` (run by themselves later).
-Status launch_host(rpp_context *ctx, const std::vector<Instance> &ins, Launch &L,
+Status launch_host(rpp_context *ctx, Launch &L,
                    rpp_result **out, std::vector<int> &alone) {
     const std::vector<int> &idx = L.idx;
     const int k = (int)idx.size();
@@ -637,7 +637,7 @@ Status run_batch(rpp_context *ctx, Workspace &ws, const std::vector<Instance> &i
         const bool more = i + 1 < plan.size();
         Workspace &wn = *wsp[overlap ? (i + 1) & 1 : 0];
         if (!overlap) {
-            st = launch_host(ctx, ins, cur, out, overflow);
+            st = launch_host(ctx, cur, out, overflow);
             if (st.ok() && more)
                 st = launch_device(ctx, wn, ins, plan[i + 1].idx, plan[i + 1].nmax,
                                    plan[i + 1].dimcap, s, L[(i + 1) & 1]);
@@ -646,7 +646,7 @@ Status run_batch(rpp_context *ctx, Workspace &ws, const std::vector<Instance> &i
         Status hs;
         std::thread host([&] {
             try {
-                hs = launch_host(ctx, ins, cur, out, overflow);
+                hs = launch_host(ctx, cur, out, overflow);
             } catch (const std::exception &e) {
                 hs = fail(RPP_E_NOMEM, std::string("batched host reduction: ") + e.what());
             }
