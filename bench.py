@@ -49,7 +49,7 @@ def parse_args():
     ap.add_argument("--no-census", action="store_true",
                     help="skip the apparent-pair census of random edge orders")
     ap.add_argument("--no-extras", action="store_true",
-                    help="only the torus steps: no serving, census or differentiation section")
+                    help="only the torus steps: no serving, census, differentiation or S^3 section")
     return ap.parse_args()
 
 
@@ -299,6 +299,90 @@ def backward_bench(rpp, torch, dev, reps: int = 10):
 
 
 # ---------------------------------------------------------------------------
+# 192 points on S^3, H0-H2 (the stand-in for the paper's sphere_3_192)
+
+
+def sphere_bench(rpp, torch, dev, reps: int = 10, stream_count: int = 512):
+    """Time per barcode of 192 points on S^3 with H0-H2 (full filtration)
+    alone; its apparent fraction per dimension beside the paper's for its
+    sphere_3_192 dataset (another sample of the same distribution); and its
+    latency as one large request submitted to the server amid a Poisson
+    stream of small serving-mix requests, with that stream's p99."""
+    import threading
+    from paper_2003_07989_gb300 import inputs as I
+    X = I.sphere_s3(192, seed=0)
+    pts = torch.from_numpy(X).to(dev)
+    for _ in range(2):
+        rpp.rpp_barcodes(pts, max_dim=2)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        b = rpp.rpp_barcodes(pts, max_dim=2)
+    torch.cuda.synchronize(dev)
+    alone_ms = 1e3 * (time.perf_counter() - t0) / reps
+    st = b.stats
+    frac = {str(q): st["apparent"][q] / st["columns"][q] for q in (1, 2) if st["columns"][q]}
+    # the same request amid a stream of small ones; one untimed pass first
+    # (the fused buckets' autotuning, the slots' first allocations)
+    reqs = I.serving_requests(stream_count, rate_per_s=2000.0, seed=1)
+    rpp.rpp_barcodes_batched([r.points for r in reqs], max_dim=1,
+                             quantiles=[r.threshold_quantile for r in reqs])
+    at = reqs[len(reqs) // 2].arrival_s  # the large request arrives mid-stream
+    srv = rpp.Server(max_slots=8, max_batch=64)
+
+    def one_pass():
+        done, sub = {}, {}
+        lock = threading.Lock()
+        finished = threading.Event()
+
+        def poller():
+            while True:
+                with lock:
+                    if finished.is_set() and len(done) == len(sub):
+                        return
+                got = srv.next(20)
+                if got is not None:
+                    done[got[0]] = time.perf_counter()
+
+        th = threading.Thread(target=poller)
+        start = time.perf_counter()
+        th.start()
+        big = None
+        for r in reqs:
+            if big is None and r.arrival_s >= at:
+                now = time.perf_counter() - start
+                if now < at:
+                    time.sleep(at - now)
+                big = srv.submit(X, 2)
+                with lock:
+                    sub[big] = at
+            now = time.perf_counter() - start
+            if now < r.arrival_s:
+                time.sleep(r.arrival_s - now)
+            t = srv.submit(r.points, 1, quantile=r.threshold_quantile)
+            with lock:
+                sub[t] = r.arrival_s
+        finished.set()
+        th.join()
+        return {t: 1e3 * (done[t] - start - a) for t, a in sub.items()}, big
+
+    one_pass()
+    lat, big = one_pass()
+    srv.close()
+    small = sorted(v for t, v in lat.items() if t != big)
+    return {"n": 192, "max_dim": 2, "ms_alone": alone_ms,
+            "columns": {str(q): st["columns"][q] for q in (1, 2)},
+            "apparent_fraction": frac,
+            "paper_apparent_fraction_sphere_3_192": {"1": 0.99707909, "2": 0.99734764},
+            "served_ms": lat[big], "stream_requests": len(small),
+            "stream_p50_ms": small[len(small) // 2],
+            "stream_p99_ms": small[min(len(small) - 1, int(0.99 * len(small)))],
+            "workload": "192 points uniform on S^3 (normalised Gaussian 4-vectors, seed 0), "
+                        "full filtration, H0-H2; served amid 512 serving-mix requests "
+                        "(Poisson, 2000/s, seed 1)"}
+
+
+# ---------------------------------------------------------------------------
 # apparent-pair census of random edge orders (the paper's apparent-rate experiment)
 
 
@@ -512,6 +596,7 @@ def main():
         serving = serving_bench(rpp, args.serving_requests, args.serving_slots)
     census = None if (args.no_census or args.no_extras) else census_bench(rpp, torch, dev, ctx)
     backward = None if args.no_extras else backward_bench(rpp, torch, dev)
+    sphere = None if args.no_extras else sphere_bench(rpp, torch, dev)
     h2d = X.nbytes
     d2h = sum(len(iv) * (8 + 16) for iv in e2e_results[0].intervals)
     line = {
@@ -529,6 +614,7 @@ def main():
         "serving": serving,
         "apparent_census": census,
         "differentiation": backward,
+        "sphere_h2": sphere,
         "breakdown": {
             "kernels": kernels,
             "host_reduce_ms": statistics.mean(s["ms_host_reduce"] for s in st),
