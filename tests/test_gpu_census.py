@@ -28,9 +28,12 @@ def rpp():
     return m
 
 
-@pytest.mark.parametrize("case", ["torus60", "rank45", "cube50", "ties40"])
+@pytest.mark.parametrize("case", ["torus60", "rank45", "cube50", "ties40", "sphere192"])
 def test_census_equals_oracle(rpp, case):
-    if case == "torus60":
+    if case == "sphere192":  # the stand-in for the paper's sphere_3_192 (its Table of
+        # apparent percentages per dimension counts pairs of the full filtration)
+        D = O.distance_matrix(I.sphere_s3(192, seed=0))
+    elif case == "torus60":
         D = O.distance_matrix(I.noisy_torus(60, seed=3))
     elif case == "rank45":
         D = I.rank_distances(45, seed=1)
