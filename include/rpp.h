@@ -213,7 +213,8 @@ void rpp_results_free(rpp_result *const *results, int32_t count);
  *   thresholds    per cloud threshold (+INFINITY = full), or NULL for all full.
  *   quantiles     per cloud quantile in (0,1] overriding the threshold, or NULL.
  *   stream        CUDA stream for every copy and launch (NULL: legacy stream).
- *   out[i]        result of cloud i (free each with rpp_result_free).
+ *   out[i]        result of cloud i (free each with rpp_result_free, or all of
+ *                 them with rpp_results_free; rpp_results_gather copies them).
  * Errors: RPP_E_INVALID (a cloud's arguments, or non-finite coordinates),
  * RPP_E_NOMEM, RPP_E_CUDA. On error no result is returned. */
 rpp_status rpp_barcodes_batched(rpp_context *ctx, int32_t batch, const float *const *data,
