@@ -224,8 +224,12 @@ rpp_status rpp_barcodes_batched(rpp_context *ctx, int32_t batch, const float *co
 
 /* Batch behaviour of a context. fused = 0 runs every cloud of a batch through
  * the one-at-a-time pipeline (for comparisons); autotune = 0 keeps the default
- * launch shape (256 threads, 8 lanes per column) for buckets not yet tuned.
- * Both default to 1. Errors: RPP_E_INVALID for a NULL context. */
+ * launch shapes for size buckets not yet tuned: 256 threads and 8 lanes per
+ * column in the fused pass, and in the single-instance apparent pass 4 lanes
+ * with 2 (n <= 256) or 4 candidate blocks a step. With autotune = 1 the first
+ * instance of a bucket times the candidate shapes on its own columns (every
+ * shape gives the same results). Both default to 1. Errors: RPP_E_INVALID for
+ * a NULL context. */
 rpp_status rpp_context_set_batch(rpp_context *ctx, int32_t fused, int32_t autotune);
 
 /* The launch shape the autotuner chose for the bucket of clouds with up to

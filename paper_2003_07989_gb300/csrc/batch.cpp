@@ -26,7 +26,7 @@ using namespace rpp;
 rpp::Tuning rpp_context::tuning_for(int64_t n, int p) {
     rpp::Tuning t;
     (void)p;
-    t.group = n <= 256 ? 42 : 44;  // 4 lanes, 2 or 4 candidate blocks a step (measured)
+    t.group = n <= 256 ? 42 : 44;  // untuned default: 4 lanes, 2 or 4 candidate blocks a step
     return t;
 }
 

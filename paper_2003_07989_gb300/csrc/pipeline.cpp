@@ -16,6 +16,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <mutex>
 #include <thread>
@@ -333,6 +334,62 @@ void sort_result(rpp_result *res, int q) {
     cr.swap(cr2);
 }
 
+// Launch shape of the single-instance apparent pass for dimension p and the
+// size bucket of n (the next power of two): the context's tuned one, or, on
+// the bucket's first instance (with autotuning on), the fastest of the
+// candidate shapes timed on this instance's columns. Every shape writes the
+// same outputs; the timing launches count into a scratch copy of the state,
+// so the call's counters are those of the one real launch.
+static Status apparent_shape(rpp_context *ctx, Workspace &ws, int p, int64_t n, DevState *st,
+                             const std::function<void(int, DevState *)> &launch, cudaStream_t s,
+                             int *group) {
+    int64_t bucket = 1;
+    while (bucket < n) bucket <<= 1;
+    const std::pair<int, int64_t> key(p, bucket);
+    *group = ctx->tuning_for(n, p).group;
+    {
+        std::lock_guard<std::mutex> g(ctx->tune_mu);
+        auto it = ctx->apparent_tuning.find(key);
+        if (it != ctx->apparent_tuning.end()) {
+            *group = it->second;
+            return Status();
+        }
+    }
+    if (!ctx->autotune) return Status();
+    void *vp;
+    RPP_TRY(ws.dev(ws.state_tune, sizeof(DevState), &vp));
+    DevState *scratch = (DevState *)vp;
+    RPP_CK(cudaMemcpyAsync(scratch, st, sizeof(DevState), cudaMemcpyDeviceToDevice, s));
+    cudaEvent_t e0, e1;
+    RPP_CK(cudaEventCreate(&e0));
+    RPP_CK(cudaEventCreate(&e1));
+    float best = 0.0f;
+    for (int g : {8, 82, 42, 44, 4}) {
+        float ms = 0.0f;
+        for (int rep = 0; rep < 2; ++rep) {  // the first run warms the caches
+            cudaEventRecord(e0, s);
+            launch(g, scratch);
+            cudaEventRecord(e1, s);
+            cudaError_t e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return fail(RPP_E_CUDA, std::string("apparent-pass tuning: ") + cudaGetErrorString(e));
+            }
+            cudaEventElapsedTime(&ms, e0, e1);
+        }
+        if (g == 8 || ms < best) {
+            best = ms;
+            *group = g;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::lock_guard<std::mutex> g(ctx->tune_mu);
+    ctx->apparent_tuning.emplace(key, *group);
+    return Status();
+}
+
 Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStream_t s,
                     rpp_result *res) {
     const double t0 = now_ms();
@@ -580,10 +637,14 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
         }
 
         if (dim1) {
-            const Tuning tu = ctx->tuning_for(n, 1);
+            auto run = [&](int g, DevState *state) {
+                launch_apparent(D, ld, n, 1, d_binom, hi1, lo1, cols, state, status, pivot,
+                                pdiam, g, ctx->sms, s);
+            };
+            int group;
+            RPP_TRY(apparent_shape(ctx, ws, 1, n, st, run, s, &group));
             T.begin(ST_APPARENT);
-            launch_apparent(D, ld, n, 1, d_binom, hi1, lo1, cols, st, status, pivot, pdiam,
-                            tu.group, ctx->sms, s);
+            run(group, st);
             T.end();
             T.begin(ST_PARTITION);
             launch_partition(status, hi1, lo1, pivot, pdiam, cols, app_tau, app_sigma, left, st, s);
@@ -669,10 +730,14 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
             }
             RPP_CK(cudaMemsetAsync(status, 0, N, s));
             RPP_CK(cudaMemsetAsync(&st->napp, 0, 2 * sizeof(unsigned long long), s));
-            const Tuning tu = ctx->tuning_for(n, p);
+            auto run = [&](int g, DevState *state) {
+                launch_apparent(D, ld, n, p, d_binom, key_hi, key_lo, N, state, status, pivot,
+                                pdiam, g, ctx->sms, s);
+            };
+            int group;
+            RPP_TRY(apparent_shape(ctx, ws, p, n, st, run, s, &group));
             T.begin(ST_APPARENT);
-            launch_apparent(D, ld, n, p, d_binom, key_hi, key_lo, N, st, status, pivot, pdiam,
-                            tu.group, ctx->sms, s);
+            run(group, st);
             T.end();
             T.begin(ST_PARTITION);
             launch_partition(status, key_hi, key_lo, pivot, pdiam, N, app_tau, app_sigma, left,

@@ -68,7 +68,7 @@ struct Workspace {
     int device = 0;
     size_t budget = 0;        // 0 = unbounded
     size_t device_bytes = 0;  // currently held
-    DevBuf X, Dsrc, D, state, binom, key_hi, key_lo, tmp_hi, tmp_lo, tmp_val, tiles, hist,
+    DevBuf X, Dsrc, D, state, state_tune, binom, key_hi, key_lo, tmp_hi, tmp_lo, tmp_val, tiles, hist,
         status, pivot, pdiam, app_tau, app_sigma, left, bitmap, mst, up, nbr, h0;
     HostBuf h_hi, h_lo, h_tau, h_sigma, h_left, h_D, h_state, h_mst, h_up, h_nbr, h_ehi, h_eab;
     Binomial binom_host;      // cached table
@@ -147,6 +147,8 @@ struct rpp_context {
     bool autotune = true;
     std::mutex tune_mu;
     std::map<int, rpp::BatchConfig> batch_tuning;  // bucket nmax -> chosen shape
+    // the single-instance apparent pass: (p, size bucket) -> launch shape
+    std::map<std::pair<int, int64_t>, int> apparent_tuning;
 };
 
 namespace rpp {

@@ -199,3 +199,21 @@ def test_critical_edges_realise_endpoints(rpp):
                 assert D[bu, bv] == b
             if math.isfinite(d):
                 assert D[du, dv] == d
+
+
+def test_apparent_shape_tuning_changes_nothing(rpp):
+    """The apparent pass's launch shape, tuned per size bucket on the first
+    instance or left at its default, gives the same barcodes, realising edges
+    and counters (the tuning launches count into a scratch state)."""
+    tuned, fixed = rpp.Context(0), rpp.Context(0)
+    fixed.set_batch(fused=True, autotune=False)
+    for X, md in ((I.noisy_torus(400, seed=3), 1), (I.sphere_s3(60, seed=2), 2)):
+        a = rpp.rpp_barcodes(_cuda(X), max_dim=md, context=tuned)
+        b = rpp.rpp_barcodes(_cuda(X), max_dim=md, context=fixed)
+        c = rpp.rpp_barcodes(_cuda(X), max_dim=md, context=tuned)  # the tuned shape
+        for q in range(md + 1):
+            assert np.array_equal(a.intervals[q], b.intervals[q])
+            assert np.array_equal(a.critical[q], b.critical[q])
+            assert np.array_equal(c.intervals[q], b.intervals[q])
+        for k in ("columns", "apparent", "leftover", "scanned", "additions"):
+            assert a.stats[k] == b.stats[k] == c.stats[k], k
