@@ -48,6 +48,10 @@ def parse_args():
     ap.add_argument("--serving-slots", type=int, default=8)
     ap.add_argument("--no-census", action="store_true",
                     help="skip the apparent-pair census of random edge orders")
+    ap.add_argument("--profile-batched", action="store_true",
+                    help="profiling aid: one batched call over the serving mix's clouds of "
+                         "257-512 points inside an NVTX range 'batched' (after an untimed "
+                         "call), then exit")
     ap.add_argument("--no-extras", action="store_true",
                     help="only the torus steps: no serving, census, differentiation or S^3 section")
     return ap.parse_args()
@@ -511,6 +515,21 @@ def main():
     from paper_2003_07989_gb300 import inputs as I
 
     torch.cuda.set_device(local)
+    if args.profile_batched:
+        reqs = [r for r in I.serving_requests(4096, seed=0) if r.points.shape[0] > 256]
+        clouds = [r.points for r in reqs]
+        qs = [r.threshold_quantile for r in reqs]
+        rpp.rpp_barcodes_batched(clouds, max_dim=1, quantiles=qs)  # autotuning, allocations
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("batched")
+        t0 = time.perf_counter()
+        out = rpp.rpp_barcodes_batched(clouds, max_dim=1, quantiles=qs)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        torch.cuda.nvtx.range_pop()
+        print(json.dumps({"profile_batched": len(clouds), "ms": 1e3 * dt,
+                          "h1_intervals": sum(len(b.intervals[1]) for b in out)}))
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist

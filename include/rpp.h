@@ -233,8 +233,10 @@ rpp_status rpp_barcodes_batched(rpp_context *ctx, int32_t batch, const float *co
 rpp_status rpp_context_set_batch(rpp_context *ctx, int32_t fused, int32_t autotune);
 
 /* The launch shape the autotuner chose for the bucket of clouds with up to
- * nmax points (64, 128, 256, 512 or 1024): threads per block and lanes per
- * column of the apparent-pair test; both 0 if the bucket has not run yet.
+ * nmax points (64, 128, 256, 512 or 1024): threads per block and the
+ * apparent-pair test's shape, G lanes per column testing one block of G
+ * candidates a step (group = G) or U blocks (group = 10 G + U); both 0 if the
+ * bucket has not run yet.
  * Errors: RPP_E_INVALID for a NULL argument. */
 rpp_status rpp_context_batch_tuning(rpp_context *ctx, int32_t nmax, int32_t *threads,
                                     int32_t *group);

@@ -220,8 +220,10 @@ Status fused_graph(Workspace &ws, const BatchPlan &plan, const Caps &c, const Bu
 // inputs are already on the device) and keep the fastest for the bucket.
 Status autotune(rpp_context *ctx, const Bufs &b, const Caps &caps, int nmax, int dimcap,
                 int nclouds, cudaStream_t s, BatchConfig *best) {
-    static const BatchConfig cands[] = {{128, 4}, {128, 8}, {256, 4}, {256, 8},
-                                        {256, 16}, {512, 8}, {512, 16}};
+    // (threads, group): group = lanes per column G, or 10 G + U for U
+    // candidate blocks a step
+    static const BatchConfig cands[] = {{128, 4}, {128, 8}, {256, 4}, {256, 8}, {256, 16},
+                                        {512, 8}, {512, 16}, {256, 42}, {256, 44}, {512, 42}};
     cudaEvent_t e0, e1;
     RPP_CK(cudaEventCreate(&e0));
     RPP_CK(cudaEventCreate(&e1));

@@ -90,7 +90,7 @@ __host__ __device__ inline size_t batch_smem_bytes(int nmax, int points_floats) 
     return b;
 }
 
-template <int G>
+template <int G, int U>
 __global__ void __launch_bounds__(512) k_batch_h1(
     const float *__restrict__ pts, const BatchCloud *__restrict__ clouds,
     const int32_t *__restrict__ order, BatchCtl *ctl, int nmax, int points_floats,
@@ -349,34 +349,56 @@ __global__ void __launch_bounds__(512) k_batch_h1(
                 }
                 if (!__any_sync(FULL_MASK, have)) break;
 
-                bool ok = false;
-                float du = 0.0f, dw = 0.0f;
-                const int x = scan - gl;
-                if (have && x >= 0 && x != u && x != w) {
-                    du = D[u * ld + x];
-                    dw = D[w * ld + x];
-                    const float mx = fmaxf(du, dw);
-                    ok = mx <= diam;
-                    const float cd = fmaxf(mx, diam);
-                    if (cd <= t && cd < best_d) {
-                        best_d = cd;
-                        best_v = x;
+                // U blocks of G candidates per step: lane gl tests scan - gl - j G,
+                // every block's loads in flight before any test
+                bool ok[U];
+                float du[U], dw[U];
+#pragma unroll
+                for (int j = 0; j < U; ++j) {
+                    ok[j] = false;
+                    du[j] = dw[j] = 0.0f;
+                    const int x = scan - gl - j * G;
+                    if (have && x >= 0 && x != u && x != w) {
+                        du[j] = D[u * ld + x];
+                        dw[j] = D[w * ld + x];
+                        const float mx = fmaxf(du[j], dw[j]);
+                        ok[j] = mx <= diam;
+                        const float cd = fmaxf(mx, diam);
+                        if (cd <= t && cd < best_d) {
+                            best_d = cd;
+                            best_v = x;
+                        }
                     }
                 }
-                const unsigned ball = __ballot_sync(FULL_MASK, ok);
+                unsigned gbs[U];
+#pragma unroll
+                for (int j = 0; j < U; ++j) gbs[j] = (__ballot_sync(FULL_MASK, ok[j]) & gmask) >> (grp * G);
                 bool emit = false;  // this lane writes a leftover column
                 Leftover L;
                 if (have) {
-                    const unsigned gb = (ball & gmask) >> (grp * G);
-                    if (gb) {
-                        const int first = __ffs(gb) - 1;  // lowest lane: largest vertex
+                    int first = -1, fj = 0;  // the largest qualifying vertex
+#pragma unroll
+                    for (int j = U - 1; j >= 0; --j)
+                        if (gbs[j]) {
+                            first = __ffs(gbs[j]) - 1;
+                            fj = j;
+                        }
+                    if (first >= 0) {
                         if (gl == first) {
+                            const int x = scan - gl - fj * G;
+                            float dux = du[0], dwx = dw[0];
+#pragma unroll
+                            for (int j = 1; j < U; ++j)
+                                if (fj == j) {
+                                    dux = du[j];
+                                    dwx = dw[j];
+                                }
                             // candidates a sequential scan examines up to x
                             scanned += (unsigned long long)(n - x - (u > x) - (w > x));
                             // facets of tau = {u, w, x} before sigma drop a vertex above x
                             bool apparent = true;
-                            if (u > x && dw == diam) apparent = false;  // facet {w, x}
-                            if (w > x && du == diam) apparent = false;  // facet {u, x}
+                            if (u > x && dwx == diam) apparent = false;  // facet {w, x}
+                            if (w > x && dux == diam) apparent = false;  // facet {u, x}
                             aw[e] = apparent ? (uint16_t)x : (uint16_t)0xFFFFu;
                             if (apparent) {
                                 ++napp;
@@ -390,7 +412,7 @@ __global__ void __launch_bounds__(512) k_batch_h1(
                         }
                         have = false;
                         e += ngroups;
-                    } else if (scan - G < 0) {
+                    } else if (scan - U * G < 0) {
                         // no cofacet of equal diameter: the oldest cofacet inside t
 #pragma unroll
                         for (int o = G / 2; o > 0; o >>= 1) {
@@ -418,7 +440,7 @@ __global__ void __launch_bounds__(512) k_batch_h1(
                         have = false;
                         e += ngroups;
                     } else {
-                        scan -= G;
+                        scan -= U * G;
                     }
                 }
                 if (emit) {
@@ -522,26 +544,26 @@ __global__ void k_gather_points(const float *const *__restrict__ src,
     for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) pts[C.pt_off + i] = s[i];
 }
 
-template <int G>
+template <int G, int U>
 BatchPlan plan_g(int nmax, int dimcap, BatchConfig cfg, int sms) {
     BatchPlan P;
     P.nmax = nmax;
     P.dimcap = dimcap;
     P.cfg = cfg;
     P.smem = batch_smem_bytes(nmax, nmax * dimcap);
-    allow_dynamic_smem((const void *)k_batch_h1<G>, P.smem);
+    allow_dynamic_smem((const void *)k_batch_h1<G, U>, P.smem);
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_h1<G>, cfg.threads, P.smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_h1<G, U>, cfg.threads, P.smem);
     P.blocks = std::max(1, sms * std::max(1, per_sm));
     return P;
 }
 
-template <int G>
+template <int G, int U>
 void launch_g(const BatchPlan &P, const float *pts, const BatchCloud *clouds, const int32_t *order,
               BatchCtl *ctl, float *Dbuf, uint64_t *mst_out, BatchOut *outs, Leftover *left,
               int32_t *left_cloud, uint64_t left_cap, uint16_t *app_w, cudaStream_t s) {
     ++g_launches;
-    k_batch_h1<G><<<P.blocks, P.cfg.threads, P.smem, s>>>(pts, clouds, order, ctl, P.nmax,
+    k_batch_h1<G, U><<<P.blocks, P.cfg.threads, P.smem, s>>>(pts, clouds, order, ctl, P.nmax,
                                                           P.nmax * P.dimcap, Dbuf, mst_out, outs,
                                                           left, left_cloud, left_cap, app_w);
 }
@@ -549,11 +571,14 @@ void launch_g(const BatchPlan &P, const float *pts, const BatchCloud *clouds, co
 }  // namespace
 
 BatchPlan plan_batch_h1(int nmax, int dimcap, BatchConfig cfg, int sms) {
-    switch (cfg.group) {
-        case 4: return plan_g<4>(nmax, dimcap, cfg, sms);
-        case 16: return plan_g<16>(nmax, dimcap, cfg, sms);
-        case 32: return plan_g<32>(nmax, dimcap, cfg, sms);
-        default: cfg.group = 8; return plan_g<8>(nmax, dimcap, cfg, sms);
+    switch (cfg.group) {  // G lanes, or 10 G + U for U candidate blocks a step
+        case 4: return plan_g<4, 1>(nmax, dimcap, cfg, sms);
+        case 16: return plan_g<16, 1>(nmax, dimcap, cfg, sms);
+        case 32: return plan_g<32, 1>(nmax, dimcap, cfg, sms);
+        case 42: return plan_g<4, 2>(nmax, dimcap, cfg, sms);
+        case 44: return plan_g<4, 4>(nmax, dimcap, cfg, sms);
+        case 82: return plan_g<8, 2>(nmax, dimcap, cfg, sms);
+        default: cfg.group = 8; return plan_g<8, 1>(nmax, dimcap, cfg, sms);
     }
 }
 
@@ -562,10 +587,13 @@ void launch_batch_h1(const BatchPlan &P, const float *pts, const BatchCloud *clo
                      BatchOut *outs, Leftover *left, int32_t *left_cloud, uint64_t left_cap,
                      uint16_t *app_w, cudaStream_t s) {
     switch (P.cfg.group) {
-        case 4: launch_g<4>(P, pts, clouds, order, ctl, Dbuf, mst_out, outs, left, left_cloud, left_cap, app_w, s); break;
-        case 16: launch_g<16>(P, pts, clouds, order, ctl, Dbuf, mst_out, outs, left, left_cloud, left_cap, app_w, s); break;
-        case 32: launch_g<32>(P, pts, clouds, order, ctl, Dbuf, mst_out, outs, left, left_cloud, left_cap, app_w, s); break;
-        default: launch_g<8>(P, pts, clouds, order, ctl, Dbuf, mst_out, outs, left, left_cloud, left_cap, app_w, s);
+        case 4: launch_g<4, 1>(P, pts, clouds, order, ctl, Dbuf, mst_out, outs, left, left_cloud, left_cap, app_w, s); break;
+        case 16: launch_g<16, 1>(P, pts, clouds, order, ctl, Dbuf, mst_out, outs, left, left_cloud, left_cap, app_w, s); break;
+        case 32: launch_g<32, 1>(P, pts, clouds, order, ctl, Dbuf, mst_out, outs, left, left_cloud, left_cap, app_w, s); break;
+        case 42: launch_g<4, 2>(P, pts, clouds, order, ctl, Dbuf, mst_out, outs, left, left_cloud, left_cap, app_w, s); break;
+        case 44: launch_g<4, 4>(P, pts, clouds, order, ctl, Dbuf, mst_out, outs, left, left_cloud, left_cap, app_w, s); break;
+        case 82: launch_g<8, 2>(P, pts, clouds, order, ctl, Dbuf, mst_out, outs, left, left_cloud, left_cap, app_w, s); break;
+        default: launch_g<8, 1>(P, pts, clouds, order, ctl, Dbuf, mst_out, outs, left, left_cloud, left_cap, app_w, s);
     }
 }
 

@@ -173,7 +173,7 @@ struct BatchOut {
 // `left_cloud`) while fewer than left_cap; ctl->left_count counts them all.
 // `group` is the lane-group width of the test.
 struct BatchConfig {
-    int threads = 256, group = 8;
+    int threads = 256, group = 8;  // group: G lanes per column, or 10 G + U for U blocks a step
 };
 // Control block of one fused launch (device memory).
 struct BatchCtl {
