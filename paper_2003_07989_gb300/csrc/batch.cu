@@ -243,13 +243,23 @@ __global__ void __launch_bounds__(512) k_batch_h1(
             for (int u = warp; u < n; u += nwarps) {
                 const int cu = S.comp[u];
                 uint64_t bk = ~0ull;
-                for (int w = lane; w < n; w += 32) {
-                    if (w == u || S.comp[w] == cu) continue;
-                    const float d = D[u * ld + w];
-                    if (d > t) continue;
-                    const uint32_t e = (uint32_t)(u > w ? edge_cidx(u, w) : edge_cidx(w, u));
-                    const uint64_t key = ((uint64_t)__float_as_uint(d) << 32) | (uint64_t)(~e);
-                    bk = key < bk ? key : bk;
+                for (int w0 = lane; w0 < n; w0 += 4 * 32) {
+                    // four entries a lane, their loads issued before any test
+                    float d[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int w = w0 + 32 * i;
+                        d[i] = w < n ? D[u * ld + w] : 0.0f;
+                    }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int w = w0 + 32 * i;
+                        if (w >= n || w == u || S.comp[w] == cu || d[i] > t) continue;
+                        const uint32_t e = (uint32_t)(u > w ? edge_cidx(u, w) : edge_cidx(w, u));
+                        const uint64_t key =
+                            ((uint64_t)__float_as_uint(d[i]) << 32) | (uint64_t)(~e);
+                        bk = key < bk ? key : bk;
+                    }
                 }
                 bk = warp_min_u64(bk);
                 if (lane == 0 && bk != ~0ull) atomicMin((unsigned long long *)&S.best[cu], bk);
