@@ -75,7 +75,16 @@ struct BatchSmem {
     uint32_t *mst;    // [p2] MST edge indices, sorted
     uint32_t *hist;   // [256]
     float *X;         // staged points (or null)
+    uint32_t *cleared;  // [C(nmax,2) / 32] forest edges as bits (null above CLEARED_BITS_NMAX)
 };
+
+// Buckets up to this many points keep the forest's edges as a bitmap in
+// shared memory (16 KB at 512 points); larger ones search the sorted list.
+constexpr int CLEARED_BITS_NMAX = 512;
+
+__host__ __device__ inline size_t cleared_words(int nmax) {
+    return nmax <= CLEARED_BITS_NMAX ? ((size_t)nmax * (nmax - 1) / 2 + 31) / 32 : 0;
+}
 
 __host__ __device__ inline int pow2_at_least(int x) {
     int p = 1;
@@ -87,7 +96,7 @@ __host__ __device__ inline size_t batch_smem_bytes(int nmax, int points_floats) 
     const int p2 = pow2_at_least(nmax);
     size_t b = (size_t)nmax * 8 + 3 * (size_t)nmax * 4 + (size_t)p2 * 4 + 256 * 4;
     if (points_floats <= SMEM_POINTS) b += (size_t)points_floats * 4;
-    return b;
+    return b + cleared_words(nmax) * 4;
 }
 
 template <int G, int U>
@@ -118,6 +127,8 @@ __global__ void __launch_bounds__(512) k_batch_h1(
         S.hist = (uint32_t *)p;
         p += 256 * 4;
         S.X = points_floats <= SMEM_POINTS ? (float *)p : nullptr;
+        if (S.X) p += (size_t)points_floats * 4;
+        S.cleared = cleared_words(nmax) ? (uint32_t *)p : nullptr;
     }
     __shared__ int s_cloud;
     __shared__ unsigned int s_rbits, s_err, s_nm, s_changed, s_digit, s_rank;
@@ -320,6 +331,13 @@ __global__ void __launch_bounds__(512) k_batch_h1(
                 }
                 __syncthreads();
             }
+        if (S.cleared) {  // the forest's edges as bits: one lookup per column
+            for (uint32_t i = threadIdx.x; i < (m + 31) / 32; i += blockDim.x) S.cleared[i] = 0u;
+            __syncthreads();
+            for (int i = threadIdx.x; i < nm; i += blockDim.x)
+                atomicOr(&S.cleared[S.mst[i] >> 5], 1u << (S.mst[i] & 31));
+            __syncthreads();
+        }
 
         // ---- 4. apparent-pair test of the other edges inside t ----
         if (s_err == 0 && C.max_dim >= 1) {
@@ -337,13 +355,19 @@ __global__ void __launch_bounds__(512) k_batch_h1(
                     edge_decode(e, &u, &w);
                     diam = D[u * ld + w];
                     if (diam <= t) {
-                        int lo = 0, hi = nm;  // cleared (MST) column?
-                        while (lo < hi) {
-                            const int mid = (lo + hi) >> 1;
-                            if (S.mst[mid] < e) lo = mid + 1;
-                            else hi = mid;
+                        bool cleared;  // a forest (cleared) column?
+                        if (S.cleared) {
+                            cleared = (S.cleared[e >> 5] >> (e & 31)) & 1u;
+                        } else {
+                            int lo = 0, hi = nm;
+                            while (lo < hi) {
+                                const int mid = (lo + hi) >> 1;
+                                if (S.mst[mid] < e) lo = mid + 1;
+                                else hi = mid;
+                            }
+                            cleared = lo < nm && S.mst[lo] == e;
                         }
-                        if (lo < nm && S.mst[lo] == e) {
+                        if (cleared) {
                             if (gl == 0) aw[e] = 0xFFFFu;
                             e += ngroups;
                             continue;
