@@ -32,6 +32,7 @@ namespace rpp {
 namespace {
 
 constexpr int SMEM_POINTS = 8192;  // points staged in shared memory up to this many floats
+constexpr uint32_t EDGE_CHUNK = 32;  // consecutive edges a lane group takes in the apparent test
 
 __device__ __forceinline__ uint64_t edge_cidx(int a, int b) {  // a > b
     return (uint64_t)a * (uint64_t)(a - 1) / 2 + (uint64_t)b;
@@ -344,15 +345,29 @@ __global__ void __launch_bounds__(512) k_batch_h1(
             const int gl = lane % G, grp = lane / G;
             const unsigned gmask = (G == 32) ? FULL_MASK : (((1u << G) - 1u) << (grp * G));
             const uint32_t ngroups = blockDim.x / G;
-            uint32_t e = threadIdx.x / G;
+            // a group's edges: chunks of EDGE_CHUNK consecutive indices (chunk
+            // g, g + ngroups, ...), walked with (u, w) updated in place, so
+            // an edge is decoded once per chunk and its row is read in order
+            uint32_t e = (threadIdx.x / G) * EDGE_CHUNK;
+            int u = 0, w = 0;
+            if (e < m) edge_decode(e, &u, &w);
+            auto advance = [&]() {
+                ++e;
+                if ((e & (EDGE_CHUNK - 1)) == 0) {
+                    e += (ngroups - 1) * EDGE_CHUNK;
+                    if (e < m) edge_decode(e, &u, &w);
+                } else if (++w == u) {
+                    ++u;
+                    w = 0;
+                }
+            };
             unsigned long long napp = 0, nleft = 0, scanned = 0;
             bool have = false;
-            int u = 0, w = 0, scan = 0, best_v = -1;
+            int scan = 0, best_v = -1;
             float diam = 0.0f, best_d = 0.0f;
             uint16_t *aw = app_w + C.aw_off;
             for (;;) {
                 while (!have && e < m) {
-                    edge_decode(e, &u, &w);
                     diam = D[u * ld + w];
                     if (diam <= t) {
                         bool cleared;  // a forest (cleared) column?
@@ -369,7 +384,7 @@ __global__ void __launch_bounds__(512) k_batch_h1(
                         }
                         if (cleared) {
                             if (gl == 0) aw[e] = 0xFFFFu;
-                            e += ngroups;
+                            advance();
                             continue;
                         }
                         have = true;
@@ -378,7 +393,7 @@ __global__ void __launch_bounds__(512) k_batch_h1(
                         best_v = -1;
                     } else {
                         if (gl == 0) aw[e] = 0xFFFFu;
-                        e += ngroups;
+                        advance();
                     }
                 }
                 if (!__any_sync(FULL_MASK, have)) break;
@@ -438,6 +453,7 @@ __global__ void __launch_bounds__(512) k_batch_h1(
                                 ++napp;
                             } else {
                                 emit = true;
+                                L.sigma = edge_cidx(u, w);
                                 const int a = max(u, x), c = min(w, x);
                                 const int b = u + w + x - a - c;
                                 L.pivot = tri_cidx(a, b, c);
@@ -445,7 +461,7 @@ __global__ void __launch_bounds__(512) k_batch_h1(
                             }
                         }
                         have = false;
-                        e += ngroups;
+                        advance();
                     } else if (scan - U * G < 0) {
                         // no cofacet of equal diameter: the oldest cofacet inside t
 #pragma unroll
@@ -460,6 +476,7 @@ __global__ void __launch_bounds__(512) k_batch_h1(
                         if (gl == 0) {
                             scanned += (unsigned long long)(n - 2);
                             emit = true;
+                            L.sigma = edge_cidx(u, w);
                             aw[e] = 0xFFFFu;
                             if (best_v >= 0) {
                                 const int x2 = best_v;
@@ -472,13 +489,12 @@ __global__ void __launch_bounds__(512) k_batch_h1(
                             L.pdiam = best_d;
                         }
                         have = false;
-                        e += ngroups;
+                        advance();
                     } else {
                         scan -= U * G;
                     }
                 }
-                if (emit) {
-                    L.sigma = edge_cidx(u, w);
+                if (emit) {  // L.sigma was set before the group moved on
                     L.diam = diam;
                     L.index = ((uint64_t)(~__float_as_uint(diam)) << 32) | (uint64_t)L.sigma;
                 }
