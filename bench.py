@@ -12,8 +12,10 @@ threshold that clearing kept) per second of whole-step time.
 
 Under torchrun each rank computes its own cloud (seed = rank); the value is the
 columns of all ranks divided by the slowest rank's time (weak scaling).
-`--impl reference` times the CPU oracle (the plain standard reduction) on a
-bounded sample of the same workload on the host cores.
+`--impl reference` times the CPU oracle in its COHOM_CLEAR mode (Kruskal H0,
+then Alg. 1 on the coboundary matrix with the clearing lemma; no apparent
+pairs) on a bounded sample of the same workload on the host cores: the first
+500 of the torus's points per step, which its config states.
 """
 from __future__ import annotations
 
@@ -159,7 +161,9 @@ def traffic_for(stage):
 
 
 def algorithmic_bytes(stage, st):
-    """Bytes a stage must move per launch by its definition."""
+    """Bytes a stage must move per launch by its definition: the per-unit
+    figures (distance reads per examined candidate, key and output bytes per
+    column, key bytes per sort pass) times the units of one launch."""
     p = 1
     cols = st["columns"][p] + st["cleared"][p]
     if stage == "apparent":
@@ -430,9 +434,10 @@ def census_bench(rpp, torch, dev, ctx):
 
 
 def oracle_rate(n_sample: int, seed: int):
-    """The oracle (plain standard reduction, Kruskal H0 + coboundary reduction
-    with clearing) on the first n_sample points of the same torus cloud:
-    dimension-1 columns processed per second, and the threads it used."""
+    """The oracle in its COHOM_CLEAR mode (Kruskal H0, then the standard
+    reduction of the coboundary matrix with the clearing lemma) on the first
+    n_sample points of the same torus cloud: dimension-1 columns processed per
+    second, and the threads it used."""
     from oracle import oracle as O
     from paper_2003_07989_gb300 import inputs as I
     X = I.noisy_torus(N_POINTS, seed=seed)[:n_sample]
@@ -485,7 +490,9 @@ def run_reference(args, rank, world):
         "unit": "simplices/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000.0 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": bench_config(world),
+        "config": dict(bench_config(world), sample_points=n_sample,
+                       sample=f"each step computes the first {n_sample} of the {N_POINTS} "
+                              f"torus points"),
         "cpu_baseline": {"value": value, "unit": "simplices/s", "cores": cores, "kind": "oracle",
                          "sample": f"first {n_sample} of the 2000 torus points per step"},
         "e2e": {"value": value, "unit": "simplices/s", "h2d_bytes_per_step": 0,

@@ -291,12 +291,15 @@ rpp_status rpp_distance_matrix(rpp_context *ctx, const float *points, int64_t n,
  *   count_out  host, receives the number of edges written.
  * It allocates nothing: its scratch is one static device array of about
  * 3.3 MB (up to 262,144 edges) that every GPU loading the library holds until
- * the process exits. The first call on a device looks up that array's device
- * address; make that first call before any stream capture. All calls share the
+ * the process exits. The first call on a device may be the one that loads the
+ * library's device code there, and so the one that places that array on the
+ * device; make that first call before any stream capture. Every call looks up
+ * the array's device address for the current device. All calls share the
  * array, so calls that overlap on the GPU (other streams, other threads) race
  * and must be serialised by the caller. Returns RPP_E_INVALID for n above the
- * bound, a short capacity, or D not in device memory; RPP_E_CUDA if a CUDA
- * call fails. Waits for its stream before returning. */
+ * bound, a short capacity, D or an output not in memory of the current
+ * device, or a stream of another device; RPP_E_CUDA if a CUDA call fails.
+ * Waits for its stream before returning. */
 rpp_status rpp_filtration_edges_noalloc(const float *D, int64_t n, float threshold,
                                         float *diam_out, uint64_t *cidx_out, int64_t capacity,
                                         int64_t *count_out, void *stream);

@@ -1,7 +1,8 @@
 """torch.autograd.Function over rpp_barcodes_batched / rpp_barcodes_backward.
 
 Forward computes the barcodes of a batch of clouds on the GPU; the interval
-endpoints come back as CUDA tensors. Backward calls the library's backward
+endpoints come back as CUDA tensors (gathered from every result at once and
+copied to the device in one pinned transfer per dtype). Backward calls the library's backward
 kernel, which sends each endpoint's gradient to the two points of the edge
 that realises it (an endpoint is the length of that edge).
 """
@@ -44,29 +45,31 @@ def _forward_handles(points: torch.Tensor, max_dim: int, thresholds=None, contex
     return ctx, [outs[i] for i in range(B)]
 
 
-def _flatten(handles):
-    """births, deaths, cloud index, dimension of every interval, in
-    (cloud, dimension, interval) order."""
+def _flatten(handles, max_dim: int):
+    """births, deaths (float32 [2, m]) and cloud index, dimension (int64
+    [2, m]) of every interval, in (cloud, dimension, interval) order, gathered
+    from all results with one rpp_results_gather call per dimension."""
     L = N.lib()
-    births, deaths, cloud, dims = [], [], [], []
-    for i, h in enumerate(handles):
-        st = N.Stats()
-        N.check(L.rpp_result_stats(h, C.byref(st)), "rpp_result_stats")
-        for q in range(st.max_dim + 1):
-            k = L.rpp_result_count(h, q)
-            if k <= 0:
-                continue
-            iv = np.ctypeslib.as_array(C.cast(L.rpp_result_intervals(h, q), C.POINTER(C.c_float)),
-                                       shape=(2 * k,)).reshape(k, 2)
-            births.append(iv[:, 0].copy())
-            deaths.append(iv[:, 1].copy())
-            cloud.append(np.full(k, i, np.int64))
-            dims.append(np.full(k, q, np.int64))
-    if not births:
-        z = np.zeros(0, np.float32)
-        return z, z, np.zeros(0, np.int64), np.zeros(0, np.int64)
-    return (np.concatenate(births), np.concatenate(deaths), np.concatenate(cloud),
-            np.concatenate(dims))
+    B = len(handles)
+    arr = (C.c_void_p * B)(*handles)
+    ivs, clouds, dims = [], [], []
+    for q in range(max_dim + 1):
+        offs = np.zeros(B + 1, np.int64)
+        N.check(L.rpp_results_gather(arr, B, q, offs.ctypes.data, None, None),
+                "rpp_results_gather")
+        iv = np.empty((int(offs[-1]), 2), np.float32)
+        if len(iv):
+            N.check(L.rpp_results_gather(arr, B, q, offs.ctypes.data, iv.ctypes.data, None),
+                    "rpp_results_gather")
+        ivs.append(iv)
+        clouds.append(np.repeat(np.arange(B, dtype=np.int64), np.diff(offs)))
+        dims.append(np.full(len(iv), q, np.int64))
+    iv = np.concatenate(ivs)
+    cloud = np.concatenate(clouds)
+    dim = np.concatenate(dims)
+    order = np.argsort(cloud, kind="stable")  # dimension-major -> cloud-major
+    return (np.ascontiguousarray(iv[order].T),
+            np.ascontiguousarray(np.stack([cloud[order], dim[order]])))
 
 
 class RipsPersistence(torch.autograd.Function):
@@ -75,17 +78,20 @@ class RipsPersistence(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, points, max_dim: int):
+        # The intervals are formed on the host (the submatrix reduction runs
+        # there), so they reach the device once: two pinned buffers, copied
+        # without blocking on the points' stream.
         lctx, handles = _forward_handles(points, max_dim)
         keep = _Handles(handles)
-        b, d, cl, dm = _flatten(handles)
+        bd, cd = _flatten(handles, max_dim)
         dev = points.device
         ctx.keep = keep
         ctx.lctx = lctx
         ctx.save_for_backward(points)
-        births = torch.from_numpy(b).to(dev)
-        deaths = torch.from_numpy(d).to(dev)
-        cloud = torch.from_numpy(cl).to(dev)
-        dims = torch.from_numpy(dm).to(dev)
+        f = torch.from_numpy(bd).pin_memory().to(dev, non_blocking=True)
+        i = torch.from_numpy(cd).pin_memory().to(dev, non_blocking=True)
+        births, deaths = f[0], f[1]
+        cloud, dims = i[0], i[1]
         ctx.mark_non_differentiable(cloud, dims)
         return births, deaths, cloud, dims
 

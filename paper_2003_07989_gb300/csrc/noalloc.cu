@@ -10,7 +10,6 @@
 // declared below. Every GPU that loads the library holds that array until the
 // process exits.
 #include <cmath>
-#include <mutex>
 #include <string>
 
 #include "../../include/rpp.h"
@@ -33,11 +32,10 @@ constexpr size_t SCRATCH_BYTES = up256(OFF_TMP_LO + NA_MAX_EDGES * sizeof(uint64
 
 // The scratch of rpp_filtration_edges_noalloc (about 3.3 MB per GPU). In host
 // code this name is only a stand-in: its device address comes from
-// cudaGetSymbolAddress.
+// cudaGetSymbolAddress, looked up on every call with the caller's device
+// current (a cached address would go stale if the device were reset and the
+// module placed elsewhere).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[SCRATCH_BYTES];
-
-std::mutex g_setup_mu;
-void *g_scratch_addr[256] = {};  // per device, filled by the first call on it
 
 // Zero the counters, set the threshold, and write C(v, k) for k = 0, 1, 2.
 __global__ void k_noalloc_init(DevState *st, float t, uint64_t *binom, int64_t n) {
@@ -91,35 +89,48 @@ extern "C" rpp_status rpp_filtration_edges_noalloc(const float *D, int64_t n, fl
         set_last_error("rpp_filtration_edges_noalloc: output capacity below C(n, 2)");
         return RPP_E_INVALID;
     }
-    cudaPointerAttributes attr;
-    if (cudaPointerGetAttributes(&attr, D) != cudaSuccess ||
-        (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)) {
-        cudaGetLastError();
-        set_last_error("rpp_filtration_edges_noalloc: D must be device memory");
-        return RPP_E_INVALID;
-    }
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) {
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
         set_last_error("rpp_filtration_edges_noalloc: no current CUDA device");
         return RPP_E_CUDA;
     }
-    unsigned char *base;
-    {
-        std::lock_guard<std::mutex> g(g_setup_mu);
-        if (!g_scratch_addr[dev]) {
-            void *p = nullptr;
-            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-            if (e != cudaSuccess) {
-                cudaGetLastError();
-                set_last_error(std::string("rpp_filtration_edges_noalloc: cudaGetSymbolAddress: ") +
-                               cudaGetErrorString(e));
-                return RPP_E_CUDA;
-            }
-            g_scratch_addr[dev] = p;
+    // D and both outputs must be memory of the current device (the scratch
+    // address below is the current device's), and so must the stream
+    const void *bufs[3] = {D, diam_out, cidx_out};
+    const char *names[3] = {"D", "diam_out", "cidx_out"};
+    for (int i = 0; i < 3; ++i) {
+        cudaPointerAttributes attr;
+        if (cudaPointerGetAttributes(&attr, bufs[i]) != cudaSuccess ||
+            (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged) ||
+            (attr.type == cudaMemoryTypeDevice && attr.device != dev)) {
+            cudaGetLastError();
+            set_last_error(std::string("rpp_filtration_edges_noalloc: ") + names[i] +
+                           " must be device memory of the current device");
+            return RPP_E_INVALID;
         }
-        base = (unsigned char *)g_scratch_addr[dev];
     }
     cudaStream_t s = (cudaStream_t)stream;
+    if (s) {
+        int sdev = -1;
+        if (cudaStreamGetDevice(s, &sdev) != cudaSuccess || sdev != dev) {
+            cudaGetLastError();
+            set_last_error("rpp_filtration_edges_noalloc: the stream belongs to another device");
+            return RPP_E_INVALID;
+        }
+    }
+    unsigned char *base = nullptr;
+    {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            set_last_error(std::string("rpp_filtration_edges_noalloc: cudaGetSymbolAddress: ") +
+                           cudaGetErrorString(e));
+            return RPP_E_CUDA;
+        }
+        base = (unsigned char *)p;
+    }
     DevState *st = (DevState *)(base + OFF_STATE);
     uint64_t *binom = (uint64_t *)(base + OFF_BINOM);
     uint32_t *hist = (uint32_t *)(base + OFF_HIST);

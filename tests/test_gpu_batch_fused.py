@@ -5,7 +5,8 @@ per size bucket (distances, threshold, spanning forest and apparent-pair test
 in one block per cloud, a captured CUDA graph per bucket, autotuned launch
 shapes). A context with fused=False runs the same clouds one at a time through
 the per-instance pipeline; both must agree bit for bit on intervals, realising
-edges, thresholds and column counts, and a sample must equal the CPU oracle.
+edges, thresholds and column counts. Clouds of every bucket (up to 90 points,
+and 129-256, 257-512 and 513-1024 points) must also equal the CPU oracle.
 """
 import math
 
@@ -119,6 +120,29 @@ def test_matches_oracle(rpp, ctx_fused):
         res = O.barcodes(D, 1, O.distance_quantile(D, r.threshold_quantile))
         for q in (0, 1):
             assert np.array_equal(a.intervals[q], res.barcode(q)), (r.index, q)
+
+
+@pytest.mark.parametrize("lo,hi,nmax", [(129, 256, 256), (257, 512, 512), (513, 1024, 1024)])
+def test_large_buckets_match_oracle(rpp, lo, hi, nmax):
+    """The fused kernel's larger buckets against the oracle itself: the
+    257-512 bucket keeps the spanning forest as a shared-memory bitmap and
+    the 513-1024 bucket finds forest edges by binary search, so each bucket's
+    own code path is compared with the CPU oracle, interval by interval, on
+    serving-mix clouds at the 0.6 quantile (a fresh context, so the bucket's
+    tuning record shows that the fused launch ran)."""
+    reqs = I.serving_requests(4, seed=31 + lo, n_range=(lo, hi))
+    ctx = rpp.Context(0)
+    got = rpp.rpp_barcodes_batched([r.points for r in reqs], max_dim=1,
+                                   quantiles=[r.threshold_quantile for r in reqs], context=ctx)
+    assert ctx.batch_tuning(nmax) != (0, 0)
+    for r, a in zip(reqs, got):
+        assert lo <= r.points.shape[0] <= hi
+        D = O.distance_matrix(r.points)
+        t = O.distance_quantile(D, r.threshold_quantile)
+        assert a.stats["threshold"] == t
+        res = O.barcodes(D, 1, t)
+        for q in (0, 1):
+            assert np.array_equal(a.intervals[q], res.barcode(q)), (r.index, r.kind, q)
 
 
 def test_launches_split_at_bucket_capacity(rpp, ctx_fused, ctx_alone):

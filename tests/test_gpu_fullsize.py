@@ -1,8 +1,11 @@
 """Full-size parity: the 2000-point torus (H0-H1) and 192 points on S^3
 (H0-H2), in the bench's configuration, against barcodes the oracle computed
-offline (tests/golden/make_golden.py, which calls only oracle/). The stored
-float32 points are the input, so the comparison does not depend on how a
-machine's libm rounds the generators.
+offline (tests/golden/make_golden.py, which calls only oracle/), and a
+300-point torus against the oracle's coboundary reduction with no clearing
+and no Kruskal H0 (COHOM), so that a large comparison does not rest only on
+the oracle mode that shares the GPU path's two shortcuts. The stored float32
+points are the input, so the comparison does not depend on how a machine's
+libm rounds the generators.
 
 At full size the apparent-pair set is also checked on a sample of columns
 against the oracle's definition, one column at a time.
@@ -51,7 +54,7 @@ def rpp():
     return m
 
 
-@pytest.mark.parametrize("name", ["torus2000", "sphere192"])
+@pytest.mark.parametrize("name", ["torus2000", "sphere192", "torus300_cohom"])
 def test_fullsize_barcodes_equal_oracle(rpp, name):
     import torch
     g = np.load(os.path.join(GOLDEN, f"{name}.npz"))

@@ -111,32 +111,55 @@ def test_columns_and_apparent_pairs_bit_exact(rpp, rec_ctx, idx):
 # barcodes
 
 
+# Oracle mode per case: the literal form with none of the shortcuts, HOM
+# (Alg. 1 on the explicit boundary matrix, no clearing, no cohomology),
+# wherever it finishes in seconds; COHOM (the coboundary reduction without clearing) for
+# the 150-point 2-sphere; COHOM_CLEAR only for the 200-point torus, whose
+# 300-point sibling is compared with COHOM in test_gpu_fullsize.py.
+HOM, COHOM, CLEAR = O.MODE_HOM, O.MODE_COHOM, O.MODE_COHOM_CLEAR
+
+
 def _barcode_cases():
-    cases = [("cfg1_cube50_seed0", I.uniform_cube(50, 3, 0), "points", 1, math.inf, None)]
+    cases = [("cfg1_cube50_seed0", I.uniform_cube(50, 3, 0), "points", 1, math.inf, None, HOM)]
     for i, (n, dim) in enumerate([(33, 2), (64, 3), (65, 4), (97, 8), (130, 3)]):
-        cases.append((f"blob{n}", I.blob_cloud(n, dim, 10 + i), "points", 1, math.inf, None))
-    cases.append(("torus200", I.noisy_torus(200, seed=7), "points", 1, math.inf, None))
-    cases.append(("sphere60_h2", I.sphere_s3(60, seed=8), "points", 2, math.inf, None))
-    cases.append(("cube40_h3", I.uniform_cube(40, 3, 9), "points", 3, math.inf, None))
-    cases.append(("ties50", I.integer_distances(50, 5, 11), "distances", 2, math.inf, None))
-    cases.append(("ties2_40", I.integer_distances(40, 2, 12), "distances", 1, math.inf, None))
-    cases.append(("circle80_t", I.circle_cloud(80, 1.0, 0.05, 2, 13), "points", 1, 0.4, None))
-    cases.append(("cube70_t0", I.uniform_cube(70, 3, 14), "points", 1, 0.0, None))
-    cases.append(("cube90_q", I.uniform_cube(90, 3, 15), "points", 1, math.inf, 0.6))
-    cases.append(("sphere2_q", I.sphere2_cloud(150, 1.0, 0.05, 5, 16), "points", 2, math.inf, 0.3))
-    cases.append(("blob_q1", I.blob_cloud(60, 2, 17), "points", 1, math.inf, 1.0))
+        cases.append((f"blob{n}", I.blob_cloud(n, dim, 10 + i), "points", 1, math.inf, None, HOM))
+    cases.append(("torus200", I.noisy_torus(200, seed=7), "points", 1, math.inf, None, CLEAR))
+    cases.append(("sphere60_h2", I.sphere_s3(60, seed=8), "points", 2, math.inf, None, HOM))
+    cases.append(("cube40_h3", I.uniform_cube(40, 3, 9), "points", 3, math.inf, None, HOM))
+    cases.append(("ties50", I.integer_distances(50, 5, 11), "distances", 2, math.inf, None, HOM))
+    cases.append(("ties2_40", I.integer_distances(40, 2, 12), "distances", 1, math.inf, None, HOM))
+    cases.append(("circle80_t", I.circle_cloud(80, 1.0, 0.05, 2, 13), "points", 1, 0.4, None, HOM))
+    cases.append(("cube70_t0", I.uniform_cube(70, 3, 14), "points", 1, 0.0, None, HOM))
+    cases.append(("cube90_q", I.uniform_cube(90, 3, 15), "points", 1, math.inf, 0.6, HOM))
+    cases.append(("sphere2_q", I.sphere2_cloud(150, 1.0, 0.05, 5, 16), "points", 2, math.inf, 0.3,
+                  COHOM))
+    cases.append(("blob_q1", I.blob_cloud(60, 2, 17), "points", 1, math.inf, 1.0, HOM))
     return cases
 
 
 @pytest.mark.parametrize("idx", range(16))
 def test_barcodes_bit_exact(rpp, idx):
-    name, X, kind, max_dim, t, q = _barcode_cases()[idx]
+    name, X, kind, max_dim, t, q, mode = _barcode_cases()[idx]
     D = O.distance_matrix(X) if kind == "points" else X
     t_ref = O.distance_quantile(D, q) if q is not None else t
-    ref = O.barcodes(D, max_dim, t_ref, O.MODE_COHOM_CLEAR)
+    ref = O.barcodes(D, max_dim, t_ref, mode)
     for data in (X, _cuda(X)):
         got = rpp.rpp_barcodes(data, max_dim=max_dim, threshold=t, kind=kind, quantile=q)
         _check_barcodes(got, ref, max_dim, name)
+
+
+def test_cfg4_clouds_against_the_boundary_matrix_oracle(rpp):
+    """Four clouds of the differentiation workload (128 points on noisy
+    planar circles, full filtration, H0-H1) against Alg. 1 on the explicit
+    boundary matrix of all 341,376 triangles, with no clearing, no
+    cohomology and no apparent pairs: through the single-instance path and
+    through the fused batched launch of the 128-point bucket."""
+    clouds = I.noisy_circles(4, 128, seed=0)
+    batched = rpp.rpp_barcodes_batched([c for c in clouds], max_dim=1)
+    for i, X in enumerate(clouds):
+        ref = O.barcodes(O.distance_matrix(X), 1, math.inf, O.MODE_HOM)
+        _check_barcodes(rpp.rpp_barcodes(_cuda(X), max_dim=1), ref, 1, f"cloud{i}")
+        _check_barcodes(batched[i], ref, 1, f"batched cloud{i}")
 
 
 def test_degenerate_sizes(rpp):
@@ -148,12 +171,12 @@ def test_degenerate_sizes(rpp):
     # duplicate points: zero distances, zero-length H0 bars dropped
     X = np.repeat(I.uniform_cube(20, 3, 30), 2, axis=0)
     got = rpp.rpp_barcodes(X, max_dim=1)
-    _check_barcodes(got, O.barcodes(O.distance_matrix(X), 1, math.inf, O.MODE_COHOM_CLEAR), 1)
+    _check_barcodes(got, O.barcodes(O.distance_matrix(X), 1, math.inf, O.MODE_HOM), 1)
     # every distance equal
     D = np.ones((30, 30), np.float32)
     np.fill_diagonal(D, 0)
     got = rpp.rpp_barcodes(D, max_dim=2, kind="distances")
-    _check_barcodes(got, O.barcodes(D, 2, math.inf, O.MODE_COHOM_CLEAR), 2)
+    _check_barcodes(got, O.barcodes(D, 2, math.inf, O.MODE_HOM), 2)
     assert got.stats["apparent"][1] == math.comb(29, 2)
 
 
@@ -176,7 +199,7 @@ def test_invalid_inputs(rpp):
             rpp.rpp_barcodes(X, **{"max_dim": 1, **kw})
     # the context stays usable after errors
     got = rpp.rpp_barcodes(X, max_dim=1)
-    _check_barcodes(got, O.barcodes(O.distance_matrix(X), 1, math.inf, O.MODE_COHOM_CLEAR), 1)
+    _check_barcodes(got, O.barcodes(O.distance_matrix(X), 1, math.inf, O.MODE_HOM), 1)
 
 
 def test_deterministic(rpp):

@@ -447,3 +447,17 @@ def test_cofacet_lexicographic_property():
         for c in itertools.combinations(range(n - 1), 2):
             tau = O.apparent_one(D, 1, c)
             assert tau is not None and tau[0] == n - 1
+
+
+def test_torus300_golden_no_clearing_equals_clearing_mode():
+    """The stored 300-point torus barcodes were computed by the coboundary
+    reduction WITHOUT clearing (COHOM); the clearing mode, which starts from
+    Kruskal's H0 and skips the cleared columns (Clearing Lemma), must give
+    the same intervals on the same stored points."""
+    import os
+    g = np.load(os.path.join(os.path.dirname(__file__), "golden", "torus300_cohom.npz"))
+    assert str(g["oracle_mode"]) == "COHOM"
+    D = O.distance_matrix(g["points"])
+    P = O.barcodes(D, 1, math.inf, O.MODE_COHOM_CLEAR)
+    for q in (0, 1):
+        assert np.array_equal(P.barcode(q), g[f"H{q}"]), q
