@@ -173,11 +173,12 @@ def algorithmic_bytes(stage, st):
     if stage == "build_columns":
         return st["candidates"][p] * 4 + cols * 12
     if stage in ("sort_columns", "sort_pairs"):
+        # launches: (prep), histogram, offsets, one per pass, finish
         launches = st["stage_launches"][3 if stage == "sort_columns" else 6]
-        passes = max(0, (launches - 1) // 3)
+        passes = max(0, launches - (4 if stage == "sort_columns" else 3))
         n = cols if stage == "sort_columns" else st["apparent"][p]
         w = 12 if stage == "sort_columns" else 16
-        return n * w + passes * n * (w + 2 * w)  # histogram read + per pass count/scatter
+        return n * w + passes * n * 2 * w  # histogram read + per pass one read and one write
     if stage == "partition":
         return cols * (1 + 12 + 12) + st["apparent"][p] * 16 + st["leftover"][p] * 32
     return None
@@ -402,6 +403,52 @@ def sphere_bench(rpp, torch, dev, reps: int = 10, stream_count: int = 512):
 
 # ---------------------------------------------------------------------------
 # apparent-pair census of random edge orders (the paper's apparent-rate experiment)
+
+
+def filtration_bench(rpp, torch, dev, reps: int = 5):
+    """The HBM-bound stage: the dimension-2 filtration (every triangle inside
+    the enclosing radius, no clearing) of the 2000-point torus, built and
+    radix-sorted on the device through rpp_filtration, the columns left in the
+    workspace. Build: 1.33e9 candidates decoded, 12 B written per kept
+    triangle. Sort: per pass one read and one write of the 12-byte keys, plus
+    the histogram sweep (12 B) and the minimum sweep (4 B)."""
+    from paper_2003_07989_gb300 import _native as N
+    from paper_2003_07989_gb300 import inputs as I
+    X = torch.from_numpy(I.noisy_torus(N_POINTS, seed=0)).to(dev)
+    ctx = rpp.Context(dev.index or 0, record=N.RPP_RECORD_TIMING)
+    try:
+        rpp.rpp_filtration(X, 2, out=False, context=ctx)  # allocation, first launch
+        torch.cuda.synchronize(dev)
+        builds, sorts, launches, st = [], [], [], None
+        for _ in range(reps):
+            _, _, st = rpp.rpp_filtration(X, 2, out=False, context=ctx)
+            builds.append(st["stage_ms"][2])
+            sorts.append(st["stage_ms"][3])
+            launches.append(st["stage_launches"][3])
+        m = st["columns"][2]
+        cand = st["candidates"][2]
+        passes = max(0, launches[0] - 4)  # prep, histogram, offsets, passes, finish
+        build_ms, sort_ms = statistics.median(builds), statistics.median(sorts)
+        build_bytes = 12 * m + 4 * N_POINTS * N_POINTS  # columns written, D read once
+        sort_bytes = m * (4 + 12 + passes * 24)
+        peak, kind = measured_peaks()
+        return {
+            "workload": "2000-point noisy torus (seed 0), dimension-2 columns inside the "
+                        "enclosing radius, no clearing; build + radix sort on the device",
+            "candidates": cand, "columns": m, "sort_passes": passes,
+            "build_ms": build_ms, "sort_ms": sort_ms,
+            "build_gbs": build_bytes / (build_ms / 1e3) / 1e9,
+            "sort_gbs": sort_bytes / (sort_ms / 1e3) / 1e9,
+            "build_frac_of_hbm": build_bytes / (build_ms / 1e3) / 1e9 / peak,
+            "sort_frac_of_hbm": sort_bytes / (sort_ms / 1e3) / 1e9 / peak,
+            "peak_gbs": peak, "peak_source": kind,
+            "candidates_per_s": cand / (build_ms / 1e3),
+            "keys_sorted_per_s": m / (sort_ms / 1e3),
+        }
+    finally:
+        ctx.close()
+        del X
+        torch.cuda.empty_cache()
 
 
 def census_bench(rpp, torch, dev, ctx):
@@ -633,6 +680,7 @@ def main():
     census = None if (args.no_census or args.no_extras) else census_bench(rpp, torch, dev, ctx)
     backward = None if args.no_extras else backward_bench(rpp, torch, dev)
     sphere = None if args.no_extras else sphere_bench(rpp, torch, dev)
+    filtration = None if args.no_extras else filtration_bench(rpp, torch, dev)
     h2d = X.nbytes
     d2h = sum(len(iv) * (8 + 16) for iv in e2e_results[0].intervals)
     line = {
@@ -651,6 +699,7 @@ def main():
         "apparent_census": census,
         "differentiation": backward,
         "sphere_h2": sphere,
+        "filtration_dim2": filtration,
         "breakdown": {
             "kernels": kernels,
             "host_reduce_ms": statistics.mean(s["ms_host_reduce"] for s in st),

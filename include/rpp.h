@@ -151,7 +151,7 @@ rpp_status rpp_barcodes(rpp_context *ctx, const float *data, rpp_input_kind kind
  * (0, 1] of the C(n,2) pairwise distances (the ceil(q * C(n,2))-th smallest
  * distance). */
 rpp_status rpp_barcodes_quantile(rpp_context *ctx, const float *data, rpp_input_kind kind,
-                                 int64_t n, int32_t dim, int32_t max_dim, float quantile,
+                                 int64_t n, int32_t dim, int32_t max_dim, double quantile,
                                  void *stream, rpp_result **out);
 
 /* Apparent-pair census of dimension 1 (Sec. "Experiments on the Apparent
@@ -167,6 +167,30 @@ rpp_status rpp_barcodes_quantile(rpp_context *ctx, const float *data, rpp_input_
  * Errors: RPP_E_INVALID, RPP_E_OVERFLOW, RPP_E_NOMEM, RPP_E_CUDA. */
 rpp_status rpp_apparent_census(rpp_context *ctx, const float *data, rpp_input_kind kind,
                                int64_t n, int32_t dim, void *stream, rpp_stats *out);
+
+/* The filtration construction of one dimension on its own (Alg. 6 and Alg.
+ * 7 without clearing, Sec. "Filtration Construction with Clearing"): every
+ * p-simplex with diameter <= min(threshold, R), R the enclosing radius, in
+ * coboundary order (decreasing diameter, then increasing combinatorial index,
+ * Sec. "The Coboundary Matrix"). Columns are built on the device and sorted
+ * there by the library's radix sort.
+ *   data, kind, n, dim, threshold, stream  as in rpp_barcodes; n >= p + 1.
+ *   p          1 <= p <= RPP_MAX_DIM; C(n, p+1) candidates must not exceed
+ *              2^32 (RPP_E_NOMEM otherwise).
+ *   diam_out, cidx_out  caller-owned arrays (device or host memory) of
+ *              `capacity` entries receiving the diameters and indices, or
+ *              both NULL to leave the columns in the context's workspace
+ *              (for timing: only the count and the counters come back).
+ *   count_out  receives the number of columns (also when capacity is short).
+ *   stats_out  optional: candidates[p], columns[p], threshold,
+ *              enclosing_radius, stage_ms (with RPP_RECORD_TIMING),
+ *              kernel_launches, ms_total.
+ * Errors: RPP_E_INVALID (arguments, invalid distances, capacity below the
+ * count), RPP_E_OVERFLOW, RPP_E_NOMEM, RPP_E_CUDA. */
+rpp_status rpp_filtration(rpp_context *ctx, const float *data, rpp_input_kind kind, int64_t n,
+                          int32_t dim, int32_t p, float threshold, void *stream, float *diam_out,
+                          uint64_t *cidx_out, int64_t capacity, int64_t *count_out,
+                          rpp_stats *stats_out);
 
 /* Number of intervals of dimension p (0 <= p <= max_dim) in a result. */
 int64_t rpp_result_count(const rpp_result *res, int32_t p);
@@ -219,7 +243,7 @@ void rpp_results_free(rpp_result *const *results, int32_t count);
  * RPP_E_NOMEM, RPP_E_CUDA. On error no result is returned. */
 rpp_status rpp_barcodes_batched(rpp_context *ctx, int32_t batch, const float *const *data,
                                 const int64_t *n, const int32_t *dim, int32_t max_dim,
-                                const float *thresholds, const float *quantiles, void *stream,
+                                const float *thresholds, const double *quantiles, void *stream,
                                 rpp_result **out);
 
 /* Batch behaviour of a context. fused = 0 runs every cloud of a batch through
@@ -343,7 +367,7 @@ rpp_status rpp_server_create(rpp_context *ctx, const rpp_server_config *cfg, rpp
 /* Submit one request (points copied at submission, host or device memory).
  * Returns RPP_E_BUSY if the request alone can never fit the memory bound. */
 rpp_status rpp_server_submit(rpp_server *srv, const float *points, int64_t n, int32_t dim,
-                             int32_t max_dim, float threshold, float quantile,
+                             int32_t max_dim, float threshold, double quantile,
                              uint64_t *ticket);
 /* Wait up to timeout_ms (< 0: forever) for a request; RPP_E_TIMEOUT if not done. */
 rpp_status rpp_server_poll(rpp_server *srv, uint64_t ticket, int32_t timeout_ms,

@@ -13,10 +13,11 @@ binding functions raises if the library was not built.
 """
 from ._native import RppError
 from .api import (Barcodes, Context, Server, default_context, rpp_apparent_census,
-                  rpp_barcodes, rpp_barcodes_batched, rpp_distance_matrix)
+                  rpp_barcodes, rpp_barcodes_batched, rpp_distance_matrix, rpp_filtration)
 
 __all__ = ["Barcodes", "Context", "RppError", "Server", "default_context", "rpp_apparent_census",
-           "rpp_barcodes", "rpp_barcodes_batched", "rpp_distance_matrix", "rips_persistence",
+           "rpp_barcodes", "rpp_barcodes_batched", "rpp_distance_matrix", "rpp_filtration",
+           "rips_persistence",
            "total_persistence"]
 
 

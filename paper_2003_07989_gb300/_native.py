@@ -24,6 +24,7 @@ EXPORTED = [
     "rpp_result_columns", "rpp_result_apparent", "rpp_filtration_edges_noalloc",
     "rpp_context_set_batch", "rpp_context_batch_tuning", "rpp_apparent_census",
     "rpp_results_gather", "rpp_results_stats", "rpp_results_free", "rpp_server_next",
+    "rpp_filtration",
 ]
 RPP_RECORD_COLUMNS, RPP_RECORD_APPARENT, RPP_RECORD_TIMING = 1, 2, 4
 STAGES = ["distance", "enclosing_radius", "build_columns", "sort_columns", "apparent",
@@ -82,7 +83,7 @@ def lib():
     L.rpp_context_destroy.argtypes = [vp]
     L.rpp_context_destroy.restype = None
     L.rpp_barcodes.argtypes = [vp, vp, C.c_int, i64, i32, i32, C.c_float, vp, C.POINTER(vp)]
-    L.rpp_barcodes_quantile.argtypes = [vp, vp, C.c_int, i64, i32, i32, C.c_float, vp,
+    L.rpp_barcodes_quantile.argtypes = [vp, vp, C.c_int, i64, i32, i32, C.c_double, vp,
                                         C.POINTER(vp)]
     L.rpp_apparent_census.argtypes = [vp, vp, C.c_int, i64, i32, vp, C.POINTER(Stats)]
     L.rpp_result_count.argtypes = [vp, i32]
@@ -97,11 +98,11 @@ def lib():
     L.rpp_result_free.argtypes = [vp]
     L.rpp_result_free.restype = None
     L.rpp_barcodes_batched.argtypes = [vp, i32, C.POINTER(vp), C.POINTER(i64), C.POINTER(i32),
-                                       i32, fp, fp, vp, C.POINTER(vp)]
+                                       i32, fp, C.POINTER(C.c_double), vp, C.POINTER(vp)]
     L.rpp_barcodes_backward.argtypes = [vp, i32, vp, C.POINTER(i64), i32, C.POINTER(vp),
                                         vp, vp, vp, vp]
     L.rpp_server_create.argtypes = [vp, C.POINTER(ServerConfig), C.POINTER(vp)]
-    L.rpp_server_submit.argtypes = [vp, vp, i64, i32, i32, C.c_float, C.c_float,
+    L.rpp_server_submit.argtypes = [vp, vp, i64, i32, i32, C.c_float, C.c_double,
                                     C.POINTER(C.c_uint64)]
     L.rpp_server_poll.argtypes = [vp, C.c_uint64, i32, C.POINTER(vp)]
     L.rpp_server_next.argtypes = [vp, i32, C.POINTER(C.c_uint64), C.POINTER(vp)]
@@ -126,12 +127,15 @@ def lib():
     L.rpp_results_free.argtypes = [C.POINTER(vp), i32]
     L.rpp_results_free.restype = None
     L.rpp_context_batch_tuning.argtypes = [vp, i32, C.POINTER(i32), C.POINTER(i32)]
+    L.rpp_filtration.argtypes = [vp, vp, C.c_int, i64, i32, i32, C.c_float, vp, vp, vp, i64,
+                                 C.POINTER(i64), C.POINTER(Stats)]
     for name in ("rpp_context_set_batch", "rpp_context_batch_tuning",
                  "rpp_context_create", "rpp_barcodes", "rpp_barcodes_quantile",
                  "rpp_distance_matrix", "rpp_context_set_record", "rpp_filtration_edges_noalloc",
                  "rpp_result_stats", "rpp_barcodes_batched", "rpp_barcodes_backward",
                  "rpp_server_create", "rpp_server_submit", "rpp_server_poll",
-                 "rpp_results_gather", "rpp_results_stats", "rpp_server_next"):
+                 "rpp_results_gather", "rpp_results_stats", "rpp_server_next",
+                 "rpp_filtration"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L

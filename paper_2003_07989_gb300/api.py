@@ -242,6 +242,43 @@ def rpp_apparent_census(data, kind: str = "points", stream=None,
     return _stats_dict(st)
 
 
+def rpp_filtration(data, p: int, threshold: float = math.inf, kind: str = "points",
+                   out=None, stream=None, context: Context | None = None):
+    """Dimension-p columns without clearing (rpp_filtration): every p-simplex
+    with diameter <= min(threshold, enclosing radius), in coboundary order.
+
+    out=None returns host arrays (diam float32[m], cidx uint64[m]) and the
+    counters; out=False leaves the columns in the library's workspace and
+    returns only (None, None, stats) (for timing); out=(diam, cidx) takes two
+    caller tensors (device or host) of equal capacity."""
+    ptr, keep, is_cuda, dev = _as_input(data)
+    ctx = context or default_context(dev or 0)
+    kd = N.RPP_INPUT_POINTS if kind == "points" else N.RPP_INPUT_DISTANCES
+    n = int(keep.shape[0])
+    dim = int(keep.shape[1]) if kd == N.RPP_INPUT_POINTS else 0
+    s = _stream_ptr(stream, is_cuda)
+    L = N.lib()
+    count = C.c_int64(-1)
+    st = N.Stats()
+    if out is False:
+        N.check(L.rpp_filtration(ctx.handle, ptr, kd, n, dim, p, threshold, s, None, None, 0,
+                                 C.byref(count), C.byref(st)), "rpp_filtration")
+        return None, None, _stats_dict(st)
+    if out is None:
+        cap = math.comb(n, p + 1)
+        diam = np.empty(max(cap, 1), np.float32)
+        cidx = np.empty(max(cap, 1), np.uint64)
+        dptr, iptr = diam.ctypes.data, cidx.ctypes.data
+    else:
+        diam, cidx = out
+        cap = int(diam.shape[0])
+        dptr, iptr = diam.data_ptr(), cidx.data_ptr()
+    N.check(L.rpp_filtration(ctx.handle, ptr, kd, n, dim, p, threshold, s, dptr, iptr, cap,
+                             C.byref(count), C.byref(st)), "rpp_filtration")
+    k = count.value
+    return diam[:k], cidx[:k], _stats_dict(st)
+
+
 def rpp_distance_matrix(points, stream=None, context: Context | None = None) -> np.ndarray:
     """The library's float32 distance matrix of a point cloud (host copy)."""
     ptr, keep, is_cuda, dev = _as_input(points)
@@ -264,7 +301,7 @@ def rpp_barcodes_batched(clouds, max_dim: int = 1, thresholds=None, quantiles=No
     ns = (C.c_int64 * B)(*[int(k.shape[0]) for _, k, _, _ in items])
     dims = (C.c_int32 * B)(*[int(k.shape[1]) for _, k, _, _ in items])
     th = (C.c_float * B)(*thresholds) if thresholds is not None else None
-    qs = (C.c_float * B)(*quantiles) if quantiles is not None else None
+    qs = (C.c_double * B)(*quantiles) if quantiles is not None else None
     outs = (C.c_void_p * B)()
     s = _stream_ptr(stream, any(cu for _, _, cu, _ in items))
     N.check(N.lib().rpp_barcodes_batched(ctx.handle, B, ptrs, ns, dims, max_dim, th, qs, s, outs),

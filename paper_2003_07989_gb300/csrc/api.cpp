@@ -124,7 +124,7 @@ rpp_status rpp_barcodes(rpp_context *ctx, const float *data, rpp_input_kind kind
 }
 
 rpp_status rpp_barcodes_quantile(rpp_context *ctx, const float *data, rpp_input_kind kind,
-                                 int64_t n, int32_t dim, int32_t max_dim, float quantile,
+                                 int64_t n, int32_t dim, int32_t max_dim, double quantile,
                                  void *stream, rpp_result **out) {
     Instance in;
     in.data = data;
@@ -134,7 +134,7 @@ rpp_status rpp_barcodes_quantile(rpp_context *ctx, const float *data, rpp_input_
     in.max_dim = max_dim;
     in.threshold = INFINITY;
     in.quantile = quantile;
-    if (!(quantile > 0.0f && quantile <= 1.0f)) {
+    if (!(quantile > 0.0 && quantile <= 1.0)) {
         set_last_error("quantile must be in (0, 1]");
         return RPP_E_INVALID;
     }
@@ -161,6 +161,44 @@ rpp_status rpp_apparent_census(rpp_context *ctx, const float *data, rpp_input_ki
     *out = res->stats;
     delete res;
     return RPP_OK;
+}
+
+rpp_status rpp_filtration(rpp_context *ctx, const float *data, rpp_input_kind kind, int64_t n,
+                          int32_t dim, int32_t p, float threshold, void *stream, float *diam_out,
+                          uint64_t *cidx_out, int64_t capacity, int64_t *count_out,
+                          rpp_stats *stats_out) {
+    if (!count_out) {
+        set_last_error("count_out is NULL");
+        return RPP_E_INVALID;
+    }
+    if (p < 1 || p > RPP_MAX_DIM) {
+        set_last_error("p must be in [1, RPP_MAX_DIM]");
+        return RPP_E_INVALID;
+    }
+    if ((diam_out || cidx_out) && capacity < 0) {
+        set_last_error("capacity must be >= 0");
+        return RPP_E_INVALID;
+    }
+    Instance in;
+    in.data = data;
+    in.kind = kind;
+    in.n = n;
+    in.dim = dim;
+    in.max_dim = p;
+    in.threshold = threshold;
+    Status v = validate_instance(in);
+    if (!v.ok()) return report(v);
+    if (!ctx) {
+        set_last_error("ctx is NULL");
+        return RPP_E_INVALID;
+    }
+    Workspace *ws = ctx->acquire();
+    rpp_stats S;
+    Status st = run_filtration(ctx, *ws, in, p, (cudaStream_t)stream, diam_out, cidx_out,
+                               capacity, count_out, S);
+    ctx->release(ws);
+    if (stats_out) *stats_out = S;
+    return report(st);
 }
 
 int64_t rpp_result_count(const rpp_result *res, int32_t p) {

@@ -39,11 +39,12 @@ template <int P, int G, int U>
 __global__ void __launch_bounds__(256, 8) k_apparent(
     const float *__restrict__ D, int64_t ld, int64_t n, const uint64_t *__restrict__ gB,
     bool smem_table, const uint32_t *__restrict__ key_hi, const uint64_t *__restrict__ key_lo,
-    uint64_t ncols, DevState *__restrict__ st, uint8_t *__restrict__ status,
-    uint64_t *__restrict__ pivot, float *__restrict__ pdiam) {
+    uint64_t ncols_cap, const unsigned long long *d_ncols, DevState *__restrict__ st,
+    uint8_t *__restrict__ status, uint64_t *__restrict__ pivot, float *__restrict__ pdiam) {
     extern __shared__ uint64_t sB[];
     const uint64_t *B = stage_binomial(gB, n, P + 2, sB, smem_table);
     const float t = st->t;
+    const uint64_t ncols = count_of(d_ncols, ncols_cap);
     // candidate vertices a sequential scan examines before its exit (the
     // algorithmic count, independent of the lanes' and blocks' over-reads)
     unsigned long long scanned = 0;
@@ -181,12 +182,190 @@ __global__ void __launch_bounds__(256, 8) k_apparent(
     if (lane == 0 && w) atomicAdd(&st->scanned, w);
 }
 
+// The same test with vectorised reads: a group of G lanes scans windows of
+// 4 G consecutive candidates, lane l reading the four candidates
+// x0 + 4 (G - 1 - l) .. + 3 of every row of sigma as one aligned float4
+// (rows start on 128-byte boundaries and hold ld = n rounded up to 32 floats,
+// so a window never leaves its row). The group reads 16 G contiguous bytes of
+// each row per window and U windows per step, every load in flight before any
+// test. The largest qualifying candidate is the first lane of the ballot with
+// a hit, and the largest of that lane's hits; the rest is the scalar kernel's.
+template <int P, int G, int U>
+__global__ void __launch_bounds__(256, 8) k_apparent_vec(
+    const float *__restrict__ D, int64_t ld, int64_t n, const uint64_t *__restrict__ gB,
+    bool smem_table, const uint32_t *__restrict__ key_hi, const uint64_t *__restrict__ key_lo,
+    uint64_t ncols_cap, const unsigned long long *d_ncols, DevState *__restrict__ st,
+    uint8_t *__restrict__ status, uint64_t *__restrict__ pivot, float *__restrict__ pdiam) {
+    static_assert(4 * G <= 32, "a window must stay inside the 32-float row padding");
+    extern __shared__ uint64_t sB[];
+    const uint64_t *B = stage_binomial(gB, n, P + 2, sB, smem_table);
+    const float t = st->t;
+    const uint64_t ncols = count_of(d_ncols, ncols_cap);
+    constexpr int W = 4 * G;  // candidates per window
+    unsigned long long scanned = 0;
+    const int lane = threadIdx.x & 31;
+    const int grp = lane / G, gl = lane % G;
+    const unsigned gmask = (G == 32) ? FULL_MASK : (((1u << G) - 1u) << (grp * G));
+    const uint64_t ngroups = ((uint64_t)gridDim.x * blockDim.x) / G;
+    uint64_t c = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+
+    bool have = false;
+    int v[P + 1];
+    const float *row[P + 1];
+    float diam = 0.0f, best_d = 0.0f;
+    int x0 = 0, best_v = -1;  // x0: lowest candidate of the current step's first window
+
+    for (;;) {
+        if (!have) {
+            while (c < ncols && status[c] == COL_CLEARED) c += ngroups;
+            if (c < ncols) {
+                have = true;
+                diam = __uint_as_float(~key_hi[c]);
+                decode_simplex<P>(key_lo[c], B, n, v);
+#pragma unroll
+                for (int i = 0; i <= P; ++i) row[i] = D + (int64_t)v[i] * ld;
+                x0 = (int)(((n - 1) / W) * W);
+                best_d = __uint_as_float(0x7f800000u);
+                best_v = -1;
+            }
+        }
+        if (!__any_sync(FULL_MASK, have)) break;
+
+        float4 f[U][P + 1];
+        int xb[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            xb[u] = x0 - u * W + 4 * (G - 1 - gl);  // this lane's lowest candidate
+            if (have && xb[u] >= 0) {
+#pragma unroll
+                for (int i = 0; i <= P; ++i)
+                    f[u][i] = __ldg(reinterpret_cast<const float4 *>(row[i] + xb[u]));
+            }
+        }
+        unsigned hit[U];  // bit k: candidate xb + k qualifies
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            hit[u] = 0;
+            if (have && xb[u] >= 0) {
+#pragma unroll
+                for (int k = 3; k >= 0; --k) {
+                    const int x = xb[u] + k;
+                    bool member = x > (int)n - 1;
+#pragma unroll
+                    for (int i = 0; i <= P; ++i) member |= (x == v[i]);
+                    if (member) continue;
+                    float m = 0.0f;
+#pragma unroll
+                    for (int i = 0; i <= P; ++i) {
+                        const float e = k == 0 ? f[u][i].x : k == 1 ? f[u][i].y
+                                                   : k == 2 ? f[u][i].z : f[u][i].w;
+                        m = fmaxf(m, e);
+                    }
+                    if (m <= diam) hit[u] |= 1u << k;
+                    const float cd = fmaxf(m, diam);
+                    if (cd <= t && cd < best_d) {
+                        best_d = cd;
+                        best_v = x;
+                    }
+                }
+            }
+        }
+        unsigned gb[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            gb[u] = (__ballot_sync(FULL_MASK, hit[u] != 0) & gmask) >> (grp * G);
+        if (have) {
+            int first = -1, fu = 0;  // first window with a hit, its lowest lane
+#pragma unroll
+            for (int u = U - 1; u >= 0; --u)
+                if (gb[u]) {
+                    first = __ffs(gb[u]) - 1;
+                    fu = u;
+                }
+            if (first >= 0) {
+                if (gl == first) {
+                    unsigned h = hit[0];
+                    float4 fx[P + 1];
+#pragma unroll
+                    for (int i = 0; i <= P; ++i) fx[i] = f[0][i];
+                    int xl = xb[0];
+#pragma unroll
+                    for (int u = 1; u < U; ++u)
+                        if (fu == u) {
+                            h = hit[u];
+                            xl = xb[u];
+#pragma unroll
+                            for (int i = 0; i <= P; ++i) fx[i] = f[u][i];
+                        }
+                    const int k = 31 - __clz(h);  // the largest qualifying candidate
+                    const int x = xl + k;
+                    float dx[P + 1];
+#pragma unroll
+                    for (int i = 0; i <= P; ++i)
+                        dx[i] = k == 0 ? fx[i].x : k == 1 ? fx[i].y : k == 2 ? fx[i].z : fx[i].w;
+                    bool apparent = true;
+#pragma unroll
+                    for (int i = 0; i <= P; ++i) {
+                        if (v[i] > x) {  // facet tau - {v_i} precedes sigma
+                            float fd = 0.0f;
+#pragma unroll
+                            for (int kk = 0; kk <= P; ++kk)
+                                if (kk != i) fd = fmaxf(fd, dx[kk]);
+#pragma unroll
+                            for (int a = 0; a <= P; ++a)
+#pragma unroll
+                                for (int b = a + 1; b <= P; ++b)
+                                    if (a != i && b != i) fd = fmaxf(fd, row[a][v[b]]);
+                            if (fd == diam) apparent = false;
+                        }
+                    }
+                    status[c] = apparent ? COL_APPARENT : COL_LEFTOVER;
+                    pivot[c] = cofacet_index<P>(v, x, B, n);
+                    pdiam[c] = diam;
+                    int above = 0;  // vertices of sigma above x
+#pragma unroll
+                    for (int i = 0; i <= P; ++i) above += v[i] > x;
+                    scanned += (unsigned long long)(n - x - above);
+                }
+                have = false;
+                c += ngroups;
+            } else if (x0 - U * W < 0) {
+                // every vertex seen, none of equal diameter: reduce the oldest cofacet
+#pragma unroll
+                for (int o = G / 2; o > 0; o >>= 1) {
+                    const float od = __shfl_xor_sync(gmask, best_d, o);
+                    const int ov = __shfl_xor_sync(gmask, best_v, o);
+                    if (od < best_d || (od == best_d && ov > best_v)) {
+                        best_d = od;
+                        best_v = ov;
+                    }
+                }
+                if (gl == 0) {
+                    status[c] = COL_LEFTOVER;
+                    pivot[c] = best_v >= 0 ? cofacet_index<P>(v, best_v, B, n) : NO_PIVOT;
+                    pdiam[c] = best_d;
+                    scanned += (unsigned long long)(n - (P + 1));
+                }
+                have = false;
+                c += ngroups;
+            } else {
+                x0 -= U * W;
+            }
+        }
+    }
+    unsigned long long w = scanned;
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(FULL_MASK, w, o);
+    if (lane == 0 && w) atomicAdd(&st->scanned, w);
+}
+
 __global__ void __launch_bounds__(256) k_partition(
     const uint8_t *__restrict__ status, const uint32_t *__restrict__ key_hi,
     const uint64_t *__restrict__ key_lo, const uint64_t *__restrict__ pivot,
-    const float *__restrict__ pdiam, uint64_t ncols, uint64_t *__restrict__ app_tau,
-    uint64_t *__restrict__ app_sigma, Leftover *__restrict__ left, DevState *st) {
+    const float *__restrict__ pdiam, uint64_t ncols_cap, const unsigned long long *d_ncols,
+    uint64_t *__restrict__ app_tau, uint64_t *__restrict__ app_sigma, Leftover *__restrict__ left,
+    DevState *st) {
     const int lane = threadIdx.x & 31;
+    const uint64_t ncols = count_of(d_ncols, ncols_cap);
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < ncols;
          base += stride) {
@@ -225,8 +404,8 @@ __global__ void __launch_bounds__(256) k_partition(
 template <int P, int G, int U>
 void apparent_pg(const float *D, int64_t ld, int64_t n, const uint64_t *binom,
                  const uint32_t *key_hi, const uint64_t *key_lo, uint64_t ncols,
-                 DevState *st, uint8_t *status, uint64_t *pivot, float *pdiam, int sms,
-                 cudaStream_t s) {
+                 const unsigned long long *d_ncols, DevState *st, uint8_t *status,
+                 uint64_t *pivot, float *pdiam, int sms, cudaStream_t s) {
     const size_t table = (size_t)(P + 3) * (n + 1) * sizeof(uint64_t);
     const bool smem = table <= 48 * 1024;
     int per_sm = 0;
@@ -239,24 +418,49 @@ void apparent_pg(const float *D, int64_t ld, int64_t n, const uint64_t *binom,
     if (blocks == 0) return;
     ++g_launches;
     k_apparent<P, G, U><<<(unsigned)blocks, 256, smem ? table : 0, s>>>(
-        D, ld, n, binom, smem, key_hi, key_lo, ncols, st, status, pivot, pdiam);
+        D, ld, n, binom, smem, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam);
+}
+
+template <int P, int G, int U>
+void apparent_vec(const float *D, int64_t ld, int64_t n, const uint64_t *binom,
+                  const uint32_t *key_hi, const uint64_t *key_lo, uint64_t ncols,
+                  const unsigned long long *d_ncols, DevState *st, uint8_t *status,
+                  uint64_t *pivot, float *pdiam, int sms, cudaStream_t s) {
+    const size_t table = (size_t)(P + 3) * (n + 1) * sizeof(uint64_t);
+    const bool smem = table <= 48 * 1024;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apparent_vec<P, G, U>, 256,
+                                                  smem ? table : 0);
+    if (per_sm < 1) per_sm = 1;
+    uint64_t blocks = (uint64_t)sms * per_sm;
+    const uint64_t need = (ncols * G + 255) / 256;
+    if (need < blocks) blocks = need;
+    if (blocks == 0) return;
+    ++g_launches;
+    k_apparent_vec<P, G, U><<<(unsigned)blocks, 256, smem ? table : 0, s>>>(
+        D, ld, n, binom, smem, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam);
 }
 
 // group: lanes per column G (4, 8, 16, 32) for one candidate block per step,
-// or 10 G + U for U blocks (42, 44, 82).
+// or 10 G + U for U blocks (42, 44, 82); 100 + 10 G + U for the vectorised
+// test with U windows of 4 G candidates a step (121, 141, 142, 181).
 template <int P>
 void apparent_p(int group, const float *D, int64_t ld, int64_t n, const uint64_t *binom,
                 const uint32_t *key_hi, const uint64_t *key_lo, uint64_t ncols,
-                DevState *st, uint8_t *status, uint64_t *pivot, float *pdiam, int sms,
-                cudaStream_t s) {
+                const unsigned long long *d_ncols, DevState *st, uint8_t *status,
+                uint64_t *pivot, float *pdiam, int sms, cudaStream_t s) {
     switch (group) {
-        case 4: apparent_pg<P, 4, 1>(D, ld, n, binom, key_hi, key_lo, ncols, st, status, pivot, pdiam, sms, s); break;
-        case 16: apparent_pg<P, 16, 1>(D, ld, n, binom, key_hi, key_lo, ncols, st, status, pivot, pdiam, sms, s); break;
-        case 32: apparent_pg<P, 32, 1>(D, ld, n, binom, key_hi, key_lo, ncols, st, status, pivot, pdiam, sms, s); break;
-        case 42: apparent_pg<P, 4, 2>(D, ld, n, binom, key_hi, key_lo, ncols, st, status, pivot, pdiam, sms, s); break;
-        case 82: apparent_pg<P, 8, 2>(D, ld, n, binom, key_hi, key_lo, ncols, st, status, pivot, pdiam, sms, s); break;
-        case 44: apparent_pg<P, 4, 4>(D, ld, n, binom, key_hi, key_lo, ncols, st, status, pivot, pdiam, sms, s); break;
-        default: apparent_pg<P, 8, 1>(D, ld, n, binom, key_hi, key_lo, ncols, st, status, pivot, pdiam, sms, s); break;
+        case 4: apparent_pg<P, 4, 1>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, sms, s); break;
+        case 16: apparent_pg<P, 16, 1>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, sms, s); break;
+        case 32: apparent_pg<P, 32, 1>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, sms, s); break;
+        case 42: apparent_pg<P, 4, 2>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, sms, s); break;
+        case 82: apparent_pg<P, 8, 2>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, sms, s); break;
+        case 44: apparent_pg<P, 4, 4>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, sms, s); break;
+        case 121: apparent_vec<P, 2, 1>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, sms, s); break;
+        case 141: apparent_vec<P, 4, 1>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, sms, s); break;
+        case 142: apparent_vec<P, 4, 2>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, sms, s); break;
+        case 181: apparent_vec<P, 8, 1>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, sms, s); break;
+        default: apparent_pg<P, 8, 1>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, sms, s); break;
     }
 }
 
@@ -264,27 +468,28 @@ void apparent_p(int group, const float *D, int64_t ld, int64_t n, const uint64_t
 
 void launch_apparent(const float *D, int64_t ld, int64_t n, int p, const uint64_t *binom,
                      const uint32_t *key_hi, const uint64_t *key_lo, uint64_t ncols,
-                     DevState *st, uint8_t *status, uint64_t *pivot, float *pdiam, int group,
-                     int sms, cudaStream_t s) {
+                     const unsigned long long *d_ncols, DevState *st, uint8_t *status,
+                     uint64_t *pivot, float *pdiam, int group, int sms, cudaStream_t s) {
     if (ncols == 0) return;
     switch (p) {
-        case 1: apparent_p<1>(group, D, ld, n, binom, key_hi, key_lo, ncols, st, status, pivot, pdiam, sms, s); break;
-        case 2: apparent_p<2>(group, D, ld, n, binom, key_hi, key_lo, ncols, st, status, pivot, pdiam, sms, s); break;
-        case 3: apparent_p<3>(group, D, ld, n, binom, key_hi, key_lo, ncols, st, status, pivot, pdiam, sms, s); break;
-        case 4: apparent_p<4>(group, D, ld, n, binom, key_hi, key_lo, ncols, st, status, pivot, pdiam, sms, s); break;
+        case 1: apparent_p<1>(group, D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, sms, s); break;
+        case 2: apparent_p<2>(group, D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, sms, s); break;
+        case 3: apparent_p<3>(group, D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, sms, s); break;
+        case 4: apparent_p<4>(group, D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, sms, s); break;
         default: break;
     }
 }
 
 void launch_partition(const uint8_t *status, const uint32_t *key_hi, const uint64_t *key_lo,
-                      const uint64_t *pivot, const float *pdiam, uint64_t ncols, uint64_t *app_tau,
+                      const uint64_t *pivot, const float *pdiam, uint64_t ncols,
+                      const unsigned long long *d_ncols, uint64_t *app_tau,
                       uint64_t *app_sigma, Leftover *left, DevState *st, cudaStream_t s) {
     if (ncols == 0) return;
     uint64_t blocks = (ncols + 255) / 256;
     if (blocks > 152 * 8) blocks = 152 * 8;
     ++g_launches;
     k_partition<<<(unsigned)blocks, 256, 0, s>>>(status, key_hi, key_lo, pivot, pdiam, ncols,
-                                                  app_tau, app_sigma, left, st);
+                                                  d_ncols, app_tau, app_sigma, left, st);
 }
 
 }  // namespace rpp

@@ -308,10 +308,9 @@ Status launch_device(rpp_context *ctx, Workspace &ws, const std::vector<Instance
         c.pt_off = pt;
         c.d_off = dd;
         c.mst_off = ms;
-        c.t_user = in.quantile > 0.0f ? INFINITY : in.threshold;
-        c.quantile = in.quantile;
+        c.t_user = in.quantile > 0.0 ? INFINITY : in.threshold;
+        c.qrank = in.quantile > 0.0 ? quantile_rank(in.quantile, (uint64_t)in.n) : 0;
         c.max_dim = in.max_dim;
-        c.pad = 0;
         c.aw_off = aw;
         const size_t cnt = (size_t)c.n * c.dim;
         if (is_device_pointer(in.data)) {
@@ -685,7 +684,7 @@ Status run_batch(rpp_context *ctx, Workspace &ws, const std::vector<Instance> &i
 extern "C" rpp_status rpp_barcodes_batched(rpp_context *ctx, int32_t batch,
                                            const float *const *data, const int64_t *n,
                                            const int32_t *dim, int32_t max_dim,
-                                           const float *thresholds, const float *quantiles,
+                                           const float *thresholds, const double *quantiles,
                                            void *stream, rpp_result **out) {
     if (!ctx || batch < 0 || (batch > 0 && (!data || !n || !dim || !out))) {
         set_last_error("rpp_barcodes_batched: invalid arguments");
@@ -700,7 +699,7 @@ extern "C" rpp_status rpp_barcodes_batched(rpp_context *ctx, int32_t batch,
         in.dim = dim[i];
         in.max_dim = max_dim;
         in.threshold = thresholds ? thresholds[i] : INFINITY;
-        in.quantile = quantiles ? quantiles[i] : 0.0f;
+        in.quantile = quantiles ? quantiles[i] : 0.0;
         Status v = validate_instance(in);
         if (!v.ok()) {
             v.msg = "cloud " + std::to_string(i) + ": " + v.msg;

@@ -190,8 +190,8 @@ __global__ void __launch_bounds__(512) k_batch_h1(
         const uint32_t m = (uint32_t)n * (uint32_t)(n - 1) / 2;
 
         // ---- 2. nearest-rank quantile: radix select over the C(n, 2) distances ----
-        if (C.quantile > 0.0f && m > 0 && s_err == 0) {
-            uint64_t rk = (uint64_t)ceil((double)C.quantile * (double)m);
+        if (C.qrank > 0 && m > 0 && s_err == 0) {
+            uint64_t rk = C.qrank;
             rk = rk < 1 ? 1 : (rk > m ? m : rk);
             uint32_t prefix = 0, mask = 0, rank = (uint32_t)rk;
             for (int shift = 24; shift >= 0; shift -= 8) {

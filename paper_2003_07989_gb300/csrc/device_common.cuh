@@ -76,6 +76,14 @@ __device__ __forceinline__ uint64_t cofacet_index(const int *v, int w, const uin
     return c;
 }
 
+// A launch's item count: min(*d_count, cap) when the count lives in device
+// memory (launches queued before the host knows it), else cap.
+__device__ __forceinline__ uint64_t count_of(const unsigned long long *d_count, uint64_t cap) {
+    if (!d_count) return cap;
+    const uint64_t c = *d_count;
+    return c < cap ? c : cap;
+}
+
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));

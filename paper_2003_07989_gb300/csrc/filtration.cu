@@ -2,11 +2,12 @@
 // Sec. "Filtration Construction with Clearing").
 //
 // Every index c in [0, C(n, p+1)) names one p-simplex. A thread decodes c with
-// the binomial table staged in shared memory, takes the diameter (the largest
-// of the C(p+1, 2) distances among its vertices, Sec. 2), and keeps the simplex
-// when diam <= t and it was not paired as a death in dimension p-1 (the
-// clearing lemma, Sec. "Clearing Lemma"; the previous dimension's deaths are a
-// bitmap over indices). Instead of writing (-inf, +inf) sentinels for dropped
+// the binomial table staged in shared memory (once per run of indices that
+// share all vertices but the lowest, see k_build_columns), takes the diameter
+// (the largest of the C(p+1, 2) distances among its vertices, Sec. 2), and
+// keeps the simplex when diam <= t and it was not paired as a death in
+// dimension p-1 (the clearing lemma, Sec. "Clearing Lemma"; the previous
+// dimension's deaths are a bitmap over indices). Instead of writing (-inf, +inf) sentinels for dropped
 // simplices and sorting everything as Alg. 6/7 do, kept simplices are
 // compacted with warp-aggregated atomics (Sec. "Warp-based Filtering"): one
 // atomic per warp reserves space, lanes write at their ballot rank. The sort
@@ -19,10 +20,20 @@ namespace rpp {
 
 namespace {
 
+// Indices c of one run share every vertex but the lowest: the p-simplex
+// {v_0 > ... > v_p} has c = C(v_0, p+1) + ... + C(v_{p-1}, 2) + v_p, so for a
+// fixed prefix (v_0, ..., v_{p-1}) the run c, c+1, ... walks v_p = 0, 1, ...,
+// v_{p-1} - 1. A warp takes a chunk of consecutive indices, lane l index
+// c0 + l + 32 k; a lane decodes its index once and then only adds 32 to v_p
+// (decoding again when v_p runs past v_{p-1}, i.e. into the next prefix).
+// Per index that leaves p distance reads, D[v_i][v_p] for i < p, which the
+// lanes of a warp take from the same rows at consecutive columns (coalesced),
+// and the prefix's own diameter, computed once per decode.
 template <int P>
 __global__ void __launch_bounds__(256) k_build_columns(const float *__restrict__ D, int64_t ld,
                                                         int64_t n, const uint64_t *__restrict__ gB,
                                                         bool smem_table, uint64_t total,
+                                                        uint64_t chunk,
                                                         const uint32_t *__restrict__ cleared,
                                                         DevState *st, uint32_t *__restrict__ key_hi,
                                                         uint64_t *__restrict__ key_lo) {
@@ -30,30 +41,49 @@ __global__ void __launch_bounds__(256) k_build_columns(const float *__restrict__
     const uint64_t *B = stage_binomial(gB, n, P + 1, sB, smem_table);
     const float t = st->t;
     const int lane = threadIdx.x & 31;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < total;
-         base += stride) {
-        const uint64_t c = base + lane;
-        bool keep = false;
-        float d = 0.0f;
-        if (c < total && !(cleared && ((cleared[c >> 5] >> (c & 31)) & 1u))) {
-            int v[P + 1];
-            decode_simplex<P>(c, B, n, v);
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t c0 = warp * chunk; c0 < total; c0 += nwarps * chunk) {
+        const uint64_t cend = c0 + chunk < total ? c0 + chunk : total;
+        int v[P + 1];
+        const float *row[P];
+        float pd = 0.0f;  // diameter of the prefix v_0 .. v_{p-1}
+        bool fresh = true;
+        for (uint64_t c = c0 + lane;; c += 32) {
+            const bool valid = c < cend;
+            if (!__any_sync(FULL_MASK, valid)) break;
+            bool keep = false;
+            float d = 0.0f;
+            if (valid) {
+                if (!fresh) v[P] += 32;
+                if (fresh || v[P] >= v[P - 1]) {
+                    decode_simplex<P>(c, B, n, v);
+                    pd = 0.0f;
 #pragma unroll
-            for (int a = 0; a <= P; ++a)
+                    for (int a = 0; a < P; ++a) {
+                        row[a] = D + (int64_t)v[a] * ld;
 #pragma unroll
-                for (int b = a + 1; b <= P; ++b) d = fmaxf(d, D[(int64_t)v[a] * ld + v[b]]);
-            keep = d <= t;
-        }
-        const unsigned ball = __ballot_sync(FULL_MASK, keep);
-        if (ball) {
-            unsigned long long off = 0;
-            if (lane == 0) off = atomicAdd(&st->ncols, (unsigned long long)__popc(ball));
-            off = __shfl_sync(FULL_MASK, off, 0);
-            if (keep) {
-                const uint64_t pos = off + __popc(ball & lanemask_lt());
-                key_hi[pos] = ~__float_as_uint(d);
-                key_lo[pos] = c;
+                        for (int b = a + 1; b < P; ++b) pd = fmaxf(pd, row[a][v[b]]);
+                    }
+                    fresh = false;
+                }
+                if (!(cleared && ((cleared[c >> 5] >> (c & 31)) & 1u))) {
+                    d = pd;
+#pragma unroll
+                    for (int a = 0; a < P; ++a) d = fmaxf(d, row[a][v[P]]);
+                    keep = d <= t;
+                }
+            }
+            const unsigned ball = __ballot_sync(FULL_MASK, keep);
+            if (ball) {
+                unsigned long long off = 0;
+                if (lane == 0) off = atomicAdd(&st->ncols, (unsigned long long)__popc(ball));
+                off = __shfl_sync(FULL_MASK, off, 0);
+                if (keep) {
+                    const uint64_t pos = off + __popc(ball & lanemask_lt());
+                    key_hi[pos] = ~__float_as_uint(d);
+                    key_lo[pos] = c;
+                }
             }
         }
     }
@@ -68,6 +98,13 @@ __global__ void k_edge_pairs(const uint64_t *__restrict__ lo, uint64_t count,
         decode_edge(lo[i], v);
         out[i] = ((uint32_t)v[0] << 16) | (uint32_t)v[1];
     }
+}
+
+__global__ void k_invert_u32(const uint32_t *__restrict__ in, uint64_t count,
+                             uint32_t *__restrict__ out) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride)
+        out[i] = ~in[i];
 }
 
 __global__ void k_bitmap_set(const uint64_t *__restrict__ idx, uint64_t count,
@@ -102,9 +139,16 @@ void build_p(const float *D, int64_t ld, int64_t n, const uint64_t *binom, uint6
     const uint64_t cap = 152ull * 8;
     if (blocks > cap) blocks = cap;
     if (blocks == 0) return;
+    // chunks of consecutive indices per warp: long enough that a lane's
+    // single decode serves many indices, short enough to spread the work
+    const uint64_t warps = blocks * 8;
+    uint64_t chunk = (total + warps - 1) / warps;
+    chunk = (chunk + 31) / 32 * 32;
+    if (chunk > 2048) chunk = 2048;
+    if (chunk < 32) chunk = 32;
     ++g_launches;
     k_build_columns<P><<<(unsigned)blocks, 256, smem ? table : 0, s>>>(
-        D, ld, n, binom, smem, total, cleared, st, key_hi, key_lo);
+        D, ld, n, binom, smem, total, chunk, cleared, st, key_hi, key_lo);
 }
 
 }  // namespace
@@ -133,6 +177,14 @@ void launch_lower_bound_u32(const uint32_t *a, uint64_t n, uint32_t key, unsigne
                             cudaStream_t s) {
     ++g_launches;
     k_lower_bound_u32<<<1, 1, 0, s>>>(a, n, key, out);
+}
+
+void launch_invert_u32(const uint32_t *in, uint64_t count, uint32_t *out, cudaStream_t s) {
+    if (count == 0) return;
+    uint64_t blocks = (count + 255) / 256;
+    if (blocks > 152ull * 8) blocks = 152ull * 8;
+    ++g_launches;
+    k_invert_u32<<<(unsigned)blocks, 256, 0, s>>>(in, count, out);
 }
 
 void launch_bitmap_set(const uint64_t *idx, uint64_t count, uint32_t *bitmap, cudaStream_t s) {

@@ -149,10 +149,12 @@ __global__ void k_h0_jump(int64_t n, const int32_t *__restrict__ comp,
 // (key_hi, key_lo) = (~bits(d), index)); the column there is marked cleared.
 __global__ void k_h0_clear(const unsigned long long *__restrict__ mst,
                            const unsigned *__restrict__ nmst, const uint32_t *__restrict__ key_hi,
-                           const uint64_t *__restrict__ key_lo, uint64_t ncols,
-                           uint8_t *__restrict__ status, uint32_t *__restrict__ pos) {
+                           const uint64_t *__restrict__ key_lo, uint64_t ncols_cap,
+                           const unsigned long long *d_ncols, uint8_t *__restrict__ status,
+                           uint32_t *__restrict__ pos) {
     const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= *nmst) return;
+    const uint64_t ncols = count_of(d_ncols, ncols_cap);
     const unsigned long long bk = mst[i];
     const uint32_t hi = ~(uint32_t)(bk >> 32);
     const uint64_t lo = (uint64_t)(~(uint32_t)bk);
@@ -195,10 +197,12 @@ void launch_h0_forest(const float *D, int64_t ld, int64_t n, DevState *st, int32
 
 void launch_h0_clear(const unsigned long long *mst, const unsigned *nmst, int64_t n,
                      const uint32_t *key_hi, const uint64_t *key_lo, uint64_t ncols,
-                     uint8_t *status, uint32_t *pos, cudaStream_t s) {
+                     const unsigned long long *d_ncols, uint8_t *status, uint32_t *pos,
+                     cudaStream_t s) {
     if (n < 2 || ncols == 0) return;
     ++g_launches;
-    k_h0_clear<<<blocks_for(n, 256), 256, 0, s>>>(mst, nmst, key_hi, key_lo, ncols, status, pos);
+    k_h0_clear<<<blocks_for(n, 256), 256, 0, s>>>(mst, nmst, key_hi, key_lo, ncols, d_ncols,
+                                                  status, pos);
 }
 
 }  // namespace rpp

@@ -81,20 +81,22 @@ void launch_build_columns(const float *D, int64_t ld, int64_t n, int p, const ui
                           uint64_t total, const uint32_t *cleared, DevState *st,
                           uint32_t *key_hi, uint64_t *key_lo, cudaStream_t s);
 
-// LSD radix sort of (hi, lo) keys, ascending in (hi, lo), with an optional
-// 64-bit payload. Sorts lo bits [0, lo_bits) then hi bits [0, hi_bits). The
-// result is left in (hi, lo, val); tmp_* are scratch of the same sizes.
-// `tile_counts` needs radix_tile_counts_size(n) entries.
-size_t radix_tile_counts_size(uint64_t n);
+// LSD radix sort of (hi, lo) keys, ascending in (hi, lo) (hi may be null: lo
+// alone), with an optional 64-bit payload; lo < 2^lo_bits. The key count is
+// min(*d_count, n_cap) when d_count (device memory) is given, else n_cap, so
+// the sort needs nothing from the host. The result is left in (hi, lo, val);
+// tmp_* are buffers of the same sizes, scratch holds radix_scratch_bytes(n_cap)
+// bytes. A bounded wait that runs out ORs ERR_INTERNAL into *err (device).
+constexpr uint64_t RADIX_SORT_TILE = 2048;          // keys per tile of one sort pass
+constexpr size_t RADIX_SORT_CTL_BYTES = 64 * 1024;  // the sort's control block
+constexpr size_t radix_scratch_bound(uint64_t n_cap) {
+    return RADIX_SORT_CTL_BYTES +
+           (size_t)((n_cap + RADIX_SORT_TILE - 1) / RADIX_SORT_TILE + 1) * 256 * 8;
+}
+size_t radix_scratch_bytes(uint64_t n_cap);  // = radix_scratch_bound(n_cap)
 void radix_sort(uint32_t *hi, uint64_t *lo, uint64_t *val, uint32_t *tmp_hi, uint64_t *tmp_lo,
-                uint64_t *tmp_val, uint32_t *tile_counts, uint32_t *digit_hist, uint64_t n,
-                int lo_bits, int hi_bits, cudaStream_t s);
-
-// radix_sort without payload and without any allocation (host_hist: caller
-// buffer of 12 * 256 entries).
-void radix_sort_noalloc(uint32_t *hi, uint64_t *lo, uint32_t *tmp_hi, uint64_t *tmp_lo,
-                        uint32_t *tile_counts, uint32_t *digit_hist, uint32_t *host_hist,
-                        uint64_t n, int lo_bits, int hi_bits, cudaStream_t s);
+                uint64_t *tmp_val, void *scratch, uint64_t n_cap,
+                const unsigned long long *d_count, int lo_bits, unsigned *err, cudaStream_t s);
 
 // H0 of one instance on the device: the minimum spanning forest of the edges
 // inside st->t under the filtration's order of edges (Boruvka, a fixed number
@@ -107,9 +109,14 @@ void launch_h0_forest(const float *D, int64_t ld, int64_t n, DevState *st, int32
                       unsigned long long *mst, unsigned *nmst, unsigned *flags, cudaStream_t s);
 // Mark the forest's columns cleared in the sorted dimension-1 array (ncols
 // columns, ascending (key_hi, key_lo)); pos[i] receives the position of edge i.
+// The column count is min(*d_ncols, ncols) when d_ncols (device) is given.
 void launch_h0_clear(const unsigned long long *mst, const unsigned *nmst, int64_t n,
                      const uint32_t *key_hi, const uint64_t *key_lo, uint64_t ncols,
-                     uint8_t *status, uint32_t *pos, cudaStream_t s);
+                     const unsigned long long *d_ncols, uint8_t *status, uint32_t *pos,
+                     cudaStream_t s);
+
+// out[i] = ~in[i] (sort keys ~bits(diameter) back to diameter bits).
+void launch_invert_u32(const uint32_t *in, uint64_t count, uint32_t *out, cudaStream_t s);
 
 // The vertices of edge indices, packed (a << 16) | b with a > b (n <= 65535).
 void launch_edge_pairs(const uint64_t *lo, uint64_t count, uint32_t *out, cudaStream_t s);
@@ -117,16 +124,18 @@ void launch_edge_pairs(const uint64_t *lo, uint64_t count, uint32_t *out, cudaSt
 
 // Apparent-pair pass (Alg. 3 with the Apparent Pairs Lemma) over the columns
 // [0, ncols) in coboundary order. Writes status, pivot and pivot diameter.
+// (ncols, d_ncols: the column count is min(*d_ncols, ncols) when d_ncols,
+// device memory, is given; grids are sized for ncols.)
 void launch_apparent(const float *D, int64_t ld, int64_t n, int p, const uint64_t *binom,
                      const uint32_t *key_hi, const uint64_t *key_lo, uint64_t ncols,
-                     DevState *st, uint8_t *status, uint64_t *pivot, float *pdiam,
-                     int group, int sms, cudaStream_t s);
+                     const unsigned long long *d_ncols, DevState *st, uint8_t *status,
+                     uint64_t *pivot, float *pdiam, int group, int sms, cudaStream_t s);
 
 // Partition: apparent columns -> (tau, sigma) pairs; leftover columns -> Leftover.
 void launch_partition(const uint8_t *status, const uint32_t *key_hi, const uint64_t *key_lo,
                       const uint64_t *pivot, const float *pdiam, uint64_t ncols,
-                      uint64_t *app_tau, uint64_t *app_sigma, Leftover *left, DevState *st,
-                      cudaStream_t s);
+                      const unsigned long long *d_ncols, uint64_t *app_tau,
+                      uint64_t *app_sigma, Leftover *left, DevState *st, cudaStream_t s);
 
 // First position i in [0, n) with a[i] >= key for ascending a, into *out.
 void launch_lower_bound_u32(const uint32_t *a, uint64_t n, uint32_t key, unsigned long long *out,
@@ -151,9 +160,8 @@ struct BatchCloud {
     int32_t n, dim, ld;
     int32_t mst_off;  // first of its n - 1 MST slots
     float t_user;     // threshold (INFINITY: none)
-    float quantile;   // > 0: threshold = the ceil(q C(n,2))-th smallest distance
     int32_t max_dim;  // 0: H0 only (no apparent-pair test)
-    int32_t pad;
+    uint64_t qrank;   // > 0: threshold = the qrank-th smallest of the C(n,2) distances
     int64_t aw_off;   // offset of its C(n,2) entries in the apparent-vertex buffer
 };
 

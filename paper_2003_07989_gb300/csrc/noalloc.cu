@@ -5,10 +5,10 @@
 // device memory pool, where every allocation has to go through that owner, and
 // latency-critical loops, where cudaMalloc and cudaFree would implicitly
 // synchronise the device. This entry point takes the caller's input and output
-// buffers and keeps its scratch (counters, binomial table, radix-sort ping-pong
-// buffers and tile histograms) in one static device array of fixed size,
-// declared below. Every GPU that loads the library holds that array until the
-// process exits.
+// buffers and keeps its scratch (counters, binomial table, the radix sort's
+// control block, look-back entries and ping-pong buffers) in one static device
+// array of fixed size, declared below. Every GPU that loads the library holds
+// that array until the process exits.
 #include <cmath>
 #include <string>
 
@@ -24,9 +24,8 @@ constexpr int64_t NA_MAX_N = 724;          // C(724, 2) = 261,726 <= NA_MAX_EDGE
 constexpr size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 constexpr size_t OFF_STATE = 0;
 constexpr size_t OFF_BINOM = up256(sizeof(DevState));
-constexpr size_t OFF_HIST = up256(OFF_BINOM + 3 * (NA_MAX_N + 1) * sizeof(uint64_t));
-constexpr size_t OFF_TILES = up256(OFF_HIST + 12 * 256 * sizeof(uint32_t));
-constexpr size_t OFF_TMP_HI = up256(OFF_TILES + ((NA_MAX_EDGES + 2047) / 2048) * 256 * 4);
+constexpr size_t OFF_SORT = up256(OFF_BINOM + 3 * (NA_MAX_N + 1) * sizeof(uint64_t));
+constexpr size_t OFF_TMP_HI = up256(OFF_SORT + radix_scratch_bound(NA_MAX_EDGES));
 constexpr size_t OFF_TMP_LO = up256(OFF_TMP_HI + NA_MAX_EDGES * sizeof(uint32_t));
 constexpr size_t SCRATCH_BYTES = up256(OFF_TMP_LO + NA_MAX_EDGES * sizeof(uint64_t));
 
@@ -53,9 +52,9 @@ __global__ void k_noalloc_init(DevState *st, float t, uint64_t *binom, int64_t n
 }
 
 // Sort keys held ~bits(diameter); turn them back into diameters.
-__global__ void k_noalloc_finish(uint32_t *key_hi, uint64_t count) {
+__global__ void k_noalloc_finish(uint32_t *key_hi, uint64_t cap, const unsigned long long *count) {
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < count) key_hi[i] = ~key_hi[i];
+    if (i < cap && i < *count) key_hi[i] = ~key_hi[i];
 }
 
 int bits_for(uint64_t x) {
@@ -133,33 +132,35 @@ extern "C" rpp_status rpp_filtration_edges_noalloc(const float *D, int64_t n, fl
     }
     DevState *st = (DevState *)(base + OFF_STATE);
     uint64_t *binom = (uint64_t *)(base + OFF_BINOM);
-    uint32_t *hist = (uint32_t *)(base + OFF_HIST);
-    uint32_t *tiles = (uint32_t *)(base + OFF_TILES);
+    void *sort_scratch = base + OFF_SORT;
     uint32_t *tmp_hi = (uint32_t *)(base + OFF_TMP_HI);
     uint64_t *tmp_lo = (uint64_t *)(base + OFF_TMP_LO);
     uint32_t *key_hi = (uint32_t *)diam_out;  // sorted as ~bits(diameter), then converted
 
+    // build, sort and conversion are queued with the edge count left on the
+    // device; one wait at the end reads the count and the sort's wait flag
     ++g_launches;
     k_noalloc_init<<<4, 256, 0, s>>>(st, threshold, binom, n);
     launch_build_columns(D, n, n, 1, binom, m, nullptr, st, key_hi, cidx_out, s);
-    unsigned long long count = 0;
-    cudaMemcpyAsync(&count, &st->ncols, sizeof(count), cudaMemcpyDeviceToHost, s);
-    cudaError_t e = cudaStreamSynchronize(s);
-    if (e == cudaSuccess) {
-        uint32_t host_hist[12 * 256];
-        radix_sort_noalloc(key_hi, cidx_out, tmp_hi, tmp_lo, tiles, hist, host_hist, count,
-                           bits_for(m > 0 ? m - 1 : 0), 32, s);
-        if (count > 0) {
-            ++g_launches;
-            k_noalloc_finish<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(key_hi, count);
-        }
-        e = cudaStreamSynchronize(s);
+    radix_sort(key_hi, cidx_out, nullptr, tmp_hi, tmp_lo, nullptr, sort_scratch, m, &st->ncols,
+               bits_for(m > 0 ? m - 1 : 0), &st->err, s);
+    if (m > 0) {
+        ++g_launches;
+        k_noalloc_finish<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(key_hi, m, &st->ncols);
     }
+    DevState hs;
+    cudaMemcpyAsync(&hs, st, sizeof(hs), cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) {
         set_last_error(std::string("rpp_filtration_edges_noalloc: ") + cudaGetErrorString(e));
         return RPP_E_CUDA;
     }
+    if (hs.err & ERR_INTERNAL) {
+        set_last_error("rpp_filtration_edges_noalloc: a bounded device wait ran out (sort)");
+        return RPP_E_CUDA;
+    }
+    const unsigned long long count = hs.ncols;
     *count_out = (int64_t)count;
     return RPP_OK;
 }

@@ -29,6 +29,12 @@ double now_ms() {
         .count();
 }
 
+uint64_t quantile_rank(double q, uint64_t n) {
+    const uint64_t m = n * (n - 1) / 2;
+    uint64_t r = (uint64_t)std::ceil(q * (double)m);
+    return std::max<uint64_t>(1, std::min<uint64_t>(r, m));
+}
+
 int bits_for(uint64_t x) {  // bits needed to write x (0 for x = 0)
     int b = 0;
     while (b < 64 && (x >> b)) ++b;
@@ -253,7 +259,7 @@ Status validate_instance(const Instance &in) {
     if (in.kind == RPP_INPUT_POINTS && in.dim < 1) return fail(RPP_E_INVALID, "dim must be >= 1");
     if (std::isnan(in.threshold) || in.threshold < 0.0f)
         return fail(RPP_E_INVALID, "threshold must be >= 0 or +INFINITY");
-    if (in.quantile != 0.0f && !(in.quantile > 0.0f && in.quantile <= 1.0f))
+    if (in.quantile != 0.0 && !(in.quantile > 0.0 && in.quantile <= 1.0))
         return fail(RPP_E_INVALID, "quantile must be in (0, 1]");
     // every index up to dimension max_dim + 1 must fit in 63 bits
     std::vector<uint64_t> store;
@@ -286,7 +292,7 @@ size_t instance_device_bytes(const Instance &in) {
     if (in.kind == RPP_INPUT_POINTS) total += slack((size_t)n * in.dim * 4);
     else total += slack((size_t)n * n * 4);
     const size_t per = 4 + 8 + 4 + 8 + 8 + 1 + 8 + 4 + 8 + 8 + sizeof(Leftover);
-    total += slack(maxcand * per) + slack(radix_tile_counts_size(maxcand) * 4) + slack(12 * 256 * 4);
+    total += slack(maxcand * per) + slack(radix_scratch_bytes(maxcand));
     total += slack((size_t)n * 4) + slack(maxcand / 8 + 8) + slack(maxcand * 8);
     total += slack((size_t)n * n * 8);  // neighbour lists
     total += slack(512 + (size_t)n * 32);  // the H0 forest
@@ -369,7 +375,7 @@ static Status apparent_shape(rpp_context *ctx, Workspace &ws, int p, int64_t n, 
     const int fallback = *group;
     float base_ms = 0.0f, best = 0.0f;
     std::vector<std::pair<int, float>> timed;
-    for (int g : {fallback, 8, 82, 42, 44, 4}) {
+    for (int g : {fallback, 8, 82, 42, 44, 4, 141, 142, 181, 121}) {
         if (g == fallback && !timed.empty()) continue;
         float ms = 0.0f, low = 0.0f;
         for (int rep = 0; rep < 4; ++rep) {
@@ -401,33 +407,22 @@ static Status apparent_shape(rpp_context *ctx, Workspace &ws, int p, int64_t n, 
     return Status();
 }
 
-Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStream_t s,
-                    rpp_result *res) {
-    const double t0 = now_ms();
-    double dev_ms = 0.0, red_ms = 0.0, h0_ms = 0.0;
-    RPP_TRY(validate_instance(in));
-    RPP_CK(cudaSetDevice(ws.device));
-    const int64_t n = in.n;
-    const int max_dim = in.max_dim;
-    const int64_t ld = (n + 31) / 32 * 32;
-    res->max_dim = max_dim;
-    for (int q = 0; q <= RPP_MAX_DIM; ++q) {
-        res->iv[q].clear();
-        res->cr[q].clear();
-    }
-    rpp_stats &S = res->stats;
-    std::memset(&S, 0, sizeof S);
-    S.n = n;
-    S.max_dim = max_dim;
-    StageTimer T;
-    T.on = (ctx->record & RPP_RECORD_TIMING) != 0;
-    T.s = s;
-    T.ws = &ws;
-    const long long launches0 = g_launches;
-    unsigned long long scanned_prev = 0;
+// The stages every entry point starts with: the binomial table (rows
+// 0..kmax, cached per workspace), the zeroed device state, the distance
+// matrix (from points with the fixed formula, or a caller's matrix copied and
+// validated) with row stride ld = n rounded up to 32, the enclosing radius R
+// and the threshold st->t = min(t, R) (+inf for a quantile, set later).
+struct Prologue {
+    uint64_t *d_binom = nullptr;
+    DevState *st = nullptr;
+    DevState *hst = nullptr;  // pinned host copy for read-backs
+    float *D = nullptr;
+};
 
-    // binomial table, cached per (n, kmax)
-    const int kmax = max_dim + 2 < 3 ? 3 : max_dim + 2;
+static Status prologue(Workspace &ws, const Instance &in, int kmax, cudaStream_t s, StageTimer &T,
+                       Prologue &P) {
+    const int64_t n = in.n;
+    const int64_t ld = (n + 31) / 32 * 32;
     void *vp;
     if (ws.binom_n != n || ws.binom_k < kmax) {
         fill_binomial(n, kmax, ws.binom_store, ws.binom_host);
@@ -435,7 +430,6 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
         ws.binom_k = kmax;
         ws.binom_on_device = false;
     }
-    const Binomial &B = ws.binom_host;
     RPP_TRY(ws.dev(ws.binom, ws.binom_store.size() * 8, &vp));
     uint64_t *d_binom = (uint64_t *)vp;
     if (!ws.binom_on_device) {
@@ -478,11 +472,128 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
         launch_copy_validate_distances(src, n, D, ld, st, s);
         T.end();
     }
-    const float t_user = in.quantile > 0.0f ? INFINITY : in.threshold;
+    const float t_user = in.quantile > 0.0 ? INFINITY : in.threshold;
     T.begin(ST_RADIUS);
     launch_enclosing_radius(D, n, ld, st, t_user, s);
     T.end();
     RPP_CK(cudaGetLastError());
+    P.d_binom = d_binom;
+    P.st = st;
+    P.hst = hst;
+    P.D = D;
+    return Status();
+}
+
+// The filtration construction of dimension p alone (no clearing): the
+// prologue, every p-simplex with diameter <= min(t, R) built and sorted in
+// coboundary order, then optionally copied to the caller's arrays (device or
+// host memory). The sort's key count stays on the device until the end.
+Status run_filtration(rpp_context *ctx, Workspace &ws, const Instance &in, int p, cudaStream_t s,
+                      float *diam_out, uint64_t *cidx_out, int64_t capacity, int64_t *count,
+                      rpp_stats &S) {
+    const double t0 = now_ms();
+    RPP_TRY(validate_instance(in));
+    if (p < 1 || p > in.max_dim) return fail(RPP_E_INVALID, "p must be in [1, RPP_MAX_DIM]");
+    if (in.n < p + 1) return fail(RPP_E_INVALID, "n must be at least p + 1");
+    RPP_CK(cudaSetDevice(ws.device));
+    const int64_t n = in.n;
+    const int64_t ld = (n + 31) / 32 * 32;
+    std::memset(&S, 0, sizeof S);
+    S.n = n;
+    S.max_dim = p;
+    StageTimer T;
+    T.on = (ctx->record & RPP_RECORD_TIMING) != 0;
+    T.s = s;
+    T.ws = &ws;
+    const long long launches0 = g_launches;
+    Prologue pro;
+    RPP_TRY(prologue(ws, in, std::max(3, p + 2), s, T, pro));
+    const Binomial &B = ws.binom_host;
+    const uint64_t cand = B.at(p + 1, n);
+    S.candidates[p] = (int64_t)cand;
+    uint32_t *key_hi, *tmp_hi;
+    uint64_t *key_lo, *tmp_lo;
+    void *sort_scratch;
+    RPP_TRY(ws.dev(ws.key_hi, cand * 4, (void **)&key_hi));
+    RPP_TRY(ws.dev(ws.key_lo, cand * 8, (void **)&key_lo));
+    RPP_TRY(ws.dev(ws.tmp_hi, cand * 4, (void **)&tmp_hi));
+    RPP_TRY(ws.dev(ws.tmp_lo, cand * 8, (void **)&tmp_lo));
+    RPP_TRY(ws.dev(ws.tiles, radix_scratch_bytes(cand), &sort_scratch));
+    T.begin(ST_BUILD);
+    launch_build_columns(pro.D, ld, n, p, pro.d_binom, cand, nullptr, pro.st, key_hi, key_lo, s);
+    T.end();
+    T.begin(ST_SORT);
+    radix_sort(key_hi, key_lo, nullptr, tmp_hi, tmp_lo, nullptr, sort_scratch, cand,
+               &pro.st->ncols, bits_for(cand - 1), &pro.st->err, s);
+    T.end();
+    RPP_CK(cudaGetLastError());
+    const double a = now_ms();
+    RPP_CK(cudaMemcpyAsync(pro.hst, pro.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    RPP_CK(cudaStreamSynchronize(s));
+    S.ms_device = now_ms() - a;
+    const DevState &h = *pro.hst;
+    if (h.err & ~(unsigned)ERR_INTERNAL) return fail(RPP_E_INVALID, "invalid input distances");
+    if (h.err & ERR_INTERNAL) return fail(RPP_E_CUDA, "a bounded device wait ran out (sort)");
+    const uint64_t N = h.ncols;
+    S.threshold = h.t;
+    S.enclosing_radius = h.R;
+    S.columns[p] = (int64_t)N;
+    *count = (int64_t)N;
+    if (diam_out || cidx_out) {
+        if ((int64_t)N > capacity)
+            return fail(RPP_E_INVALID, "capacity is below the column count (" + std::to_string(N) +
+                                           ")");
+        if (N > 0) {
+            if (diam_out) {  // ~bits(diameter) back to diameters, in the scratch buffer
+                launch_invert_u32(key_hi, N, tmp_hi, s);
+                RPP_CK(cudaMemcpyAsync(diam_out, tmp_hi, N * 4, cudaMemcpyDefault, s));
+            }
+            if (cidx_out) RPP_CK(cudaMemcpyAsync(cidx_out, key_lo, N * 8, cudaMemcpyDefault, s));
+            RPP_CK(cudaStreamSynchronize(s));
+        }
+    }
+    if (T.on) RPP_CK(cudaStreamSynchronize(s));
+    T.collect(S);
+    S.kernel_launches = g_launches - launches0;
+    S.ms_total = now_ms() - t0;
+    return Status();
+}
+
+Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStream_t s,
+                    rpp_result *res) {
+    const double t0 = now_ms();
+    double dev_ms = 0.0, red_ms = 0.0, h0_ms = 0.0;
+    RPP_TRY(validate_instance(in));
+    RPP_CK(cudaSetDevice(ws.device));
+    const int64_t n = in.n;
+    const int max_dim = in.max_dim;
+    const int64_t ld = (n + 31) / 32 * 32;
+    res->max_dim = max_dim;
+    for (int q = 0; q <= RPP_MAX_DIM; ++q) {
+        res->iv[q].clear();
+        res->cr[q].clear();
+    }
+    rpp_stats &S = res->stats;
+    std::memset(&S, 0, sizeof S);
+    S.n = n;
+    S.max_dim = max_dim;
+    StageTimer T;
+    T.on = (ctx->record & RPP_RECORD_TIMING) != 0;
+    T.s = s;
+    T.ws = &ws;
+    const long long launches0 = g_launches;
+    unsigned long long scanned_prev = 0;
+
+    // binomial table, state, distances, enclosing radius and threshold
+    const int kmax = max_dim + 2 < 3 ? 3 : max_dim + 2;
+    void *vp;
+    Prologue pro;
+    RPP_TRY(prologue(ws, in, kmax, s, T, pro));
+    const Binomial &B = ws.binom_host;
+    uint64_t *d_binom = pro.d_binom;
+    DevState *st = pro.st;
+    DevState *hst = pro.hst;
+    float *D = pro.D;
     if (in.census) {  // every edge: neither a threshold nor the enclosing radius
         static const float inf = INFINITY;
         RPP_CK(cudaMemcpyAsync(&st->t, &inf, sizeof(float), cudaMemcpyHostToDevice, s));
@@ -496,7 +607,8 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
     // buffers sized for the largest dimension
     uint64_t maxcand = 0;
     for (int p = 1; p <= std::max(1, max_dim); ++p) maxcand = std::max(maxcand, B.at(p + 1, n));
-    uint32_t *key_hi, *tmp_hi, *tiles, *hist;
+    uint32_t *key_hi, *tmp_hi;
+    void *sort_scratch;
     uint64_t *key_lo, *tmp_lo, *tmp_val, *pivot, *app_tau, *app_sigma;
     uint8_t *status;
     float *pdiam;
@@ -506,8 +618,7 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
     RPP_TRY(ws.dev(ws.tmp_hi, maxcand * 4, (void **)&tmp_hi));
     RPP_TRY(ws.dev(ws.tmp_lo, maxcand * 8, (void **)&tmp_lo));
     RPP_TRY(ws.dev(ws.tmp_val, maxcand * 8, (void **)&tmp_val));
-    RPP_TRY(ws.dev(ws.tiles, radix_tile_counts_size(maxcand) * 4, (void **)&tiles));
-    RPP_TRY(ws.dev(ws.hist, 12 * 256 * 4, (void **)&hist));
+    RPP_TRY(ws.dev(ws.tiles, radix_scratch_bytes(maxcand), &sort_scratch));
     RPP_TRY(ws.dev(ws.status, maxcand, (void **)&status));
     RPP_TRY(ws.dev(ws.pivot, maxcand * 8, (void **)&pivot));
     RPP_TRY(ws.dev(ws.pdiam, maxcand * 4, (void **)&pdiam));
@@ -570,23 +681,27 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
         // ---- dimension 1 columns: every edge inside the threshold, sorted ----
         const uint64_t m = B.at(2, n);
         S.candidates[1] = (int64_t)m;
+        // build, sort, forest, apparent pass and partition are queued without
+        // a host round trip: their column count stays in device memory
+        // (st->ncols), and grids are sized for the m candidates
         T.begin(ST_BUILD);
         launch_build_columns(D, ld, n, 1, d_binom, m, nullptr, st, key_hi, key_lo, s);
         T.end();
         RPP_CK(cudaGetLastError());
-        RPP_TRY(read_state());
-        const uint64_t N = hst->ncols;
         T.begin(ST_SORT);
-        radix_sort(key_hi, key_lo, nullptr, tmp_hi, tmp_lo, nullptr, tiles, hist, N,
-                   bits_for(m - 1), 32, s);
+        radix_sort(key_hi, key_lo, nullptr, tmp_hi, tmp_lo, nullptr, sort_scratch, m, &st->ncols,
+                   bits_for(m - 1), &st->err, s);
         T.end();
         RPP_CK(cudaGetLastError());
         uint64_t begin = 0;
-        if (in.quantile > 0.0f) {
+        uint64_t cols = m;  // a bound until the state is read back
+        const unsigned long long *d_cols = &st->ncols;
+        if (in.quantile > 0.0) {
+            RPP_TRY(read_state());
+            const uint64_t N = hst->ncols;
             // threshold = ceil(q m)-th smallest distance; distances above R were
             // dropped, and if the quantile lies above R, R itself is used.
-            uint64_t r = (uint64_t)std::ceil((double)in.quantile * (double)m);
-            r = std::max<uint64_t>(1, std::min<uint64_t>(r, m));
+            const uint64_t r = quantile_rank(in.quantile, (uint64_t)n);
             if (r <= N) {
                 uint32_t kh;
                 RPP_CK(cudaMemcpyAsync(&kh, key_hi + (N - r), 4, cudaMemcpyDeviceToHost, s));
@@ -599,12 +714,12 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
                 RPP_TRY(read_state());
                 begin = hst->begin;
             }
+            cols = N - begin;
+            d_cols = nullptr;
         }
         S.threshold = t;
         I.t = t;
-        const uint64_t cols = N - begin;
         edges_begin = begin;
-        edges_count = cols;
 
         // ---- H0: the minimum spanning forest inside t, on the device ----
         const double a0 = now_ms();
@@ -619,7 +734,7 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
         if (dim1) {  // its edges are the cleared dimension-1 columns
             RPP_CK(cudaMemsetAsync(status, 0, cols, s));
             T.begin(ST_OTHER);
-            launch_h0_clear(h0_mst, h0_count, n, hi1, lo1, cols, status, h0_pos, s);
+            launch_h0_clear(h0_mst, h0_count, n, hi1, lo1, cols, d_cols, status, h0_pos, s);
             T.end();
             RPP_CK(cudaGetLastError());
         }
@@ -630,6 +745,11 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
                                    cudaMemcpyDeviceToHost, s));
         h0_ms += now_ms() - a0;
         if ((ctx->record & RPP_RECORD_COLUMNS) && max_dim >= 1) {
+            if (d_cols) {
+                RPP_TRY(read_state());
+                cols = hst->ncols;
+                d_cols = nullptr;
+            }
             std::vector<uint32_t> hh(cols);
             std::vector<uint64_t> ll(cols);
             RPP_CK(cudaMemcpyAsync(hh.data(), key_hi + begin, cols * 4, cudaMemcpyDeviceToHost, s));
@@ -649,8 +769,8 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
 
         if (dim1) {
             auto run = [&](int g, DevState *state) {
-                launch_apparent(D, ld, n, 1, d_binom, hi1, lo1, cols, state, status, pivot,
-                                pdiam, g, ctx->sms, s);
+                launch_apparent(D, ld, n, 1, d_binom, hi1, lo1, cols, d_cols, state, status,
+                                pivot, pdiam, g, ctx->sms, s);
             };
             int group;
             RPP_TRY(apparent_shape(ctx, ws, 1, n, st, run, s, &group));
@@ -658,7 +778,8 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
             run(group, st);
             T.end();
             T.begin(ST_PARTITION);
-            launch_partition(status, hi1, lo1, pivot, pdiam, cols, app_tau, app_sigma, left, st, s);
+            launch_partition(status, hi1, lo1, pivot, pdiam, cols, d_cols, app_tau, app_sigma, left,
+                             st, s);
             T.end();
             RPP_CK(cudaGetLastError());
         }
@@ -673,7 +794,8 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
         if (n >= 2) {
             RPP_TRY(read_state());  // the forest's copies are in
             if (hst->err & ERR_INTERNAL)
-                return fail(RPP_E_CUDA, "H0 forest: a root search exceeded its bound");
+                return fail(RPP_E_CUDA, "a bounded device loop or wait ran out (H0 forest or sort)");
+            edges_count = hst->ncols - edges_begin;
             nm = *(const unsigned *)h0_host;
             const unsigned long long *keys = (const unsigned long long *)(h0_host + 16);
             int v[2];
@@ -720,15 +842,19 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
             launch_build_columns(D, ld, n, p, d_binom, cand, bitmap, st, key_hi, key_lo, s);
             T.end();
             RPP_CK(cudaGetLastError());
-            RPP_TRY(read_state());
-            const uint64_t N = hst->ncols;
-            S.columns[p] = (int64_t)N;
+            // as in dimension 1, the count stays on the device until the
+            // partition has run
+            uint64_t N = cand;
+            const unsigned long long *d_n = &st->ncols;
             S.cleared[p] = (int64_t)(prev_napp + prev_deaths.size());
             T.begin(ST_SORT);
-            radix_sort(key_hi, key_lo, nullptr, tmp_hi, tmp_lo, nullptr, tiles, hist, N,
-                       bits_for(cand - 1), 32, s);
+            radix_sort(key_hi, key_lo, nullptr, tmp_hi, tmp_lo, nullptr, sort_scratch, cand,
+                       &st->ncols, bits_for(cand - 1), &st->err, s);
             T.end();
             if (ctx->record & RPP_RECORD_COLUMNS) {
+                RPP_TRY(read_state());
+                N = hst->ncols;
+                d_n = nullptr;
                 std::vector<uint32_t> hh(N);
                 res->col_idx[p].resize(N);
                 RPP_CK(cudaMemcpyAsync(hh.data(), key_hi, N * 4, cudaMemcpyDeviceToHost, s));
@@ -742,8 +868,8 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
             RPP_CK(cudaMemsetAsync(status, 0, N, s));
             RPP_CK(cudaMemsetAsync(&st->napp, 0, 2 * sizeof(unsigned long long), s));
             auto run = [&](int g, DevState *state) {
-                launch_apparent(D, ld, n, p, d_binom, key_hi, key_lo, N, state, status, pivot,
-                                pdiam, g, ctx->sms, s);
+                launch_apparent(D, ld, n, p, d_binom, key_hi, key_lo, N, d_n, state, status,
+                                pivot, pdiam, g, ctx->sms, s);
             };
             int group;
             RPP_TRY(apparent_shape(ctx, ws, p, n, st, run, s, &group));
@@ -751,12 +877,15 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
             run(group, st);
             T.end();
             T.begin(ST_PARTITION);
-            launch_partition(status, key_hi, key_lo, pivot, pdiam, N, app_tau, app_sigma, left,
-                             st, s);
+            launch_partition(status, key_hi, key_lo, pivot, pdiam, N, d_n, app_tau, app_sigma,
+                             left, st, s);
             T.end();
             RPP_CK(cudaGetLastError());
         }
         RPP_TRY(read_state());
+        if (hst->err & ERR_INTERNAL)
+            return fail(RPP_E_CUDA, "a bounded device wait ran out (sort)");
+        if (p >= 2) S.columns[p] = (int64_t)hst->ncols;
         const uint64_t napp = hst->napp, nleft = hst->nleft;
         S.apparent[p] = (int64_t)napp;
         S.leftover[p] = (int64_t)nleft;
@@ -778,7 +907,8 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
             // reduction takes the owner of an apparent tau as its youngest facet)
             T.begin(ST_PAIRSORT);
             radix_sort(nullptr, app_tau, record_app ? app_sigma : nullptr, nullptr, tmp_lo,
-                       tmp_val, tiles, hist, napp, bits_for(B.at(p + 2, n) - 1), 0, s);
+                       tmp_val, sort_scratch, napp, nullptr, bits_for(B.at(p + 2, n) - 1),
+                       &st->err, s);
             T.end();
             RPP_CK(cudaGetLastError());
         }
@@ -821,6 +951,8 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
                 I.edge_ab = nullptr;
                 I.nedges = 0;
             }
+            // the state again (the pair sort's wait flag), read with the copies below
+            RPP_CK(cudaMemcpyAsync(hst, st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
             if (!I.nbr) {  // neighbour lists for the lazy coboundaries, once per instance
                 uint64_t *dn, *hn;
                 RPP_TRY(ws.dev(ws.nbr, (size_t)n * n * 8, (void **)&dn));
@@ -844,6 +976,8 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
                 RPP_CK(cudaStreamSynchronize(s));
                 dev_ms += now_ms() - a;
             }
+            if (hst->err & ERR_INTERNAL)
+                return fail(RPP_E_CUDA, "a bounded device wait ran out (pair sort)");
             double a = now_ms();
             std::sort(hleft, hleft + nleft,
                       [](const Leftover &x, const Leftover &y) { return x.index < y.index; });

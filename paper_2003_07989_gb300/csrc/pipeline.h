@@ -60,6 +60,9 @@ inline const char *source_name(const char *path) {
     return b;
 }
 int bits_for(uint64_t x);  // bits needed to write x (0 for x = 0)
+// Nearest rank of the q-quantile among the C(n, 2) distances: ceil(q C(n, 2)),
+// clamped to [1, C(n, 2)].
+uint64_t quantile_rank(double q, uint64_t n);
 Status fail(rpp_status code, const std::string &msg);
 float bits_to_float(uint32_t b);
 
@@ -107,7 +110,7 @@ struct Instance {
     int32_t dim = 0;
     int32_t max_dim = 1;
     float threshold = INFINITY;
-    float quantile = 0.0f;  // > 0: threshold by quantile
+    double quantile = 0.0;  // > 0: threshold by quantile
     // apparent-pair census: dimension 1 of the full filtration (no threshold,
     // no enclosing-radius cut), stopping after the apparent-pair pass
     bool census = false;
@@ -171,6 +174,10 @@ int64_t batch_bucket(const Instance &in);
 // instances (an upper bound).
 size_t batch_device_bytes(const std::vector<Instance> &ins);
 // Device bytes a workspace holds after running this instance.
+// rpp_filtration: dimension p's columns without clearing, built and sorted.
+Status run_filtration(rpp_context *ctx, Workspace &ws, const Instance &in, int p, cudaStream_t s,
+                      float *diam_out, uint64_t *cidx_out, int64_t capacity, int64_t *count,
+                      rpp_stats &S);
 size_t instance_device_bytes(const Instance &in);
 // Validate an instance before any GPU work.
 Status validate_instance(const Instance &in);

@@ -2,20 +2,29 @@
 // optional 64-bit payload (the "GPU-sort" of Alg. 7, whose implementation the
 // paper leaves open).
 //
-// Keys are 96-bit: a 64-bit low word (the combinatorial index) and a 32-bit
-// high word (the inverted diameter bits). 8-bit digits are processed from the
-// least significant upwards, so each pass must be stable. One histogram kernel
-// first counts every digit position at once; passes whose digit is the same
-// for every key are skipped. Each remaining pass is reduce-then-scan:
-//   count   : per 2048-key tile, a 256-bin histogram of the pass's digit,
-//             stored digit-major (all tiles of digit 0, then digit 1, ...);
-//   scan    : one block per digit: the digit's start among all keys (from the
-//             up-front histogram) plus an exclusive scan over the tiles;
-//   scatter : each tile ranks its keys stably (warp match + per-warp counts in
-//             tile order) and writes them to their final positions.
+// A key is the composite C = ((hi - hi_min) << lo_bits) | lo, where hi_min is
+// the smallest hi among the keys (found on the device) and lo < 2^lo_bits;
+// ascending C is ascending (hi, lo). C is sorted 8 bits at a time, from the
+// least significant digit up, every pass stable. Nothing comes back to the
+// host: the key count may itself live in device memory, and the passes whose
+// digit is the same for every key are skipped by the kernels themselves.
+//   prep    : the smallest hi (one atomic per block);
+//   hist    : one sweep counts every digit position at once;
+//   offsets : per digit position, the exclusive start of each digit value,
+//             whether the pass is needed, and which buffer holds its input
+//             (the parity of the needed passes before it);
+//   onesweep: one kernel per pass. A block takes the next tile of keys (tile
+//             order comes from an atomic ticket, so every tile it waits on
+//             belongs to a block already running), ranks its keys stably
+//             (per-warp match and counts in key order), publishes its digit
+//             counts, adds up the counts of the tiles before it by decoupled
+//             look-back (a tile that knows its inclusive prefix publishes it,
+//             so a look-back stops there), and scatters its keys to their
+//             final positions of this pass. Waits on another tile's entry are
+//             bounded; a wait that runs out sets ERR_INTERNAL and continues.
+//   finish  : copies the keys back into the caller's arrays when an odd
+//             number of passes ran.
 #include <cuda_runtime.h>
-
-#include <vector>
 
 #include "device_common.cuh"
 #include "internal.h"
@@ -25,242 +34,312 @@ namespace rpp {
 namespace {
 
 constexpr int RADIX = 256;
-constexpr int SORT_THREADS = 256;
-constexpr int SORT_ITEMS = 8;
-constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;
-constexpr int MAX_DIGITS = 12;  // 8 low-word digits + 4 high-word digits
+constexpr int MAXP = 12;             // 96-bit composite keys at most
+constexpr int OS_THREADS = 256;
+constexpr int OS_WARPS = OS_THREADS / 32;
+constexpr int OS_ITEMS = 8;          // keys per thread
+constexpr int OS_WARP_KEYS = 32 * OS_ITEMS;
+constexpr int OS_TILE = OS_THREADS * OS_ITEMS;
+static_assert(OS_TILE == RADIX_SORT_TILE, "tile size shared with the scratch bound");
+constexpr uint64_t LB_AGG = 1ull << 62;     // tile count only
+constexpr uint64_t LB_PREFIX = 2ull << 62;  // inclusive count of every tile up to this one
+constexpr uint64_t LB_FLAGS = 3ull << 62;
+constexpr int LB_EPOCH_SHIFT = 56;          // pass + 1 in bits 56..61
+constexpr uint64_t LB_VALUE = (1ull << LB_EPOCH_SHIFT) - 1;
+constexpr long long LB_SPIN_LIMIT = 1ll << 22;
 
-__device__ __forceinline__ unsigned digit_of(const uint32_t *hi, const uint64_t *lo, uint64_t i,
-                                             int sel) {
-    if (sel < 8) return (unsigned)((lo[i] >> (8 * sel)) & 0xffu);
-    return (hi[i] >> (8 * (sel - 8))) & 0xffu;
+// Control block at the start of the scratch; zeroed before each sort.
+struct SortCtl {
+    unsigned long long hist[MAXP][RADIX];
+    unsigned long long start[MAXP][RADIX];  // exclusive start of each digit value
+    unsigned int tile_ticket[MAXP];
+    unsigned int active[MAXP];               // pass needed (its digit is not constant)
+    unsigned int src[MAXP];                  // 1: the pass reads the scratch buffers
+    unsigned int final_src;
+    unsigned int hi_min_inv;                 // ~(smallest hi), so that zero is the start
+    unsigned int pad[3];
+};
+
+static_assert(sizeof(SortCtl) <= RADIX_SORT_CTL_BYTES, "control block bound");
+constexpr size_t ctl_bytes() { return RADIX_SORT_CTL_BYTES; }
+
+__device__ __forceinline__ uint64_t key_count(const unsigned long long *d_count, uint64_t n_cap) {
+    if (!d_count) return n_cap;
+    const uint64_t c = *d_count;
+    return c < n_cap ? c : n_cap;
 }
 
-__global__ void __launch_bounds__(SORT_THREADS) k_hist_all(const uint32_t *__restrict__ hi,
-                                                           const uint64_t *__restrict__ lo,
-                                                           uint64_t n, int nlo, int nhi,
-                                                           uint32_t *__restrict__ hist) {
-    __shared__ uint32_t sh[MAX_DIGITS * RADIX];
-    for (int i = threadIdx.x; i < MAX_DIGITS * RADIX; i += SORT_THREADS) sh[i] = 0;
+template <bool HAS_HI>
+__device__ __forceinline__ unsigned digit_of(uint32_t h, uint64_t l, uint32_t hi_min, int lo_bits,
+                                             int shift) {
+    if constexpr (HAS_HI) {
+        const unsigned __int128 c = ((unsigned __int128)(h - hi_min) << lo_bits) | l;
+        return (unsigned)(c >> shift) & 0xffu;
+    } else {
+        return shift < 64 ? (unsigned)(l >> shift) & 0xffu : 0u;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_sort_prep(const uint32_t *__restrict__ hi, uint64_t n_cap,
+                                                   const unsigned long long *d_count, SortCtl *ctl) {
+    const uint64_t n = key_count(d_count, n_cap);
+    uint32_t m = 0xffffffffu;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        m = min(m, hi[i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(FULL_MASK, m, o));
+    __shared__ uint32_t s_min[8];
+    if ((threadIdx.x & 31) == 0) s_min[threadIdx.x >> 5] = m;
     __syncthreads();
-    const uint64_t stride = (uint64_t)gridDim.x * SORT_THREADS;
-    for (uint64_t i = (uint64_t)blockIdx.x * SORT_THREADS + threadIdx.x; i < n; i += stride) {
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = min(m, s_min[w]);
+        atomicMax(&ctl->hi_min_inv, ~m);
+    }
+}
+
+template <bool HAS_HI>
+__global__ void __launch_bounds__(256) k_sort_hist(const uint32_t *__restrict__ hi,
+                                                   const uint64_t *__restrict__ lo, uint64_t n_cap,
+                                                   const unsigned long long *d_count, int lo_bits,
+                                                   int passes, SortCtl *ctl) {
+    __shared__ unsigned int sh[MAXP * RADIX];
+    for (int i = threadIdx.x; i < passes * RADIX; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+    const uint64_t n = key_count(d_count, n_cap);
+    const uint32_t hmin = HAS_HI ? ~ctl->hi_min_inv : 0u;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const uint64_t l = lo[i];
-        for (int d = 0; d < nlo; ++d) atomicAdd(&sh[d * RADIX + ((l >> (8 * d)) & 0xff)], 1u);
-        if (nhi) {
-            const uint32_t h = hi[i];
-            for (int d = 0; d < nhi; ++d)
-                atomicAdd(&sh[(8 + d) * RADIX + ((h >> (8 * d)) & 0xff)], 1u);
-        }
+        const uint32_t h = HAS_HI ? hi[i] : 0u;
+        for (int p = 0; p < passes; ++p)
+            atomicAdd(&sh[p * RADIX + digit_of<HAS_HI>(h, l, hmin, lo_bits, 8 * p)], 1u);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < MAX_DIGITS * RADIX; i += SORT_THREADS)
-        if (sh[i]) atomicAdd(&hist[i], sh[i]);
+    for (int i = threadIdx.x; i < passes * RADIX; i += blockDim.x)
+        if (sh[i]) atomicAdd(&ctl->hist[i / RADIX][i % RADIX], (unsigned long long)sh[i]);
 }
 
-__global__ void __launch_bounds__(SORT_THREADS) k_count(const uint32_t *__restrict__ hi,
-                                                        const uint64_t *__restrict__ lo, uint64_t n,
-                                                        int sel, uint32_t *__restrict__ counts) {
-    __shared__ uint32_t sh[RADIX];
-    sh[threadIdx.x] = 0;
-    __syncthreads();
-    const uint64_t base = (uint64_t)blockIdx.x * SORT_TILE;
-#pragma unroll
-    for (int j = 0; j < SORT_ITEMS; ++j) {
-        const uint64_t i = base + (uint64_t)j * SORT_THREADS + threadIdx.x;
-        if (i < n) atomicAdd(&sh[digit_of(hi, lo, i, sel)], 1u);
-    }
-    __syncthreads();
-    counts[(uint64_t)threadIdx.x * gridDim.x + blockIdx.x] = sh[threadIdx.x];  // digit-major
-}
-
-// Block d owns digit d: offsets of (tile, d) = keys with a smaller digit (an
-// exclusive scan of the digit totals, redone by every block) + keys with
-// digit d in earlier tiles (an exclusive scan over this digit's tile counts).
-constexpr int SCAN_THREADS = 256;
-
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_digit(uint32_t *__restrict__ counts,
-                                                             uint64_t ntiles,
-                                                             const uint32_t *__restrict__ digit_total) {
-    __shared__ uint32_t warp_sums[SCAN_THREADS / 32];
-    __shared__ uint32_t carry;
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const int d = blockIdx.x;
-    // 1. start of digit d: sum of the totals of digits below d
-    uint32_t x = tid < d ? digit_total[tid] : 0u;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(FULL_MASK, x, o);
-    if (lane == 0) warp_sums[w] = x;
-    __syncthreads();
-    if (tid == 0) {
-        uint32_t b = 0;
-        for (int i = 0; i < SCAN_THREADS / 32; ++i) b += warp_sums[i];
-        carry = b;
-    }
-    __syncthreads();
-    // 2. running exclusive scan over the tiles, SCAN_THREADS tiles per round
-    uint32_t *row = counts + (uint64_t)d * ntiles;
-    for (uint64_t t0 = 0; t0 < ntiles; t0 += SCAN_THREADS) {
-        const uint64_t t = t0 + tid;
-        const uint32_t c = t < ntiles ? row[t] : 0u;
-        uint32_t incl = c;
+// One block of RADIX threads: thread d owns digit value d.
+__global__ void __launch_bounds__(RADIX) k_sort_offsets(uint64_t n_cap,
+                                                        const unsigned long long *d_count,
+                                                        int passes, SortCtl *ctl) {
+    __shared__ unsigned long long s_warp[RADIX / 32];
+    __shared__ unsigned int s_const[MAXP];
+    const uint64_t n = key_count(d_count, n_cap);
+    const int d = threadIdx.x, lane = d & 31, w = d >> 5;
+    for (int p = 0; p < passes; ++p) {
+        const unsigned long long c = ctl->hist[p][d];
+        if (d == 0) s_const[p] = 0;
+        unsigned long long incl = c;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(FULL_MASK, incl, o);
+            const unsigned long long y = __shfl_up_sync(FULL_MASK, incl, o);
             if (lane >= o) incl += y;
         }
-        __syncthreads();  // carry and warp_sums of the previous round are read
-        if (lane == 31) warp_sums[w] = incl;
+        if (lane == 31) s_warp[w] = incl;
         __syncthreads();
-        uint32_t before = carry;
-        for (int i = 0; i < w; ++i) before += warp_sums[i];
-        if (t < ntiles) row[t] = before + incl - c;
+        unsigned long long before = 0;
+        for (int k = 0; k < w; ++k) before += s_warp[k];
+        ctl->start[p][d] = before + incl - c;
+        if (c == n) s_const[p] = 1;  // one digit value holds every key
         __syncthreads();
-        if (tid == SCAN_THREADS - 1) carry = before + incl;
+    }
+    if (d == 0) {
+        unsigned int parity = 0;
+        for (int p = 0; p < passes; ++p) {
+            const unsigned int act = (n > 1 && !s_const[p]) ? 1u : 0u;
+            ctl->active[p] = act;
+            ctl->src[p] = parity;
+            parity ^= act;
+        }
+        ctl->final_src = parity;
     }
 }
 
-__global__ void __launch_bounds__(SORT_THREADS) k_scatter(
-    const uint32_t *__restrict__ hi_in, const uint64_t *__restrict__ lo_in,
-    const uint64_t *__restrict__ val_in, uint32_t *__restrict__ hi_out,
-    uint64_t *__restrict__ lo_out, uint64_t *__restrict__ val_out, uint64_t n, int sel,
-    const uint32_t *__restrict__ offsets) {
-    constexpr int WARPS = SORT_THREADS / 32;
-    __shared__ uint32_t s_run[RADIX];
-    __shared__ uint32_t s_warp[WARPS][RADIX];
+template <bool HAS_HI, bool HAS_VAL>
+__global__ void __launch_bounds__(OS_THREADS) k_onesweep(
+    uint32_t *__restrict__ hi_a, uint64_t *__restrict__ lo_a, uint64_t *__restrict__ val_a,
+    uint32_t *__restrict__ hi_b, uint64_t *__restrict__ lo_b, uint64_t *__restrict__ val_b,
+    uint64_t n_cap, const unsigned long long *d_count, int lo_bits, int pass, SortCtl *ctl,
+    unsigned long long *lookback, unsigned *err) {
+    __shared__ unsigned int s_warp[OS_WARPS][RADIX];  // per-warp counts, then starts
+    __shared__ unsigned long long s_base[RADIX];      // global start of each digit for this tile
+    __shared__ unsigned int s_tile;
+    if (!ctl->active[pass]) return;
+    const uint64_t n = key_count(d_count, n_cap);
+    const uint64_t ntiles = (n + OS_TILE - 1) / OS_TILE;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    s_run[tid] = offsets[(uint64_t)tid * gridDim.x + blockIdx.x];
-    const uint64_t base = (uint64_t)blockIdx.x * SORT_TILE;
-    for (int j = 0; j < SORT_ITEMS; ++j) {
-        const uint64_t i = base + (uint64_t)j * SORT_THREADS + tid;
-        const bool valid = i < n;
-        const unsigned d = valid ? digit_of(hi_in, lo_in, i, sel) : RADIX;
+    if (tid == 0) s_tile = atomicAdd(&ctl->tile_ticket[pass], 1u);
 #pragma unroll
-        for (int k = 0; k < WARPS; ++k) s_warp[k][tid] = 0;
-        __syncthreads();
-        const unsigned peers = __match_any_sync(FULL_MASK, d);
-        const unsigned rank = __popc(peers & lanemask_lt());
-        if (valid && rank == 0) s_warp[w][d] = __popc(peers);
-        __syncthreads();
-        {  // thread tid owns digit tid: exclusive scan over the warps of this round
-            uint32_t run = s_run[tid];
+    for (int k = 0; k < OS_WARPS; ++k) s_warp[k][tid] = 0;
+    __syncthreads();
+    const uint64_t tile = s_tile;
+    if (tile >= ntiles) return;  // grids are sized for the largest count
+    const bool from_b = ctl->src[pass] != 0;
+    const uint32_t *hs = from_b ? hi_b : hi_a;
+    const uint64_t *ls = from_b ? lo_b : lo_a;
+    const uint64_t *vs = from_b ? val_b : val_a;
+    uint32_t *hd = from_b ? hi_a : hi_b;
+    uint64_t *ld = from_b ? lo_a : lo_b;
+    uint64_t *vd = from_b ? val_a : val_b;
+    const uint32_t hmin = HAS_HI ? ~ctl->hi_min_inv : 0u;
+    const int shift = 8 * pass;
+
+    // keys of this warp: item j of lane l is key base + j * 32 + l (key order
+    // is (warp, item, lane), so per-warp ranks in item order are stable)
+    const uint64_t base = tile * OS_TILE + (uint64_t)w * OS_WARP_KEYS;
+    uint64_t kl[OS_ITEMS], kv[OS_ITEMS];
+    uint32_t kh[OS_ITEMS];
+    unsigned dg[OS_ITEMS], rk[OS_ITEMS];
 #pragma unroll
-            for (int k = 0; k < WARPS; ++k) {
-                uint32_t c = s_warp[k][tid];
-                s_warp[k][tid] = run;
-                run += c;
+    for (int j = 0; j < OS_ITEMS; ++j) {
+        const uint64_t i = base + (uint64_t)j * 32 + lane;
+        const bool ok = i < n;
+        kl[j] = ok ? ls[i] : 0;
+        kh[j] = (HAS_HI && ok) ? hs[i] : 0u;
+        if constexpr (HAS_VAL) kv[j] = ok ? vs[i] : 0;
+        dg[j] = ok ? digit_of<HAS_HI>(kh[j], kl[j], hmin, lo_bits, shift) : RADIX;
+    }
+#pragma unroll
+    for (int j = 0; j < OS_ITEMS; ++j) {
+        const unsigned peers = __match_any_sync(FULL_MASK, dg[j]);
+        const unsigned before = __popc(peers & lanemask_lt());
+        const unsigned cnt = dg[j] < RADIX ? s_warp[w][dg[j]] : 0u;
+        rk[j] = cnt + before;
+        __syncwarp();
+        if (dg[j] < RADIX && before == 0) s_warp[w][dg[j]] = cnt + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // thread tid owns digit value tid: starts of each warp's run, tile count
+    unsigned int run = 0;
+#pragma unroll
+    for (int k = 0; k < OS_WARPS; ++k) {
+        const unsigned int c = s_warp[k][tid];
+        s_warp[k][tid] = run;
+        run += c;
+    }
+    const uint64_t epoch = (uint64_t)(pass + 1) << LB_EPOCH_SHIFT;
+    unsigned long long *mine = lookback + tile * RADIX + tid;
+    if (tile == 0) {
+        atomicExch(mine, (unsigned long long)(LB_PREFIX | epoch | run));
+        s_base[tid] = ctl->start[pass][tid];
+    } else {
+        atomicExch(mine, (unsigned long long)(LB_AGG | epoch | run));
+        uint64_t excl = 0;
+        for (int64_t t = (int64_t)tile - 1; t >= 0; --t) {
+            const volatile unsigned long long *e =
+                (const volatile unsigned long long *)(lookback + (uint64_t)t * RADIX + tid);
+            unsigned long long v = *e;
+            long long spins = 0;
+            while (((v & LB_FLAGS) == 0 || (v & ~LB_FLAGS & ~LB_VALUE) != epoch) &&
+                   spins < LB_SPIN_LIMIT) {
+                if (spins > 64) __nanosleep(64);
+                ++spins;
+                v = *e;
             }
-            s_run[tid] = run;
+            if (spins >= LB_SPIN_LIMIT) {  // never expected: report and go on
+                atomicOr(err, ERR_INTERNAL);
+                break;
+            }
+            excl += v & LB_VALUE;
+            if ((v & LB_FLAGS) == LB_PREFIX) break;
         }
-        __syncthreads();
-        if (valid) {
-            const uint32_t pos = s_warp[w][d] + rank;
-            lo_out[pos] = lo_in[i];
-            if (hi_in) hi_out[pos] = hi_in[i];
-            if (val_in) val_out[pos] = val_in[i];
+        atomicExch(mine, (unsigned long long)(LB_PREFIX | epoch | (excl + run)));
+        s_base[tid] = ctl->start[pass][tid] + excl;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < OS_ITEMS; ++j) {
+        if (dg[j] < RADIX) {
+            const uint64_t pos = s_base[dg[j]] + s_warp[w][dg[j]] + rk[j];
+            if (pos < n) {  // always: the counts partition the keys
+                ld[pos] = kl[j];
+                if constexpr (HAS_HI) hd[pos] = kh[j];
+                if constexpr (HAS_VAL) vd[pos] = kv[j];
+            }
         }
-        __syncthreads();
+    }
+}
+
+// After the passes: keys that ended in the scratch buffers go back.
+__global__ void __launch_bounds__(256) k_sort_finish(uint32_t *__restrict__ hi,
+                                                     uint64_t *__restrict__ lo,
+                                                     uint64_t *__restrict__ val,
+                                                     const uint32_t *__restrict__ thi,
+                                                     const uint64_t *__restrict__ tlo,
+                                                     const uint64_t *__restrict__ tval,
+                                                     uint64_t n_cap,
+                                                     const unsigned long long *d_count,
+                                                     const SortCtl *ctl) {
+    if (!ctl->final_src) return;
+    const uint64_t n = key_count(d_count, n_cap);
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        lo[i] = tlo[i];
+        if (hi) hi[i] = thi[i];
+        if (val) val[i] = tval[i];
+    }
+}
+
+template <bool HAS_HI, bool HAS_VAL>
+void sort_passes(uint32_t *hi, uint64_t *lo, uint64_t *val, uint32_t *thi, uint64_t *tlo,
+                 uint64_t *tval, SortCtl *ctl, unsigned long long *lookback, uint64_t n_cap,
+                 const unsigned long long *d_count, int lo_bits, int passes, unsigned *err,
+                 cudaStream_t s) {
+    const uint64_t ntiles = (n_cap + OS_TILE - 1) / OS_TILE;
+    for (int p = 0; p < passes; ++p) {
+        ++g_launches;
+        k_onesweep<HAS_HI, HAS_VAL><<<(unsigned)ntiles, OS_THREADS, 0, s>>>(
+            hi, lo, val, thi, tlo, tval, n_cap, d_count, lo_bits, p, ctl, lookback, err);
     }
 }
 
 }  // namespace
 
-size_t radix_tile_counts_size(uint64_t n) {
-    return (size_t)((n + SORT_TILE - 1) / SORT_TILE) * RADIX;
-}
+size_t radix_scratch_bytes(uint64_t n_cap) { return radix_scratch_bound(n_cap); }
 
 void radix_sort(uint32_t *hi, uint64_t *lo, uint64_t *val, uint32_t *tmp_hi, uint64_t *tmp_lo,
-                uint64_t *tmp_val, uint32_t *tile_counts, uint32_t *digit_hist, uint64_t n,
-                int lo_bits, int hi_bits, cudaStream_t s) {
-    if (n <= 1) return;
-    // absent key halves or payloads have no scratch either, so the buffer
-    // swaps below never pair a null array with a live one
-    if (!hi) tmp_hi = nullptr;
-    if (!val) tmp_val = nullptr;
-    const int nlo = (lo_bits + 7) / 8, nhi = hi ? (hi_bits + 7) / 8 : 0;
-    cudaMemsetAsync(digit_hist, 0, MAX_DIGITS * RADIX * sizeof(uint32_t), s);
-    uint64_t hb = (n + SORT_THREADS - 1) / SORT_THREADS;
+                uint64_t *tmp_val, void *scratch, uint64_t n_cap,
+                const unsigned long long *d_count, int lo_bits, unsigned *err, cudaStream_t s) {
+    if (n_cap <= 1) return;
+    if (lo_bits < 1) lo_bits = 1;
+    const int bits = lo_bits + (hi ? 32 : 0);
+    int passes = (bits + 7) / 8;
+    if (passes > MAXP) passes = MAXP;
+    SortCtl *ctl = (SortCtl *)scratch;
+    unsigned long long *lookback = (unsigned long long *)((char *)scratch + ctl_bytes());
+    cudaMemsetAsync(scratch, 0, radix_scratch_bytes(n_cap), s);
+    uint64_t hb = (n_cap + 255) / 256;
     if (hb > 152 * 4) hb = 152 * 4;
+    if (hi) {
+        ++g_launches;
+        k_sort_prep<<<(unsigned)hb, 256, 0, s>>>(hi, n_cap, d_count, ctl);
+        ++g_launches;
+        k_sort_hist<true><<<(unsigned)hb, 256, 0, s>>>(hi, lo, n_cap, d_count, lo_bits, passes, ctl);
+    } else {
+        ++g_launches;
+        k_sort_hist<false><<<(unsigned)hb, 256, 0, s>>>(hi, lo, n_cap, d_count, lo_bits, passes,
+                                                        ctl);
+    }
     ++g_launches;
-    k_hist_all<<<(unsigned)hb, SORT_THREADS, 0, s>>>(hi, lo, n, nlo, nhi, digit_hist);
-    std::vector<uint32_t> h(MAX_DIGITS * RADIX);
-    cudaMemcpyAsync(h.data(), digit_hist, h.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
-    cudaStreamSynchronize(s);
-    std::vector<int> passes;
-    for (int d = 0; d < MAX_DIGITS; ++d) {
-        if (d < 8 && d >= nlo) continue;
-        if (d >= 8 && d - 8 >= nhi) continue;
-        bool constant = false;
-        for (int b = 0; b < RADIX; ++b)
-            if (h[d * RADIX + b] == n) constant = true;
-        if (!constant) passes.push_back(d);
-    }
-    const uint64_t ntiles = (n + SORT_TILE - 1) / SORT_TILE;
-    uint32_t *hi_a = hi, *hi_b = tmp_hi;
-    uint64_t *lo_a = lo, *lo_b = tmp_lo, *val_a = val, *val_b = tmp_val;
-    for (int sel : passes) {
-        ++g_launches;
-        k_count<<<(unsigned)ntiles, SORT_THREADS, 0, s>>>(hi_a, lo_a, n, sel, tile_counts);
-        ++g_launches;
-        k_scan_digit<<<RADIX, SCAN_THREADS, 0, s>>>(tile_counts, ntiles, digit_hist + sel * RADIX);
-        ++g_launches;
-        k_scatter<<<(unsigned)ntiles, SORT_THREADS, 0, s>>>(
-            hi_a, lo_a, val_a, hi_a ? hi_b : nullptr, lo_b, val_a ? val_b : nullptr, n, sel,
-            tile_counts);
-        std::swap(hi_a, hi_b);
-        std::swap(lo_a, lo_b);
-        std::swap(val_a, val_b);
-    }
-    if (passes.size() & 1) {  // result sits in the scratch buffers: copy it back
-        cudaMemcpyAsync(lo, lo_a, n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s);
-        if (hi) cudaMemcpyAsync(hi, hi_a, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
-        if (val) cudaMemcpyAsync(val, val_a, n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s);
-    }
-}
-
-// The same sort driven without any allocation: the histogram comes back into
-// the caller's host buffer host_hist (12 * 256 entries), and no payload.
-void radix_sort_noalloc(uint32_t *hi, uint64_t *lo, uint32_t *tmp_hi, uint64_t *tmp_lo,
-                        uint32_t *tile_counts, uint32_t *digit_hist, uint32_t *host_hist,
-                        uint64_t n, int lo_bits, int hi_bits, cudaStream_t s) {
-    if (n <= 1) return;
-    const int nlo = (lo_bits + 7) / 8, nhi = (hi_bits + 7) / 8;
-    cudaMemsetAsync(digit_hist, 0, MAX_DIGITS * RADIX * sizeof(uint32_t), s);
-    uint64_t hb = (n + SORT_THREADS - 1) / SORT_THREADS;
-    if (hb > 152 * 4) hb = 152 * 4;
+    k_sort_offsets<<<1, RADIX, 0, s>>>(n_cap, d_count, passes, ctl);
+    if (hi && val)
+        sort_passes<true, true>(hi, lo, val, tmp_hi, tmp_lo, tmp_val, ctl, lookback, n_cap, d_count,
+                                lo_bits, passes, err, s);
+    else if (hi)
+        sort_passes<true, false>(hi, lo, nullptr, tmp_hi, tmp_lo, nullptr, ctl, lookback, n_cap,
+                                 d_count, lo_bits, passes, err, s);
+    else if (val)
+        sort_passes<false, true>(nullptr, lo, val, nullptr, tmp_lo, tmp_val, ctl, lookback, n_cap,
+                                 d_count, lo_bits, passes, err, s);
+    else
+        sort_passes<false, false>(nullptr, lo, nullptr, nullptr, tmp_lo, nullptr, ctl, lookback,
+                                  n_cap, d_count, lo_bits, passes, err, s);
     ++g_launches;
-    k_hist_all<<<(unsigned)hb, SORT_THREADS, 0, s>>>(hi, lo, n, nlo, nhi, digit_hist);
-    cudaMemcpyAsync(host_hist, digit_hist, MAX_DIGITS * RADIX * sizeof(uint32_t),
-                    cudaMemcpyDeviceToHost, s);
-    cudaStreamSynchronize(s);
-    int passes[MAX_DIGITS], np = 0;
-    for (int d = 0; d < MAX_DIGITS; ++d) {
-        if (d < 8 && d >= nlo) continue;
-        if (d >= 8 && d - 8 >= nhi) continue;
-        bool constant = false;
-        for (int b = 0; b < RADIX; ++b)
-            if (host_hist[d * RADIX + b] == n) constant = true;
-        if (!constant) passes[np++] = d;
-    }
-    const uint64_t ntiles = (n + SORT_TILE - 1) / SORT_TILE;
-    uint32_t *hi_a = hi, *hi_b = tmp_hi;
-    uint64_t *lo_a = lo, *lo_b = tmp_lo;
-    for (int k = 0; k < np; ++k) {
-        const int sel = passes[k];
-        ++g_launches;
-        k_count<<<(unsigned)ntiles, SORT_THREADS, 0, s>>>(hi_a, lo_a, n, sel, tile_counts);
-        ++g_launches;
-        k_scan_digit<<<RADIX, SCAN_THREADS, 0, s>>>(tile_counts, ntiles, digit_hist + sel * RADIX);
-        ++g_launches;
-        k_scatter<<<(unsigned)ntiles, SORT_THREADS, 0, s>>>(hi_a, lo_a, nullptr, hi_b, lo_b,
-                                                            nullptr, n, sel, tile_counts);
-        std::swap(hi_a, hi_b);
-        std::swap(lo_a, lo_b);
-    }
-    if (np & 1) {
-        cudaMemcpyAsync(lo, lo_a, n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s);
-        cudaMemcpyAsync(hi, hi_a, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
-    }
+    k_sort_finish<<<(unsigned)hb, 256, 0, s>>>(hi, lo, val, tmp_hi, tmp_lo, tmp_val, n_cap, d_count,
+                                               ctl);
 }
 
 }  // namespace rpp

@@ -205,7 +205,7 @@ rpp_status rpp_server_create(rpp_context *ctx, const rpp_server_config *cfg, rpp
 }
 
 rpp_status rpp_server_submit(rpp_server *srv, const float *points, int64_t n, int32_t dim,
-                             int32_t max_dim, float threshold, float quantile, uint64_t *ticket) {
+                             int32_t max_dim, float threshold, double quantile, uint64_t *ticket) {
     if (!srv || !points || !ticket) {
         set_last_error("rpp_server_submit: invalid arguments");
         return RPP_E_INVALID;

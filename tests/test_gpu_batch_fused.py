@@ -139,7 +139,9 @@ def test_large_buckets_match_oracle(rpp, lo, hi, nmax):
         assert lo <= r.points.shape[0] <= hi
         D = O.distance_matrix(r.points)
         t = O.distance_quantile(D, r.threshold_quantile)
-        assert a.stats["threshold"] == t
+        # the library cuts at min(t, enclosing radius), which leaves every
+        # nonzero interval unchanged; the oracle takes t itself
+        assert a.stats["threshold"] == min(t, O.enclosing_radius(D))
         res = O.barcodes(D, 1, t)
         for q in (0, 1):
             assert np.array_equal(a.intervals[q], res.barcode(q)), (r.index, r.kind, q)
