@@ -451,6 +451,49 @@ def filtration_bench(rpp, torch, dev, reps: int = 5):
         torch.cuda.empty_cache()
 
 
+def sparse_bench(rpp, torch, dev, reps: int = 3, t: float = 1.4, max_dim: int = 2):
+    """The thresholded workload (the paper's sparse o3 row): 4096 random
+    matrices of O(3) as points of R^9, threshold 1.4 (about 2.8% of the
+    edges), H0-H2. C(4096, 3) > 2^32, so only the thresholded construction of
+    dimension 2 (cliques of the threshold graph) can run it. Times the whole
+    call from device-resident points (CUDA events), its stages, and the
+    dimension-2 columns per second through the apparent-pair pass."""
+    from paper_2003_07989_gb300 import _native as N
+    from paper_2003_07989_gb300 import inputs as I
+    X = torch.from_numpy(I.orthogonal3(4096, seed=0)).to(dev)
+    ctx = rpp.Context(dev.index or 0, record=N.RPP_RECORD_TIMING)
+    try:
+        rpp.rpp_barcodes(X, max_dim=max_dim, threshold=t, context=ctx)  # allocation, tuning
+        stream = torch.cuda.current_stream(dev)
+        times, res = [], None
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = rpp.rpp_barcodes(X, max_dim=max_dim, threshold=t, context=ctx)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        st = res.stats
+        ms = statistics.median(times)
+        return {
+            "workload": f"4096 random O(3) matrices in R^9 (seed 0), threshold {t}, "
+                        f"H0-H{max_dim}, thresholded construction of dimensions >= 2",
+            "ms": ms, "sparse": st["sparse"][:max_dim + 1],
+            "edges_inside_t": st["columns"][1] + st["cleared"][1],
+            "columns": st["columns"][:max_dim + 1], "apparent": st["apparent"][:max_dim + 1],
+            "leftover": st["leftover"][:max_dim + 1],
+            "intervals": [len(iv) for iv in res.intervals],
+            "stage_ms": dict(zip(N.STAGES, [round(x, 4) for x in st["stage_ms"]])),
+            "host_reduce_ms": st["ms_host_reduce"],
+            "simplices_per_s": sum(st["columns"][1:max_dim + 1]) / (ms / 1e3),
+        }
+    finally:
+        ctx.close()
+        del X
+        torch.cuda.empty_cache()
+
+
 def census_bench(rpp, torch, dev, ctx):
     """Dimension-1 apparent fraction of uniformly random total orders of the
     C(n,2) edges (the paper's random permutations of 1..C(n,2)), full
@@ -681,6 +724,7 @@ def main():
     backward = None if args.no_extras else backward_bench(rpp, torch, dev)
     sphere = None if args.no_extras else sphere_bench(rpp, torch, dev)
     filtration = None if args.no_extras else filtration_bench(rpp, torch, dev)
+    sparse = None if args.no_extras else sparse_bench(rpp, torch, dev)
     h2d = X.nbytes
     d2h = sum(len(iv) * (8 + 16) for iv in e2e_results[0].intervals)
     line = {
@@ -700,6 +744,7 @@ def main():
         "differentiation": backward,
         "sphere_h2": sphere,
         "filtration_dim2": filtration,
+        "thresholded_o3": sparse,
         "breakdown": {
             "kernels": kernels,
             "host_reduce_ms": statistics.mean(s["ms_host_reduce"] for s in st),

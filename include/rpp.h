@@ -120,6 +120,8 @@ typedef struct {
     double ms_host_reduce;                /* wall time of the submatrix reductions */
     double ms_host_h0;                    /* wall time of the H0 stage (forest, intervals) */
     double ms_total;
+    int64_t sparse[RPP_MAX_DIM + 1];      /* 1 where dimension p's columns were built as cliques
+                                             of the threshold graph (rpp_context_set_sparse) */
 } rpp_stats;
 
 typedef struct rpp_context rpp_context;
@@ -255,6 +257,21 @@ rpp_status rpp_barcodes_batched(rpp_context *ctx, int32_t batch, const float *co
  * shape gives the same results). Both default to 1. Errors: RPP_E_INVALID for
  * a NULL context. */
 rpp_status rpp_context_set_batch(rpp_context *ctx, int32_t fused, int32_t autotune);
+
+/* How dimensions p >= 2 are built (Sec. "Computation Induced by Sparse
+ * 1-Skeletons"). With a threshold t far below the enclosing radius most of the
+ * C(n, p+1) indices name simplices with an edge longer than t; the thresholded
+ * construction instead lists the cliques of the graph of edges inside t
+ * (every p-simplex from its facet without its lowest vertex and a common
+ * neighbour below it), clears by binary search in the previous dimension's
+ * sorted deaths, and tests apparent pairs over neighbour lists only. Both
+ * constructions give the same columns and barcodes.
+ *   mode 0 (default): thresholded when fewer than a quarter of the C(n, 2)
+ *          edges lie inside t, or when C(n, p+1) >= 2^32;
+ *   mode 1: always thresholded; mode 2: never (C(n, p+1) >= 2^32 then fails
+ *          with RPP_E_NOMEM).
+ * Errors: RPP_E_INVALID for a NULL context or another mode. */
+rpp_status rpp_context_set_sparse(rpp_context *ctx, int32_t mode);
 
 /* The launch shape the autotuner chose for the bucket of clouds with up to
  * nmax points (64, 128, 256, 512 or 1024): threads per block and the

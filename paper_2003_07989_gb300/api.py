@@ -44,6 +44,11 @@ class Context:
         N.check(N.lib().rpp_context_set_batch(self.handle, int(fused), int(autotune)),
                 "rpp_context_set_batch")
 
+    def set_sparse(self, mode: int = 0):
+        """rpp_context_set_sparse: 0 chooses the thresholded construction of
+        dimensions >= 2 by edge density, 1 always takes it, 2 never."""
+        N.check(N.lib().rpp_context_set_sparse(self.handle, int(mode)), "rpp_context_set_sparse")
+
     def batch_tuning(self, nmax: int):
         """(threads, lanes per column) the autotuner chose for a size bucket,
         (0, 0) if it has not run."""

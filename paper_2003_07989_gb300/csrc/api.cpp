@@ -201,6 +201,15 @@ rpp_status rpp_filtration(rpp_context *ctx, const float *data, rpp_input_kind ki
     return report(st);
 }
 
+rpp_status rpp_context_set_sparse(rpp_context *ctx, int32_t mode) {
+    if (!ctx || mode < 0 || mode > 2) {
+        set_last_error("rpp_context_set_sparse: NULL context or mode not in 0..2");
+        return RPP_E_INVALID;
+    }
+    ctx->sparse_mode = mode;
+    return RPP_OK;
+}
+
 int64_t rpp_result_count(const rpp_result *res, int32_t p) {
     if (!res || p < 0 || p > res->max_dim) return -1;
     return (int64_t)res->iv[p].size();

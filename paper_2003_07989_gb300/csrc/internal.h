@@ -149,6 +149,34 @@ bool launch_sort_rows(const float *D, int64_t ld, int64_t n, uint64_t *out, cuda
 // Set bit `idx[i]` of a bitmap for every i.
 void launch_bitmap_set(const uint64_t *idx, uint64_t count, uint32_t *bitmap, cudaStream_t s);
 
+// ---- thresholded (sparse 1-skeleton) construction, dimensions p >= 2 --------
+
+// Neighbour lists of the threshold graph (D[a][w] <= st->t, w != a), ascending.
+// fill = false: off[0..n] = offsets (off holds n + 1 entries); fill = true:
+// nbr[off[a] .. off[a+1]) = the neighbours of a (nbr holds off[n] entries).
+void launch_csr_build(const float *D, int64_t ld, int64_t n, const DevState *st,
+                      unsigned long long *off, uint32_t *nbr, bool fill, cudaStream_t s);
+// The p-simplices inside st->t, each found from its facet without its lowest
+// vertex among the (p-1)-simplices `prev` (indices; every (p-1)-simplex inside
+// t must be listed). Clearing: indices in dead_a or dead_b (sorted) are not
+// columns. write = false counts into cnt[0] (simplices) and cnt[1] (columns);
+// write = true appends columns (key_hi = ~bits(diam), key_lo = index; at most
+// col_cap) and, if all_out is given, every simplex's index (at most all_cap),
+// advancing cnt[1] and cnt[0] (zero them first).
+void launch_sparse_build(const float *D, int64_t ld, int64_t n, int p, const uint64_t *binom,
+                         const uint64_t *prev, uint64_t nprev, const unsigned long long *off,
+                         const uint32_t *nbr, const DevState *st, const uint64_t *dead_a,
+                         uint64_t ndead_a, const uint64_t *dead_b, uint64_t ndead_b, bool write,
+                         unsigned long long *cnt, uint32_t *key_hi, uint64_t *key_lo,
+                         uint64_t col_cap, uint64_t *all_out, uint64_t all_cap, cudaStream_t s);
+// The apparent-pair pass over sorted columns of dimension p with candidates
+// from the neighbour lists (same outputs as launch_apparent).
+void launch_apparent_sparse(const float *D, int64_t ld, int64_t n, int p, const uint64_t *binom,
+                            const unsigned long long *off, const uint32_t *nbr,
+                            const uint32_t *key_hi, const uint64_t *key_lo, uint64_t ncols,
+                            const unsigned long long *d_ncols, DevState *st, uint8_t *status,
+                            uint64_t *pivot, float *pdiam, int sms, cudaStream_t s);
+
 // ---- fused batch of small clouds, dimensions 0 and 1 ------------------------
 
 constexpr int BATCH_NMAX = 1024;  // largest cloud of the fused pass

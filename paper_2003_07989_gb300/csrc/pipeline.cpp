@@ -60,7 +60,8 @@ float bits_to_float(uint32_t b) {
 Workspace::~Workspace() {
     DevBuf *d[] = {&X,    &Dsrc,  &D,      &state,   &binom,     &key_hi, &key_lo,
                    &tmp_hi, &tmp_lo, &tmp_val, &tiles, &hist,      &status, &pivot,
-                   &pdiam, &app_tau, &app_sigma, &left, &bitmap, &mst,    &up, &nbr, &h0};
+                   &pdiam, &app_tau, &app_sigma, &left, &bitmap, &mst,    &up, &nbr, &h0,
+                   &state_tune, &csr_off, &csr_nbr, &sp_a, &sp_b, &sp_c, &sp_cnt};
     for (DevBuf *b : d)
         if (b->p) cudaFree(b->p);
     HostBuf *h[] = {&h_hi,    &h_lo,  &h_tau, &h_sigma, &h_left,
@@ -270,9 +271,6 @@ Status validate_instance(const Instance &in) {
     // H0's forest keys hold 32-bit edge indices (for max_dim = 0 too)
     if ((uint64_t)in.n * (uint64_t)(in.n - 1) / 2 >= (1ull << 32))
         return fail(RPP_E_OVERFLOW, "C(n, 2) does not fit the 32-bit edge index (n > 92682)");
-    for (int p = 1; p <= in.max_dim; ++p)
-        if (B.at(p + 1, in.n) >= (1ull << 32))
-            return fail(RPP_E_NOMEM, "more than 2^32 candidate simplices in one dimension");
     return Status();
 }
 
@@ -510,6 +508,8 @@ Status run_filtration(rpp_context *ctx, Workspace &ws, const Instance &in, int p
     RPP_TRY(prologue(ws, in, std::max(3, p + 2), s, T, pro));
     const Binomial &B = ws.binom_host;
     const uint64_t cand = B.at(p + 1, n);
+    if (cand >= (1ull << 32))
+        return fail(RPP_E_NOMEM, "more than 2^32 candidate simplices in dimension p");
     S.candidates[p] = (int64_t)cand;
     uint32_t *key_hi, *tmp_hi;
     uint64_t *key_lo, *tmp_lo;
@@ -605,8 +605,8 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
     RPP_CK(cudaMemcpyAsync(hD, D, (size_t)n * ld * sizeof(float), cudaMemcpyDeviceToHost, s));
 
     // buffers sized for the largest dimension
-    uint64_t maxcand = 0;
-    for (int p = 1; p <= std::max(1, max_dim); ++p) maxcand = std::max(maxcand, B.at(p + 1, n));
+    // sized for dimension 1 here; dimensions p >= 2 grow them to their need
+    const uint64_t maxcand = std::max<uint64_t>(1, B.at(2, n));
     uint32_t *key_hi, *tmp_hi;
     void *sort_scratch;
     uint64_t *key_lo, *tmp_lo, *tmp_val, *pivot, *app_tau, *app_sigma;
@@ -625,6 +625,41 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
     RPP_TRY(ws.dev(ws.app_tau, maxcand * 8, (void **)&app_tau));
     RPP_TRY(ws.dev(ws.app_sigma, maxcand * 8, (void **)&app_sigma));
     RPP_TRY(ws.dev(ws.left, maxcand * sizeof(Leftover), (void **)&left));
+    // Growth for a dimension p >= 2 of `cap` columns: the key arrays and the
+    // sort's scratch before its build (they hold nothing live then), the
+    // per-column outputs after it (the build may read the previous
+    // dimension's apparent taus). A buffer that grows is reallocated, so the
+    // stream is drained first.
+    auto grow_columns = [&](uint64_t cap) -> Status {
+        cap = std::max<uint64_t>(1, cap);
+        if (ws.key_lo.bytes < cap * 8 || ws.tiles.bytes < radix_scratch_bytes(cap))
+            RPP_CK(cudaStreamSynchronize(s));
+        RPP_TRY(ws.dev(ws.key_hi, cap * 4, (void **)&key_hi));
+        RPP_TRY(ws.dev(ws.key_lo, cap * 8, (void **)&key_lo));
+        RPP_TRY(ws.dev(ws.tmp_hi, cap * 4, (void **)&tmp_hi));
+        RPP_TRY(ws.dev(ws.tmp_lo, cap * 8, (void **)&tmp_lo));
+        RPP_TRY(ws.dev(ws.tiles, radix_scratch_bytes(cap), &sort_scratch));
+        return Status();
+    };
+    auto grow_outputs = [&](uint64_t cap) -> Status {
+        cap = std::max<uint64_t>(1, cap);
+        if (ws.app_tau.bytes < cap * 8 || ws.left.bytes < cap * sizeof(Leftover))
+            RPP_CK(cudaStreamSynchronize(s));
+        RPP_TRY(ws.dev(ws.tmp_val, cap * 8, (void **)&tmp_val));
+        RPP_TRY(ws.dev(ws.status, cap, (void **)&status));
+        RPP_TRY(ws.dev(ws.pivot, cap * 8, (void **)&pivot));
+        RPP_TRY(ws.dev(ws.pdiam, cap * 4, (void **)&pdiam));
+        RPP_TRY(ws.dev(ws.app_tau, cap * 8, (void **)&app_tau));
+        RPP_TRY(ws.dev(ws.app_sigma, cap * 8, (void **)&app_sigma));
+        RPP_TRY(ws.dev(ws.left, cap * sizeof(Leftover), (void **)&left));
+        return Status();
+    };
+    // the thresholded construction's state (dimensions p >= 2)
+    unsigned long long *csr_off = nullptr;
+    uint32_t *csr_nbr = nullptr;
+    uint64_t *sp_prev = nullptr;  // every simplex of the last sparse dimension
+    uint64_t sp_prev_count = 0;
+    bool sp_prev_valid = false;
 
     auto read_state = [&]() -> Status {
         double a = now_ms();
@@ -815,40 +850,130 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
         }
     }
 
+    // Dimensions p >= 2 take the thresholded construction (cliques of the
+    // threshold graph) when the edges inside t are a small share of all
+    // edges, or when some C(n, p+1) is too large to enumerate; else every
+    // index. One choice for all of them: a thresholded dimension builds its
+    // simplices from the full list the one below it left.
+    bool sparse_dims = false;
+    if (max_dim >= 2 && n >= 2) {
+        const uint64_t m1 = B.at(2, n);
+        const double density = m1 ? (double)edges_count / (double)m1 : 1.0;
+        bool huge = false;
+        for (int p = 2; p <= max_dim; ++p) huge |= B.at(p + 1, n) >= (1ull << 32);
+        sparse_dims = ctx->sparse_mode == 1 ||
+                      (ctx->sparse_mode == 0 && (density < SPARSE_DENSITY || huge));
+    }
+
     // ---- dimensions p = 1 .. max_dim ----
     for (int p = 1; p <= max_dim && n >= 2; ++p) {
         if (p >= 2) {
-            // clearing bitmap from the deaths of dimension p-1
             const uint64_t cand = B.at(p + 1, n);
             S.candidates[p] = (int64_t)cand;
-            uint32_t *bitmap;
-            RPP_TRY(ws.dev(ws.bitmap, (cand + 31) / 32 * 4, (void **)&bitmap));
-            RPP_CK(cudaMemsetAsync(bitmap, 0, (cand + 31) / 32 * 4, s));
-            T.begin(ST_OTHER);
-            launch_bitmap_set(app_tau, prev_napp, bitmap, s);
-            T.end();
+            S.cleared[p] = (int64_t)(prev_napp + prev_deaths.size());
+            const bool sparse = sparse_dims;
+            if (!sparse && cand >= (1ull << 32))
+                return fail(RPP_E_NOMEM, "more than 2^32 candidate simplices in dimension " +
+                                             std::to_string(p) + " (the thresholded path is off)");
+            // the previous dimension's deaths: apparent taus (sorted on the
+            // device) and the host's pairs, sorted here
+            std::sort(prev_deaths.begin(), prev_deaths.end());
+            uint64_t *up = nullptr;
             if (!prev_deaths.empty()) {
-                uint64_t *up;
                 RPP_TRY(ws.dev(ws.up, prev_deaths.size() * 8, (void **)&up));
                 RPP_TRY(ws.host(ws.h_up, prev_deaths.size() * 8, &vp));
                 std::memcpy(vp, prev_deaths.data(), prev_deaths.size() * 8);
                 RPP_CK(cudaMemcpyAsync(up, vp, prev_deaths.size() * 8, cudaMemcpyHostToDevice, s));
-                T.begin(ST_OTHER);
-                launch_bitmap_set(up, prev_deaths.size(), bitmap, s);
-                T.end();
             }
+            uint64_t cap = cand;  // columns the build may write
             RPP_CK(cudaMemsetAsync(&st->ncols, 0, sizeof(unsigned long long), s));
-            T.begin(ST_BUILD);
-            launch_build_columns(D, ld, n, p, d_binom, cand, bitmap, st, key_hi, key_lo, s);
-            T.end();
+            if (!sparse) {
+                RPP_TRY(grow_columns(cap));
+                // clearing bitmap from the deaths of dimension p-1
+                uint32_t *bitmap;
+                RPP_TRY(ws.dev(ws.bitmap, (cand + 31) / 32 * 4, (void **)&bitmap));
+                RPP_CK(cudaMemsetAsync(bitmap, 0, (cand + 31) / 32 * 4, s));
+                T.begin(ST_OTHER);
+                launch_bitmap_set(app_tau, prev_napp, bitmap, s);
+                if (up) launch_bitmap_set(up, prev_deaths.size(), bitmap, s);
+                T.end();
+                T.begin(ST_BUILD);
+                launch_build_columns(D, ld, n, p, d_binom, cand, bitmap, st, key_hi, key_lo, s);
+                T.end();
+            } else {
+                S.sparse[p] = 1;
+                if (!csr_off) {  // the threshold graph, once per instance
+                    RPP_TRY(ws.dev(ws.csr_off, (size_t)(n + 1) * 8, (void **)&csr_off));
+                    T.begin(ST_OTHER);
+                    launch_csr_build(D, ld, n, st, csr_off, nullptr, false, s);
+                    T.end();
+                    unsigned long long total = 0;
+                    RPP_CK(cudaMemcpyAsync(&total, csr_off + n, 8, cudaMemcpyDeviceToHost, s));
+                    RPP_CK(cudaStreamSynchronize(s));
+                    RPP_TRY(ws.dev(ws.csr_nbr, std::max<size_t>(4, total * 4), (void **)&csr_nbr));
+                    T.begin(ST_OTHER);
+                    launch_csr_build(D, ld, n, st, csr_off, csr_nbr, true, s);
+                    T.end();
+                }
+                // the (p-1)-simplices inside t: the edges (dimension 1's sorted
+                // keys, copied aside) or every simplex the previous sparse
+                // build listed
+                const uint64_t *prev;
+                uint64_t nprev;
+                if (p == 2) {
+                    RPP_TRY(ws.dev(ws.sp_a, std::max<uint64_t>(1, edges_count) * 8, &vp));
+                    if (edges_count)
+                        RPP_CK(cudaMemcpyAsync(vp, key_lo + edges_begin, edges_count * 8,
+                                               cudaMemcpyDeviceToDevice, s));
+                    prev = (const uint64_t *)vp;
+                    nprev = edges_count;
+                } else if (sp_prev_valid) {
+                    prev = sp_prev;
+                    nprev = sp_prev_count;
+                } else {
+                    return fail(RPP_E_CUDA, "thresholded build: no list of the previous dimension");
+                }
+                const bool keep_all = p < max_dim;
+                unsigned long long *cnt;
+                RPP_TRY(ws.dev(ws.sp_cnt, 16, (void **)&cnt));
+                RPP_CK(cudaMemsetAsync(cnt, 0, 16, s));
+                T.begin(ST_BUILD);
+                launch_sparse_build(D, ld, n, p, d_binom, prev, nprev, csr_off, csr_nbr, st,
+                                    app_tau, prev_napp, up, up ? prev_deaths.size() : 0, false,
+                                    cnt, nullptr, nullptr, 0, nullptr, 0, s);
+                T.end();
+                unsigned long long counts[2];
+                RPP_CK(cudaMemcpyAsync(counts, cnt, 16, cudaMemcpyDeviceToHost, s));
+                RPP_CK(cudaStreamSynchronize(s));
+                cap = counts[1];
+                RPP_TRY(grow_columns(cap));
+                uint64_t *all_out = nullptr;
+                if (keep_all) {  // the other list buffer (prev may live in one of them)
+                    DevBuf &dst = (p == 2 || prev == (const uint64_t *)ws.sp_b.p) ? ws.sp_c : ws.sp_b;
+                    RPP_TRY(ws.dev(dst, std::max<uint64_t>(1, counts[0]) * 8, &vp));
+                    all_out = (uint64_t *)vp;
+                }
+                RPP_CK(cudaMemsetAsync(cnt, 0, 16, s));
+                T.begin(ST_BUILD);
+                launch_sparse_build(D, ld, n, p, d_binom, prev, nprev, csr_off, csr_nbr, st,
+                                    app_tau, prev_napp, up, up ? prev_deaths.size() : 0, true,
+                                    cnt, key_hi, key_lo, cap, all_out, counts[0], s);
+                T.end();
+                RPP_CK(cudaMemcpyAsync(&st->ncols, cnt + 1, 8, cudaMemcpyDeviceToDevice, s));
+                sp_prev = all_out;
+                sp_prev_count = counts[0];
+                sp_prev_valid = keep_all;
+            }
             RPP_CK(cudaGetLastError());
+            // the apparent taus of p-1 have been read: the per-column outputs
+            // may grow now
+            RPP_TRY(grow_outputs(cap));
             // as in dimension 1, the count stays on the device until the
             // partition has run
-            uint64_t N = cand;
+            uint64_t N = cap;
             const unsigned long long *d_n = &st->ncols;
-            S.cleared[p] = (int64_t)(prev_napp + prev_deaths.size());
             T.begin(ST_SORT);
-            radix_sort(key_hi, key_lo, nullptr, tmp_hi, tmp_lo, nullptr, sort_scratch, cand,
+            radix_sort(key_hi, key_lo, nullptr, tmp_hi, tmp_lo, nullptr, sort_scratch, cap,
                        &st->ncols, bits_for(cand - 1), &st->err, s);
             T.end();
             if (ctx->record & RPP_RECORD_COLUMNS) {
@@ -867,15 +992,22 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
             }
             RPP_CK(cudaMemsetAsync(status, 0, N, s));
             RPP_CK(cudaMemsetAsync(&st->napp, 0, 2 * sizeof(unsigned long long), s));
-            auto run = [&](int g, DevState *state) {
-                launch_apparent(D, ld, n, p, d_binom, key_hi, key_lo, N, d_n, state, status,
-                                pivot, pdiam, g, ctx->sms, s);
-            };
-            int group;
-            RPP_TRY(apparent_shape(ctx, ws, p, n, st, run, s, &group));
-            T.begin(ST_APPARENT);
-            run(group, st);
-            T.end();
+            if (S.sparse[p]) {
+                T.begin(ST_APPARENT);
+                launch_apparent_sparse(D, ld, n, p, d_binom, csr_off, csr_nbr, key_hi, key_lo, N,
+                                       d_n, st, status, pivot, pdiam, ctx->sms, s);
+                T.end();
+            } else {
+                auto run = [&](int g, DevState *state) {
+                    launch_apparent(D, ld, n, p, d_binom, key_hi, key_lo, N, d_n, state, status,
+                                    pivot, pdiam, g, ctx->sms, s);
+                };
+                int group;
+                RPP_TRY(apparent_shape(ctx, ws, p, n, st, run, s, &group));
+                T.begin(ST_APPARENT);
+                run(group, st);
+                T.end();
+            }
             T.begin(ST_PARTITION);
             launch_partition(status, key_hi, key_lo, pivot, pdiam, N, d_n, app_tau, app_sigma,
                              left, st, s);
@@ -901,7 +1033,8 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
             return Status();
         }
         const bool record_app = (ctx->record & RPP_RECORD_APPARENT) != 0;
-        if (record_app || nleft > 0) {
+        const bool next_sparse = p < max_dim && sparse_dims;
+        if (record_app || nleft > 0 || next_sparse) {
             // the apparent taus sorted: the second layer of the pair store (the
             // sigmas ride along only when the pairs are recorded; the host
             // reduction takes the owner of an apparent tau as its youngest facet)

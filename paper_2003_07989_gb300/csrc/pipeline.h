@@ -73,6 +73,7 @@ struct Workspace {
     size_t device_bytes = 0;  // currently held
     DevBuf X, Dsrc, D, state, state_tune, binom, key_hi, key_lo, tmp_hi, tmp_lo, tmp_val, tiles, hist,
         status, pivot, pdiam, app_tau, app_sigma, left, bitmap, mst, up, nbr, h0;
+    DevBuf csr_off, csr_nbr, sp_a, sp_b, sp_c, sp_cnt;  // the thresholded construction
     HostBuf h_hi, h_lo, h_tau, h_sigma, h_left, h_D, h_state, h_mst, h_up, h_nbr, h_ehi, h_eab;
     Binomial binom_host;      // cached table
     int64_t binom_n = -1;
@@ -139,6 +140,9 @@ struct rpp_context {
     int sms = 0;
     int record = 0;  // RPP_RECORD_* flags
     int host_threads = 1;  // threads for the host reductions
+    // dimensions p >= 2: 0 chooses the thresholded (clique) construction by the
+    // share of edges inside t, 1 always takes it, 2 never
+    int sparse_mode = 0;
     std::mutex mu;
     std::vector<rpp::Workspace *> free_ws;
     std::vector<rpp::Workspace *> all_ws;
@@ -155,6 +159,10 @@ struct rpp_context {
 };
 
 namespace rpp {
+
+// Below this share of the C(n, 2) edges inside the threshold, dimensions
+// p >= 2 are built as cliques of the threshold graph (sparse.cu).
+constexpr double SPARSE_DENSITY = 0.25;
 
 // Run one instance end to end on `stream` with workspace `ws`.
 Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStream_t stream,

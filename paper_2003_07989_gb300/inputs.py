@@ -16,6 +16,8 @@ Workloads (sizes and shapes of the paper's experiments, Sec. "Experiments"):
   * ``noisy_torus``      : points on a 2-torus in R^3 plus Gaussian noise
   * ``sphere_s3``        : points uniform on S^3 in R^4 (stand-in for the paper's
                            sphere_3_192 dataset, which is not shipped here)
+  * ``orthogonal3``      : random matrices of O(3) as points of R^9 (stand-in for
+                           the paper's sparse o3 dataset)
   * ``noisy_circles``    : batches of noisy planar circles of random radius
   * ``serving_requests`` : a Poisson stream of clouds of uneven size drawn from a
                            mixture of noisy circles, noisy 2-spheres and blobs
@@ -112,6 +114,21 @@ def sphere_s3(n: int = 192, seed: int = 0) -> np.ndarray:
     g = normal(stream_seed(seed, 4), 4 * n).reshape(n, 4)
     g = g / np.linalg.norm(g, axis=1, keepdims=True)
     return g.astype(np.float32)
+
+
+def orthogonal3(n: int = 4096, seed: int = 0) -> np.ndarray:
+    """n random 3 x 3 rotation-or-reflection matrices as points of R^9 (row-major
+    entries), Haar-distributed on O(3): Gram-Schmidt of a Gaussian 3 x 3 matrix
+    (the QR factor with a positive diagonal). A synthetic stand-in for the
+    paper's sparse o3 workload (4096 points, evaluated below a threshold)."""
+    g = normal(stream_seed(seed, 11), 9 * n).reshape(n, 3, 3)
+    q = np.empty_like(g)
+    for i in range(3):  # columns, classical Gram-Schmidt in float64
+        c = g[:, :, i].copy()
+        for j in range(i):
+            c -= np.sum(q[:, :, j] * g[:, :, i], axis=1, keepdims=True) * q[:, :, j]
+        q[:, :, i] = c / np.linalg.norm(c, axis=1, keepdims=True)
+    return q.reshape(n, 9).astype(np.float32)
 
 
 def circle_cloud(n: int, radius: float, sigma: float, dim: int, seed: int) -> np.ndarray:

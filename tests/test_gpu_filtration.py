@@ -55,7 +55,7 @@ def test_filtration_equals_oracle_columns(rpp, idx):
     X = gen()
     D = O.distance_matrix(X) if kind == "points" else X
     diam, cidx, st = rpp.rpp_filtration(X, p, threshold=t, kind=kind)
-    t_used = min(t, O.enclosing_radius(D))
+    t_used = float(np.float32(min(t, O.enclosing_radius(D))))  # the library's float32 t
     assert st["threshold"] == t_used
     od, ov = O.columns(D, p, t_used)
     assert np.array_equal(diam, od), name
