@@ -29,6 +29,61 @@ namespace {
 // Per index that leaves p distance reads, D[v_i][v_p] for i < p, which the
 // lanes of a warp take from the same rows at consecutive columns (coalesced),
 // and the prefix's own diameter, computed once per decode.
+// One pass over a warp's chunk: decode once, then step v_p by 32 (decoding
+// again when v_p runs into the next prefix). Calls f(k, c, keep, d) for
+// iteration k (index c = c0 + lane + 32 k, valid when c < cend).
+template <int P, class F>
+__device__ __forceinline__ void chunk_pass(const float *__restrict__ D, int64_t ld, int64_t n,
+                                           const uint64_t *B, const uint32_t *__restrict__ cleared,
+                                           float t, uint64_t c0, uint64_t cend, int lane, F &&f) {
+    int v[P + 1];
+    const float *row[P];
+    float pd = 0.0f;  // diameter of the prefix v_0 .. v_{p-1}
+    bool fresh = true;
+    int k = 0;
+    for (uint64_t c = c0 + lane;; c += 32, ++k) {
+        const bool valid = c < cend;
+        if (!__any_sync(FULL_MASK, valid)) break;
+        bool keep = false;
+        float d = 0.0f;
+        if (valid) {
+            if (!fresh) v[P] += 32;
+            if (fresh || v[P] >= v[P - 1]) {
+                decode_simplex<P>(c, B, n, v);
+                pd = 0.0f;
+#pragma unroll
+                for (int a = 0; a < P; ++a) {
+                    row[a] = D + (int64_t)v[a] * ld;
+#pragma unroll
+                    for (int b = a + 1; b < P; ++b) pd = fmaxf(pd, row[a][v[b]]);
+                }
+                fresh = false;
+            }
+            if (!(cleared && ((cleared[c >> 5] >> (c & 31)) & 1u))) {
+                d = pd;
+#pragma unroll
+                for (int a = 0; a < P; ++a) d = fmaxf(d, row[a][v[P]]);
+                keep = d <= t;
+            }
+        }
+        f(k, c, keep, d);
+    }
+}
+
+// Indices c of one run share every vertex but the lowest: the p-simplex
+// {v_0 > ... > v_p} has c = C(v_0, p+1) + ... + C(v_{p-1}, 2) + v_p, so for a
+// fixed prefix (v_0, ..., v_{p-1}) the run c, c+1, ... walks v_p = 0, 1, ...,
+// v_{p-1} - 1. A warp takes a chunk of at most 2048 consecutive indices, lane
+// l index c0 + l + 32 k; a lane decodes its index once and then only adds 32
+// to v_p. Per index that leaves p distance reads, D[v_i][v_p] for i < p,
+// which the lanes of a warp take from the same rows at consecutive columns
+// (coalesced), and the prefix's own diameter, computed once per decode.
+// Compaction takes two passes over the chunk: the first records which
+// indices are kept (one bit per lane and step) and reserves the chunk's
+// output with ONE atomic (a warp-per-step atomic on the shared counter
+// serialises once the candidates number in the billions); the second
+// recomputes the kept diameters (their rows are in cache) and writes them at
+// their ballot ranks.
 template <int P>
 __global__ void __launch_bounds__(256) k_build_columns(const float *__restrict__ D, int64_t ld,
                                                         int64_t n, const uint64_t *__restrict__ gB,
@@ -45,47 +100,28 @@ __global__ void __launch_bounds__(256) k_build_columns(const float *__restrict__
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     for (uint64_t c0 = warp * chunk; c0 < total; c0 += nwarps * chunk) {
         const uint64_t cend = c0 + chunk < total ? c0 + chunk : total;
-        int v[P + 1];
-        const float *row[P];
-        float pd = 0.0f;  // diameter of the prefix v_0 .. v_{p-1}
-        bool fresh = true;
-        for (uint64_t c = c0 + lane;; c += 32) {
-            const bool valid = c < cend;
-            if (!__any_sync(FULL_MASK, valid)) break;
-            bool keep = false;
-            float d = 0.0f;
-            if (valid) {
-                if (!fresh) v[P] += 32;
-                if (fresh || v[P] >= v[P - 1]) {
-                    decode_simplex<P>(c, B, n, v);
-                    pd = 0.0f;
+        uint64_t kept = 0;  // bit k: this lane's index of step k is kept
+        chunk_pass<P>(D, ld, n, B, cleared, t, c0, cend, lane,
+                      [&](int k, uint64_t, bool keep, float) {
+                          if (keep) kept |= 1ull << k;
+                      });
+        unsigned cnt = __popcll(kept);
 #pragma unroll
-                    for (int a = 0; a < P; ++a) {
-                        row[a] = D + (int64_t)v[a] * ld;
-#pragma unroll
-                        for (int b = a + 1; b < P; ++b) pd = fmaxf(pd, row[a][v[b]]);
-                    }
-                    fresh = false;
-                }
-                if (!(cleared && ((cleared[c >> 5] >> (c & 31)) & 1u))) {
-                    d = pd;
-#pragma unroll
-                    for (int a = 0; a < P; ++a) d = fmaxf(d, row[a][v[P]]);
-                    keep = d <= t;
-                }
-            }
-            const unsigned ball = __ballot_sync(FULL_MASK, keep);
-            if (ball) {
-                unsigned long long off = 0;
-                if (lane == 0) off = atomicAdd(&st->ncols, (unsigned long long)__popc(ball));
-                off = __shfl_sync(FULL_MASK, off, 0);
-                if (keep) {
-                    const uint64_t pos = off + __popc(ball & lanemask_lt());
-                    key_hi[pos] = ~__float_as_uint(d);
-                    key_lo[pos] = c;
-                }
-            }
-        }
+        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(FULL_MASK, cnt, o);
+        if (cnt == 0) continue;
+        unsigned long long at = 0;
+        if (lane == 0) at = atomicAdd(&st->ncols, (unsigned long long)cnt);
+        at = __shfl_sync(FULL_MASK, at, 0);
+        chunk_pass<P>(D, ld, n, B, cleared, t, c0, cend, lane,
+                      [&](int k, uint64_t c, bool keep, float d) {
+                          const unsigned ball = __ballot_sync(FULL_MASK, keep);
+                          if (keep) {
+                              const uint64_t pos = at + __popc(ball & lanemask_lt());
+                              key_hi[pos] = ~__float_as_uint(d);
+                              key_lo[pos] = c;
+                          }
+                          at += __popc(ball);
+                      });
     }
 }
 

@@ -47,6 +47,7 @@ constexpr uint64_t LB_FLAGS = 3ull << 62;
 constexpr int LB_EPOCH_SHIFT = 56;          // pass + 1 in bits 56..61
 constexpr uint64_t LB_VALUE = (1ull << LB_EPOCH_SHIFT) - 1;
 constexpr long long LB_SPIN_LIMIT = 1ll << 22;
+constexpr int LB_WINDOW = 8;                // look-back entries loaded together
 
 // Control block at the start of the scratch; zeroed before each sort.
 struct SortCtl {
@@ -227,24 +228,45 @@ __global__ void __launch_bounds__(OS_THREADS) k_onesweep(
         s_base[tid] = ctl->start[pass][tid];
     } else {
         atomicExch(mine, (unsigned long long)(LB_AGG | epoch | run));
+        // look back over windows of LB_WINDOW tiles, their entries loaded
+        // together: with every tile of a pass resident at once the walk back
+        // to the nearest inclusive prefix can be long, and one dependent load
+        // per tile would serialise it
         uint64_t excl = 0;
-        for (int64_t t = (int64_t)tile - 1; t >= 0; --t) {
-            const volatile unsigned long long *e =
-                (const volatile unsigned long long *)(lookback + (uint64_t)t * RADIX + tid);
-            unsigned long long v = *e;
-            long long spins = 0;
-            while (((v & LB_FLAGS) == 0 || (v & ~LB_FLAGS & ~LB_VALUE) != epoch) &&
-                   spins < LB_SPIN_LIMIT) {
-                if (spins > 64) __nanosleep(64);
-                ++spins;
-                v = *e;
+        bool done = false;
+        for (int64_t t0 = (int64_t)tile - 1; t0 >= 0 && !done; t0 -= LB_WINDOW) {
+            unsigned long long w[LB_WINDOW];
+#pragma unroll
+            for (int i = 0; i < LB_WINDOW; ++i)
+                w[i] = t0 - i >= 0 ? *(const volatile unsigned long long *)(lookback +
+                                                                           (uint64_t)(t0 - i) *
+                                                                               RADIX + tid)
+                                   : 0ull;
+#pragma unroll
+            for (int i = 0; i < LB_WINDOW; ++i) {
+                if (done || t0 - i < 0) {
+                    done = true;
+                    continue;
+                }
+                const volatile unsigned long long *e =
+                    (const volatile unsigned long long *)(lookback + (uint64_t)(t0 - i) * RADIX +
+                                                          tid);
+                unsigned long long v = w[i];
+                long long spins = 0;
+                while (((v & LB_FLAGS) == 0 || (v & ~LB_FLAGS & ~LB_VALUE) != epoch) &&
+                       spins < LB_SPIN_LIMIT) {
+                    if (spins > 64) __nanosleep(64);
+                    ++spins;
+                    v = *e;
+                }
+                if (spins >= LB_SPIN_LIMIT) {  // never expected: report and go on
+                    atomicOr(err, ERR_INTERNAL);
+                    done = true;
+                    continue;
+                }
+                excl += v & LB_VALUE;
+                if ((v & LB_FLAGS) == LB_PREFIX) done = true;
             }
-            if (spins >= LB_SPIN_LIMIT) {  // never expected: report and go on
-                atomicOr(err, ERR_INTERNAL);
-                break;
-            }
-            excl += v & LB_VALUE;
-            if ((v & LB_FLAGS) == LB_PREFIX) break;
         }
         atomicExch(mine, (unsigned long long)(LB_PREFIX | epoch | (excl + run)));
         s_base[tid] = ctl->start[pass][tid] + excl;
