@@ -36,7 +36,7 @@ namespace rpp {
 namespace {
 
 template <int P, int G, int U>
-__global__ void __launch_bounds__(256, 8) k_apparent(
+__global__ void __launch_bounds__(256, P == 1 ? 8 : 4) k_apparent(
     const float *__restrict__ D, int64_t ld, int64_t n, const uint64_t *__restrict__ gB,
     bool smem_table, const uint32_t *__restrict__ key_hi, const uint64_t *__restrict__ key_lo,
     uint64_t ncols_cap, const unsigned long long *d_ncols, DevState *__restrict__ st,
@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(256, 8) k_apparent(
 // test. The largest qualifying candidate is the first lane of the ballot with
 // a hit, and the largest of that lane's hits; the rest is the scalar kernel's.
 template <int P, int G, int U>
-__global__ void __launch_bounds__(256, 8) k_apparent_vec(
+__global__ void __launch_bounds__(256, P == 1 ? 8 : 4) k_apparent_vec(
     const float *__restrict__ D, int64_t ld, int64_t n, const uint64_t *__restrict__ gB,
     bool smem_table, const uint32_t *__restrict__ key_hi, const uint64_t *__restrict__ key_lo,
     uint64_t ncols_cap, const unsigned long long *d_ncols, DevState *__restrict__ st,

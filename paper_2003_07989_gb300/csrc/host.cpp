@@ -548,6 +548,90 @@ int first_vertex(const Reducer &R, const Leftover &L, const int *v) {
     return -1;
 }
 
+// Heap keys of dimension 1, ordered like age_key. When every triangle index
+// fits in 32 bits the key packs (diameter bits, complemented index) into 64.
+struct Key64 {
+    typedef uint64_t T;
+    static constexpr T NIL = ~(T)0;  // diameter bits of a NaN: never a real key
+    static T make(float d, uint64_t idx) {
+        return ((T)float_bits(d) << 32) | (T)(uint32_t)~(uint32_t)idx;
+    }
+    static u128 wide(T k) {
+        return k == NIL ? NONE : age_key(bits_float((uint32_t)(k >> 32)), (uint32_t)~(uint32_t)k);
+    }
+};
+struct Key128 {
+    typedef u128 T;
+    static constexpr T NIL = ~(T)0;
+    static T make(float d, uint64_t idx) { return age_key(d, idx); }
+    static u128 wide(T k) { return k; }
+};
+
+// Pivots of the leftover columns of one dimension reduced so far, shared by
+// the columns that are reduced in parallel. Column j adds column i < j once
+// i is finished, and keeps a pivot that no finished column owns only when
+// every unfinished column before it has moved past that pivot: pivots only
+// move forward (an addition cancels the pivot and brings younger entries
+// only), so none of those columns can end there. The additions are then
+// those of Alg. 1 in column order, whatever the interleaving, and the lowest
+// unfinished column never waits. Columns must be started in increasing order
+// and each finished by the thread that started it.
+template <class K, class Col = std::vector<uint64_t>>
+struct Ledger {
+    std::mutex m;
+    std::condition_variable cv;
+    std::unordered_map<uint64_t, int64_t> owner;  // pivot index -> finished column
+    std::vector<Col> &V;                          // reduced columns, final once finished
+    std::vector<char> done;
+    int64_t low = 0;                              // columns below are finished
+    // Per column, a lower bound of its current pivot as a 64-bit key: exact
+    // for 64-bit keys, the diameter bits alone for 128-bit ones.
+    std::unique_ptr<std::atomic<uint64_t>[]> front;
+
+    Ledger(std::vector<Col> &V_, int64_t ncols)
+        : V(V_), done(ncols, 0), front(new std::atomic<uint64_t>[ncols]) {
+        owner.reserve((size_t)ncols * 2);
+        for (int64_t j = 0; j < ncols; ++j) front[j].store(0, std::memory_order_relaxed);
+    }
+    static uint64_t lower(u128 k) {
+        if (k == NONE) return ~0ull;
+        if (std::is_same<typename K::T, uint64_t>::value) return (uint64_t)K::make(key_diam(k), key_index(k));
+        return (uint64_t)float_bits(key_diam(k)) << 32;
+    }
+    static uint64_t upper(u128 k) {
+        if (std::is_same<typename K::T, uint64_t>::value) return (uint64_t)K::make(key_diam(k), key_index(k));
+        return ((uint64_t)float_bits(key_diam(k)) << 32) | 0xffffffffull;
+    }
+    void advance(int64_t j, u128 k) { front[j].store(lower(k), std::memory_order_relaxed); }
+
+    // The finished column that owns pivot k of column j, or -1 when k is
+    // free for j; waits while an unfinished earlier column may still end at k.
+    int64_t query(int64_t j, u128 k) {
+        const uint64_t ub = upper(k);
+        std::unique_lock<std::mutex> g(m);
+        for (int round = 0;; ++round) {
+            auto it = owner.find(key_index(k));
+            if (it != owner.end()) return it->second;
+            while (low < j && done[low]) ++low;
+            bool blocked = false;
+            for (int64_t i = low; i < j && !blocked; ++i)
+                blocked = !done[i] && front[i].load(std::memory_order_relaxed) <= ub;
+            if (!blocked) return -1;
+            // earlier columns move their pivots without notice: look again soon
+            cv.wait_for(g, std::chrono::microseconds(round < 64 ? 10 : 100));
+        }
+    }
+    // Column j is finished with pivot k (NONE: a zero column); V[j] is final.
+    void finish(int64_t j, u128 k) {
+        {
+            std::lock_guard<std::mutex> g(m);
+            if (k != NONE) owner[key_index(k)] = j;
+            done[j] = 1;
+        }
+        cv.notify_all();
+    }
+};
+
 // ---- dimensions p >= 2 -------------------------------------------------------
 
 struct ColumnState {
@@ -617,34 +701,31 @@ u128 pivot(const Reducer &R, ColumnState &S) {
     return NONE;
 }
 
-// Pivots owned by finalized leftover columns, and those columns as sums.
-struct Finalized {
-    std::unordered_map<uint64_t, int64_t> owner;  // pivot index -> leftover slot
-    std::vector<std::vector<std::pair<uint64_t, float>>> V;
-};
+typedef std::vector<std::pair<uint64_t, float>> SimplexSet;  // (index, diameter)
 
-// Walk: add owners of the pivot until it is free. With fin == nullptr only
-// apparent owners are used (Phase A).
-void walk(const Reducer &R, ColumnState &S, const Finalized *fin) {
+// Walk column j: add the owners of its pivot until the pivot is free or the
+// column is zero. Apparent owners come from the pair store; pivots of earlier
+// leftover columns from the ledger, which also holds back a pivot that an
+// unfinished earlier column may still reach (as in dimension 1).
+void walk(const Reducer &R, ColumnState &S, Ledger<Key128, SimplexSet> &led, int64_t j) {
     for (;;) {
         const u128 k = pivot(R, S);
         if (k == NONE) {
             S.cand = NONE;
             return;
         }
+        led.advance(j, k);
         ++S.reads;
-        if (fin) {
-            auto it = fin->owner.find(key_index(k));
-            if (it != fin->owner.end()) {
-                ++S.additions;
-                for (const auto &s : fin->V[it->second]) add_cursor(R, S, s.first, s.second);
-                continue;
-            }
-        }
         int s[RPP_MAX_DIM + 1], added;
         if (R.apparent_owner(k, s, &added)) {
             ++S.additions;  // its oldest cofacet is the pivot, which adds `added`
             add_cursor(R, S, s, index_host(*R.I.B, s, R.p), key_diam(k), added);
+            continue;
+        }
+        const int64_t i = led.query(j, k);
+        if (i >= 0) {
+            ++S.additions;
+            for (const auto &x : led.V[i]) add_cursor(R, S, x.first, x.second);
             continue;
         }
         S.cand = k;
@@ -660,7 +741,7 @@ void start_column(const Reducer &R, ColumnState &S, const Leftover &L) {
 }
 
 // Z/2 sum of the simplices in V: sort and drop pairs.
-void reduce_set(std::vector<std::pair<uint64_t, float>> &V) {
+void reduce_set(SimplexSet &V) {
     std::sort(V.begin(), V.end(),
               [](const std::pair<uint64_t, float> &a, const std::pair<uint64_t, float> &b) {
                   return a.first < b.first;
@@ -675,44 +756,53 @@ void reduce_set(std::vector<std::pair<uint64_t, float>> &V) {
     V.resize(o);
 }
 
+// The leftover columns of dimension p walk concurrently, one per host thread
+// at a time, in index order (the ledger makes the additions those of Alg. 1
+// in column order, whatever the interleaving).
 void reduce_general(const HostInstance &I, int p, const Leftover *left, int64_t nleft,
                     int threads, std::vector<HostPair> &out, ReduceStats &stats) {
     Reducer R(I, p);
     std::vector<ColumnState> col(nleft);
+    std::vector<SimplexSet> V(nleft);
+    Ledger<Key128, SimplexSet> led(V, nleft);
+    for (int64_t j = 0; j < nleft; ++j)
+        if (left[j].pivot != NO_PIVOT) led.advance(j, age_key(left[j].pdiam, left[j].pivot));
 
-    auto phase_a_column = [&](int64_t j) {
+    auto column = [&](int64_t j) {
         const Leftover &L = left[j];
         ColumnState &S = col[j];
         if (L.pivot == NO_PIVOT) {
             S.cand = NONE;
+            led.finish(j, NONE);
             return;
         }
         const u128 k0 = age_key(L.pdiam, L.pivot);
         int s[RPP_MAX_DIM + 1], added;
         ++S.reads;
-        if (!R.apparent_owner(k0, s, &added)) {
-            S.cand = k0;  // the unreduced pivot is free of apparent owners
+        if (!R.apparent_owner(k0, s, &added) && led.query(j, k0) < 0) {
+            S.cand = k0;  // the unreduced pivot is free
+            V[j].emplace_back(L.sigma, L.diam);
+            led.finish(j, k0);
             return;
         }
         start_column(R, S, L);
-        walk(R, S, nullptr);
+        walk(R, S, led, j);
+        reduce_set(S.V);
+        V[j].swap(S.V);
+        std::vector<Cursor>().swap(S.cur);
+        std::vector<std::pair<u128, int32_t>>().swap(S.heap);
+        led.finish(j, S.cand);
     };
+    // columns start in increasing order (the pool hands out indices in order)
     if (threads <= 1 || nleft < 16) {
-        for (int64_t j = 0; j < nleft; ++j) phase_a_column(j);
+        for (int64_t j = 0; j < nleft; ++j) column(j);
     } else {
-        pool(threads).parallel_for(nleft, phase_a_column);
+        pool(threads).parallel_for(nleft, column);
     }
 
-    Finalized fin;
-    fin.V.resize(nleft);
-    fin.owner.reserve((size_t)nleft * 2);
     for (int64_t j = 0; j < nleft; ++j) {
         const Leftover &L = left[j];
-        ColumnState &S = col[j];
-        if (S.cand != NONE && fin.owner.count(key_index(S.cand))) {
-            if (!S.started) start_column(R, S, L);
-            walk(R, S, &fin);
-        }
+        const ColumnState &S = col[j];
         HostPair P;
         P.sigma = L.sigma;
         P.birth = L.diam;
@@ -722,21 +812,12 @@ void reduce_general(const HostInstance &I, int p, const Leftover *left, int64_t 
         } else {
             P.tau = key_index(S.cand);
             P.death = key_diam(S.cand);
-            fin.owner[P.tau] = j;
-            if (S.started) {
-                reduce_set(S.V);
-                fin.V[j].swap(S.V);
-            } else {
-                fin.V[j].emplace_back(L.sigma, L.diam);
-                ++stats.free_pivot;
-            }
+            if (!S.started) ++stats.free_pivot;
         }
         out.push_back(P);
         stats.additions += S.additions;
         stats.reads += S.reads;
         stats.entries += S.entries;
-        std::vector<Cursor>().swap(S.cur);
-        std::vector<std::pair<u128, int32_t>>().swap(S.heap);
     }
 }
 
@@ -789,25 +870,6 @@ struct Cur1 {
     float bh[NB];
     float tie_key = 0.0f;
     std::vector<int32_t> ties;   // equal-diameter emissions, largest at the back
-};
-
-// Heap keys of dimension 1, ordered like age_key. When every triangle index
-// fits in 32 bits the key packs (diameter bits, complemented index) into 64.
-struct Key64 {
-    typedef uint64_t T;
-    static constexpr T NIL = ~(T)0;  // diameter bits of a NaN: never a real key
-    static T make(float d, uint64_t idx) {
-        return ((T)float_bits(d) << 32) | (T)(uint32_t)~(uint32_t)idx;
-    }
-    static u128 wide(T k) {
-        return k == NIL ? NONE : age_key(bits_float((uint32_t)(k >> 32)), (uint32_t)~(uint32_t)k);
-    }
-};
-struct Key128 {
-    typedef u128 T;
-    static constexpr T NIL = ~(T)0;
-    static T make(float d, uint64_t idx) { return age_key(d, idx); }
-    static u128 wide(T k) { return k; }
 };
 
 // 4-ary min-heap of (key, cursor) with a replace-top step (one sift where a
@@ -902,71 +964,6 @@ struct RadixHeap {
     void replace_top(E e) {
         pop();
         push(e);
-    }
-};
-
-// Pivots of the leftover columns of dimension 1 reduced so far, shared by
-// the columns that are reduced in parallel. Column j adds column i < j once
-// i is finished, and keeps a pivot that no finished column owns only when
-// every unfinished column before it has moved past that pivot: pivots only
-// move forward (an addition cancels the pivot and brings younger entries
-// only), so none of those columns can end there. The additions are then
-// those of Alg. 1 in column order, whatever the interleaving, and the lowest
-// unfinished column never waits. Columns must be started in increasing order
-// and each finished by the thread that started it.
-template <class K>
-struct Ledger {
-    std::mutex m;
-    std::condition_variable cv;
-    std::unordered_map<uint64_t, int64_t> owner;  // pivot index -> finished column
-    std::vector<std::vector<uint64_t>> &V;        // reduced columns, final once finished
-    std::vector<char> done;
-    int64_t low = 0;                              // columns below are finished
-    // Per column, a lower bound of its current pivot as a 64-bit key: exact
-    // for 64-bit keys, the diameter bits alone for 128-bit ones.
-    std::unique_ptr<std::atomic<uint64_t>[]> front;
-
-    Ledger(std::vector<std::vector<uint64_t>> &V_, int64_t ncols)
-        : V(V_), done(ncols, 0), front(new std::atomic<uint64_t>[ncols]) {
-        owner.reserve((size_t)ncols * 2);
-        for (int64_t j = 0; j < ncols; ++j) front[j].store(0, std::memory_order_relaxed);
-    }
-    static uint64_t lower(u128 k) {
-        if (k == NONE) return ~0ull;
-        if (std::is_same<typename K::T, uint64_t>::value) return (uint64_t)K::make(key_diam(k), key_index(k));
-        return (uint64_t)float_bits(key_diam(k)) << 32;
-    }
-    static uint64_t upper(u128 k) {
-        if (std::is_same<typename K::T, uint64_t>::value) return (uint64_t)K::make(key_diam(k), key_index(k));
-        return ((uint64_t)float_bits(key_diam(k)) << 32) | 0xffffffffull;
-    }
-    void advance(int64_t j, u128 k) { front[j].store(lower(k), std::memory_order_relaxed); }
-
-    // The finished column that owns pivot k of column j, or -1 when k is
-    // free for j; waits while an unfinished earlier column may still end at k.
-    int64_t query(int64_t j, u128 k) {
-        const uint64_t ub = upper(k);
-        std::unique_lock<std::mutex> g(m);
-        for (int round = 0;; ++round) {
-            auto it = owner.find(key_index(k));
-            if (it != owner.end()) return it->second;
-            while (low < j && done[low]) ++low;
-            bool blocked = false;
-            for (int64_t i = low; i < j && !blocked; ++i)
-                blocked = !done[i] && front[i].load(std::memory_order_relaxed) <= ub;
-            if (!blocked) return -1;
-            // earlier columns move their pivots without notice: look again soon
-            cv.wait_for(g, std::chrono::microseconds(round < 64 ? 10 : 100));
-        }
-    }
-    // Column j is finished with pivot k (NONE: a zero column); V[j] is final.
-    void finish(int64_t j, u128 k) {
-        {
-            std::lock_guard<std::mutex> g(m);
-            if (k != NONE) owner[key_index(k)] = j;
-            done[j] = 1;
-        }
-        cv.notify_all();
     }
 };
 

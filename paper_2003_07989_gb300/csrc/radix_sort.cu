@@ -15,12 +15,13 @@
 //             (the parity of the needed passes before it);
 //   onesweep: one kernel per pass. A block takes the next tile of keys (tile
 //             order comes from an atomic ticket, so every tile it waits on
-//             belongs to a block already running), ranks its keys stably
-//             (per-warp match and counts in key order), publishes its digit
-//             counts, adds up the counts of the tiles before it by decoupled
-//             look-back (a tile that knows its inclusive prefix publishes it,
-//             so a look-back stops there), and scatters its keys to their
-//             final positions of this pass. Waits on another tile's entry are
+//             belongs to a block already running), counts its digits in
+//             shared memory and publishes the counts at once, ranks its keys
+//             stably (per-warp match and counts in key order), adds up the
+//             counts of the tiles before it by decoupled look-back (a tile
+//             that knows its inclusive prefix publishes it, so a look-back
+//             stops there), and scatters its keys to their final positions
+//             of this pass. Waits on another tile's entry are
 //             bounded; a wait that runs out sets ERR_INTERNAL and continues.
 //   finish  : copies the keys back into the caller's arrays when an odd
 //             number of passes ran.
@@ -47,7 +48,7 @@ constexpr uint64_t LB_FLAGS = 3ull << 62;
 constexpr int LB_EPOCH_SHIFT = 56;          // pass + 1 in bits 56..61
 constexpr uint64_t LB_VALUE = (1ull << LB_EPOCH_SHIFT) - 1;
 constexpr long long LB_SPIN_LIMIT = 1ll << 22;
-constexpr int LB_WINDOW = 8;                // look-back entries loaded together
+constexpr int LB_WINDOW = 4;                // look-back entries loaded together
 
 // Control block at the start of the scratch; zeroed before each sort.
 struct SortCtl {
@@ -159,12 +160,13 @@ __global__ void __launch_bounds__(RADIX) k_sort_offsets(uint64_t n_cap,
 }
 
 template <bool HAS_HI, bool HAS_VAL>
-__global__ void __launch_bounds__(OS_THREADS) k_onesweep(
+__global__ void __launch_bounds__(OS_THREADS, 4) k_onesweep(
     uint32_t *__restrict__ hi_a, uint64_t *__restrict__ lo_a, uint64_t *__restrict__ val_a,
     uint32_t *__restrict__ hi_b, uint64_t *__restrict__ lo_b, uint64_t *__restrict__ val_b,
     uint64_t n_cap, const unsigned long long *d_count, int lo_bits, int pass, SortCtl *ctl,
     unsigned long long *lookback, unsigned *err) {
     __shared__ unsigned int s_warp[OS_WARPS][RADIX];  // per-warp counts, then starts
+    __shared__ unsigned int s_hist[RADIX];            // the tile's digit counts
     __shared__ unsigned long long s_base[RADIX];      // global start of each digit for this tile
     __shared__ unsigned int s_tile;
     if (!ctl->active[pass]) return;
@@ -174,6 +176,7 @@ __global__ void __launch_bounds__(OS_THREADS) k_onesweep(
     if (tid == 0) s_tile = atomicAdd(&ctl->tile_ticket[pass], 1u);
 #pragma unroll
     for (int k = 0; k < OS_WARPS; ++k) s_warp[k][tid] = 0;
+    s_hist[tid] = 0;
     __syncthreads();
     const uint64_t tile = s_tile;
     if (tile >= ntiles) return;  // grids are sized for the largest count
@@ -192,7 +195,7 @@ __global__ void __launch_bounds__(OS_THREADS) k_onesweep(
     const uint64_t base = tile * OS_TILE + (uint64_t)w * OS_WARP_KEYS;
     uint64_t kl[OS_ITEMS], kv[OS_ITEMS];
     uint32_t kh[OS_ITEMS];
-    unsigned dg[OS_ITEMS], rk[OS_ITEMS];
+    unsigned dg[OS_ITEMS];  // digit (RADIX: no key), then (rank in the warp << 16) | digit
 #pragma unroll
     for (int j = 0; j < OS_ITEMS; ++j) {
         const uint64_t i = base + (uint64_t)j * 32 + lane;
@@ -201,44 +204,39 @@ __global__ void __launch_bounds__(OS_THREADS) k_onesweep(
         kh[j] = (HAS_HI && ok) ? hs[i] : 0u;
         if constexpr (HAS_VAL) kv[j] = ok ? vs[i] : 0;
         dg[j] = ok ? digit_of<HAS_HI>(kh[j], kl[j], hmin, lo_bits, shift) : RADIX;
+        if (ok) atomicAdd(&s_hist[dg[j]], 1u);
     }
+    __syncthreads();
+    // The tile's counts go out first, before its ranking, so that later tiles
+    // looking back find them (and soon this tile's inclusive prefix) without
+    // waiting on the ranking.
+    const uint64_t epoch = (uint64_t)(pass + 1) << LB_EPOCH_SHIFT;
+    unsigned long long *mine = lookback + tile * RADIX + tid;
+    const unsigned int own = s_hist[tid];
+    if (tile == 0) atomicExch(mine, (unsigned long long)(LB_PREFIX | epoch | own));
+    else atomicExch(mine, (unsigned long long)(LB_AGG | epoch | own));
 #pragma unroll
     for (int j = 0; j < OS_ITEMS; ++j) {
         const unsigned peers = __match_any_sync(FULL_MASK, dg[j]);
         const unsigned before = __popc(peers & lanemask_lt());
         const unsigned cnt = dg[j] < RADIX ? s_warp[w][dg[j]] : 0u;
-        rk[j] = cnt + before;
         __syncwarp();
         if (dg[j] < RADIX && before == 0) s_warp[w][dg[j]] = cnt + __popc(peers);
+        dg[j] |= (cnt + before) << 16;
         __syncwarp();
     }
-    __syncthreads();
-    // thread tid owns digit value tid: starts of each warp's run, tile count
-    unsigned int run = 0;
-#pragma unroll
-    for (int k = 0; k < OS_WARPS; ++k) {
-        const unsigned int c = s_warp[k][tid];
-        s_warp[k][tid] = run;
-        run += c;
-    }
-    const uint64_t epoch = (uint64_t)(pass + 1) << LB_EPOCH_SHIFT;
-    unsigned long long *mine = lookback + tile * RADIX + tid;
+    // thread tid owns digit value tid: look back for the tiles before this one
     if (tile == 0) {
-        atomicExch(mine, (unsigned long long)(LB_PREFIX | epoch | run));
         s_base[tid] = ctl->start[pass][tid];
     } else {
-        atomicExch(mine, (unsigned long long)(LB_AGG | epoch | run));
-        // look back over windows of LB_WINDOW tiles, their entries loaded
-        // together: with every tile of a pass resident at once the walk back
-        // to the nearest inclusive prefix can be long, and one dependent load
-        // per tile would serialise it
+        // windows of LB_WINDOW entries loaded together
         uint64_t excl = 0;
         bool done = false;
         for (int64_t t0 = (int64_t)tile - 1; t0 >= 0 && !done; t0 -= LB_WINDOW) {
-            unsigned long long w[LB_WINDOW];
+            unsigned long long e[LB_WINDOW];
 #pragma unroll
             for (int i = 0; i < LB_WINDOW; ++i)
-                w[i] = t0 - i >= 0 ? *(const volatile unsigned long long *)(lookback +
+                e[i] = t0 - i >= 0 ? *(const volatile unsigned long long *)(lookback +
                                                                            (uint64_t)(t0 - i) *
                                                                                RADIX + tid)
                                    : 0ull;
@@ -248,16 +246,16 @@ __global__ void __launch_bounds__(OS_THREADS) k_onesweep(
                     done = true;
                     continue;
                 }
-                const volatile unsigned long long *e =
+                const volatile unsigned long long *src =
                     (const volatile unsigned long long *)(lookback + (uint64_t)(t0 - i) * RADIX +
                                                           tid);
-                unsigned long long v = w[i];
+                unsigned long long v = e[i];
                 long long spins = 0;
                 while (((v & LB_FLAGS) == 0 || (v & ~LB_FLAGS & ~LB_VALUE) != epoch) &&
                        spins < LB_SPIN_LIMIT) {
                     if (spins > 64) __nanosleep(64);
                     ++spins;
-                    v = *e;
+                    v = *src;
                 }
                 if (spins >= LB_SPIN_LIMIT) {  // never expected: report and go on
                     atomicOr(err, ERR_INTERNAL);
@@ -268,14 +266,23 @@ __global__ void __launch_bounds__(OS_THREADS) k_onesweep(
                 if ((v & LB_FLAGS) == LB_PREFIX) done = true;
             }
         }
-        atomicExch(mine, (unsigned long long)(LB_PREFIX | epoch | (excl + run)));
+        atomicExch(mine, (unsigned long long)(LB_PREFIX | epoch | (excl + own)));
         s_base[tid] = ctl->start[pass][tid] + excl;
+    }
+    __syncthreads();  // the ranks' per-warp counts are complete
+    unsigned int run = 0;
+#pragma unroll
+    for (int k = 0; k < OS_WARPS; ++k) {
+        const unsigned int c = s_warp[k][tid];
+        s_warp[k][tid] = run;
+        run += c;
     }
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < OS_ITEMS; ++j) {
-        if (dg[j] < RADIX) {
-            const uint64_t pos = s_base[dg[j]] + s_warp[w][dg[j]] + rk[j];
+        const unsigned d = dg[j] & 0xffffu;
+        if (d < RADIX) {
+            const uint64_t pos = s_base[d] + s_warp[w][d] + (dg[j] >> 16);
             if (pos < n) {  // always: the counts partition the keys
                 ld[pos] = kl[j];
                 if constexpr (HAS_HI) hd[pos] = kh[j];

@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(256) k_sparse_build(
 // vertex first: a group of G lanes reads G consecutive list entries per block
 // and U blocks per step.
 template <int P, int G, int U>
-__global__ void __launch_bounds__(256, 8) k_apparent_sparse(
+__global__ void __launch_bounds__(256, 4) k_apparent_sparse(
     const float *__restrict__ D, int64_t ld, int64_t n, const uint64_t *__restrict__ B,
     const unsigned long long *__restrict__ off, const uint32_t *__restrict__ nbr,
     const uint32_t *__restrict__ key_hi, const uint64_t *__restrict__ key_lo, uint64_t ncols_cap,
