@@ -40,7 +40,8 @@ __global__ void __launch_bounds__(256, P == 1 ? 8 : 4) k_apparent(
     const float *__restrict__ D, int64_t ld, int64_t n, const uint64_t *__restrict__ gB,
     bool smem_table, const uint32_t *__restrict__ key_hi, const uint64_t *__restrict__ key_lo,
     uint64_t ncols_cap, const unsigned long long *d_ncols, DevState *__restrict__ st,
-    uint8_t *__restrict__ status, uint64_t *__restrict__ pivot, float *__restrict__ pdiam) {
+    uint8_t *__restrict__ status, uint64_t *__restrict__ pivot, float *__restrict__ pdiam,
+    uint16_t *__restrict__ aw) {
     extern __shared__ uint64_t sB[];
     const uint64_t *B = stage_binomial(gB, n, P + 2, sB, smem_table);
     const float t = st->t;
@@ -145,6 +146,7 @@ __global__ void __launch_bounds__(256, P == 1 ? 8 : 4) k_apparent(
                     status[c] = apparent ? COL_APPARENT : COL_LEFTOVER;
                     pivot[c] = cofacet_index<P>(v, x, B, n);
                     pdiam[c] = diam;
+                    if (P == 1 && aw && apparent) aw[key_lo[c]] = (uint16_t)x;
                     int above = 0;  // vertices of sigma above x
 #pragma unroll
                     for (int i = 0; i <= P; ++i) above += v[i] > x;
@@ -195,7 +197,8 @@ __global__ void __launch_bounds__(256, P == 1 ? 8 : 4) k_apparent_vec(
     const float *__restrict__ D, int64_t ld, int64_t n, const uint64_t *__restrict__ gB,
     bool smem_table, const uint32_t *__restrict__ key_hi, const uint64_t *__restrict__ key_lo,
     uint64_t ncols_cap, const unsigned long long *d_ncols, DevState *__restrict__ st,
-    uint8_t *__restrict__ status, uint64_t *__restrict__ pivot, float *__restrict__ pdiam) {
+    uint8_t *__restrict__ status, uint64_t *__restrict__ pivot, float *__restrict__ pdiam,
+    uint16_t *__restrict__ aw) {
     static_assert(4 * G <= 32, "a window must stay inside the 32-float row padding");
     extern __shared__ uint64_t sB[];
     const uint64_t *B = stage_binomial(gB, n, P + 2, sB, smem_table);
@@ -322,6 +325,7 @@ __global__ void __launch_bounds__(256, P == 1 ? 8 : 4) k_apparent_vec(
                     status[c] = apparent ? COL_APPARENT : COL_LEFTOVER;
                     pivot[c] = cofacet_index<P>(v, x, B, n);
                     pdiam[c] = diam;
+                    if (P == 1 && aw && apparent) aw[key_lo[c]] = (uint16_t)x;
                     int above = 0;  // vertices of sigma above x
 #pragma unroll
                     for (int i = 0; i <= P; ++i) above += v[i] > x;
@@ -405,7 +409,7 @@ template <int P, int G, int U>
 void apparent_pg(const float *D, int64_t ld, int64_t n, const uint64_t *binom,
                  const uint32_t *key_hi, const uint64_t *key_lo, uint64_t ncols,
                  const unsigned long long *d_ncols, DevState *st, uint8_t *status,
-                 uint64_t *pivot, float *pdiam, int sms, cudaStream_t s) {
+                 uint64_t *pivot, float *pdiam, uint16_t *aw, int sms, cudaStream_t s) {
     const size_t table = (size_t)(P + 3) * (n + 1) * sizeof(uint64_t);
     const bool smem = table <= 48 * 1024;
     int per_sm = 0;
@@ -418,14 +422,14 @@ void apparent_pg(const float *D, int64_t ld, int64_t n, const uint64_t *binom,
     if (blocks == 0) return;
     ++g_launches;
     k_apparent<P, G, U><<<(unsigned)blocks, 256, smem ? table : 0, s>>>(
-        D, ld, n, binom, smem, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam);
+        D, ld, n, binom, smem, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw);
 }
 
 template <int P, int G, int U>
 void apparent_vec(const float *D, int64_t ld, int64_t n, const uint64_t *binom,
                   const uint32_t *key_hi, const uint64_t *key_lo, uint64_t ncols,
                   const unsigned long long *d_ncols, DevState *st, uint8_t *status,
-                  uint64_t *pivot, float *pdiam, int sms, cudaStream_t s) {
+                  uint64_t *pivot, float *pdiam, uint16_t *aw, int sms, cudaStream_t s) {
     const size_t table = (size_t)(P + 3) * (n + 1) * sizeof(uint64_t);
     const bool smem = table <= 48 * 1024;
     int per_sm = 0;
@@ -438,7 +442,7 @@ void apparent_vec(const float *D, int64_t ld, int64_t n, const uint64_t *binom,
     if (blocks == 0) return;
     ++g_launches;
     k_apparent_vec<P, G, U><<<(unsigned)blocks, 256, smem ? table : 0, s>>>(
-        D, ld, n, binom, smem, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam);
+        D, ld, n, binom, smem, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw);
 }
 
 // group: lanes per column G (4, 8, 16, 32) for one candidate block per step,
@@ -448,19 +452,19 @@ template <int P>
 void apparent_p(int group, const float *D, int64_t ld, int64_t n, const uint64_t *binom,
                 const uint32_t *key_hi, const uint64_t *key_lo, uint64_t ncols,
                 const unsigned long long *d_ncols, DevState *st, uint8_t *status,
-                uint64_t *pivot, float *pdiam, int sms, cudaStream_t s) {
+                uint64_t *pivot, float *pdiam, uint16_t *aw, int sms, cudaStream_t s) {
     switch (group) {
-        case 4: apparent_pg<P, 4, 1>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, sms, s); break;
-        case 16: apparent_pg<P, 16, 1>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, sms, s); break;
-        case 32: apparent_pg<P, 32, 1>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, sms, s); break;
-        case 42: apparent_pg<P, 4, 2>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, sms, s); break;
-        case 82: apparent_pg<P, 8, 2>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, sms, s); break;
-        case 44: apparent_pg<P, 4, 4>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, sms, s); break;
-        case 121: apparent_vec<P, 2, 1>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, sms, s); break;
-        case 141: apparent_vec<P, 4, 1>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, sms, s); break;
-        case 142: apparent_vec<P, 4, 2>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, sms, s); break;
-        case 181: apparent_vec<P, 8, 1>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, sms, s); break;
-        default: apparent_pg<P, 8, 1>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, sms, s); break;
+        case 4: apparent_pg<P, 4, 1>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, sms, s); break;
+        case 16: apparent_pg<P, 16, 1>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, sms, s); break;
+        case 32: apparent_pg<P, 32, 1>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, sms, s); break;
+        case 42: apparent_pg<P, 4, 2>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, sms, s); break;
+        case 82: apparent_pg<P, 8, 2>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, sms, s); break;
+        case 44: apparent_pg<P, 4, 4>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, sms, s); break;
+        case 121: apparent_vec<P, 2, 1>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, sms, s); break;
+        case 141: apparent_vec<P, 4, 1>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, sms, s); break;
+        case 142: apparent_vec<P, 4, 2>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, sms, s); break;
+        case 181: apparent_vec<P, 8, 1>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, sms, s); break;
+        default: apparent_pg<P, 8, 1>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, sms, s); break;
     }
 }
 
@@ -469,13 +473,14 @@ void apparent_p(int group, const float *D, int64_t ld, int64_t n, const uint64_t
 void launch_apparent(const float *D, int64_t ld, int64_t n, int p, const uint64_t *binom,
                      const uint32_t *key_hi, const uint64_t *key_lo, uint64_t ncols,
                      const unsigned long long *d_ncols, DevState *st, uint8_t *status,
-                     uint64_t *pivot, float *pdiam, int group, int sms, cudaStream_t s) {
+                     uint64_t *pivot, float *pdiam, uint16_t *aw, int group, int sms,
+                     cudaStream_t s) {
     if (ncols == 0) return;
     switch (p) {
-        case 1: apparent_p<1>(group, D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, sms, s); break;
-        case 2: apparent_p<2>(group, D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, sms, s); break;
-        case 3: apparent_p<3>(group, D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, sms, s); break;
-        case 4: apparent_p<4>(group, D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, sms, s); break;
+        case 1: apparent_p<1>(group, D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, sms, s); break;
+        case 2: apparent_p<2>(group, D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, sms, s); break;
+        case 3: apparent_p<3>(group, D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, sms, s); break;
+        case 4: apparent_p<4>(group, D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, sms, s); break;
         default: break;
     }
 }

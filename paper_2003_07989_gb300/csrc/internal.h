@@ -126,10 +126,13 @@ void launch_edge_pairs(const uint64_t *lo, uint64_t count, uint32_t *out, cudaSt
 // [0, ncols) in coboundary order. Writes status, pivot and pivot diameter.
 // (ncols, d_ncols: the column count is min(*d_ncols, ncols) when d_ncols,
 // device memory, is given; grids are sized for ncols.)
+// aw (dimension 1, may be null): aw[edge index] = the vertex the edge's
+// apparent pair adds, written for apparent columns (the caller fills 0xFFFF).
 void launch_apparent(const float *D, int64_t ld, int64_t n, int p, const uint64_t *binom,
                      const uint32_t *key_hi, const uint64_t *key_lo, uint64_t ncols,
                      const unsigned long long *d_ncols, DevState *st, uint8_t *status,
-                     uint64_t *pivot, float *pdiam, int group, int sms, cudaStream_t s);
+                     uint64_t *pivot, float *pdiam, uint16_t *aw, int group, int sms,
+                     cudaStream_t s);
 
 // Partition: apparent columns -> (tau, sigma) pairs; leftover columns -> Leftover.
 void launch_partition(const uint8_t *status, const uint32_t *key_hi, const uint64_t *key_lo,

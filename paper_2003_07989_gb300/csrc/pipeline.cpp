@@ -61,11 +61,11 @@ Workspace::~Workspace() {
     DevBuf *d[] = {&X,    &Dsrc,  &D,      &state,   &binom,     &key_hi, &key_lo,
                    &tmp_hi, &tmp_lo, &tmp_val, &tiles, &hist,      &status, &pivot,
                    &pdiam, &app_tau, &app_sigma, &left, &bitmap, &mst,    &up, &nbr, &h0,
-                   &state_tune, &csr_off, &csr_nbr, &sp_a, &sp_b, &sp_c, &sp_cnt};
+                   &state_tune, &csr_off, &csr_nbr, &sp_a, &sp_b, &sp_c, &sp_cnt, &aw};
     for (DevBuf *b : d)
         if (b->p) cudaFree(b->p);
-    HostBuf *h[] = {&h_hi,    &h_lo,  &h_tau, &h_sigma, &h_left,
-                    &h_D,     &h_state, &h_mst, &h_up,  &h_nbr, &h_ehi, &h_eab};
+    HostBuf *h[] = {&h_hi,    &h_lo,  &h_tau, &h_sigma, &h_left, &h_D,  &h_state,
+                    &h_mst,   &h_up,  &h_nbr, &h_ehi,   &h_eab,  &h_aw};
     for (HostBuf *b : h)
         if (b->p) cudaFreeHost(b->p);
     DevBuf *bd[] = {&b_pts, &b_clouds, &b_order, &b_ctl, &b_D,   &b_mst,  &b_outs,
@@ -709,6 +709,9 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
         h0_flags = h0_count + 1;  // 64 words
     }
     uint64_t edges_begin = 0, edges_count = 0;  // dimension-1 columns (MST edges included)
+    // the apparent vertex of every edge (dimension 1), for vertices that fit 16 bits
+    const bool use_aw = !in.census && max_dim >= 1 && n <= 65535;
+    uint16_t *d_aw = nullptr;
     std::vector<uint64_t> prev_deaths;  // host-found deaths of the previous dimension
     uint64_t prev_napp = 0;
 
@@ -803,9 +806,16 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
         }
 
         if (dim1) {
+            // each edge's apparent vertex: the host's owner test for
+            // dimension 1 reads it directly, so the apparent taus need no
+            // sort (they still clear dimension 2)
+            if (use_aw) {
+                RPP_TRY(ws.dev(ws.aw, B.at(2, n) * 2, (void **)&d_aw));
+                RPP_CK(cudaMemsetAsync(d_aw, 0xFF, B.at(2, n) * 2, s));
+            }
             auto run = [&](int g, DevState *state) {
                 launch_apparent(D, ld, n, 1, d_binom, hi1, lo1, cols, d_cols, state, status,
-                                pivot, pdiam, g, ctx->sms, s);
+                                pivot, pdiam, d_aw, g, ctx->sms, s);
             };
             int group;
             RPP_TRY(apparent_shape(ctx, ws, 1, n, st, run, s, &group));
@@ -1000,7 +1010,7 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
             } else {
                 auto run = [&](int g, DevState *state) {
                     launch_apparent(D, ld, n, p, d_binom, key_hi, key_lo, N, d_n, state, status,
-                                    pivot, pdiam, g, ctx->sms, s);
+                                    pivot, pdiam, nullptr, g, ctx->sms, s);
                 };
                 int group;
                 RPP_TRY(apparent_shape(ctx, ws, p, n, st, run, s, &group));
@@ -1034,7 +1044,8 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
         }
         const bool record_app = (ctx->record & RPP_RECORD_APPARENT) != 0;
         const bool next_sparse = p < max_dim && sparse_dims;
-        if (record_app || nleft > 0 || next_sparse) {
+        const bool by_vertex = p == 1 && d_aw != nullptr;  // owner test from the vertices
+        if (record_app || (nleft > 0 && !by_vertex) || next_sparse) {
             // the apparent taus sorted: the second layer of the pair store (the
             // sigmas ride along only when the pairs are recorded; the host
             // reduction takes the owner of an apparent tau as its youngest facet)
@@ -1060,13 +1071,23 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
             Leftover *hleft;
             uint64_t *htau;
             RPP_TRY(ws.host(ws.h_left, nleft * sizeof(Leftover), (void **)&hleft));
-            RPP_TRY(ws.host(ws.h_tau, napp * 8, (void **)&htau));
-            RPP_CK(cudaMemcpyAsync(htau, app_tau, napp * 8, cudaMemcpyDeviceToHost, s));
-            I.app_tau = htau;
-            I.napp = napp;
+            if (by_vertex) {
+                uint16_t *haw;
+                RPP_TRY(ws.host(ws.h_aw, B.at(2, n) * 2, (void **)&haw));
+                RPP_CK(cudaMemcpyAsync(haw, d_aw, B.at(2, n) * 2, cudaMemcpyDeviceToHost, s));
+                I.app_w = haw;
+                I.app_tau = nullptr;
+                I.napp = 0;
+            } else {
+                RPP_TRY(ws.host(ws.h_tau, napp * 8, (void **)&htau));
+                RPP_CK(cudaMemcpyAsync(htau, app_tau, napp * 8, cudaMemcpyDeviceToHost, s));
+                I.app_w = nullptr;
+                I.app_tau = htau;
+                I.napp = napp;
+            }
             if (p == 1 && edges_count > 0 && n <= 65535) {
                 // the sorted edges as vertex pairs, for the sweep of long walks
-                // (tmp_hi is free once the pair sort has run)
+                // (tmp_hi is free once the pair sort, if any, has run)
                 uint32_t *he, *hab;
                 RPP_TRY(ws.host(ws.h_ehi, edges_count * 4, (void **)&he));
                 RPP_TRY(ws.host(ws.h_eab, edges_count * 4, (void **)&hab));

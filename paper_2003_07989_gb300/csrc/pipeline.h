@@ -74,6 +74,8 @@ struct Workspace {
     DevBuf X, Dsrc, D, state, state_tune, binom, key_hi, key_lo, tmp_hi, tmp_lo, tmp_val, tiles, hist,
         status, pivot, pdiam, app_tau, app_sigma, left, bitmap, mst, up, nbr, h0;
     DevBuf csr_off, csr_nbr, sp_a, sp_b, sp_c, sp_cnt;  // the thresholded construction
+    DevBuf aw;    // dimension 1: the vertex each edge's apparent pair adds
+    HostBuf h_aw;
     HostBuf h_hi, h_lo, h_tau, h_sigma, h_left, h_D, h_state, h_mst, h_up, h_nbr, h_ehi, h_eab;
     Binomial binom_host;      // cached table
     int64_t binom_n = -1;
