@@ -753,6 +753,9 @@ def main():
             "apparent": s0["apparent"][1], "leftover": s0["leftover"][1],
             "free_pivot": s0["free_pivot"][1], "additions": s0["additions"][1],
             "scanned": s0["scanned"][1], "intervals_h1": s0["intervals"][1],
+            "sweep_levels": s0["sweep_levels"][1], "sweep_pivots": s0["sweep_pivots"][1],
+            "sweep_idle_tests": s0["sweep_idle"][1],
+            "sweep_walks_ms": statistics.mean(s["ms_sweep_walks"] for s in st),
             "apparent_pass_simplices_per_s": s0["columns"][1] / (stage_ms[4] / 1000.0)
             if stage_ms[4] > 0 else None,
         },

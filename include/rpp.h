@@ -122,6 +122,12 @@ typedef struct {
     double ms_total;
     int64_t sparse[RPP_MAX_DIM + 1];      /* 1 where dimension p's columns were built as cliques
                                              of the threshold graph (rpp_context_set_sparse) */
+    int64_t sweep_pivots[RPP_MAX_DIM + 1]; /* nonzero entries the level sweeps found (each
+                                             then added an owner or ended its walk) */
+    int64_t sweep_idle[RPP_MAX_DIM + 1];  /* level tests passed at once: no edge of the walk's
+                                             set at either end of the level's edge */
+    double ms_sweep_walks;                /* wall time of the walks that swept, summed over
+                                             walks (they may overlap in time) */
 } rpp_stats;
 
 typedef struct rpp_context rpp_context;

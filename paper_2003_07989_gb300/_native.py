@@ -52,7 +52,8 @@ class Stats(C.Structure):
                 ("kernel_launches", C.c_int64),
                 ("stage_ms", C.c_double * 8), ("stage_launches", C.c_int64 * 8),
                 ("ms_device", C.c_double), ("ms_host_reduce", C.c_double),
-                ("ms_host_h0", C.c_double), ("ms_total", C.c_double), ("sparse", _A)]
+                ("ms_host_h0", C.c_double), ("ms_total", C.c_double), ("sparse", _A),
+                ("sweep_pivots", _A), ("sweep_idle", _A), ("ms_sweep_walks", C.c_double)]
 
 
 class ServerConfig(C.Structure):

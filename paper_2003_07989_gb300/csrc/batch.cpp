@@ -541,6 +541,9 @@ Status launch_host(rpp_context *ctx, Launch &L,
                 S.store_reads[1] = rs.reads;
                 S.entries[1] = rs.entries;
                 S.sweep_levels[1] = rs.levels;
+                S.sweep_pivots[1] = rs.sweep_pivots;
+                S.sweep_idle[1] = rs.sweep_idle;
+                S.ms_sweep_walks = rs.sweep_walk_ms;
                 int vs[2], vt[3];
                 for (const HostPair &P : pairs) {
                     if (P.tau != NO_PIVOT && !(P.death > P.birth)) continue;

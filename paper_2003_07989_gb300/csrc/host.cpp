@@ -983,6 +983,9 @@ struct Walk1 {
         heap;
     std::vector<uint64_t> V;      // edges of V (indices)
     int64_t additions = 0, reads = 0, entries = 0, levels = 0;
+    int64_t sweep_pivots = 0;
+    mutable int64_t sweep_idle = 0;
+    bool swept = false;  // the walk entered sweep mode at least once
     int threads = 1;
 
     // rows_: the calling thread's scratch of n x 2 ceil(n / 64) words, all
@@ -1550,7 +1553,10 @@ struct Walk1 {
 
     // Oldest triangle of edge E still to come that is odd now (w, or -1).
     int level_head(const LevelEdge &E) const {
-        if (deg[E.a] == 0 && deg[E.b] == 0) return -1;
+        if (deg[E.a] == 0 && deg[E.b] == 0) {
+            ++sweep_idle;
+            return -1;
+        }
         const uint64_t *Pa = P + (int64_t)E.a * S, *Pb = P + (int64_t)E.b * S;
         const uint64_t *Aa = adj + (int64_t)E.a * S, *Ab = adj + (int64_t)E.b * S;
         const uint64_t flip = vbit(E.a, E.b) ? ~0ull : 0ull;
@@ -1586,6 +1592,7 @@ struct Walk1 {
         cur.clear();
         heap.clear();
         sweep = true;
+        swept = true;
         P = rows;
         deg.assign(n, 0);
         for (uint64_t e : V) {  // V has no repeats here (heap mode or a rebuilt set)
@@ -1646,6 +1653,11 @@ struct Walk1 {
 
     // Oldest nonzero entry in sweep mode; the sweep moves past it.
     u128 pivot_sweep() {
+        const u128 k = pivot_sweep_levels();
+        if (k != NONE) ++sweep_pivots;
+        return k;
+    }
+    u128 pivot_sweep_levels() {
         for (;;) {
             if (lev.size() == 1) {
                 LevelEdge &E = lev[0];
@@ -1774,6 +1786,8 @@ void reduce_p1(const HostInstance &I, const Leftover *left, int64_t nleft, int t
     std::vector<std::vector<uint64_t>> V(nleft);  // reduced columns as edge sets
     std::vector<char> walked(nleft, 0);
     std::vector<int64_t> adds(nleft, 0), reads(nleft, 0), entries(nleft, 0), levels(nleft, 0);
+    std::vector<int64_t> spiv(nleft, 0), sidle(nleft, 0);
+    std::vector<double> sms(nleft, 0.0);
     Ledger<K> led(V, nleft);
     for (int64_t j = 0; j < nleft; ++j)
         if (left[j].pivot != NO_PIVOT) led.advance(j, age_key(left[j].pdiam, left[j].pivot));
@@ -1796,8 +1810,14 @@ void reduce_p1(const HostInstance &I, const Leftover *left, int64_t nleft, int t
         Walk1<K> W(I, R, adjacency_scratch(I.n), threads);
         int v[2];
         decode_host(*I.B, L.sigma, 1, I.n, v);
+        const auto w0 = std::chrono::steady_clock::now();
         W.add_edge(v[0], v[1], L.diam, first_vertex(R, L, v));
         const u128 k = W.walk(led, j);
+        if (W.swept)
+            sms[j] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - w0)
+                         .count();
+        spiv[j] = W.sweep_pivots;
+        sidle[j] = W.sweep_idle;
         V[j] = W.edges();
         piv[j] = k;
         walked[j] = 1;
@@ -1832,6 +1852,9 @@ void reduce_p1(const HostInstance &I, const Leftover *left, int64_t nleft, int t
         stats.reads += reads[j];
         stats.entries += entries[j];
         stats.levels += levels[j];
+        stats.sweep_pivots += spiv[j];
+        stats.sweep_idle += sidle[j];
+        stats.sweep_walk_ms += sms[j];
     }
 }
 

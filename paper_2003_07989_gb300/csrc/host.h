@@ -55,6 +55,11 @@ struct HostPair {
 // ---- submatrix reduction ----------------------------------------------------
 struct ReduceStats {
     int64_t free_pivot = 0, additions = 0, reads = 0, entries = 0, levels = 0;
+    // sweeps of long dimension-1 walks: pivots found level by level, level
+    // tests passed with no edge of V at either end, and the wall time of the
+    // walks that swept (summed over walks, which may overlap in time)
+    int64_t sweep_pivots = 0, sweep_idle = 0;
+    double sweep_walk_ms = 0.0;
 };
 
 // Run fn(0) .. fn(count - 1) on the library's persistent host threads, the

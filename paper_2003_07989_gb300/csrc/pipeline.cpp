@@ -1142,6 +1142,9 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
             S.store_reads[p] = rs.reads;
             S.entries[p] = rs.entries;
             S.sweep_levels[p] = rs.levels;
+            S.sweep_pivots[p] = rs.sweep_pivots;
+            S.sweep_idle[p] = rs.sweep_idle;
+            S.ms_sweep_walks += rs.sweep_walk_ms;
             red_ms += now_ms() - a;
         }
         // intervals of dimension p and the deaths that clear dimension p + 1
