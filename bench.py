@@ -54,6 +54,9 @@ def parse_args():
                     help="profiling aid: one batched call over the serving mix's clouds of "
                          "257-512 points inside an NVTX range 'batched' (after an untimed "
                          "call), then exit")
+    ap.add_argument("--profile-filtration", action="store_true",
+                    help="profiling aid: the dimension-2 filtration (build and sort, no "
+                         "clearing) of the first 1000 torus points, three times, then exit")
     ap.add_argument("--no-extras", action="store_true",
                     help="only the torus steps: no serving, census, differentiation or S^3 section")
     return ap.parse_args()
@@ -612,6 +615,15 @@ def main():
     from paper_2003_07989_gb300 import inputs as I
 
     torch.cuda.set_device(local)
+    if args.profile_filtration:
+        X = torch.from_numpy(I.noisy_torus(N_POINTS, seed=0)[:1000]).cuda()
+        c = rpp.Context(local)
+        for _ in range(3):
+            _, _, st = rpp.rpp_filtration(X, 2, out=False, context=c)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_filtration": 1000, "columns": st["columns"][2],
+                          "candidates": st["candidates"][2]}))
+        return
     if args.profile_batched:
         reqs = [r for r in I.serving_requests(4096, seed=0) if r.points.shape[0] > 256]
         clouds = [r.points for r in reqs]
