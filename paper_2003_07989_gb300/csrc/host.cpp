@@ -756,48 +756,84 @@ void reduce_set(SimplexSet &V) {
     V.resize(o);
 }
 
-// The leftover columns of dimension p walk concurrently, one per host thread
-// at a time, in index order (the ledger makes the additions those of Alg. 1
-// in column order, whatever the interleaving).
+// Two phases. A: every column walks on its own (in parallel, no shared
+// state) while its pivots have apparent owners, and stops at the first pivot
+// without one. B: the columns then finish concurrently, one per host thread
+// at a time, in index order: a column whose pivot an earlier leftover column
+// owns adds that column's reduced column and walks on under the ledger, which
+// makes the additions those of Alg. 1 in column order whatever the
+// interleaving (as in dimension 1). Most columns leave phase B after one
+// ledger query.
 void reduce_general(const HostInstance &I, int p, const Leftover *left, int64_t nleft,
                     int threads, std::vector<HostPair> &out, ReduceStats &stats) {
     Reducer R(I, p);
     std::vector<ColumnState> col(nleft);
     std::vector<SimplexSet> V(nleft);
     Ledger<Key128, SimplexSet> led(V, nleft);
-    for (int64_t j = 0; j < nleft; ++j)
-        if (left[j].pivot != NO_PIVOT) led.advance(j, age_key(left[j].pdiam, left[j].pivot));
 
-    auto column = [&](int64_t j) {
+    auto phase_a_column = [&](int64_t j) {
         const Leftover &L = left[j];
         ColumnState &S = col[j];
         if (L.pivot == NO_PIVOT) {
             S.cand = NONE;
-            led.finish(j, NONE);
             return;
         }
         const u128 k0 = age_key(L.pdiam, L.pivot);
         int s[RPP_MAX_DIM + 1], added;
         ++S.reads;
-        if (!R.apparent_owner(k0, s, &added) && led.query(j, k0) < 0) {
-            S.cand = k0;  // the unreduced pivot is free
-            V[j].emplace_back(L.sigma, L.diam);
-            led.finish(j, k0);
+        if (!R.apparent_owner(k0, s, &added)) {
+            S.cand = k0;  // the unreduced pivot is free of apparent owners
             return;
         }
         start_column(R, S, L);
-        walk(R, S, led, j);
-        reduce_set(S.V);
-        V[j].swap(S.V);
+        for (;;) {  // apparent owners only
+            const u128 k = pivot(R, S);
+            if (k == NONE) {
+                S.cand = NONE;
+                return;
+            }
+            ++S.reads;
+            if (!R.apparent_owner(k, s, &added)) {
+                S.cand = k;
+                return;
+            }
+            ++S.additions;
+            add_cursor(R, S, s, index_host(*R.I.B, s, R.p), key_diam(k), added);
+        }
+    };
+    auto phase_b_column = [&](int64_t j) {
+        const Leftover &L = left[j];
+        ColumnState &S = col[j];
+        if (S.cand != NONE) {
+            const int64_t i = led.query(j, S.cand);
+            if (i >= 0) {  // owned by an earlier leftover column: add it and walk on
+                if (!S.started) start_column(R, S, L);
+                ++S.additions;
+                for (const auto &x : led.V[i]) add_cursor(R, S, x.first, x.second);
+                walk(R, S, led, j);
+            }
+        }
+        if (S.started) {
+            reduce_set(S.V);
+            V[j].swap(S.V);
+        } else {
+            V[j].emplace_back(L.sigma, L.diam);
+        }
         std::vector<Cursor>().swap(S.cur);
         std::vector<std::pair<u128, int32_t>>().swap(S.heap);
         led.finish(j, S.cand);
     };
+    if (threads <= 1 || nleft < 16) {
+        for (int64_t j = 0; j < nleft; ++j) phase_a_column(j);
+    } else {
+        pool(threads).parallel_for(nleft, phase_a_column);
+    }
+    for (int64_t j = 0; j < nleft; ++j) led.advance(j, col[j].cand);  // NONE: past everything
     // columns start in increasing order (the pool hands out indices in order)
     if (threads <= 1 || nleft < 16) {
-        for (int64_t j = 0; j < nleft; ++j) column(j);
+        for (int64_t j = 0; j < nleft; ++j) phase_b_column(j);
     } else {
-        pool(threads).parallel_for(nleft, column);
+        pool(threads).parallel_for(nleft, phase_b_column);
     }
 
     for (int64_t j = 0; j < nleft; ++j) {
