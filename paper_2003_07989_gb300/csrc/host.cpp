@@ -567,6 +567,12 @@ struct Key128 {
     static u128 wide(T k) { return k; }
 };
 
+inline int bits_of(uint64_t x) {  // bits needed to write x
+    int b = 0;
+    while (b < 64 && (x >> b)) ++b;
+    return b;
+}
+
 // Pivots of the leftover columns of one dimension reduced so far, shared by
 // the columns that are reduced in parallel. Column j adds column i < j once
 // i is finished, and keeps a pivot that no finished column owns only when
@@ -584,30 +590,37 @@ struct Ledger {
     std::vector<Col> &V;                          // reduced columns, final once finished
     std::vector<char> done;
     int64_t low = 0;                              // columns below are finished
-    // Per column, a lower bound of its current pivot as a 64-bit key: exact
-    // for 64-bit keys, the diameter bits alone for 128-bit ones.
+    int waiting = 0;                              // queries waiting (under m)
+    // Per column, its current pivot as a 64-bit image that preserves the age
+    // order (an image that is smaller or equal for every older key): exact
+    // for 64-bit keys; for 128-bit ones the diameter bits over the top 32
+    // bits of the complemented index, taken over idx_bits significant bits
+    // (exact when they number 32 or fewer).
     std::unique_ptr<std::atomic<uint64_t>[]> front;
+    int idx_bits = 64;
 
-    Ledger(std::vector<Col> &V_, int64_t ncols)
-        : V(V_), done(ncols, 0), front(new std::atomic<uint64_t>[ncols]) {
+    Ledger(std::vector<Col> &V_, int64_t ncols, int idx_bits_ = 64)
+        : V(V_), done(ncols, 0), front(new std::atomic<uint64_t>[ncols]), idx_bits(idx_bits_) {
         owner.reserve((size_t)ncols * 2);
         for (int64_t j = 0; j < ncols; ++j) front[j].store(0, std::memory_order_relaxed);
     }
-    static uint64_t lower(u128 k) {
+    uint64_t image(u128 k) const {
         if (k == NONE) return ~0ull;
         if (std::is_same<typename K::T, uint64_t>::value) return (uint64_t)K::make(key_diam(k), key_index(k));
-        return (uint64_t)float_bits(key_diam(k)) << 32;
+        const uint64_t idx = key_index(k);
+        const int b = idx_bits < 64 ? idx_bits : 64;
+        const uint64_t rev = (b == 64 ? ~0ull : ((1ull << b) - 1)) - idx;  // larger index: smaller
+        const uint64_t top = b > 32 ? rev >> (b - 32) : rev;
+        return ((uint64_t)float_bits(key_diam(k)) << 32) | top;
     }
-    static uint64_t upper(u128 k) {
-        if (std::is_same<typename K::T, uint64_t>::value) return (uint64_t)K::make(key_diam(k), key_index(k));
-        return ((uint64_t)float_bits(key_diam(k)) << 32) | 0xffffffffull;
-    }
-    void advance(int64_t j, u128 k) { front[j].store(lower(k), std::memory_order_relaxed); }
+    void advance(int64_t j, u128 k) { front[j].store(image(k), std::memory_order_relaxed); }
 
     // The finished column that owns pivot k of column j, or -1 when k is
-    // free for j; waits while an unfinished earlier column may still end at k.
+    // free for j; waits while an unfinished earlier column may still end at k
+    // (its pivot's image is at most k's: pivots only move forward, and the
+    // image keeps their order).
     int64_t query(int64_t j, u128 k) {
-        const uint64_t ub = upper(k);
+        const uint64_t ub = image(k);
         std::unique_lock<std::mutex> g(m);
         for (int round = 0;; ++round) {
             auto it = owner.find(key_index(k));
@@ -618,17 +631,21 @@ struct Ledger {
                 blocked = !done[i] && front[i].load(std::memory_order_relaxed) <= ub;
             if (!blocked) return -1;
             // earlier columns move their pivots without notice: look again soon
+            ++waiting;
             cv.wait_for(g, std::chrono::microseconds(round < 64 ? 10 : 100));
+            --waiting;
         }
     }
     // Column j is finished with pivot k (NONE: a zero column); V[j] is final.
     void finish(int64_t j, u128 k) {
+        bool wake;
         {
             std::lock_guard<std::mutex> g(m);
             if (k != NONE) owner[key_index(k)] = j;
             done[j] = 1;
+            wake = waiting > 0;
         }
-        cv.notify_all();
+        if (wake) cv.notify_all();
     }
 };
 
@@ -769,7 +786,8 @@ void reduce_general(const HostInstance &I, int p, const Leftover *left, int64_t 
     Reducer R(I, p);
     std::vector<ColumnState> col(nleft);
     std::vector<SimplexSet> V(nleft);
-    Ledger<Key128, SimplexSet> led(V, nleft);
+    // cofacet indices (the pivots) stay below C(n, p+2)
+    Ledger<Key128, SimplexSet> led(V, nleft, bits_of(I.B->at(p + 2, I.n)));
 
     auto phase_a_column = [&](int64_t j) {
         const Leftover &L = left[j];
@@ -1824,7 +1842,7 @@ void reduce_p1(const HostInstance &I, const Leftover *left, int64_t nleft, int t
     std::vector<int64_t> adds(nleft, 0), reads(nleft, 0), entries(nleft, 0), levels(nleft, 0);
     std::vector<int64_t> spiv(nleft, 0), sidle(nleft, 0);
     std::vector<double> sms(nleft, 0.0);
-    Ledger<K> led(V, nleft);
+    Ledger<K> led(V, nleft, bits_of(I.B->at(3, I.n)));
     for (int64_t j = 0; j < nleft; ++j)
         if (left[j].pivot != NO_PIVOT) led.advance(j, age_key(left[j].pdiam, left[j].pivot));
 
