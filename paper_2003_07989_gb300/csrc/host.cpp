@@ -630,9 +630,17 @@ struct Ledger {
             for (int64_t i = low; i < j && !blocked; ++i)
                 blocked = !done[i] && front[i].load(std::memory_order_relaxed) <= ub;
             if (!blocked) return -1;
-            // earlier columns move their pivots without notice: look again soon
+            // earlier columns move their pivots without notice: look again
+            // soon (a short spin first: a sleep's timer slack is longer than
+            // most waits)
+            if (round < 256) {
+                g.unlock();
+                std::this_thread::yield();
+                g.lock();
+                continue;
+            }
             ++waiting;
-            cv.wait_for(g, std::chrono::microseconds(round < 64 ? 10 : 100));
+            cv.wait_for(g, std::chrono::microseconds(round < 320 ? 10 : 100));
             --waiting;
         }
     }
@@ -773,6 +781,8 @@ void reduce_set(SimplexSet &V) {
     V.resize(o);
 }
 
+constexpr double PHASE_B_SERIAL_MS = 4.0;
+
 // Two phases. A: every column walks on its own (in parallel, no shared
 // state) while its pivots have apparent owners, and stops at the first pivot
 // without one. B: the columns then finish concurrently, one per host thread
@@ -780,7 +790,8 @@ void reduce_set(SimplexSet &V) {
 // owns adds that column's reduced column and walks on under the ledger, which
 // makes the additions those of Alg. 1 in column order whatever the
 // interleaving (as in dimension 1). Most columns leave phase B after one
-// ledger query.
+// ledger query; phase B runs in order on the calling thread until it proves
+// long, then concurrently.
 void reduce_general(const HostInstance &I, int p, const Leftover *left, int64_t nleft,
                     int threads, std::vector<HostPair> &out, ReduceStats &stats) {
     Reducer R(I, p);
@@ -847,11 +858,23 @@ void reduce_general(const HostInstance &I, int p, const Leftover *left, int64_t 
         pool(threads).parallel_for(nleft, phase_a_column);
     }
     for (int64_t j = 0; j < nleft; ++j) led.advance(j, col[j].cand);  // NONE: past everything
-    // columns start in increasing order (the pool hands out indices in order)
-    if (threads <= 1 || nleft < 16) {
-        for (int64_t j = 0; j < nleft; ++j) phase_b_column(j);
-    } else {
-        pool(threads).parallel_for(nleft, phase_b_column);
+    // In order on this thread while that stays cheap (most columns leave
+    // after one query, and then the ledger's coordination would cost more
+    // than it saves); once phase B has taken PHASE_B_SERIAL_MS, the remaining
+    // columns go to the host threads (they start in increasing order: the
+    // pool hands out indices in order).
+    const auto b0 = std::chrono::steady_clock::now();
+    int64_t j = 0;
+    for (; j < nleft; ++j) {
+        if (threads > 1 && (j & 63) == 0 &&
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - b0)
+                    .count() > PHASE_B_SERIAL_MS)
+            break;
+        phase_b_column(j);
+    }
+    if (j < nleft) {
+        const int64_t first = j;
+        pool(threads).parallel_for(nleft - first, [&](int64_t i) { phase_b_column(first + i); });
     }
 
     for (int64_t j = 0; j < nleft; ++j) {

@@ -48,7 +48,7 @@ constexpr uint64_t LB_FLAGS = 3ull << 62;
 constexpr int LB_EPOCH_SHIFT = 56;          // pass + 1 in bits 56..61
 constexpr uint64_t LB_VALUE = (1ull << LB_EPOCH_SHIFT) - 1;
 constexpr long long LB_SPIN_LIMIT = 1ll << 22;
-constexpr int LB_WINDOW = 16;               // look-back entries loaded together
+constexpr int LB_WINDOW = 4;                // look-back entries loaded together
 
 // Control block at the start of the scratch; zeroed before each sort.
 struct SortCtl {
@@ -168,9 +168,6 @@ __global__ void __launch_bounds__(OS_THREADS, 4) k_onesweep(
     __shared__ unsigned int s_warp[OS_WARPS][RADIX];  // per-warp counts, then starts
     __shared__ unsigned int s_hist[RADIX];            // the tile's digit counts
     __shared__ unsigned long long s_base[RADIX];      // global start of each digit for this tile
-    // look-back window, thread-private columns (thread tid only touches
-    // s_lb[.][tid]): LB_WINDOW loads in flight without LB_WINDOW registers
-    __shared__ unsigned long long s_lb[LB_WINDOW][OS_THREADS];
     __shared__ unsigned int s_tile;
     if (!ctl->active[pass]) return;
     const uint64_t n = key_count(d_count, n_cap);
@@ -236,12 +233,14 @@ __global__ void __launch_bounds__(OS_THREADS, 4) k_onesweep(
         uint64_t excl = 0;
         bool done = false;
         for (int64_t t0 = (int64_t)tile - 1; t0 >= 0 && !done; t0 -= LB_WINDOW) {
+            unsigned long long e[LB_WINDOW];
 #pragma unroll
             for (int i = 0; i < LB_WINDOW; ++i)
-                s_lb[i][tid] = t0 - i >= 0 ? *(const volatile unsigned long long *)(lookback +
-                                                                                  (uint64_t)(t0 - i) *
-                                                                                      RADIX + tid)
-                                           : 0ull;
+                e[i] = t0 - i >= 0 ? *(const volatile unsigned long long *)(lookback +
+                                                                           (uint64_t)(t0 - i) *
+                                                                               RADIX + tid)
+                                   : 0ull;
+#pragma unroll
             for (int i = 0; i < LB_WINDOW; ++i) {
                 if (done || t0 - i < 0) {
                     done = true;
@@ -250,7 +249,7 @@ __global__ void __launch_bounds__(OS_THREADS, 4) k_onesweep(
                 const volatile unsigned long long *src =
                     (const volatile unsigned long long *)(lookback + (uint64_t)(t0 - i) * RADIX +
                                                           tid);
-                unsigned long long v = s_lb[i][tid];
+                unsigned long long v = e[i];
                 long long spins = 0;
                 while (((v & LB_FLAGS) == 0 || (v & ~LB_FLAGS & ~LB_VALUE) != epoch) &&
                        spins < LB_SPIN_LIMIT) {
