@@ -128,6 +128,8 @@ typedef struct {
                                              set at either end of the level's edge */
     double ms_sweep_walks;                /* wall time of the walks that swept, summed over
                                              walks (they may overlap in time) */
+    int64_t device_columns[RPP_MAX_DIM + 1]; /* leftover columns reduced on the device
+                                             (batched clouds of <= 512 points) */
 } rpp_stats;
 
 typedef struct rpp_context rpp_context;
@@ -278,6 +280,18 @@ rpp_status rpp_context_set_batch(rpp_context *ctx, int32_t fused, int32_t autotu
  *          with RPP_E_NOMEM).
  * Errors: RPP_E_INVALID for a NULL context or another mode. */
 rpp_status rpp_context_set_sparse(rpp_context *ctx, int32_t mode);
+
+/* Where the batched clouds' leftover columns of dimension 1 are reduced
+ * (Alg. 1, the submatrix reduction of Sec. "Core System Optimizations").
+ * on = 1 (default): clouds of up to 512 points in a fused launch reduce them
+ * on the device, one warp per cloud in column order, right after the fused
+ * pass; a cloud whose walks grow past the device's budget (more than 64
+ * additions for one column, or a column summing more than 64 edges: the long
+ * walks the host sweeps) is reduced on the host instead. on = 0: every cloud
+ * is reduced on the host. Both give the same barcodes; rpp_stats.
+ * device_columns counts the columns reduced on the device.
+ * Errors: RPP_E_INVALID for a NULL context. */
+rpp_status rpp_context_set_device_reduce(rpp_context *ctx, int32_t on);
 
 /* The launch shape the autotuner chose for the bucket of clouds with up to
  * nmax points (64, 128, 256, 512 or 1024): threads per block and the

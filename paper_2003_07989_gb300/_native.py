@@ -24,7 +24,7 @@ EXPORTED = [
     "rpp_result_columns", "rpp_result_apparent", "rpp_filtration_edges_noalloc",
     "rpp_context_set_batch", "rpp_context_batch_tuning", "rpp_apparent_census",
     "rpp_results_gather", "rpp_results_stats", "rpp_results_free", "rpp_server_next",
-    "rpp_filtration", "rpp_context_set_sparse",
+    "rpp_filtration", "rpp_context_set_sparse", "rpp_context_set_device_reduce",
 ]
 RPP_RECORD_COLUMNS, RPP_RECORD_APPARENT, RPP_RECORD_TIMING = 1, 2, 4
 STAGES = ["distance", "enclosing_radius", "build_columns", "sort_columns", "apparent",
@@ -53,7 +53,8 @@ class Stats(C.Structure):
                 ("stage_ms", C.c_double * 8), ("stage_launches", C.c_int64 * 8),
                 ("ms_device", C.c_double), ("ms_host_reduce", C.c_double),
                 ("ms_host_h0", C.c_double), ("ms_total", C.c_double), ("sparse", _A),
-                ("sweep_pivots", _A), ("sweep_idle", _A), ("ms_sweep_walks", C.c_double)]
+                ("sweep_pivots", _A), ("sweep_idle", _A), ("ms_sweep_walks", C.c_double),
+                ("device_columns", _A)]
 
 
 class ServerConfig(C.Structure):
@@ -129,6 +130,7 @@ def lib():
     L.rpp_results_free.restype = None
     L.rpp_context_batch_tuning.argtypes = [vp, i32, C.POINTER(i32), C.POINTER(i32)]
     L.rpp_context_set_sparse.argtypes = [vp, i32]
+    L.rpp_context_set_device_reduce.argtypes = [vp, i32]
     L.rpp_filtration.argtypes = [vp, vp, C.c_int, i64, i32, i32, C.c_float, vp, vp, vp, i64,
                                  C.POINTER(i64), C.POINTER(Stats)]
     for name in ("rpp_context_set_batch", "rpp_context_batch_tuning",
@@ -137,7 +139,7 @@ def lib():
                  "rpp_result_stats", "rpp_barcodes_batched", "rpp_barcodes_backward",
                  "rpp_server_create", "rpp_server_submit", "rpp_server_poll",
                  "rpp_results_gather", "rpp_results_stats", "rpp_server_next",
-                 "rpp_filtration", "rpp_context_set_sparse"):
+                 "rpp_filtration", "rpp_context_set_sparse", "rpp_context_set_device_reduce"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L

@@ -44,6 +44,12 @@ class Context:
         N.check(N.lib().rpp_context_set_batch(self.handle, int(fused), int(autotune)),
                 "rpp_context_set_batch")
 
+    def set_device_reduce(self, on: bool = True):
+        """rpp_context_set_device_reduce: batched clouds of <= 512 points reduce
+        their leftover columns on the device (on) or on the host (off)."""
+        N.check(N.lib().rpp_context_set_device_reduce(self.handle, int(on)),
+                "rpp_context_set_device_reduce")
+
     def set_sparse(self, mode: int = 0):
         """rpp_context_set_sparse: 0 chooses the thresholded construction of
         dimensions >= 2 by edge density, 1 always takes it, 2 never."""

@@ -278,6 +278,14 @@ struct Launch {
     float *hD = nullptr;             // per job: distance rows, neighbour lists, apparent vertices
     uint64_t *hN = nullptr;
     uint16_t *hA = nullptr;
+    // the device reduction: per row job its reduce job (-1: none); per reduce
+    // job its leftovers' first position, status and additions; per leftover
+    // (sorted by index within its cloud) the death index and diameter
+    std::vector<int> rjob;
+    std::vector<int64_t> rleft;
+    const int32_t *rstat = nullptr, *radds = nullptr;
+    const uint64_t *rdeath = nullptr;
+    const float *rddiam = nullptr;
 };
 
 // Device half of a fused launch: the pass itself, then the distance rows,
@@ -434,6 +442,81 @@ Status launch_device(rpp_context *ctx, Workspace &ws, const std::vector<Instance
         RPP_CK(cudaMemcpyAsync(doff, (char *)hp + nj * 4, 2 * nj * 8, cudaMemcpyHostToDevice, s));
         launch_batch_rows(b.D, b.clouds, djobs, (int)nj, doff, nmax, dD, dN, b.app_w, dA, s);
         RPP_CK(cudaGetLastError());
+        // clouds of up to REDUCE_SMALL_NMAX points reduce their leftover
+        // columns on the device (a cloud whose walks outgrow the device's
+        // budget comes back to the host reductions below)
+        L.rjob.assign(nj, -1);
+        L.rleft.clear();
+        L.rstat = L.radds = nullptr;
+        L.rdeath = nullptr;
+        L.rddiam = nullptr;
+        if (ctx->device_reduce) {
+            std::vector<ReduceJob> rj;
+            int64_t lpos = 0;
+            int rnmax = 0;
+            for (size_t q = 0; q < nj; ++q) {
+                const int j = jobs[q];
+                const BatchCloud &c = b.h_clouds[j];
+                if (c.n > REDUCE_SMALL_NMAX) continue;
+                std::vector<Leftover> &Lv = W[j].left;
+                std::sort(Lv.begin(), Lv.end(),
+                          [](const Leftover &x, const Leftover &y) { return x.index < y.index; });
+                ReduceJob R;
+                R.d_off = off[q];
+                R.aw_off = aoff[q];
+                R.left_off = lpos;
+                R.nleft = (int64_t)Lv.size();
+                R.n = c.n;
+                R.t = b.h_outs[j].t;
+                L.rjob[q] = (int)rj.size();
+                L.rleft.push_back(lpos);
+                rj.push_back(R);
+                lpos += (int64_t)Lv.size();
+                rnmax = std::max(rnmax, c.n);
+            }
+            if (!rj.empty()) {
+                const size_t nr = rj.size(), nl = (size_t)lpos;
+                const size_t in_bytes = nr * sizeof(ReduceJob) + nl * sizeof(Leftover);
+                RPP_TRY(ws.host(ws.hr_in, in_bytes, &hp));
+                std::memcpy(hp, rj.data(), nr * sizeof(ReduceJob));
+                Leftover *hl = (Leftover *)((char *)hp + nr * sizeof(ReduceJob));
+                for (size_t q = 0; q < nj; ++q)
+                    if (L.rjob[q] >= 0) {
+                        const std::vector<Leftover> &Lv = W[jobs[q]].left;
+                        std::memcpy(hl + L.rleft[L.rjob[q]], Lv.data(), Lv.size() * sizeof(Leftover));
+                    }
+                void *dj, *dl, *dvp, *dvc, *dde, *ddd, *dst;
+                RPP_TRY(ws.dev(ws.r_jobs, nr * sizeof(ReduceJob), &dj));
+                RPP_TRY(ws.dev(ws.r_left, std::max<size_t>(nl, 1) * sizeof(Leftover), &dl));
+                RPP_TRY(ws.dev(ws.r_vpool, std::max<size_t>(reduce_small_vpool_words(nl), 1) * 4, &dvp));
+                RPP_TRY(ws.dev(ws.r_vcnt, std::max<size_t>(nl, 1), &dvc));
+                RPP_TRY(ws.dev(ws.r_death, std::max<size_t>(nl, 1) * 8, &dde));
+                RPP_TRY(ws.dev(ws.r_ddiam, std::max<size_t>(nl, 1) * 4, &ddd));
+                RPP_TRY(ws.dev(ws.r_stat, nr * 8, &dst));
+                RPP_CK(cudaMemcpyAsync(dj, hp, nr * sizeof(ReduceJob), cudaMemcpyHostToDevice, s));
+                if (nl)
+                    RPP_CK(cudaMemcpyAsync(dl, hl, nl * sizeof(Leftover), cudaMemcpyHostToDevice, s));
+                launch_reduce_small(dD, dA, (const ReduceJob *)dj, (int)nr, rnmax,
+                                    (const Leftover *)dl, (uint32_t *)dvp, (uint8_t *)dvc,
+                                    (uint64_t *)dde, (float *)ddd, (int32_t *)dst,
+                                    (int32_t *)dst + nr, s);
+                RPP_CK(cudaGetLastError());
+                const size_t out_bytes = nl * 8 + nl * 4 + nr * 8;
+                RPP_TRY(ws.host(ws.hr_out, std::max<size_t>(out_bytes, 8), &hp));
+                uint64_t *hde = (uint64_t *)hp;
+                float *hdd = (float *)(hde + nl);
+                int32_t *hst = (int32_t *)(hdd + nl);
+                if (nl) {
+                    RPP_CK(cudaMemcpyAsync(hde, dde, nl * 8, cudaMemcpyDeviceToHost, s));
+                    RPP_CK(cudaMemcpyAsync(hdd, ddd, nl * 4, cudaMemcpyDeviceToHost, s));
+                }
+                RPP_CK(cudaMemcpyAsync(hst, dst, nr * 8, cudaMemcpyDeviceToHost, s));
+                L.rdeath = hde;
+                L.rddiam = hdd;
+                L.rstat = hst;
+                L.radds = hst + nr;
+            }
+        }
         RPP_TRY(ws.host(ws.hb_Dout, (size_t)rows * 4, &hp));
         hD = (float *)hp;
         RPP_TRY(ws.host(ws.hb_nbr, (size_t)rows * 8, &hp));
@@ -520,6 +603,7 @@ Status launch_host(rpp_context *ctx, Launch &L,
             S.scanned[1] = (int64_t)o.scanned;
             if (W[j].job >= 0) {
                 const double a3 = now_ms();
+                const int rj = L.rjob.empty() ? -1 : L.rjob[W[j].job];
                 HostInstance I;
                 I.n = n;
                 I.D = hD + off[W[j].job];
@@ -530,12 +614,27 @@ Status launch_host(rpp_context *ctx, Launch &L,
                 I.napp = 0;
                 I.app_w = hA + aoff[W[j].job];  // the apparent pairs found on the GPU
                 I.t = o.t;
-                std::vector<Leftover> &L = W[j].left;
-                std::sort(L.begin(), L.end(),
-                          [](const Leftover &x, const Leftover &y) { return x.index < y.index; });
+                std::vector<Leftover> &Lv = W[j].left;
                 std::vector<HostPair> pairs;
                 ReduceStats rs;
-                reduce_leftovers(I, 1, L.data(), (int64_t)L.size(), inner, pairs, rs);
+                if (rj >= 0 && L.rstat[rj] == 0) {  // reduced on the device
+                    const int64_t base = L.rleft[rj];
+                    for (size_t q = 0; q < Lv.size(); ++q) {
+                        HostPair P;
+                        P.sigma = Lv[q].sigma;
+                        P.birth = Lv[q].diam;
+                        P.tau = L.rdeath[base + (int64_t)q];
+                        P.death = P.tau == NO_PIVOT ? INFINITY : L.rddiam[base + (int64_t)q];
+                        pairs.push_back(P);
+                    }
+                    rs.additions = L.radds[rj];
+                    S.device_columns[1] = (int64_t)Lv.size();
+                } else {
+                    std::sort(Lv.begin(), Lv.end(), [](const Leftover &x, const Leftover &y) {
+                        return x.index < y.index;
+                    });
+                    reduce_leftovers(I, 1, Lv.data(), (int64_t)Lv.size(), inner, pairs, rs);
+                }
                 S.free_pivot[1] = rs.free_pivot;
                 S.additions[1] = rs.additions;
                 S.store_reads[1] = rs.reads;
@@ -718,6 +817,15 @@ extern "C" rpp_status rpp_barcodes_batched(rpp_context *ctx, int32_t batch,
     if (ws2) ctx->release(ws2);
     ctx->release(ws);
     if (!s.ok()) return report(s);
+    return RPP_OK;
+}
+
+extern "C" rpp_status rpp_context_set_device_reduce(rpp_context *ctx, int32_t on) {
+    if (!ctx) {
+        set_last_error("rpp_context_set_device_reduce: ctx is NULL");
+        return RPP_E_INVALID;
+    }
+    ctx->device_reduce = on != 0;
     return RPP_OK;
 }
 

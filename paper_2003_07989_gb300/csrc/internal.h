@@ -246,6 +246,26 @@ void launch_batch_rows(const float *Dbuf, const BatchCloud *clouds, const int32_
                        const int64_t *out_off, int nmax, float *Dout, uint64_t *nbr,
                        const uint16_t *app_w, uint16_t *aw_out, cudaStream_t s);
 
+// The dimension-1 reduction of small clouds' leftover columns on the device
+// (reduce_small.cu), one warp per job: job i reduces the nleft leftover
+// columns left[left_off .. left_off + nleft) (sorted by index) of a cloud of
+// n points whose distance rows are D + d_off (stride n) and whose apparent
+// vertices are aw + aw_off, inside threshold t. Per column it writes the
+// death (triangle index, NO_PIVOT if essential) and its diameter; status[i]
+// is 0 when the job finished, 1 when a column's walk outgrew the device's
+// budget (the host then reduces the whole cloud); adds[i] counts additions.
+struct ReduceJob {
+    int64_t d_off, aw_off, left_off, nleft;
+    int32_t n;
+    float t;
+};
+constexpr int REDUCE_SMALL_NMAX = 512;  // largest cloud the device reduces
+size_t reduce_small_vpool_words(uint64_t nleft);
+void launch_reduce_small(const float *D, const uint16_t *aw, const ReduceJob *jobs, int njobs,
+                         int nmax, const Leftover *left, uint32_t *vpool, uint8_t *vcnt,
+                         uint64_t *death, float *ddiam, int32_t *status, int32_t *adds,
+                         cudaStream_t s);
+
 // Gather clouds given by device pointers into the packed point buffer.
 void launch_gather_points(const float *const *src, const BatchCloud *clouds, int nclouds,
                           float *pts, cudaStream_t s);

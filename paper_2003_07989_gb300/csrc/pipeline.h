@@ -90,6 +90,9 @@ struct Workspace {
     HostBuf hb_awout;
     HostBuf hb_pts, hb_clouds, hb_order, hb_ctl, hb_outs, hb_mst, hb_left, hb_lcloud, hb_jobs,
         hb_off, hb_Dout, hb_nbr, hb_src;
+    // the device reduction of small clouds' leftover columns
+    DevBuf r_jobs, r_left, r_vpool, r_vcnt, r_death, r_ddiam, r_stat;
+    HostBuf hr_in, hr_out;
     // captured fused launches by (shape, buffer addresses), most recent last
     std::vector<std::pair<std::vector<uintptr_t>, cudaGraphExec_t>> graphs;
     cudaStream_t capture_stream = nullptr;
@@ -153,6 +156,7 @@ struct rpp_context {
     void release(rpp::Workspace *ws);
     // the fused batch pass: launch shape per size bucket, filled by the autotuner
     bool batch_fused = true;  // false: every cloud of a batch takes run_instance
+    bool device_reduce = true;  // fused clouds of <= 512 points reduce on the device
     bool autotune = true;
     std::mutex tune_mu;
     std::map<int, rpp::BatchConfig> batch_tuning;  // bucket nmax -> chosen shape

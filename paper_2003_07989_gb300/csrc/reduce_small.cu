@@ -1,0 +1,245 @@
+// reduce_small.cu -- the submatrix reduction of dimension 1 (Alg. 1 on the
+// leftover columns, Sec. "Core System Optimizations") on the device, for the
+// clouds of a fused batch whose columns' walks are short.
+//
+// One warp takes one cloud and reduces its leftover columns in index order,
+// exactly as Alg. 1 does (each column's additions only read columns before
+// it). A column is the coboundary of an edge set V (the reduction-matrix
+// form): V starts as the column's own edge, and an addition toggles edges in
+// V (an apparent owner adds its one edge; an earlier leftover column adds its
+// final edge set). V is kept as an adjacency bitset of the cloud in shared
+// memory, so a triangle {x, y, w} has nonzero coefficient exactly when an odd
+// number of its three edges are set.
+//   * The first pivot is the column's unreduced pivot, which the fused pass
+//     found (the oldest cofacet inside the threshold).
+//   * The owner of a pivot tau: its youngest facet s (longest edge, ties by
+//     the smaller index) owns it as an apparent pair when the fused pass
+//     recorded tau's extra vertex as s's apparent vertex; otherwise an
+//     earlier leftover column whose final pivot is tau; otherwise the pivot
+//     is free and the column is paired with it.
+//   * After an addition every entry up to and including the old pivot is
+//     zero (the owner's column has that pivot and nothing older), so the next
+//     pivot is the oldest nonzero triangle younger than it: the warp scans
+//     every (edge of V, third vertex) pair and takes the minimum age key among
+//     odd triangles inside the threshold.
+// A cloud whose column needs more than RS_BUDGET additions, or whose V grows
+// past RS_VMAX edges (the long walks that the host sweeps level by level),
+// stops and is handed back whole: status 1, and the host reduces it.
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace rpp {
+
+namespace {
+
+constexpr int RS_VMAX = 64;     // edges of V per column kept by the device
+constexpr int RS_BUDGET = 64;   // additions per column before the cloud goes back
+
+// Age key of a triangle: diameter bits over the complemented index; ascending
+// key is the filtration order (older first: smaller diameter, then larger index).
+__device__ __forceinline__ uint64_t tri_key(float d, uint32_t idx) {
+    return ((uint64_t)__float_as_uint(d) << 32) | (uint64_t)(0xffffffffu - idx);
+}
+
+__device__ __forceinline__ uint32_t c3(uint32_t v) {
+    return (uint32_t)((uint64_t)v * (v - 1) * (v - 2) / 6);
+}
+__device__ __forceinline__ uint32_t c2(uint32_t v) { return v * (v - 1) / 2; }
+
+// Index of the triangle with vertices a, b, c (any order).
+__device__ __forceinline__ uint32_t tri_index(int a, int b, int c) {
+    int v0 = a, v1 = b, v2 = c;
+    if (v0 < v1) { const int s = v0; v0 = v1; v1 = s; }
+    if (v1 < v2) { const int s = v1; v1 = v2; v2 = s; }
+    if (v0 < v1) { const int s = v0; v0 = v1; v1 = s; }
+    return c3((uint32_t)v0) + c2((uint32_t)v1) + (uint32_t)v2;
+}
+
+// Vertices v0 > v1 > v2 of triangle index t.
+__device__ __forceinline__ void tri_vertices(uint32_t t, int *v) {
+    int x = (int)cbrtf(6.0f * (float)t) + 1;
+    if (x < 2) x = 2;
+    while (x > 2 && c3((uint32_t)x) > t) --x;
+    while (c3((uint32_t)(x + 1)) <= t) ++x;
+    v[0] = x;
+    int e[2];
+    decode_edge((uint64_t)(t - c3((uint32_t)x)), e);
+    v[1] = e[0];
+    v[2] = e[1];
+}
+
+__device__ __forceinline__ bool vbit(const uint32_t *bits, int w32, int a, int b) {
+    return (bits[a * w32 + (b >> 5)] >> (b & 31)) & 1u;
+}
+
+// Toggle edge e = {x > y} in V (bitset and list); lane 0 updates the list.
+// Returns false when the list would overflow.
+__device__ bool toggle(uint32_t *bits, int w32, uint32_t *vlist, int &vcount, uint32_t e) {
+    int xy[2];
+    decode_edge((uint64_t)e, xy);
+    const int x = xy[0], y = xy[1];
+    const bool in = vbit(bits, w32, x, y);
+    const int lane = threadIdx.x & 31;
+    if (in) {  // leaves V: swap-remove from the list
+        int pos = -1;
+        for (int i = lane; i < vcount; i += 32)
+            if (vlist[i] == e) pos = i;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) pos = max(pos, __shfl_xor_sync(FULL_MASK, pos, o));
+        if (pos < 0) return false;  // list and bits disagree: never expected, hand the cloud back
+        __syncwarp();
+        if (lane == 0) {
+            vlist[pos] = vlist[vcount - 1];
+            bits[x * w32 + (y >> 5)] ^= 1u << (y & 31);
+            bits[y * w32 + (x >> 5)] ^= 1u << (x & 31);
+        }
+        --vcount;
+    } else {
+        if (vcount >= RS_VMAX) return false;
+        if (lane == 0) {
+            vlist[vcount] = e;
+            bits[x * w32 + (y >> 5)] ^= 1u << (y & 31);
+            bits[y * w32 + (x >> 5)] ^= 1u << (x & 31);
+        }
+        ++vcount;
+    }
+    __syncwarp();
+    return true;
+}
+
+__global__ void __launch_bounds__(32) k_reduce_small(
+    const float *__restrict__ Dall, const uint16_t *__restrict__ awall,
+    const ReduceJob *__restrict__ jobs, const Leftover *__restrict__ left,
+    uint32_t *__restrict__ vpool, uint8_t *__restrict__ vcnt, uint64_t *__restrict__ death,
+    float *__restrict__ ddiam, int32_t *__restrict__ status, int32_t *__restrict__ adds_out) {
+    extern __shared__ uint32_t bits[];
+    __shared__ uint32_t vlist[RS_VMAX];
+    const ReduceJob J = jobs[blockIdx.x];
+    const int n = J.n, w32 = (n + 31) >> 5, lane = threadIdx.x & 31;
+    const float *D = Dall + J.d_off;  // row stride n
+    const uint16_t *aw = awall + J.aw_off;
+    const Leftover *L = left + J.left_off;
+    const float t = J.t;
+    for (int i = lane; i < n * w32; i += 32) bits[i] = 0;
+    __syncwarp();
+    int total_adds = 0;
+    bool bail = false;
+    for (int64_t j = 0; j < J.nleft && !bail; ++j) {
+        const uint32_t sigma = (uint32_t)L[j].sigma;
+        int vcount = 0;
+        toggle(bits, w32, vlist, vcount, sigma);
+        bool have = L[j].pivot != NO_PIVOT;
+        uint64_t k = have ? tri_key(L[j].pdiam, (uint32_t)L[j].pivot) : ~0ull;
+        int adds = 0;
+        while (have) {
+            // the owner of pivot k
+            const uint32_t tau = 0xffffffffu - (uint32_t)k;
+            int v[3];
+            tri_vertices(tau, v);
+            const float fd[3] = {D[v[1] * n + v[2]], D[v[0] * n + v[2]], D[v[0] * n + v[1]]};
+            int r = 0;  // facets in increasing index order: without v0, v1, v2
+            for (int i = 1; i < 3; ++i)
+                if (fd[i] > fd[r]) r = i;
+            const int sa = r == 0 ? v[1] : v[0], sb = r == 2 ? v[1] : v[2];
+            const uint32_t s = c2((uint32_t)sa) + (uint32_t)sb;
+            int owner = -1;  // 0: apparent; 1: a leftover column
+            int64_t oi = -1;
+            if (aw[s] == (uint16_t)v[r]) {
+                owner = 0;
+            } else {
+                for (int64_t i = lane; i < j; i += 32)
+                    if (death[J.left_off + i] == (uint64_t)tau) oi = i;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const int64_t x = __shfl_xor_sync(FULL_MASK, oi, o);
+                    oi = x > oi ? x : oi;
+                }
+                if (oi >= 0) owner = 1;
+            }
+            if (owner < 0) break;  // free: the column is paired with k
+            if (++adds > RS_BUDGET) {
+                bail = true;
+                break;
+            }
+            if (owner == 0) {
+                if (!toggle(bits, w32, vlist, vcount, s)) {
+                    bail = true;
+                    break;
+                }
+            } else {
+                const uint32_t *Vi = vpool + (J.left_off + oi) * RS_VMAX;
+                const int ci = vcnt[J.left_off + oi];
+                for (int q = 0; q < ci && !bail; ++q)
+                    if (!toggle(bits, w32, vlist, vcount, Vi[q])) bail = true;
+                if (bail) break;
+            }
+            // the next pivot: the oldest odd triangle younger than k
+            uint64_t best = ~0ull;
+            for (int q = 0; q < vcount; ++q) {
+                int xy[2];
+                decode_edge((uint64_t)vlist[q], xy);
+                const int x = xy[0], y = xy[1];
+                const float dxy = D[x * n + y];
+                const float *rx = D + (int64_t)x * n, *ry = D + (int64_t)y * n;
+                for (int w = lane; w < n; w += 32) {
+                    if (w == x || w == y) continue;
+                    const float d = fmaxf(dxy, fmaxf(rx[w], ry[w]));
+                    if (!(d <= t)) continue;
+                    if (vbit(bits, w32, x, w) ^ vbit(bits, w32, y, w)) continue;  // even
+                    const uint64_t key = tri_key(d, tri_index(x, y, w));
+                    if (key > k && key < best) best = key;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const uint64_t x = __shfl_xor_sync(FULL_MASK, best, o);
+                best = x < best ? x : best;
+            }
+            if (best == ~0ull) have = false;  // zero column: an essential class
+            else k = best;
+        }
+        total_adds += adds;
+        if (!bail) {
+            if (lane == 0) {
+                death[J.left_off + j] = have ? (uint64_t)(0xffffffffu - (uint32_t)k) : NO_PIVOT;
+                ddiam[J.left_off + j] = have ? __uint_as_float((uint32_t)(k >> 32)) : 0.0f;
+                vcnt[J.left_off + j] = (uint8_t)vcount;
+            }
+            for (int q = lane; q < vcount; q += 32)
+                vpool[(J.left_off + j) * RS_VMAX + q] = vlist[q];
+        }
+        __syncwarp();
+        // clear V's bits for the next column (by the list, before it changes)
+        for (int q = 0; q < vcount; ++q) {
+            int xy[2];
+            decode_edge((uint64_t)vlist[q], xy);
+            if (lane == 0) {
+                bits[xy[0] * w32 + (xy[1] >> 5)] &= ~(1u << (xy[1] & 31));
+                bits[xy[1] * w32 + (xy[0] >> 5)] &= ~(1u << (xy[0] & 31));
+            }
+        }
+        __syncwarp();
+    }
+    if (lane == 0) {
+        status[blockIdx.x] = bail ? 1 : 0;
+        adds_out[blockIdx.x] = total_adds;
+    }
+}
+
+}  // namespace
+
+size_t reduce_small_vpool_words(uint64_t nleft) { return (size_t)nleft * RS_VMAX; }
+
+void launch_reduce_small(const float *D, const uint16_t *aw, const ReduceJob *jobs, int njobs,
+                         int nmax, const Leftover *left, uint32_t *vpool, uint8_t *vcnt,
+                         uint64_t *death, float *ddiam, int32_t *status, int32_t *adds,
+                         cudaStream_t s) {
+    if (njobs <= 0) return;
+    const size_t smem = (size_t)nmax * ((nmax + 31) / 32) * 4;
+    allow_dynamic_smem((const void *)k_reduce_small, smem);
+    ++g_launches;
+    k_reduce_small<<<(unsigned)njobs, 32, smem, s>>>(D, aw, jobs, left, vpool, vcnt, death, ddiam,
+                                                    status, adds);
+}
+
+}  // namespace rpp
