@@ -19,9 +19,12 @@
 //     is free and the column is paired with it.
 //   * After an addition every entry up to and including the old pivot is
 //     zero (the owner's column has that pivot and nothing older), so the next
-//     pivot is the oldest nonzero triangle younger than it: the warp scans
-//     every (edge of V, third vertex) pair and takes the minimum age key among
-//     odd triangles inside the threshold.
+//     pivot is the oldest nonzero triangle younger than it. Each edge of V
+//     keeps a lazy cursor: its oldest cofacet inside the threshold that the
+//     column has not passed (found by a warp scan of the third vertices). The
+//     smallest head is a nonzero entry when an odd number of V's edges hold
+//     it (a triangle's edges in V all have it as their head); an even one
+//     cancels, and those cursors move on.
 // A cloud whose column needs more than RS_BUDGET additions, or whose V grows
 // past RS_VMAX edges (the long walks that the host sweeps level by level),
 // stops and is handed back whole: status 1, and the host reduces it.
@@ -68,44 +71,112 @@ __device__ __forceinline__ void tri_vertices(uint32_t t, int *v) {
     v[2] = e[1];
 }
 
-__device__ __forceinline__ bool vbit(const uint32_t *bits, int w32, int a, int b) {
-    return (bits[a * w32 + (b >> 5)] >> (b & 31)) & 1u;
-}
-
-// Toggle edge e = {x > y} in V (bitset and list); lane 0 updates the list.
-// Returns false when the list would overflow.
-__device__ bool toggle(uint32_t *bits, int w32, uint32_t *vlist, int &vcount, uint32_t e) {
+// The oldest cofacet of edge e = {x > y} inside the threshold with age key
+// above `after` (~0 if none): the warp scans the third vertices.
+__device__ uint64_t cursor_next(const float *D, int n, float t, uint32_t e, uint64_t after) {
     int xy[2];
     decode_edge((uint64_t)e, xy);
     const int x = xy[0], y = xy[1];
-    const bool in = vbit(bits, w32, x, y);
-    const int lane = threadIdx.x & 31;
-    if (in) {  // leaves V: swap-remove from the list
-        int pos = -1;
-        for (int i = lane; i < vcount; i += 32)
-            if (vlist[i] == e) pos = i;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) pos = max(pos, __shfl_xor_sync(FULL_MASK, pos, o));
-        if (pos < 0) return false;  // list and bits disagree: never expected, hand the cloud back
-        __syncwarp();
-        if (lane == 0) {
-            vlist[pos] = vlist[vcount - 1];
-            bits[x * w32 + (y >> 5)] ^= 1u << (y & 31);
-            bits[y * w32 + (x >> 5)] ^= 1u << (x & 31);
-        }
-        --vcount;
-    } else {
-        if (vcount >= RS_VMAX) return false;
-        if (lane == 0) {
-            vlist[vcount] = e;
-            bits[x * w32 + (y >> 5)] ^= 1u << (y & 31);
-            bits[y * w32 + (x >> 5)] ^= 1u << (x & 31);
-        }
-        ++vcount;
+    const float dxy = D[x * n + y];
+    const float *rx = D + (int64_t)x * n, *ry = D + (int64_t)y * n;
+    uint64_t best = ~0ull;
+    for (int w = threadIdx.x & 31; w < n; w += 32) {
+        if (w == x || w == y) continue;
+        const float d = fmaxf(dxy, fmaxf(rx[w], ry[w]));
+        if (!(d <= t)) continue;
+        const uint64_t key = tri_key(d, tri_index(x, y, w));
+        if (key > after && key < best) best = key;
     }
-    __syncwarp();
-    return true;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t v = __shfl_xor_sync(FULL_MASK, best, o);
+        best = v < best ? v : best;
+    }
+    return best;
 }
+
+// V as an edge list with one lazy cursor per edge (its next cofacet, by age,
+// that the working column has not passed) and an adjacency bitset for
+// membership. Lane 0 writes the shared arrays; every lane keeps vcount.
+struct VSet {
+    uint32_t *bits;
+    int w32;
+    uint32_t *edge;
+    uint64_t *head;
+    int vcount;
+    __device__ bool in(int a, int b) const { return (bits[a * w32 + (b >> 5)] >> (b & 31)) & 1u; }
+    __device__ void flip(int x, int y) {
+        bits[x * w32 + (y >> 5)] ^= 1u << (y & 31);
+        bits[y * w32 + (x >> 5)] ^= 1u << (x & 31);
+    }
+    // Toggle e in V; an entering edge's cursor starts past `after`. False when
+    // the list would overflow (or, never expected, misses a member).
+    __device__ bool toggle(const float *D, int n, float t, uint32_t e, uint64_t after) {
+        int xy[2];
+        decode_edge((uint64_t)e, xy);
+        const int lane = threadIdx.x & 31;
+        if (in(xy[0], xy[1])) {  // leaves V: swap-remove
+            int pos = -1;
+            for (int i = lane; i < vcount; i += 32)
+                if (edge[i] == e) pos = i;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) pos = max(pos, __shfl_xor_sync(FULL_MASK, pos, o));
+            if (pos < 0) return false;
+            __syncwarp();
+            if (lane == 0) {
+                edge[pos] = edge[vcount - 1];
+                head[pos] = head[vcount - 1];
+                flip(xy[0], xy[1]);
+            }
+            --vcount;
+        } else {
+            if (vcount >= RS_VMAX) return false;
+            const uint64_t h = cursor_next(D, n, t, e, after);
+            if (lane == 0) {
+                edge[vcount] = e;
+                head[vcount] = h;
+                flip(xy[0], xy[1]);
+            }
+            ++vcount;
+        }
+        __syncwarp();
+        return true;
+    }
+    // Every cursor at or before k moves past k.
+    __device__ void pass(const float *D, int n, float t, uint64_t k) {
+        for (int q = 0; q < vcount; ++q) {
+            const uint64_t h = head[q];
+            if (h <= k) {
+                const uint64_t nh = cursor_next(D, n, t, edge[q], k);
+                if ((threadIdx.x & 31) == 0) head[q] = nh;
+                __syncwarp();
+            }
+        }
+    }
+    // The oldest nonzero entry of the working column past the cursors: the
+    // smallest head held by an odd number of V's edges (a triangle's edges in
+    // V all have it as their head, the cursors being past every older entry);
+    // even ones cancel and their cursors move on. ~0 if the column is zero.
+    __device__ uint64_t pivot(const float *D, int n, float t) {
+        const int lane = threadIdx.x & 31;
+        for (;;) {
+            uint64_t m = ~0ull;
+            for (int q = lane; q < vcount; q += 32) m = head[q] < m ? head[q] : m;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const uint64_t v = __shfl_xor_sync(FULL_MASK, m, o);
+                m = v < m ? v : m;
+            }
+            if (m == ~0ull) return m;
+            int c = 0;
+            for (int q = lane; q < vcount; q += 32) c += head[q] == m;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(FULL_MASK, c, o);
+            if (c & 1) return m;
+            pass(D, n, t, m);
+        }
+    }
+};
 
 __global__ void __launch_bounds__(32) k_reduce_small(
     const float *__restrict__ Dall, const uint16_t *__restrict__ awall,
@@ -113,7 +184,8 @@ __global__ void __launch_bounds__(32) k_reduce_small(
     uint32_t *__restrict__ vpool, uint8_t *__restrict__ vcnt, uint64_t *__restrict__ death,
     float *__restrict__ ddiam, int32_t *__restrict__ status, int32_t *__restrict__ adds_out) {
     extern __shared__ uint32_t bits[];
-    __shared__ uint32_t vlist[RS_VMAX];
+    __shared__ uint32_t s_edge[RS_VMAX];
+    __shared__ uint64_t s_head[RS_VMAX];
     const ReduceJob J = jobs[blockIdx.x];
     const int n = J.n, w32 = (n + 31) >> 5, lane = threadIdx.x & 31;
     const float *D = Dall + J.d_off;  // row stride n
@@ -122,14 +194,23 @@ __global__ void __launch_bounds__(32) k_reduce_small(
     const float t = J.t;
     for (int i = lane; i < n * w32; i += 32) bits[i] = 0;
     __syncwarp();
+    VSet V{bits, w32, s_edge, s_head, 0};
     int total_adds = 0;
     bool bail = false;
     for (int64_t j = 0; j < J.nleft && !bail; ++j) {
-        const uint32_t sigma = (uint32_t)L[j].sigma;
-        int vcount = 0;
-        toggle(bits, w32, vlist, vcount, sigma);
+        V.vcount = 0;
         bool have = L[j].pivot != NO_PIVOT;
         uint64_t k = have ? tri_key(L[j].pdiam, (uint32_t)L[j].pivot) : ~0ull;
+        // the column's own edge; its oldest cofacet is the unreduced pivot k
+        if (lane == 0) {
+            int xy[2];
+            decode_edge(L[j].sigma, xy);
+            s_edge[0] = (uint32_t)L[j].sigma;
+            s_head[0] = k;
+            V.flip(xy[0], xy[1]);
+        }
+        V.vcount = 1;
+        __syncwarp();
         int adds = 0;
         while (have) {
             // the owner of pivot k
@@ -161,8 +242,9 @@ __global__ void __launch_bounds__(32) k_reduce_small(
                 bail = true;
                 break;
             }
+            // the addition (every entry up to k is then zero), cursors past k
             if (owner == 0) {
-                if (!toggle(bits, w32, vlist, vcount, s)) {
+                if (!V.toggle(D, n, t, s, k)) {
                     bail = true;
                     break;
                 }
@@ -170,49 +252,28 @@ __global__ void __launch_bounds__(32) k_reduce_small(
                 const uint32_t *Vi = vpool + (J.left_off + oi) * RS_VMAX;
                 const int ci = vcnt[J.left_off + oi];
                 for (int q = 0; q < ci && !bail; ++q)
-                    if (!toggle(bits, w32, vlist, vcount, Vi[q])) bail = true;
+                    if (!V.toggle(D, n, t, Vi[q], k)) bail = true;
                 if (bail) break;
             }
-            // the next pivot: the oldest odd triangle younger than k
-            uint64_t best = ~0ull;
-            for (int q = 0; q < vcount; ++q) {
-                int xy[2];
-                decode_edge((uint64_t)vlist[q], xy);
-                const int x = xy[0], y = xy[1];
-                const float dxy = D[x * n + y];
-                const float *rx = D + (int64_t)x * n, *ry = D + (int64_t)y * n;
-                for (int w = lane; w < n; w += 32) {
-                    if (w == x || w == y) continue;
-                    const float d = fmaxf(dxy, fmaxf(rx[w], ry[w]));
-                    if (!(d <= t)) continue;
-                    if (vbit(bits, w32, x, w) ^ vbit(bits, w32, y, w)) continue;  // even
-                    const uint64_t key = tri_key(d, tri_index(x, y, w));
-                    if (key > k && key < best) best = key;
-                }
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const uint64_t x = __shfl_xor_sync(FULL_MASK, best, o);
-                best = x < best ? x : best;
-            }
-            if (best == ~0ull) have = false;  // zero column: an essential class
-            else k = best;
+            V.pass(D, n, t, k);
+            k = V.pivot(D, n, t);
+            if (k == ~0ull) have = false;  // zero column: an essential class
         }
         total_adds += adds;
         if (!bail) {
             if (lane == 0) {
                 death[J.left_off + j] = have ? (uint64_t)(0xffffffffu - (uint32_t)k) : NO_PIVOT;
                 ddiam[J.left_off + j] = have ? __uint_as_float((uint32_t)(k >> 32)) : 0.0f;
-                vcnt[J.left_off + j] = (uint8_t)vcount;
+                vcnt[J.left_off + j] = (uint8_t)V.vcount;
             }
-            for (int q = lane; q < vcount; q += 32)
-                vpool[(J.left_off + j) * RS_VMAX + q] = vlist[q];
+            for (int q = lane; q < V.vcount; q += 32)
+                vpool[(J.left_off + j) * RS_VMAX + q] = s_edge[q];
         }
         __syncwarp();
-        // clear V's bits for the next column (by the list, before it changes)
-        for (int q = 0; q < vcount; ++q) {
+        // clear V's bits for the next column
+        for (int q = 0; q < V.vcount; ++q) {
             int xy[2];
-            decode_edge((uint64_t)vlist[q], xy);
+            decode_edge((uint64_t)s_edge[q], xy);
             if (lane == 0) {
                 bits[xy[0] * w32 + (xy[1] >> 5)] &= ~(1u << (xy[1] & 31));
                 bits[xy[1] * w32 + (xy[0] >> 5)] &= ~(1u << (xy[0] & 31));
