@@ -283,11 +283,11 @@ rpp_status rpp_context_set_sparse(rpp_context *ctx, int32_t mode);
 
 /* Where the batched clouds' leftover columns of dimension 1 are reduced
  * (Alg. 1, the submatrix reduction of Sec. "Core System Optimizations").
- * on = 1 (default): clouds of up to 512 points in a fused launch reduce them
- * on the device, one warp per cloud in column order, right after the fused
- * pass; a cloud whose walks grow past the device's budget (more than 64
- * additions for one column, or a column summing more than 64 edges: the long
- * walks the host sweeps) is reduced on the host instead. on = 0: every cloud
+ * on = 1: clouds of up to 512 points in a fused launch reduce them on the
+ * device, one warp per cloud in column order, right after the fused pass; a
+ * cloud whose walks grow past the device's budget (more than 64 additions
+ * for one column, or a column summing more than 64 edges: the long walks the
+ * host sweeps) is reduced on the host instead. on = 0 (default): every cloud
  * is reduced on the host. Both give the same barcodes; rpp_stats.
  * device_columns counts the columns reduced on the device.
  * Errors: RPP_E_INVALID for a NULL context. */

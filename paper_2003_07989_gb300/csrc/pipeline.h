@@ -156,7 +156,7 @@ struct rpp_context {
     void release(rpp::Workspace *ws);
     // the fused batch pass: launch shape per size bucket, filled by the autotuner
     bool batch_fused = true;  // false: every cloud of a batch takes run_instance
-    bool device_reduce = true;  // fused clouds of <= 512 points reduce on the device
+    bool device_reduce = false;  // fused clouds of <= 512 points reduce on the device
     bool autotune = true;
     std::mutex tune_mu;
     std::map<int, rpp::BatchConfig> batch_tuning;  // bucket nmax -> chosen shape
