@@ -283,15 +283,27 @@ rpp_status rpp_context_set_sparse(rpp_context *ctx, int32_t mode);
 
 /* Where the batched clouds' leftover columns of dimension 1 are reduced
  * (Alg. 1, the submatrix reduction of Sec. "Core System Optimizations").
- * on = 1: clouds of up to 512 points in a fused launch reduce them on the
- * device, one warp per cloud in column order, right after the fused pass; a
- * cloud whose walks grow past the device's budget (more than 64 additions
- * for one column, or a column summing more than 64 edges: the long walks the
- * host sweeps) is reduced on the host instead. on = 0 (default): every cloud
- * is reduced on the host. Both give the same barcodes; rpp_stats.
- * device_columns counts the columns reduced on the device.
- * Errors: RPP_E_INVALID for a NULL context. */
-rpp_status rpp_context_set_device_reduce(rpp_context *ctx, int32_t on);
+ * Clouds of up to 512 points in a fused launch can be reduced on the device,
+ * one warp per cloud in column order, on a stream of the library's own that
+ * starts after the fused pass and runs beside the host reductions and the
+ * next launch's pass. A first phase walks each column with lazy cursors over
+ * its edges' cofacets and hands on a cloud whose column needs more than 64
+ * additions or sums more than 64 edges; a second phase (mode 2) redoes those
+ * clouds, letting such a column go on as a sweep over the diameter levels of
+ * the cloud's sorted edges.
+ * mode = 1 (default): the first phase only. The host threads take the clouds
+ * the device does not reduce first, then the others heaviest first; a thread
+ * reaching a cloud whose device result is on the host uses it, and otherwise
+ * reduces the cloud itself.
+ * mode = 2: both phases, and the host waits for the device's result of every
+ * cloud it sent there (a cloud whose sweep meets a level of more than 32
+ * equal edges, or whose final edge sets outgrow its pool, is still reduced on
+ * the host).
+ * mode = 0: every cloud is reduced on the host only.
+ * All modes give the same barcodes and realising edges; rpp_stats.
+ * device_columns counts the columns whose pairs came from the device.
+ * Errors: RPP_E_INVALID for a NULL context or another mode. */
+rpp_status rpp_context_set_device_reduce(rpp_context *ctx, int32_t mode);
 
 /* The launch shape the autotuner chose for the bucket of clouds with up to
  * nmax points (64, 128, 256, 512 or 1024): threads per block and the

@@ -44,10 +44,14 @@ class Context:
         N.check(N.lib().rpp_context_set_batch(self.handle, int(fused), int(autotune)),
                 "rpp_context_set_batch")
 
-    def set_device_reduce(self, on: bool = True):
-        """rpp_context_set_device_reduce: batched clouds of <= 512 points reduce
-        their leftover columns on the device (on) or on the host (off)."""
-        N.check(N.lib().rpp_context_set_device_reduce(self.handle, int(on)),
+    def set_device_reduce(self, mode=1):
+        """rpp_context_set_device_reduce: batched clouds of <= 512 points also
+        reduce their short column walks on the device, beside the host (1 or
+        True, the default); reduce every walk on the device, long ones as
+        level sweeps, with the host waiting for the results (2 or "wait"); or
+        reduce on the host only (0 or False)."""
+        m = 2 if mode == "wait" else int(mode)
+        N.check(N.lib().rpp_context_set_device_reduce(self.handle, m),
                 "rpp_context_set_device_reduce")
 
     def set_sparse(self, mode: int = 0):

@@ -14,6 +14,7 @@
 // per thread. Everything else (larger clouds, higher dimensions, recorded
 // intermediate arrays) takes the per-instance pipeline.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <numeric>
@@ -115,12 +116,17 @@ Caps caps_of(const std::vector<Instance> &ins, const std::vector<int> &idx) {
 }
 
 // Device bytes a fused launch over these clouds holds (buffers of caps_of,
-// the growth slack of Workspace::dev, and the rows of clouds with leftovers).
+// the growth slack of Workspace::dev, the rows of clouds with leftovers, and
+// the device reduction's pool, outputs and sorted edges).
 size_t launch_device_bytes(const Caps &c, uint64_t rows) {
     auto slack = [](size_t b) { return ((b + b / 4) + 255) & ~(size_t)255; };
+    const uint64_t lcap = std::min(c.left, c.aw);  // leftovers are edges
+    const size_t reduce = slack(reduce_small_vpool_words(lcap, 0) * 4 + rows / 2) +
+                          slack(lcap * (sizeof(Leftover) + 20)) + slack(rows * 9) +
+                          slack(radix_scratch_bound(rows / 2) + 64);
     return slack(c.pts * 4) + slack(c.clouds * (sizeof(BatchCloud) + 4 + sizeof(BatchOut) + 8)) +
            slack(c.D * 4) + slack(c.mst * 8) + slack(c.left * (sizeof(Leftover) + 4)) +
-           slack(c.aw * 2) + slack(rows * 12) + slack(rows) + 8 * 256;
+           slack(c.aw * 2) + slack(rows * 12) + slack(rows) + reduce + 8 * 256;
 }
 
 Status get_bufs(Workspace &ws, const Caps &c, Bufs &b) {
@@ -283,9 +289,15 @@ struct Launch {
     // (sorted by index within its cloud) the death index and diameter
     std::vector<int> rjob;
     std::vector<int64_t> rleft;
-    const int32_t *rstat = nullptr, *radds = nullptr;
-    const uint64_t *rdeath = nullptr;
-    const float *rddiam = nullptr;
+    // [0]: the first phase's (cursors), [1]: the second phase's (sweeps)
+    const int32_t *rstat[2] = {nullptr, nullptr}, *radds[2] = {nullptr, nullptr};
+    const uint64_t *rdeath[2] = {nullptr, nullptr};
+    const float *rddiam[2] = {nullptr, nullptr};
+    // recorded on the reduction's stream once a phase's results are in the
+    // host buffers above (nullptr: that phase did not run in this launch)
+    cudaEvent_t red[2] = {nullptr, nullptr};
+    int red_mode = 0;  // the context's device_reduce when launched
+    int device = 0;
 };
 
 // Device half of a fused launch: the pass itself, then the distance rows,
@@ -443,17 +455,25 @@ Status launch_device(rpp_context *ctx, Workspace &ws, const std::vector<Instance
         launch_batch_rows(b.D, b.clouds, djobs, (int)nj, doff, nmax, dD, dN, b.app_w, dA, s);
         RPP_CK(cudaGetLastError());
         // clouds of up to REDUCE_SMALL_NMAX points reduce their leftover
-        // columns on the device (a cloud whose walks outgrow the device's
-        // budget comes back to the host reductions below)
+        // columns on the device, on a stream of their own: the rows' copies to
+        // the host, the host half and the next launch's pass run meanwhile (a
+        // cloud whose walks outgrow the device's budget is reduced by the host)
         L.rjob.assign(nj, -1);
         L.rleft.clear();
-        L.rstat = L.radds = nullptr;
-        L.rdeath = nullptr;
-        L.rddiam = nullptr;
+        for (int ph = 0; ph < 2; ++ph) {
+            L.rstat[ph] = L.radds[ph] = nullptr;
+            L.rdeath[ph] = nullptr;
+            L.rddiam[ph] = nullptr;
+            L.red[ph] = nullptr;
+        }
+        L.red_mode = ctx->device_reduce;
+        L.device = ws.device;
         if (ctx->device_reduce) {
             std::vector<ReduceJob> rj;
             int64_t lpos = 0;
             int rnmax = 0;
+            uint64_t ecap = 0;  // edges inside the threshold of the reduced clouds
+            int64_t vpos = 0;   // pool words of the reduced clouds
             for (size_t q = 0; q < nj; ++q) {
                 const int j = jobs[q];
                 const BatchCloud &c = b.h_clouds[j];
@@ -468,11 +488,15 @@ Status launch_device(rpp_context *ctx, Workspace &ws, const std::vector<Instance
                 R.nleft = (int64_t)Lv.size();
                 R.n = c.n;
                 R.t = b.h_outs[j].t;
+                R.v_off = vpos;
+                R.v_cap = (int64_t)reduce_small_vpool_words(R.nleft, (uint64_t)c.n);
+                vpos += R.v_cap;
                 L.rjob[q] = (int)rj.size();
                 L.rleft.push_back(lpos);
                 rj.push_back(R);
                 lpos += (int64_t)Lv.size();
                 rnmax = std::max(rnmax, c.n);
+                ecap += b.h_outs[j].ncols;
             }
             if (!rj.empty()) {
                 const size_t nr = rj.size(), nl = (size_t)lpos;
@@ -485,36 +509,86 @@ Status launch_device(rpp_context *ctx, Workspace &ws, const std::vector<Instance
                         const std::vector<Leftover> &Lv = W[jobs[q]].left;
                         std::memcpy(hl + L.rleft[L.rjob[q]], Lv.data(), Lv.size() * sizeof(Leftover));
                     }
-                void *dj, *dl, *dvp, *dvc, *dde, *ddd, *dst;
+                if (!ws.reduce_stream)
+                    RPP_CK(cudaStreamCreateWithFlags(&ws.reduce_stream, cudaStreamNonBlocking));
+                if (!ws.ev_rows) RPP_CK(cudaEventCreateWithFlags(&ws.ev_rows, cudaEventDisableTiming));
+                if (!ws.ev_reduce)
+                    RPP_CK(cudaEventCreateWithFlags(&ws.ev_reduce, cudaEventDisableTiming));
+                if (!ws.ev_reduce_b)
+                    RPP_CK(cudaEventCreateWithFlags(&ws.ev_reduce_b, cudaEventDisableTiming));
+                cudaStream_t rs = ws.reduce_stream;
+                RPP_CK(cudaEventRecord(ws.ev_rows, s));
+                RPP_CK(cudaStreamWaitEvent(rs, ws.ev_rows, 0));
+                void *dj, *dl, *dvp, *dvs, *dvc, *dde, *ddd, *dst;
+                void *dek = nullptr, *det = nullptr, *des = nullptr, *dea = nullptr;
                 RPP_TRY(ws.dev(ws.r_jobs, nr * sizeof(ReduceJob), &dj));
                 RPP_TRY(ws.dev(ws.r_left, std::max<size_t>(nl, 1) * sizeof(Leftover), &dl));
-                RPP_TRY(ws.dev(ws.r_vpool, std::max<size_t>(reduce_small_vpool_words(nl), 1) * 4, &dvp));
-                RPP_TRY(ws.dev(ws.r_vcnt, std::max<size_t>(nl, 1), &dvc));
+                RPP_TRY(ws.dev(ws.r_vpool, std::max<size_t>((size_t)vpos, 1) * 4, &dvp));
+                RPP_TRY(ws.dev(ws.r_vstart, std::max<size_t>(nl, 1) * 4, &dvs));
+                RPP_TRY(ws.dev(ws.r_vcnt, std::max<size_t>(nl, 1) * 4, &dvc));
+                ecap = std::max<uint64_t>(ecap, 2);
+                if (ctx->device_reduce == 2) {  // the sweeps' sorted edges
+                    RPP_TRY(ws.dev(ws.r_ekeys, ecap * 8, &dek));
+                    RPP_TRY(ws.dev(ws.r_etmp, ecap * 8, &det));
+                    RPP_TRY(ws.dev(ws.r_ekaw, ecap * 2, &dea));
+                    RPP_TRY(ws.dev(ws.r_esort, radix_scratch_bytes(ecap) + 64, &des));
+                }
                 RPP_TRY(ws.dev(ws.r_death, std::max<size_t>(nl, 1) * 8, &dde));
                 RPP_TRY(ws.dev(ws.r_ddiam, std::max<size_t>(nl, 1) * 4, &ddd));
-                RPP_TRY(ws.dev(ws.r_stat, nr * 8, &dst));
-                RPP_CK(cudaMemcpyAsync(dj, hp, nr * sizeof(ReduceJob), cudaMemcpyHostToDevice, s));
+                RPP_TRY(ws.dev(ws.r_stat, nr * 16, &dst));
+                RPP_CK(cudaMemcpyAsync(dj, hp, nr * sizeof(ReduceJob), cudaMemcpyHostToDevice, rs));
                 if (nl)
-                    RPP_CK(cudaMemcpyAsync(dl, hl, nl * sizeof(Leftover), cudaMemcpyHostToDevice, s));
-                launch_reduce_small(dD, dA, (const ReduceJob *)dj, (int)nr, rnmax,
-                                    (const Leftover *)dl, (uint32_t *)dvp, (uint8_t *)dvc,
-                                    (uint64_t *)dde, (float *)ddd, (int32_t *)dst,
-                                    (int32_t *)dst + nr, s);
-                RPP_CK(cudaGetLastError());
+                    RPP_CK(cudaMemcpyAsync(dl, hl, nl * sizeof(Leftover), cudaMemcpyHostToDevice, rs));
+                ReduceSmallArgs ra;
+                ra.D = dD;
+                ra.aw = dA;
+                ra.jobs = (const ReduceJob *)dj;
+                ra.njobs = (int)nr;
+                ra.nmax = rnmax;
+                ra.left = (const Leftover *)dl;
+                ra.vpool = (uint32_t *)dvp;
+                ra.vstart = (uint32_t *)dvs;
+                ra.vcnt = (uint32_t *)dvc;
+                ra.death = (uint64_t *)dde;
+                ra.ddiam = (float *)ddd;
+                ra.status = (int32_t *)dst;
+                ra.adds = (int32_t *)dst + nr;
+                ra.status_b = (int32_t *)dst + 2 * nr;
+                ra.adds_b = (int32_t *)dst + 3 * nr;
+                ra.ekeys = (uint64_t *)dek;
+                ra.etmp = (uint64_t *)det;
+                ra.ekaw = (uint16_t *)dea;
+                ra.ecount = des ? (unsigned long long *)((char *)des + radix_scratch_bytes(ecap))
+                                : nullptr;
+                ra.eerr = des ? (unsigned *)((char *)des + radix_scratch_bytes(ecap) + 8) : nullptr;
+                ra.escratch = des;
+                ra.ecap = ecap;
+                // each phase's results (per leftover: death, diameter; per
+                // job: status, additions) are copied out behind its own event
                 const size_t out_bytes = nl * 8 + nl * 4 + nr * 8;
-                RPP_TRY(ws.host(ws.hr_out, std::max<size_t>(out_bytes, 8), &hp));
-                uint64_t *hde = (uint64_t *)hp;
-                float *hdd = (float *)(hde + nl);
-                int32_t *hst = (int32_t *)(hdd + nl);
-                if (nl) {
-                    RPP_CK(cudaMemcpyAsync(hde, dde, nl * 8, cudaMemcpyDeviceToHost, s));
-                    RPP_CK(cudaMemcpyAsync(hdd, ddd, nl * 4, cudaMemcpyDeviceToHost, s));
+                for (int ph = 0; ph < (ctx->device_reduce == 2 ? 2 : 1); ++ph) {
+                    if (ph == 0) launch_reduce_small(ra, rs);
+                    else launch_reduce_small_sweep(ra, rs);
+                    RPP_CK(cudaGetLastError());
+                    RPP_TRY(ws.host(ph == 0 ? ws.hr_out : ws.hr_out_b, std::max<size_t>(out_bytes, 8),
+                                    &hp));
+                    uint64_t *hde = (uint64_t *)hp;
+                    float *hdd = (float *)(hde + nl);
+                    int32_t *hst = (int32_t *)(hdd + nl);
+                    if (nl) {
+                        RPP_CK(cudaMemcpyAsync(hde, dde, nl * 8, cudaMemcpyDeviceToHost, rs));
+                        RPP_CK(cudaMemcpyAsync(hdd, ddd, nl * 4, cudaMemcpyDeviceToHost, rs));
+                    }
+                    RPP_CK(cudaMemcpyAsync(hst, (int32_t *)dst + 2 * ph * nr, nr * 8,
+                                           cudaMemcpyDeviceToHost, rs));
+                    cudaEvent_t ev = ph == 0 ? ws.ev_reduce : ws.ev_reduce_b;
+                    RPP_CK(cudaEventRecord(ev, rs));
+                    L.red[ph] = ev;
+                    L.rdeath[ph] = hde;
+                    L.rddiam[ph] = hdd;
+                    L.rstat[ph] = hst;
+                    L.radds[ph] = hst + nr;
                 }
-                RPP_CK(cudaMemcpyAsync(hst, dst, nr * 8, cudaMemcpyDeviceToHost, s));
-                L.rdeath = hde;
-                L.rddiam = hdd;
-                L.rstat = hst;
-                L.radds = hst + nr;
             }
         }
         RPP_TRY(ws.host(ws.hb_Dout, (size_t)rows * 4, &hp));
@@ -552,11 +626,43 @@ Status launch_host(rpp_context *ctx, Launch &L,
     const long long launches = L.launches;
     const int inner = (int)off.size() >= ctx->host_threads ? 1 : ctx->host_threads;
     std::vector<rpp_result *> res(k, nullptr);
-    // the heaviest reductions first (most leftover columns, then most
-    // points), so that the threads do not wait on one long cloud at the end
+    // whether cloud j went to the device reduction
+    auto sent = [&](int j) {
+        return W[j].job >= 0 && !L.rjob.empty() && L.rjob[W[j].job] >= 0;
+    };
+    // Whether phase ph of the device reduction has its results on the host.
+    // With red_mode 1 a thread that finds them missing reduces the cloud
+    // itself (both give the same pairs); with red_mode 2 it waits for them.
+    std::atomic<bool> red_done[2];
+    for (int ph = 0; ph < 2; ++ph) red_done[ph].store(false);
+    auto device_done = [&](int ph) {
+        if (!L.red[ph]) return false;
+        if (red_done[ph].load(std::memory_order_acquire)) return true;
+        cudaSetDevice(L.device);
+        const cudaError_t e =
+            L.red_mode == 2 ? cudaEventSynchronize(L.red[ph]) : cudaEventQuery(L.red[ph]);
+        if (e == cudaSuccess) {
+            red_done[ph].store(true, std::memory_order_release);
+            return true;
+        }
+        cudaGetLastError();  // not ready (or failed: reported by the final synchronize)
+        return false;
+    };
+    // The phase whose result job rj takes (-1: the host reduces it).
+    auto device_phase = [&](int rj) {
+        if (rj < 0) return -1;
+        if (device_done(0) && L.rstat[0][rj] == 0) return 0;
+        if (device_done(1) && L.rstat[1][rj] == 0) return 1;
+        return -1;
+    };
+    // clouds the device does not reduce first, then the heaviest reductions
+    // first (most leftover columns, then most points), so that the threads do
+    // not wait on one long cloud at the end and reach the lightest clouds,
+    // which the device reduces, last
     std::vector<int> sched(k);
     for (int j = 0; j < k; ++j) sched[j] = j;
     std::stable_sort(sched.begin(), sched.end(), [&](int x, int y) {
+        if (sent(x) != sent(y)) return !sent(x);
         if (W[x].left.size() != W[y].left.size()) return W[x].left.size() > W[y].left.size();
         return b.h_clouds[x].n > b.h_clouds[y].n;
     });
@@ -617,17 +723,18 @@ Status launch_host(rpp_context *ctx, Launch &L,
                 std::vector<Leftover> &Lv = W[j].left;
                 std::vector<HostPair> pairs;
                 ReduceStats rs;
-                if (rj >= 0 && L.rstat[rj] == 0) {  // reduced on the device
+                const int ph = device_phase(rj);
+                if (ph >= 0) {  // reduced on the device
                     const int64_t base = L.rleft[rj];
                     for (size_t q = 0; q < Lv.size(); ++q) {
                         HostPair P;
                         P.sigma = Lv[q].sigma;
                         P.birth = Lv[q].diam;
-                        P.tau = L.rdeath[base + (int64_t)q];
-                        P.death = P.tau == NO_PIVOT ? INFINITY : L.rddiam[base + (int64_t)q];
+                        P.tau = L.rdeath[ph][base + (int64_t)q];
+                        P.death = P.tau == NO_PIVOT ? INFINITY : L.rddiam[ph][base + (int64_t)q];
                         pairs.push_back(P);
                     }
-                    rs.additions = L.radds[rj];
+                    rs.additions = L.radds[ph][rj];
                     S.device_columns[1] = (int64_t)Lv.size();
                 } else {
                     std::sort(Lv.begin(), Lv.end(), [](const Leftover &x, const Leftover &y) {
@@ -665,6 +772,16 @@ Status launch_host(rpp_context *ctx, Launch &L,
         S.ms_total = now_ms() - t0;
         res[j] = r;
     });
+    for (int ph = 0; ph < 2; ++ph) {  // the reduction's buffers stay in use until it is done
+        if (!L.red[ph]) continue;
+        cudaSetDevice(L.device);
+        const cudaError_t e = cudaEventSynchronize(L.red[ph]);
+        if (e != cudaSuccess) {
+            for (rpp_result *r : res) rpp_result_free(r);
+            return fail(RPP_E_CUDA, std::string("device reduction of the batched clouds: ") +
+                                        cudaGetErrorString(e));
+        }
+    }
     for (int j = 0; j < k; ++j) {
         if (W[j].fallback) alone.push_back(idx[j]);
         else out[idx[j]] = res[j];
@@ -706,6 +823,10 @@ Status run_batch(rpp_context *ctx, Workspace &ws, const std::vector<Instance> &i
             alone.push_back(i);
     }
     auto cleanup = [&]() {
+        // a launch that failed before its host half may leave a device
+        // reduction writing into the workspace's buffers
+        for (Workspace *w : {&ws, ws2})
+            if (w && w->reduce_stream) cudaStreamSynchronize(w->reduce_stream);
         for (size_t i = 0; i < ins.size(); ++i)
             if (out[i]) {
                 rpp_result_free(out[i]);
@@ -820,12 +941,16 @@ extern "C" rpp_status rpp_barcodes_batched(rpp_context *ctx, int32_t batch,
     return RPP_OK;
 }
 
-extern "C" rpp_status rpp_context_set_device_reduce(rpp_context *ctx, int32_t on) {
+extern "C" rpp_status rpp_context_set_device_reduce(rpp_context *ctx, int32_t mode) {
     if (!ctx) {
         set_last_error("rpp_context_set_device_reduce: ctx is NULL");
         return RPP_E_INVALID;
     }
-    ctx->device_reduce = on != 0;
+    if (mode < 0 || mode > 2) {
+        set_last_error("rpp_context_set_device_reduce: mode must be 0, 1 or 2");
+        return RPP_E_INVALID;
+    }
+    ctx->device_reduce = mode;
     return RPP_OK;
 }
 

@@ -251,20 +251,46 @@ void launch_batch_rows(const float *Dbuf, const BatchCloud *clouds, const int32_
 // columns left[left_off .. left_off + nleft) (sorted by index) of a cloud of
 // n points whose distance rows are D + d_off (stride n) and whose apparent
 // vertices are aw + aw_off, inside threshold t. Per column it writes the
-// death (triangle index, NO_PIVOT if essential) and its diameter; status[i]
-// is 0 when the job finished, 1 when a column's walk outgrew the device's
-// budget (the host then reduces the whole cloud); adds[i] counts additions.
+// death (triangle index, NO_PIVOT if essential), its diameter, and the
+// column's final edge set (vcnt edges at vpool + v_off + vstart; the job's
+// pool holds v_cap = reduce_small_vpool_words(nleft, n) words). status[i] is
+// 0 when the job finished on the device, 1 when the host must reduce the
+// cloud; adds[i] counts additions.
 struct ReduceJob {
-    int64_t d_off, aw_off, left_off, nleft;
+    int64_t d_off, aw_off, left_off, nleft, v_off, v_cap;
     int32_t n;
     float t;
 };
 constexpr int REDUCE_SMALL_NMAX = 512;  // largest cloud the device reduces
-size_t reduce_small_vpool_words(uint64_t nleft);
-void launch_reduce_small(const float *D, const uint16_t *aw, const ReduceJob *jobs, int njobs,
-                         int nmax, const Leftover *left, uint32_t *vpool, uint8_t *vcnt,
-                         uint64_t *death, float *ddiam, int32_t *status, int32_t *adds,
-                         cudaStream_t s);
+size_t reduce_small_vpool_words(uint64_t nleft, uint64_t n);
+struct ReduceSmallArgs {
+    const float *D = nullptr;
+    const uint16_t *aw = nullptr;
+    const ReduceJob *jobs = nullptr;
+    int njobs = 0, nmax = 0;
+    const Leftover *left = nullptr;
+    uint32_t *vpool = nullptr, *vstart = nullptr, *vcnt = nullptr;
+    uint64_t *death = nullptr;
+    float *ddiam = nullptr;
+    int32_t *status = nullptr, *adds = nullptr;
+    // The second phase (clouds whose walks outgrow the cursors sweep by
+    // diameter level; launch_reduce_small_sweep): its status and additions
+    // per job (0 for jobs the first phase finished), room for ecap edge keys
+    // in ekeys and etmp, the radix sort's scratch (radix_scratch_bytes(ecap)),
+    // a key counter and an error word.
+    int32_t *status_b = nullptr, *adds_b = nullptr;
+    uint64_t *ekeys = nullptr, *etmp = nullptr;
+    uint16_t *ekaw = nullptr;  // ecap entries: each sorted edge's apparent vertex
+    void *escratch = nullptr;
+    unsigned long long *ecount = nullptr;
+    unsigned *eerr = nullptr;
+    uint64_t ecap = 0;
+};
+// The first phase (cursors only; status 1 hands a job on).
+void launch_reduce_small(const ReduceSmallArgs &a, cudaStream_t s);
+// The second phase, over the jobs the first handed on (after it, in stream
+// order): death, ddiam and the pool are written for those jobs only.
+void launch_reduce_small_sweep(const ReduceSmallArgs &a, cudaStream_t s);
 
 // Gather clouds given by device pointers into the packed point buffer.
 void launch_gather_points(const float *const *src, const BatchCloud *clouds, int nclouds,

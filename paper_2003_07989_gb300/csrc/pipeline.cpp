@@ -70,13 +70,18 @@ Workspace::~Workspace() {
         if (b->p) cudaFreeHost(b->p);
     DevBuf *bd[] = {&b_pts, &b_clouds, &b_order, &b_ctl, &b_D,   &b_mst,  &b_outs,
                     &b_left, &b_lcloud, &b_jobs, &b_off, &b_Dout, &b_nbr, &b_src,
-                    &b_aw, &b_awout, &r_jobs, &r_left, &r_vpool, &r_vcnt, &r_death, &r_ddiam,
+                    &b_aw, &b_awout, &r_jobs, &r_left, &r_vpool, &r_vstart, &r_vcnt, &r_death, &r_ddiam,
+                    &r_ekeys, &r_etmp, &r_esort, &r_ekaw,
                     &r_stat};
     for (DevBuf *b : bd)
         if (b->p) cudaFree(b->p);
     HostBuf *bh[] = {&hb_pts,  &hb_clouds, &hb_order, &hb_ctl, &hb_outs, &hb_mst,  &hb_left,
                      &hb_lcloud, &hb_jobs, &hb_off,   &hb_Dout, &hb_nbr, &hb_src, &hb_awout,
-                     &hr_in,   &hr_out};
+                     &hr_in,   &hr_out, &hr_out_b};
+    if (ev_reduce) cudaEventDestroy(ev_reduce);
+    if (ev_reduce_b) cudaEventDestroy(ev_reduce_b);
+    if (ev_rows) cudaEventDestroy(ev_rows);
+    if (reduce_stream) cudaStreamDestroy(reduce_stream);
     for (HostBuf *b : bh)
         if (b->p) cudaFreeHost(b->p);
     for (auto &g : graphs) cudaGraphExecDestroy(g.second);

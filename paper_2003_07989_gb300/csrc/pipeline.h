@@ -91,8 +91,13 @@ struct Workspace {
     HostBuf hb_pts, hb_clouds, hb_order, hb_ctl, hb_outs, hb_mst, hb_left, hb_lcloud, hb_jobs,
         hb_off, hb_Dout, hb_nbr, hb_src;
     // the device reduction of small clouds' leftover columns
-    DevBuf r_jobs, r_left, r_vpool, r_vcnt, r_death, r_ddiam, r_stat;
-    HostBuf hr_in, hr_out;
+    DevBuf r_jobs, r_left, r_vpool, r_vstart, r_vcnt, r_death, r_ddiam, r_stat;
+    DevBuf r_ekeys, r_etmp, r_esort, r_ekaw;  // its second phase: sorted edges, sort scratch
+    HostBuf hr_in, hr_out, hr_out_b;
+    cudaStream_t reduce_stream = nullptr;  // the device reduction runs beside the next pass
+    cudaEvent_t ev_rows = nullptr;         // rows of the fused launch ready
+    cudaEvent_t ev_reduce = nullptr;       // the first phase's results on the host
+    cudaEvent_t ev_reduce_b = nullptr;     // the second phase's
     // captured fused launches by (shape, buffer addresses), most recent last
     std::vector<std::pair<std::vector<uintptr_t>, cudaGraphExec_t>> graphs;
     cudaStream_t capture_stream = nullptr;
@@ -156,7 +161,11 @@ struct rpp_context {
     void release(rpp::Workspace *ws);
     // the fused batch pass: launch shape per size bucket, filled by the autotuner
     bool batch_fused = true;  // false: every cloud of a batch takes run_instance
-    bool device_reduce = false;  // fused clouds of <= 512 points reduce on the device
+    // fused clouds of <= 512 points reduce on the device: 0 never; 1 beside
+    // the host reductions, short walks only (the host takes what the device
+    // has finished when it reaches a cloud); 2 every walk, long ones as level
+    // sweeps (the host waits for the device's results)
+    int device_reduce = 1;
     bool autotune = true;
     std::mutex tune_mu;
     std::map<int, rpp::BatchConfig> batch_tuning;  // bucket nmax -> chosen shape

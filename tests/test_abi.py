@@ -53,6 +53,8 @@ def test_argument_errors_without_gpu(lib):
     assert rc == N.RPP_E_INVALID
     assert b"NULL" in lib.rpp_last_error()
     assert lib.rpp_result_count(None, 0) == -1
+    for set_mode in (lib.rpp_context_set_device_reduce, lib.rpp_context_set_sparse):
+        assert set_mode(None, 1) == N.RPP_E_INVALID
     # C(n, 2) >= 2^32 from n = 92683 on: refused by the argument checks, which
     # need no context and read no input
     tiny = (C.c_float * 4)()
