@@ -500,10 +500,18 @@ Status launch_device(rpp_context *ctx, Workspace &ws, const std::vector<Instance
             }
             if (!rj.empty()) {
                 const size_t nr = rj.size(), nl = (size_t)lpos;
-                const size_t in_bytes = nr * sizeof(ReduceJob) + nl * sizeof(Leftover);
+                const size_t in_bytes = nr * sizeof(ReduceJob) + nl * sizeof(Leftover) + nr * 4;
                 RPP_TRY(ws.host(ws.hr_in, in_bytes, &hp));
                 std::memcpy(hp, rj.data(), nr * sizeof(ReduceJob));
                 Leftover *hl = (Leftover *)((char *)hp + nr * sizeof(ReduceJob));
+                // the second phase's blocks take the heaviest clouds first
+                // (most leftover columns times points), so that no block
+                // starts a long cloud at the end
+                int32_t *hord = (int32_t *)(hl + nl);
+                for (size_t q = 0; q < nr; ++q) hord[q] = (int32_t)q;
+                std::stable_sort(hord, hord + nr, [&](int32_t x, int32_t y) {
+                    return rj[x].nleft * rj[x].n > rj[y].nleft * rj[y].n;
+                });
                 for (size_t q = 0; q < nj; ++q)
                     if (L.rjob[q] >= 0) {
                         const std::vector<Leftover> &Lv = W[jobs[q]].left;
@@ -521,13 +529,16 @@ Status launch_device(rpp_context *ctx, Workspace &ws, const std::vector<Instance
                 RPP_CK(cudaStreamWaitEvent(rs, ws.ev_rows, 0));
                 void *dj, *dl, *dvp, *dvs, *dvc, *dde, *ddd, *dst;
                 void *dek = nullptr, *det = nullptr, *des = nullptr, *dea = nullptr;
-                RPP_TRY(ws.dev(ws.r_jobs, nr * sizeof(ReduceJob), &dj));
+                RPP_TRY(ws.dev(ws.r_jobs, nr * sizeof(ReduceJob) + nr * 4 + 16, &dj));
+                int32_t *dord = (int32_t *)((char *)dj + nr * sizeof(ReduceJob));
+                unsigned *dnext = (unsigned *)(dord + nr);
                 RPP_TRY(ws.dev(ws.r_left, std::max<size_t>(nl, 1) * sizeof(Leftover), &dl));
                 RPP_TRY(ws.dev(ws.r_vpool, std::max<size_t>((size_t)vpos, 1) * 4, &dvp));
                 RPP_TRY(ws.dev(ws.r_vstart, std::max<size_t>(nl, 1) * 4, &dvs));
                 RPP_TRY(ws.dev(ws.r_vcnt, std::max<size_t>(nl, 1) * 4, &dvc));
                 ecap = std::max<uint64_t>(ecap, 2);
-                if (ctx->device_reduce == 2) {  // the sweeps' sorted edges
+                const bool sweeps = ctx->device_reduce == 2;
+                if (sweeps) {  // the sweeps' sorted edges
                     RPP_TRY(ws.dev(ws.r_ekeys, ecap * 8, &dek));
                     RPP_TRY(ws.dev(ws.r_etmp, ecap * 8, &det));
                     RPP_TRY(ws.dev(ws.r_ekaw, ecap * 2, &dea));
@@ -537,6 +548,7 @@ Status launch_device(rpp_context *ctx, Workspace &ws, const std::vector<Instance
                 RPP_TRY(ws.dev(ws.r_ddiam, std::max<size_t>(nl, 1) * 4, &ddd));
                 RPP_TRY(ws.dev(ws.r_stat, nr * 16, &dst));
                 RPP_CK(cudaMemcpyAsync(dj, hp, nr * sizeof(ReduceJob), cudaMemcpyHostToDevice, rs));
+                RPP_CK(cudaMemcpyAsync(dord, hord, nr * 4, cudaMemcpyHostToDevice, rs));
                 if (nl)
                     RPP_CK(cudaMemcpyAsync(dl, hl, nl * sizeof(Leftover), cudaMemcpyHostToDevice, rs));
                 ReduceSmallArgs ra;
@@ -563,10 +575,12 @@ Status launch_device(rpp_context *ctx, Workspace &ws, const std::vector<Instance
                 ra.eerr = des ? (unsigned *)((char *)des + radix_scratch_bytes(ecap) + 8) : nullptr;
                 ra.escratch = des;
                 ra.ecap = ecap;
+                ra.order_b = dord;
+                ra.next_b = dnext;
                 // each phase's results (per leftover: death, diameter; per
                 // job: status, additions) are copied out behind its own event
                 const size_t out_bytes = nl * 8 + nl * 4 + nr * 8;
-                for (int ph = 0; ph < (ctx->device_reduce == 2 ? 2 : 1); ++ph) {
+                for (int ph = 0; ph < (sweeps ? 2 : 1); ++ph) {
                     if (ph == 0) launch_reduce_small(ra, rs);
                     else launch_reduce_small_sweep(ra, rs);
                     RPP_CK(cudaGetLastError());

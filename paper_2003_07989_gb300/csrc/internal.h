@@ -279,6 +279,9 @@ struct ReduceSmallArgs {
     // in ekeys and etmp, the radix sort's scratch (radix_scratch_bytes(ecap)),
     // a key counter and an error word.
     int32_t *status_b = nullptr, *adds_b = nullptr;
+    const int32_t *order_b = nullptr;  // the order the second phase takes jobs in
+    unsigned *next_b = nullptr;        // its job counter
+    int blocks_b = 0;                  // its blocks (0: one per SM)
     uint64_t *ekeys = nullptr, *etmp = nullptr;
     uint16_t *ekaw = nullptr;  // ecap entries: each sorted edge's apparent vertex
     void *escratch = nullptr;

@@ -43,6 +43,8 @@
 // such a column continue as a level sweep. A cloud whose level holds more
 // than RS_LEVMAX edges of one diameter, or whose final edge sets outgrow the
 // cloud's share of the pool, goes back to the host (status 1).
+#include <algorithm>
+
 #include "device_common.cuh"
 #include "internal.h"
 
@@ -678,9 +680,10 @@ __device__ int64_t extract_v(const Cloud &C, uint32_t *out, int64_t cap) {
     return total;
 }
 
+// One job (a cloud) of either phase, by one warp.
 template <bool SWEEP>
-__global__ void __launch_bounds__(32) k_reduce_small(
-    const float *__restrict__ Dall, const uint16_t *__restrict__ awall,
+__device__ void reduce_job(
+    const int job, const float *__restrict__ Dall, const uint16_t *__restrict__ awall,
     const ReduceJob *__restrict__ jobs, const Leftover *__restrict__ left,
     const uint64_t *__restrict__ ekeys, const uint16_t *__restrict__ ekaw,
     const unsigned long long *__restrict__ ecount, const unsigned *__restrict__ eerr,
@@ -698,7 +701,6 @@ __global__ void __launch_bounds__(32) k_reduce_small(
     __shared__ uint32_t s_li[SWEEP ? RS_LEVMAX : 1];
     __shared__ uint16_t s_law[SWEEP ? RS_LEVMAX : 1];
     __shared__ int s_ba[SWEEP ? 32 : 1], s_bb[SWEEP ? 32 : 1];
-    const int job = blockIdx.x;
     const int lane = threadIdx.x & 31;
     if (SWEEP && status_in[job] != 1) {  // the first phase finished it
         if (lane == 0) {
@@ -916,6 +918,41 @@ __global__ void __launch_bounds__(32) k_reduce_small(
     }
 }
 
+// The first phase: one block (warp) per job.
+__global__ void __launch_bounds__(32) k_reduce_cursors(
+    const float *__restrict__ Dall, const uint16_t *__restrict__ awall,
+    const ReduceJob *__restrict__ jobs, const Leftover *__restrict__ left,
+    uint32_t *__restrict__ vpool, uint32_t *__restrict__ vstart, uint32_t *__restrict__ vcnt,
+    uint64_t *__restrict__ death, float *__restrict__ ddiam, int32_t *__restrict__ status,
+    int32_t *__restrict__ adds) {
+    reduce_job<false>((int)blockIdx.x, Dall, awall, jobs, left, nullptr, nullptr, nullptr, nullptr,
+                      vpool, vstart, vcnt, death, ddiam, nullptr, status, adds);
+}
+
+// The second phase: a fixed number of blocks (one per SM by default) take
+// jobs in the given order (the heaviest first) from a counter, so that the
+// next launches' fused passes keep room on the SMs.
+__global__ void __launch_bounds__(32) k_reduce_sweeps(
+    const float *__restrict__ Dall, const uint16_t *__restrict__ awall,
+    const ReduceJob *__restrict__ jobs, int njobs, const int32_t *__restrict__ order,
+    unsigned *__restrict__ next, const Leftover *__restrict__ left,
+    const uint64_t *__restrict__ ekeys, const uint16_t *__restrict__ ekaw,
+    const unsigned long long *__restrict__ ecount, const unsigned *__restrict__ eerr,
+    uint32_t *__restrict__ vpool, uint32_t *__restrict__ vstart, uint32_t *__restrict__ vcnt,
+    uint64_t *__restrict__ death, float *__restrict__ ddiam, const int32_t *__restrict__ status_in,
+    int32_t *__restrict__ status, int32_t *__restrict__ adds) {
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int jj = 0;
+        if (lane == 0) jj = (int)atomicAdd(next, 1u);
+        jj = __shfl_sync(FULL_MASK, jj, 0);
+        if (jj >= njobs) break;
+        reduce_job<true>(order[jj], Dall, awall, jobs, left, ekeys, ekaw, ecount, eerr, vpool,
+                         vstart, vcnt, death, ddiam, status_in, status, adds);
+        __syncwarp();
+    }
+}
+
 // Sweep keys of the edges inside the threshold of every cloud the first phase
 // handed on (status 1), appended through warp-aggregated atomics; a count
 // beyond cap sets *err (the clouds then go to the host).
@@ -986,11 +1023,11 @@ void launch_reduce_small(const ReduceSmallArgs &A, cudaStream_t s) {
     if (A.njobs <= 0) return;
     const size_t w32 = (size_t)(A.nmax + 31) / 32;
     const size_t smem_a = (size_t)A.nmax * w32 * 4;
-    allow_dynamic_smem((const void *)k_reduce_small<false>, smem_a);
+    allow_dynamic_smem((const void *)k_reduce_cursors, smem_a);
     ++g_launches;
-    k_reduce_small<false><<<(unsigned)A.njobs, 32, smem_a, s>>>(
-        A.D, A.aw, A.jobs, A.left, nullptr, nullptr, nullptr, nullptr, A.vpool, A.vstart, A.vcnt,
-        A.death, A.ddiam, nullptr, A.status, A.adds);
+    k_reduce_cursors<<<(unsigned)A.njobs, 32, smem_a, s>>>(A.D, A.aw, A.jobs, A.left, A.vpool,
+                                                          A.vstart, A.vcnt, A.death, A.ddiam,
+                                                          A.status, A.adds);
 }
 
 void launch_reduce_small_sweep(const ReduceSmallArgs &A, cudaStream_t s) {
@@ -999,6 +1036,7 @@ void launch_reduce_small_sweep(const ReduceSmallArgs &A, cudaStream_t s) {
     const size_t smem_b = 2 * (size_t)A.nmax * w32 * 4 + (size_t)A.nmax * 4;
     cudaMemsetAsync(A.ecount, 0, sizeof(unsigned long long), s);
     cudaMemsetAsync(A.eerr, 0, sizeof(unsigned), s);
+    cudaMemsetAsync(A.next_b, 0, sizeof(unsigned), s);
     ++g_launches;
     k_sweep_edges<<<(unsigned)A.njobs, 256, 0, s>>>(A.D, A.jobs, A.status, A.ekeys, A.ecap,
                                                     A.ecount, A.eerr);
@@ -1006,11 +1044,12 @@ void launch_reduce_small_sweep(const ReduceSmallArgs &A, cudaStream_t s) {
                EK_BITS, A.eerr, s);
     ++g_launches;
     k_sweep_aw<<<152 * 4, 256, 0, s>>>(A.ekeys, A.ecount, A.ecap, A.aw, A.jobs, A.ekaw);
-    allow_dynamic_smem((const void *)k_reduce_small<true>, smem_b);
+    allow_dynamic_smem((const void *)k_reduce_sweeps, smem_b);
+    const int blocks = std::max(1, std::min(A.njobs, A.blocks_b > 0 ? A.blocks_b : 152));
     ++g_launches;
-    k_reduce_small<true><<<(unsigned)A.njobs, 32, smem_b, s>>>(
-        A.D, A.aw, A.jobs, A.left, A.ekeys, A.ekaw, A.ecount, A.eerr, A.vpool, A.vstart, A.vcnt,
-        A.death, A.ddiam, A.status, A.status_b, A.adds_b);
+    k_reduce_sweeps<<<(unsigned)blocks, 32, smem_b, s>>>(
+        A.D, A.aw, A.jobs, A.njobs, A.order_b, A.next_b, A.left, A.ekeys, A.ekaw, A.ecount,
+        A.eerr, A.vpool, A.vstart, A.vcnt, A.death, A.ddiam, A.status, A.status_b, A.adds_b);
 }
 
 }  // namespace rpp
