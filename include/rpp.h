@@ -291,15 +291,17 @@ rpp_status rpp_context_set_sparse(rpp_context *ctx, int32_t mode);
  * additions or sums more than 64 edges; a second phase (mode 2) redoes those
  * clouds, letting such a column go on as a sweep over the diameter levels of
  * the cloud's sorted edges.
- * mode = 1 (default): the first phase only. The host threads take the clouds
+ * mode = 1: the first phase only. The host threads take the clouds
  * the device does not reduce first, then the others heaviest first; a thread
  * reaching a cloud whose device result is on the host uses it, and otherwise
- * reduces the cloud itself.
+ * reduces the cloud itself; once every cloud has its pairs the host raises
+ * a flag that stops the device's jobs, and the workspace's next launch waits
+ * for them.
  * mode = 2: both phases, and the host waits for the device's result of every
  * cloud it sent there (a cloud whose sweep meets a level of more than 32
  * equal edges, or whose final edge sets outgrow its pool, is still reduced on
  * the host).
- * mode = 0: every cloud is reduced on the host only.
+ * mode = 0 (default): every cloud is reduced on the host only.
  * All modes give the same barcodes and realising edges; rpp_stats.
  * device_columns counts the columns whose pairs came from the device.
  * Errors: RPP_E_INVALID for a NULL context or another mode. */

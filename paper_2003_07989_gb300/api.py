@@ -47,9 +47,9 @@ class Context:
     def set_device_reduce(self, mode=1):
         """rpp_context_set_device_reduce: batched clouds of <= 512 points also
         reduce their short column walks on the device, beside the host (1 or
-        True, the default); reduce every walk on the device, long ones as
-        level sweeps, with the host waiting for the results (2 or "wait"); or
-        reduce on the host only (0 or False)."""
+        True); reduce every walk on the device, long ones as level sweeps, with
+        the host waiting for the results (2 or "wait"); or reduce on the host
+        only (0 or False, the context's default)."""
         m = 2 if mode == "wait" else int(mode)
         N.check(N.lib().rpp_context_set_device_reduce(self.handle, m),
                 "rpp_context_set_device_reduce")

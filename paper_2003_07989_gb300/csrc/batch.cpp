@@ -296,6 +296,8 @@ struct Launch {
     // recorded on the reduction's stream once a phase's results are in the
     // host buffers above (nullptr: that phase did not run in this launch)
     cudaEvent_t red[2] = {nullptr, nullptr};
+    unsigned *cancel = nullptr;  // host side of the first phase's cancel flag
+    bool *pending = nullptr;     // the workspace's reduce_pending
     int red_mode = 0;  // the context's device_reduce when launched
     int device = 0;
 };
@@ -306,6 +308,10 @@ struct Launch {
 Status launch_device(rpp_context *ctx, Workspace &ws, const std::vector<Instance> &ins,
                      const std::vector<int> &idx, int nmax, int dimcap, cudaStream_t s,
                      Launch &L) {
+    if (ws.reduce_pending) {  // a cancelled device reduction may still read these buffers
+        RPP_CK(cudaEventSynchronize(ws.ev_reduce));
+        ws.reduce_pending = false;
+    }
     L.idx = idx;
     L.t0 = now_ms();
     const long long launches0 = g_launches;
@@ -467,6 +473,8 @@ Status launch_device(rpp_context *ctx, Workspace &ws, const std::vector<Instance
             L.red[ph] = nullptr;
         }
         L.red_mode = ctx->device_reduce;
+        L.cancel = nullptr;
+        L.pending = &ws.reduce_pending;
         L.device = ws.device;
         if (ctx->device_reduce) {
             std::vector<ReduceJob> rj;
@@ -577,6 +585,14 @@ Status launch_device(rpp_context *ctx, Workspace &ws, const std::vector<Instance
                 ra.ecap = ecap;
                 ra.order_b = dord;
                 ra.next_b = dnext;
+                if (!sweeps) {  // the host may finish every cloud first: let it stop the device
+                    void *hc, *dc = nullptr;
+                    RPP_TRY(ws.host(ws.hr_cancel, 64, &hc));
+                    RPP_CK(cudaHostGetDevicePointer(&dc, hc, 0));
+                    __atomic_store_n((unsigned *)hc, 0u, __ATOMIC_RELEASE);
+                    L.cancel = (unsigned *)hc;
+                    ra.cancel = (const unsigned *)dc;
+                }
                 // each phase's results (per leftover: death, diameter; per
                 // job: status, additions) are copied out behind its own event
                 const size_t out_bytes = nl * 8 + nl * 4 + nr * 8;
@@ -786,8 +802,14 @@ Status launch_host(rpp_context *ctx, Launch &L,
         S.ms_total = now_ms() - t0;
         res[j] = r;
     });
+    // every cloud has its pairs: the device's first phase may stop, and the
+    // workspace's next launch waits for it (the results here need nothing more)
+    if (L.cancel) {
+        __atomic_store_n(L.cancel, 1u, __ATOMIC_RELEASE);
+        if (L.red[0] && L.pending) *L.pending = true;
+    }
     for (int ph = 0; ph < 2; ++ph) {  // the reduction's buffers stay in use until it is done
-        if (!L.red[ph]) continue;
+        if (!L.red[ph] || (ph == 0 && L.cancel)) continue;
         cudaSetDevice(L.device);
         const cudaError_t e = cudaEventSynchronize(L.red[ph]);
         if (e != cudaSuccess) {

@@ -282,6 +282,9 @@ struct ReduceSmallArgs {
     const int32_t *order_b = nullptr;  // the order the second phase takes jobs in
     unsigned *next_b = nullptr;        // its job counter
     int blocks_b = 0;                  // its blocks (0: one per SM)
+    // First phase: a flag in mapped host memory (nullptr: none); once the
+    // host sets it the jobs stop at their next check (status 1).
+    const unsigned *cancel = nullptr;
     uint64_t *ekeys = nullptr, *etmp = nullptr;
     uint16_t *ekaw = nullptr;  // ecap entries: each sorted edge's apparent vertex
     void *escratch = nullptr;

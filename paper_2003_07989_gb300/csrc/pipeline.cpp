@@ -58,6 +58,7 @@ float bits_to_float(uint32_t b) {
 // workspace
 
 Workspace::~Workspace() {
+    if (reduce_stream) cudaStreamSynchronize(reduce_stream);  // nothing may still read the buffers
     DevBuf *d[] = {&X,    &Dsrc,  &D,      &state,   &binom,     &key_hi, &key_lo,
                    &tmp_hi, &tmp_lo, &tmp_val, &tiles, &hist,      &status, &pivot,
                    &pdiam, &app_tau, &app_sigma, &left, &bitmap, &mst,    &up, &nbr, &h0,
@@ -77,7 +78,7 @@ Workspace::~Workspace() {
         if (b->p) cudaFree(b->p);
     HostBuf *bh[] = {&hb_pts,  &hb_clouds, &hb_order, &hb_ctl, &hb_outs, &hb_mst,  &hb_left,
                      &hb_lcloud, &hb_jobs, &hb_off,   &hb_Dout, &hb_nbr, &hb_src, &hb_awout,
-                     &hr_in,   &hr_out, &hr_out_b};
+                     &hr_in,   &hr_out, &hr_out_b, &hr_cancel};
     if (ev_reduce) cudaEventDestroy(ev_reduce);
     if (ev_reduce_b) cudaEventDestroy(ev_reduce_b);
     if (ev_rows) cudaEventDestroy(ev_rows);

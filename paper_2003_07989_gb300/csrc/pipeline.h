@@ -94,10 +94,14 @@ struct Workspace {
     DevBuf r_jobs, r_left, r_vpool, r_vstart, r_vcnt, r_death, r_ddiam, r_stat;
     DevBuf r_ekeys, r_etmp, r_esort, r_ekaw;  // its second phase: sorted edges, sort scratch
     HostBuf hr_in, hr_out, hr_out_b;
+    HostBuf hr_cancel;  // the first phase's cancel flag (mapped: the device reads it)
     cudaStream_t reduce_stream = nullptr;  // the device reduction runs beside the next pass
     cudaEvent_t ev_rows = nullptr;         // rows of the fused launch ready
     cudaEvent_t ev_reduce = nullptr;       // the first phase's results on the host
     cudaEvent_t ev_reduce_b = nullptr;     // the second phase's
+    // A cancelled first phase may still be finishing on reduce_stream: the
+    // workspace's fused-launch buffers wait for ev_reduce before their next use.
+    bool reduce_pending = false;
     // captured fused launches by (shape, buffer addresses), most recent last
     std::vector<std::pair<std::vector<uintptr_t>, cudaGraphExec_t>> graphs;
     cudaStream_t capture_stream = nullptr;
@@ -165,7 +169,7 @@ struct rpp_context {
     // the host reductions, short walks only (the host takes what the device
     // has finished when it reaches a cloud); 2 every walk, long ones as level
     // sweeps (the host waits for the device's results)
-    int device_reduce = 1;
+    int device_reduce = 0;
     bool autotune = true;
     std::mutex tune_mu;
     std::map<int, rpp::BatchConfig> batch_tuning;  // bucket nmax -> chosen shape

@@ -690,7 +690,7 @@ __device__ void reduce_job(
     uint32_t *__restrict__ vpool, uint32_t *__restrict__ vstart,
     uint32_t *__restrict__ vcnt, uint64_t *__restrict__ death_all, float *__restrict__ ddiam_all,
     const int32_t *__restrict__ status_in, int32_t *__restrict__ status,
-    int32_t *__restrict__ adds_out) {
+    int32_t *__restrict__ adds_out, const unsigned *cancel) {
     extern __shared__ uint32_t dyn[];
     __shared__ uint32_t s_edge[RS_VMAX];
     __shared__ uint64_t s_head[RS_VMAX];
@@ -771,6 +771,10 @@ __device__ void reduce_job(
     int total_adds = 0;
     bool bail = false;
     for (int64_t j = 0; j < J.nleft && !bail; ++j) {
+        if (cancel && (j & 15) == 0 && *(volatile const unsigned *)cancel) {
+            bail = true;  // the host no longer needs this cloud
+            break;
+        }
         bool have = L[j].pivot != NO_PIVOT;
         uint64_t k = have ? tri_key(L[j].pdiam, (uint32_t)L[j].pivot) : ~0ull;
         bool cursors = true;  // false: the column sweeps
@@ -924,9 +928,9 @@ __global__ void __launch_bounds__(32) k_reduce_cursors(
     const ReduceJob *__restrict__ jobs, const Leftover *__restrict__ left,
     uint32_t *__restrict__ vpool, uint32_t *__restrict__ vstart, uint32_t *__restrict__ vcnt,
     uint64_t *__restrict__ death, float *__restrict__ ddiam, int32_t *__restrict__ status,
-    int32_t *__restrict__ adds) {
+    int32_t *__restrict__ adds, const unsigned *cancel) {
     reduce_job<false>((int)blockIdx.x, Dall, awall, jobs, left, nullptr, nullptr, nullptr, nullptr,
-                      vpool, vstart, vcnt, death, ddiam, nullptr, status, adds);
+                      vpool, vstart, vcnt, death, ddiam, nullptr, status, adds, cancel);
 }
 
 // The second phase: a fixed number of blocks (one per SM by default) take
@@ -948,7 +952,7 @@ __global__ void __launch_bounds__(32) k_reduce_sweeps(
         jj = __shfl_sync(FULL_MASK, jj, 0);
         if (jj >= njobs) break;
         reduce_job<true>(order[jj], Dall, awall, jobs, left, ekeys, ekaw, ecount, eerr, vpool,
-                         vstart, vcnt, death, ddiam, status_in, status, adds);
+                         vstart, vcnt, death, ddiam, status_in, status, adds, nullptr);
         __syncwarp();
     }
 }
@@ -1027,7 +1031,7 @@ void launch_reduce_small(const ReduceSmallArgs &A, cudaStream_t s) {
     ++g_launches;
     k_reduce_cursors<<<(unsigned)A.njobs, 32, smem_a, s>>>(A.D, A.aw, A.jobs, A.left, A.vpool,
                                                           A.vstart, A.vcnt, A.death, A.ddiam,
-                                                          A.status, A.adds);
+                                                          A.status, A.adds, A.cancel);
 }
 
 void launch_reduce_small_sweep(const ReduceSmallArgs &A, cudaStream_t s) {
