@@ -84,6 +84,13 @@ __device__ __forceinline__ void chunk_pass(const float *__restrict__ D, int64_t 
 // serialises once the candidates number in the billions); the second
 // recomputes the kept diameters (their rows are in cache) and writes them at
 // their ballot ranks.
+// Ordered build (k_build_count, k_chunk_offsets, k_build_write): the same
+// chunks and passes, split into three kernels. The first counts each chunk's
+// kept indices, the second turns the counts into each chunk's output offset
+// (an exclusive scan, in chunk order) and the column count, the third writes
+// every chunk at its offset. The columns then leave in increasing index
+// order, so the sort needs only the diameter digits (a stable sort keeps the
+// index order within a diameter). No kernel waits on another block.
 template <int P>
 __global__ void __launch_bounds__(256) k_build_columns(const float *__restrict__ D, int64_t ld,
                                                         int64_t n, const uint64_t *__restrict__ gB,
@@ -114,6 +121,120 @@ __global__ void __launch_bounds__(256) k_build_columns(const float *__restrict__
         at = __shfl_sync(FULL_MASK, at, 0);
         chunk_pass<P>(D, ld, n, B, cleared, t, c0, cend, lane,
                       [&](int k, uint64_t c, bool keep, float d) {
+                          const unsigned ball = __ballot_sync(FULL_MASK, keep);
+                          if (keep) {
+                              const uint64_t pos = at + __popc(ball & lanemask_lt());
+                              key_hi[pos] = ~__float_as_uint(d);
+                              key_lo[pos] = c;
+                          }
+                          at += __popc(ball);
+                      });
+    }
+}
+
+// Ordered build, first kernel: counts[chunk] = kept indices of the chunk.
+template <int P>
+__global__ void __launch_bounds__(256) k_build_count(const float *__restrict__ D, int64_t ld,
+                                                      int64_t n, const uint64_t *__restrict__ gB,
+                                                      bool smem_table, uint64_t total,
+                                                      uint64_t chunk,
+                                                      const uint32_t *__restrict__ cleared,
+                                                      const DevState *st,
+                                                      unsigned long long *__restrict__ counts) {
+    extern __shared__ uint64_t sB[];
+    const uint64_t *B = stage_binomial(gB, n, P + 1, sB, smem_table);
+    const float t = st->t;
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t id = warp; id * chunk < total; id += nwarps) {
+        const uint64_t c0 = id * chunk;
+        const uint64_t cend = c0 + chunk < total ? c0 + chunk : total;
+        unsigned cnt = 0;
+        chunk_pass<P>(D, ld, n, B, cleared, t, c0, cend, lane,
+                      [&](int, uint64_t, bool keep, float) { cnt += keep; });
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(FULL_MASK, cnt, o);
+        if (lane == 0) counts[id] = cnt;
+    }
+}
+
+// Ordered build, second kernel (one block of 1024 threads): the counts
+// become exclusive offsets in chunk order, tile by tile of 8192 with a
+// running carry; their sum is the column count.
+__global__ void __launch_bounds__(1024) k_chunk_offsets(unsigned long long *__restrict__ counts,
+                                                        uint64_t nchunks, DevState *st) {
+    constexpr int ITEMS = 8;
+    __shared__ unsigned long long s_warp[32];
+    __shared__ unsigned long long s_carry;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    if (tid == 0) s_carry = 0;
+    __syncthreads();
+    for (uint64_t base = 0; base < nchunks; base += 1024 * ITEMS) {
+        unsigned long long v[ITEMS], sum = 0;
+        const uint64_t i0 = base + (uint64_t)tid * ITEMS;
+#pragma unroll
+        for (int k = 0; k < ITEMS; ++k) {
+            v[k] = i0 + k < nchunks ? counts[i0 + k] : 0ull;
+            sum += v[k];
+        }
+        unsigned long long incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(FULL_MASK, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) s_warp[w] = incl;
+        __syncthreads();
+        if (w == 0) {
+            unsigned long long x = s_warp[lane], xi = x;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(FULL_MASK, xi, o);
+                if (lane >= o) xi += y;
+            }
+            s_warp[lane] = xi - x;  // exclusive over the warps
+        }
+        __syncthreads();
+        unsigned long long at = s_carry + s_warp[w] + incl - sum;
+#pragma unroll
+        for (int k = 0; k < ITEMS; ++k)
+            if (i0 + k < nchunks) {
+                counts[i0 + k] = at;
+                at += v[k];
+            }
+        __syncthreads();
+        if (tid == 1023) s_carry = at;
+        __syncthreads();
+    }
+    if (tid == 0) st->ncols = s_carry;
+}
+
+// Ordered build, third kernel: every chunk written at its offset.
+template <int P>
+__global__ void __launch_bounds__(256) k_build_write(const float *__restrict__ D, int64_t ld,
+                                                      int64_t n, const uint64_t *__restrict__ gB,
+                                                      bool smem_table, uint64_t total,
+                                                      uint64_t chunk,
+                                                      const uint32_t *__restrict__ cleared,
+                                                      const DevState *st,
+                                                      const unsigned long long *__restrict__ offs,
+                                                      uint32_t *__restrict__ key_hi,
+                                                      uint64_t *__restrict__ key_lo) {
+    extern __shared__ uint64_t sB[];
+    const uint64_t *B = stage_binomial(gB, n, P + 1, sB, smem_table);
+    const float t = st->t;
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t id = warp; id * chunk < total; id += nwarps) {
+        const uint64_t c0 = id * chunk;
+        const uint64_t cend = c0 + chunk < total ? c0 + chunk : total;
+        uint64_t at = offs[id];
+        if (id + 1 < (total + chunk - 1) / chunk ? offs[id + 1] == at : st->ncols == at)
+            continue;  // nothing kept
+        chunk_pass<P>(D, ld, n, B, cleared, t, c0, cend, lane,
+                      [&](int, uint64_t c, bool keep, float d) {
                           const unsigned ball = __ballot_sync(FULL_MASK, keep);
                           if (keep) {
                               const uint64_t pos = at + __popc(ball & lanemask_lt());
@@ -164,39 +285,68 @@ __global__ void k_lower_bound_u32(const uint32_t *__restrict__ a, uint64_t n, ui
     *out = lo;
 }
 
-template <int P>
-void build_p(const float *D, int64_t ld, int64_t n, const uint64_t *binom, uint64_t total,
-             const uint32_t *cleared, DevState *st, uint32_t *key_hi, uint64_t *key_lo,
-             cudaStream_t s) {
-    const size_t table = (size_t)(P + 2) * (n + 1) * sizeof(uint64_t);
-    const bool smem = table <= 160 * 1024;
-    if (smem) allow_dynamic_smem((const void *)k_build_columns<P>, table);
+// Grid and chunk of the build: chunks of consecutive indices per warp, long
+// enough that a lane's single decode serves many indices, short enough to
+// spread the work.
+uint64_t build_grid(uint64_t total, uint64_t *chunk) {
     uint64_t blocks = (total + 255) / 256;
     const uint64_t cap = 152ull * 8;
     if (blocks > cap) blocks = cap;
-    if (blocks == 0) return;
-    // chunks of consecutive indices per warp: long enough that a lane's
-    // single decode serves many indices, short enough to spread the work
     const uint64_t warps = blocks * 8;
-    uint64_t chunk = (total + warps - 1) / warps;
-    chunk = (chunk + 31) / 32 * 32;
-    if (chunk > 2048) chunk = 2048;
-    if (chunk < 32) chunk = 32;
-    ++g_launches;
-    k_build_columns<P><<<(unsigned)blocks, 256, smem ? table : 0, s>>>(
-        D, ld, n, binom, smem, total, chunk, cleared, st, key_hi, key_lo);
+    uint64_t c = warps ? (total + warps - 1) / warps : 32;
+    c = (c + 31) / 32 * 32;
+    if (c > 2048) c = 2048;
+    if (c < 32) c = 32;
+    *chunk = c;
+    return blocks;
+}
+
+template <int P>
+void build_p(const float *D, int64_t ld, int64_t n, const uint64_t *binom, uint64_t total,
+             const uint32_t *cleared, DevState *st, uint32_t *key_hi, uint64_t *key_lo,
+             unsigned long long *order, cudaStream_t s) {
+    const size_t table = (size_t)(P + 2) * (n + 1) * sizeof(uint64_t);
+    const bool smem = table <= 160 * 1024;
+    uint64_t chunk;
+    const uint64_t blocks = build_grid(total, &chunk);
+    if (blocks == 0) return;
+    const size_t sm = smem ? table : 0;
+    if (!order) {
+        if (smem) allow_dynamic_smem((const void *)k_build_columns<P>, table);
+        ++g_launches;
+        k_build_columns<P><<<(unsigned)blocks, 256, sm, s>>>(D, ld, n, binom, smem, total, chunk,
+                                                             cleared, st, key_hi, key_lo);
+        return;
+    }
+    if (smem) {
+        allow_dynamic_smem((const void *)k_build_count<P>, table);
+        allow_dynamic_smem((const void *)k_build_write<P>, table);
+    }
+    const uint64_t nchunks = (total + chunk - 1) / chunk;
+    g_launches += 3;
+    k_build_count<P><<<(unsigned)blocks, 256, sm, s>>>(D, ld, n, binom, smem, total, chunk,
+                                                       cleared, st, order);
+    k_chunk_offsets<<<1, 1024, 0, s>>>(order, nchunks, st);
+    k_build_write<P><<<(unsigned)blocks, 256, sm, s>>>(D, ld, n, binom, smem, total, chunk,
+                                                       cleared, st, order, key_hi, key_lo);
 }
 
 }  // namespace
 
+size_t build_order_bytes(uint64_t total) {
+    uint64_t chunk;
+    build_grid(total, &chunk);
+    return (size_t)((total + chunk - 1) / chunk + 1) * sizeof(unsigned long long);
+}
+
 void launch_build_columns(const float *D, int64_t ld, int64_t n, int p, const uint64_t *binom,
                           uint64_t total, const uint32_t *cleared, DevState *st, uint32_t *key_hi,
-                          uint64_t *key_lo, cudaStream_t s) {
+                          uint64_t *key_lo, cudaStream_t s, unsigned long long *order) {
     switch (p) {
-        case 1: build_p<1>(D, ld, n, binom, total, cleared, st, key_hi, key_lo, s); break;
-        case 2: build_p<2>(D, ld, n, binom, total, cleared, st, key_hi, key_lo, s); break;
-        case 3: build_p<3>(D, ld, n, binom, total, cleared, st, key_hi, key_lo, s); break;
-        case 4: build_p<4>(D, ld, n, binom, total, cleared, st, key_hi, key_lo, s); break;
+        case 1: build_p<1>(D, ld, n, binom, total, cleared, st, key_hi, key_lo, order, s); break;
+        case 2: build_p<2>(D, ld, n, binom, total, cleared, st, key_hi, key_lo, order, s); break;
+        case 3: build_p<3>(D, ld, n, binom, total, cleared, st, key_hi, key_lo, order, s); break;
+        case 4: build_p<4>(D, ld, n, binom, total, cleared, st, key_hi, key_lo, order, s); break;
         default: break;
     }
 }

@@ -75,14 +75,22 @@ void launch_enclosing_radius(const float *D, int64_t n, int64_t ld, DevState *st
 
 // Filtration construction with clearing: every cidx in [0, total) of dimension p
 // is decoded, its diameter taken, and kept when diam <= st->t and its bit in
-// `cleared` (may be null) is clear. Kept columns are appended (in no particular
-// order) as key_hi = ~bits(diam), key_lo = cidx; st->ncols counts them.
+// `cleared` (may be null) is clear. Kept columns are appended as key_hi =
+// ~bits(diam), key_lo = cidx; st->ncols counts them. With `order` (device
+// scratch of build_order_bytes(total) bytes: per-chunk counts and offsets)
+// they are written in increasing cidx and st->ncols is set to their count, so that radix_sort with lo_bits = 0 (the
+// diameter digits alone) puts them in coboundary order; without it, in no
+// particular order.
 void launch_build_columns(const float *D, int64_t ld, int64_t n, int p, const uint64_t *binom,
                           uint64_t total, const uint32_t *cleared, DevState *st,
-                          uint32_t *key_hi, uint64_t *key_lo, cudaStream_t s);
+                          uint32_t *key_hi, uint64_t *key_lo, cudaStream_t s,
+                          unsigned long long *order = nullptr);
+size_t build_order_bytes(uint64_t total);
 
 // LSD radix sort of (hi, lo) keys, ascending in (hi, lo) (hi may be null: lo
-// alone), with an optional 64-bit payload; lo < 2^lo_bits. The key count is
+// alone), with an optional 64-bit payload; lo < 2^lo_bits. lo_bits = 0 (with
+// hi): the keys arrive in increasing lo, and only hi's digits are sorted
+// (every pass is stable, so lo stays increasing within equal hi). The key count is
 // min(*d_count, n_cap) when d_count (device memory) is given, else n_cap, so
 // the sort needs nothing from the host. The result is left in (hi, lo, val);
 // tmp_* are buffers of the same sizes, scratch holds radix_scratch_bytes(n_cap)

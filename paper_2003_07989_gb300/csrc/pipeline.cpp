@@ -302,6 +302,7 @@ size_t instance_device_bytes(const Instance &in) {
     total += slack((size_t)n * 4) + slack(maxcand / 8 + 8) + slack(maxcand * 8);
     total += slack((size_t)n * n * 8);  // neighbour lists
     total += slack(512 + (size_t)n * 32);  // the H0 forest
+    total += slack(build_order_bytes(maxcand));  // the ordered build's look-back
     return total + 64 * 256;  // per-buffer rounding
 }
 
@@ -527,12 +528,15 @@ Status run_filtration(rpp_context *ctx, Workspace &ws, const Instance &in, int p
     RPP_TRY(ws.dev(ws.tmp_hi, cand * 4, (void **)&tmp_hi));
     RPP_TRY(ws.dev(ws.tmp_lo, cand * 8, (void **)&tmp_lo));
     RPP_TRY(ws.dev(ws.tiles, radix_scratch_bytes(cand), &sort_scratch));
+    unsigned long long *order;
+    RPP_TRY(ws.dev(ws.order, build_order_bytes(cand), (void **)&order));
     T.begin(ST_BUILD);
-    launch_build_columns(pro.D, ld, n, p, pro.d_binom, cand, nullptr, pro.st, key_hi, key_lo, s);
+    launch_build_columns(pro.D, ld, n, p, pro.d_binom, cand, nullptr, pro.st, key_hi, key_lo, s,
+                         order);
     T.end();
-    T.begin(ST_SORT);
+    T.begin(ST_SORT);  // the columns arrive in index order: the diameter digits alone
     radix_sort(key_hi, key_lo, nullptr, tmp_hi, tmp_lo, nullptr, sort_scratch, cand,
-               &pro.st->ncols, bits_for(cand - 1), &pro.st->err, s);
+               &pro.st->ncols, 0, &pro.st->err, s);
     T.end();
     RPP_CK(cudaGetLastError());
     const double a = now_ms();
@@ -730,13 +734,15 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
         // build, sort, forest, apparent pass and partition are queued without
         // a host round trip: their column count stays in device memory
         // (st->ncols), and grids are sized for the m candidates
+        unsigned long long *order;
+        RPP_TRY(ws.dev(ws.order, build_order_bytes(m), (void **)&order));
         T.begin(ST_BUILD);
-        launch_build_columns(D, ld, n, 1, d_binom, m, nullptr, st, key_hi, key_lo, s);
+        launch_build_columns(D, ld, n, 1, d_binom, m, nullptr, st, key_hi, key_lo, s, order);
         T.end();
         RPP_CK(cudaGetLastError());
-        T.begin(ST_SORT);
+        T.begin(ST_SORT);  // the edges arrive in index order: the diameter digits alone
         radix_sort(key_hi, key_lo, nullptr, tmp_hi, tmp_lo, nullptr, sort_scratch, m, &st->ncols,
-                   bits_for(m - 1), &st->err, s);
+                   0, &st->err, s);
         T.end();
         RPP_CK(cudaGetLastError());
         uint64_t begin = 0;
@@ -916,7 +922,10 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
                 if (up) launch_bitmap_set(up, prev_deaths.size(), bitmap, s);
                 T.end();
                 T.begin(ST_BUILD);
-                launch_build_columns(D, ld, n, p, d_binom, cand, bitmap, st, key_hi, key_lo, s);
+                unsigned long long *order;
+                RPP_TRY(ws.dev(ws.order, build_order_bytes(cand), (void **)&order));
+                launch_build_columns(D, ld, n, p, d_binom, cand, bitmap, st, key_hi, key_lo, s,
+                                     order);
                 T.end();
             } else {
                 S.sparse[p] = 1;
@@ -991,8 +1000,10 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
             uint64_t N = cap;
             const unsigned long long *d_n = &st->ncols;
             T.begin(ST_SORT);
+            // the dense build writes its columns in index order (the
+            // diameter digits alone); the thresholded one does not
             radix_sort(key_hi, key_lo, nullptr, tmp_hi, tmp_lo, nullptr, sort_scratch, cap,
-                       &st->ncols, bits_for(cand - 1), &st->err, s);
+                       &st->ncols, S.sparse[p] ? bits_for(cand - 1) : 0, &st->err, s);
             T.end();
             if (ctx->record & RPP_RECORD_COLUMNS) {
                 RPP_TRY(read_state());

@@ -75,6 +75,7 @@ struct Workspace {
         status, pivot, pdiam, app_tau, app_sigma, left, bitmap, mst, up, nbr, h0;
     DevBuf csr_off, csr_nbr, sp_a, sp_b, sp_c, sp_cnt;  // the thresholded construction
     DevBuf aw;    // dimension 1: the vertex each edge's apparent pair adds
+    DevBuf order; // the ordered filtration build's ticket and look-back counts
     HostBuf h_aw;
     HostBuf h_hi, h_lo, h_tau, h_sigma, h_left, h_D, h_state, h_mst, h_up, h_nbr, h_ehi, h_eab;
     Binomial binom_host;      // cached table

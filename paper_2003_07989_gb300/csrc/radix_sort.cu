@@ -4,7 +4,10 @@
 //
 // A key is the composite C = ((hi - hi_min) << lo_bits) | lo, where hi_min is
 // the smallest hi among the keys (found on the device) and lo < 2^lo_bits;
-// ascending C is ascending (hi, lo). C is sorted 8 bits at a time, from the
+// ascending C is ascending (hi, lo). Keys that arrive in increasing lo (the
+// ordered filtration build) take C = hi - hi_min alone (lo_bits = 0): the
+// passes are stable, so lo stays increasing within equal hi, and the sort
+// needs no pass over the index bits. C is sorted 8 bits at a time, from the
 // least significant digit up, every pass stable. Nothing comes back to the
 // host: the key count may itself live in device memory, and the passes whose
 // digit is the same for every key are skipped by the kernels themselves.
@@ -75,7 +78,9 @@ template <bool HAS_HI>
 __device__ __forceinline__ unsigned digit_of(uint32_t h, uint64_t l, uint32_t hi_min, int lo_bits,
                                              int shift) {
     if constexpr (HAS_HI) {
-        const unsigned __int128 c = ((unsigned __int128)(h - hi_min) << lo_bits) | l;
+        // lo_bits = 0: the keys are in increasing lo already; hi alone
+        const unsigned __int128 c =
+            ((unsigned __int128)(h - hi_min) << lo_bits) | (lo_bits ? l : 0ull);
         return (unsigned)(c >> shift) & 0xffu;
     } else {
         return shift < 64 ? (unsigned)(l >> shift) & 0xffu : 0u;
@@ -333,7 +338,8 @@ void radix_sort(uint32_t *hi, uint64_t *lo, uint64_t *val, uint32_t *tmp_hi, uin
                 uint64_t *tmp_val, void *scratch, uint64_t n_cap,
                 const unsigned long long *d_count, int lo_bits, unsigned *err, cudaStream_t s) {
     if (n_cap <= 1) return;
-    if (lo_bits < 1) lo_bits = 1;
+    if (lo_bits < 1 && !hi) lo_bits = 1;
+    if (lo_bits < 0) lo_bits = 0;
     const int bits = lo_bits + (hi ? 32 : 0);
     int passes = (bits + 7) / 8;
     if (passes > MAXP) passes = MAXP;
