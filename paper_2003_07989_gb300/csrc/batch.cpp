@@ -226,10 +226,14 @@ Status fused_graph(Workspace &ws, const BatchPlan &plan, const Caps &c, const Bu
 // inputs are already on the device) and keep the fastest for the bucket.
 Status autotune(rpp_context *ctx, const Bufs &b, const Caps &caps, int nmax, int dimcap,
                 int nclouds, cudaStream_t s, BatchConfig *best) {
-    // (threads, group): group = lanes per column G, or 10 G + U for U
-    // candidate blocks a step
-    static const BatchConfig cands[] = {{128, 4}, {128, 8}, {256, 4}, {256, 8}, {256, 16},
-                                        {512, 8}, {512, 16}, {256, 42}, {256, 44}, {512, 42}};
+    // (threads, group, blocks per SM): group = lanes per column G, or 10 G + U
+    // for U candidate blocks a step; a cap on the blocks per SM bounds the
+    // distance matrices in flight (their sum should stay in L2)
+    static const BatchConfig cands[] = {{128, 4, 0},   {128, 8, 0},  {256, 4, 0},  {256, 8, 0},
+                                        {256, 16, 0},  {512, 8, 0},  {512, 16, 0}, {256, 42, 0},
+                                        {256, 44, 0},  {512, 42, 0}, {512, 42, 1}, {512, 44, 1},
+                                        {256, 42, 2},  {256, 44, 2}, {512, 8, 1},
+                                        {1024, 42, 1}, {1024, 44, 1}, {1024, 8, 1}};
     cudaEvent_t e0, e1;
     RPP_CK(cudaEventCreate(&e0));
     RPP_CK(cudaEventCreate(&e1));

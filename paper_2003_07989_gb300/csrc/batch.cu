@@ -101,7 +101,7 @@ __host__ __device__ inline size_t batch_smem_bytes(int nmax, int points_floats) 
 }
 
 template <int G, int U>
-__global__ void __launch_bounds__(512) k_batch_h1(
+__global__ void __launch_bounds__(1024) k_batch_h1(
     const float *__restrict__ pts, const BatchCloud *__restrict__ clouds,
     const int32_t *__restrict__ order, BatchCtl *ctl, int nmax, int points_floats,
     float *__restrict__ Dbuf, uint64_t *__restrict__ mst_out, BatchOut *__restrict__ outs,
@@ -604,6 +604,7 @@ BatchPlan plan_g(int nmax, int dimcap, BatchConfig cfg, int sms) {
     allow_dynamic_smem((const void *)k_batch_h1<G, U>, P.smem);
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_h1<G, U>, cfg.threads, P.smem);
+    if (cfg.per_sm > 0 && cfg.per_sm < per_sm) per_sm = cfg.per_sm;
     P.blocks = std::max(1, sms * std::max(1, per_sm));
     return P;
 }

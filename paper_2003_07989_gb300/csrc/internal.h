@@ -221,6 +221,9 @@ struct BatchOut {
 // `group` is the lane-group width of the test.
 struct BatchConfig {
     int threads = 256, group = 8;  // group: G lanes per column, or 10 G + U for U blocks a step
+    // blocks per SM at most (0: as many as fit): fewer clouds in flight keep
+    // their distance matrices in L2 between the kernel's passes over them
+    int per_sm = 0;
 };
 // Control block of one fused launch (device memory).
 struct BatchCtl {
