@@ -113,6 +113,47 @@ def test_distance_matrix_within_float32_rounding_of_exact():
     assert rel.max() < 4 * 2.0 ** -24 * 3  # 3 adds + square root, each half an ulp
 
 
+def test_enclosing_radius_closed_forms():
+    """Closed forms, independent of any row max/min code: n collinear points
+    at 0, 1, ..., n-1 have R = ceil((n-1)/2) (every point's farthest point is
+    an end of the line; the middle points minimise that); a regular 2k-gon on
+    the unit circle has R = its diameter 2 (each vertex's antipode); a star
+    of unit spokes has R = 1 (its centre's row) although every other row's
+    maximum is 2. A max taken for a min, or a row skipped, gives another
+    value in each case."""
+    for n in (2, 3, 7, 10, 31):
+        X = np.zeros((n, 2), np.float32)
+        X[:, 0] = np.arange(n, dtype=np.float32)
+        assert O.enclosing_radius(O.distance_matrix(X)) == float((n - 1 + 1) // 2)
+    k = 8
+    ang = np.arange(2 * k) * (np.pi / k)
+    X = np.stack([np.cos(ang), np.sin(ang)], 1).astype(np.float32)
+    D = O.distance_matrix(X)
+    R = O.enclosing_radius(D)
+    assert abs(R - 2.0) < 1e-6
+    assert R == float(min(D[i, (i + k) % (2 * k)] for i in range(2 * k)))
+    # a star: the centre is within 1 of every other point, and every other
+    # point has a point 2 away, so R = 1 exactly (the centre's row)
+    X = np.zeros((9, 2), np.float32)
+    X[1:, 0] = [1, -1, 0, 0, 1, -1, 0, 0]
+    X[1:, 1] = [0, 0, 1, -1, 0, 0, 1, -1]
+    X[5:] *= -1
+    assert O.enclosing_radius(O.distance_matrix(X)) == 1.0
+
+
+def test_distance_quantile_closed_form():
+    """On a matrix whose C(n,2) edge values are 1.0 + r for the ranks r =
+    1..m (distinct floats in rank order), the nearest-rank q-quantile is the
+    edge of rank ceil(q m), whose value is known without sorting."""
+    n = 23
+    D = I.rank_distances(n, seed=4)
+    m = n * (n - 1) // 2
+    for q in (0.01, 0.25, 0.5, 0.6, 0.999, 1.0):
+        r = math.ceil(q * m)
+        want = np.array([0x3F800000 + r], dtype=np.uint32).view(np.float32)[0]
+        assert O.distance_quantile(D, q) == float(want), q
+
+
 def test_enclosing_radius_and_quantile_definitions():
     X = I.uniform_cube(40, 3, 5)
     D = O.distance_matrix(X)
