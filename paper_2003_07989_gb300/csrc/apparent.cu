@@ -12,9 +12,10 @@
 //      decreasing order (Alg. 5); the facets before sigma drop a vertex
 //      w > w*. sigma is apparent iff none of them has diam == diam(sigma)
 //      (condition 2; Proposition "apparent-support").
-// The kernel is bound by the latency of its L1/L2 loads, so it is compiled
-// for eight 256-thread blocks per SM (32 registers a thread) to keep more
-// warps in flight. The paper runs one thread per column. Here a group of G
+// The kernel is bound by the latency of its L1/L2 loads and by issue. It is
+// compiled for up to 64 registers a thread (dimension 1 takes 48: five
+// 256-thread blocks per SM); squeezed into 32 registers for eight blocks, the
+// test spilled to local memory and ran 4-30% slower depending on the shape. The paper runs one thread per column. Here a group of G
 // lanes owns a column and tests U blocks of G candidate vertices per step,
 // lane l taking w = scan - l - u G for u < U: the reads D[v_i][w] of a block
 // are contiguous, so a step is U coalesced loads of (p+1) short row segments
@@ -36,7 +37,7 @@ namespace rpp {
 namespace {
 
 template <int P, int G, int U>
-__global__ void __launch_bounds__(256, P == 1 ? 8 : 4) k_apparent(
+__global__ void __launch_bounds__(256, 4) k_apparent(
     const float *__restrict__ D, int64_t ld, int64_t n, const uint64_t *__restrict__ gB,
     bool smem_table, const uint32_t *__restrict__ key_hi, const uint64_t *__restrict__ key_lo,
     uint64_t ncols_cap, const unsigned long long *d_ncols, DevState *__restrict__ st,
@@ -193,7 +194,7 @@ __global__ void __launch_bounds__(256, P == 1 ? 8 : 4) k_apparent(
 // test. The largest qualifying candidate is the first lane of the ballot with
 // a hit, and the largest of that lane's hits; the rest is the scalar kernel's.
 template <int P, int G, int U>
-__global__ void __launch_bounds__(256, P == 1 ? 8 : 4) k_apparent_vec(
+__global__ void __launch_bounds__(256, 4) k_apparent_vec(
     const float *__restrict__ D, int64_t ld, int64_t n, const uint64_t *__restrict__ gB,
     bool smem_table, const uint32_t *__restrict__ key_hi, const uint64_t *__restrict__ key_lo,
     uint64_t ncols_cap, const unsigned long long *d_ncols, DevState *__restrict__ st,

@@ -59,6 +59,22 @@ __device__ __forceinline__ void decode_simplex(uint64_t c, const uint64_t *B, in
 template <int P>
 __device__ __forceinline__ uint64_t cofacet_index(const int *v, int w, const uint64_t *B,
                                                   int64_t n) {
+    if constexpr (P == 1) {
+        // a triangle {a > b > c}: C(a, 3) + C(b, 2) + c, in exact integer
+        // arithmetic (a (a-1) (a-2) < 2^63 for every admissible n)
+        uint64_t a = (uint64_t)v[0], b = (uint64_t)v[1], c = (uint64_t)w;
+        if (c > a) {
+            const uint64_t t = c;
+            c = b;
+            b = a;
+            a = t;
+        } else if (c > b) {
+            const uint64_t t = c;
+            c = b;
+            b = t;
+        }
+        return a * (a - 1) * (a - 2) / 6 + b * (b - 1) / 2 + c;
+    }
     uint64_t c = 0;
     int k = P + 2;  // the largest vertex of the cofacet carries C(., P + 2)
     bool placed = false;
