@@ -62,7 +62,8 @@ Workspace::~Workspace() {
     DevBuf *d[] = {&X,    &Dsrc,  &D,      &state,   &binom,     &key_hi, &key_lo,
                    &tmp_hi, &tmp_lo, &tmp_val, &tiles, &hist,      &status, &pivot,
                    &pdiam, &app_tau, &app_sigma, &left, &bitmap, &mst,    &up, &nbr, &h0,
-                   &state_tune, &csr_off, &csr_nbr, &sp_a, &sp_b, &sp_c, &sp_cnt, &aw};
+                   &state_tune, &csr_off, &csr_nbr, &sp_a, &sp_b, &sp_c, &sp_cnt, &aw,
+                   &order};
     for (DevBuf *b : d)
         if (b->p) cudaFree(b->p);
     HostBuf *h[] = {&h_hi,    &h_lo,  &h_tau, &h_sigma, &h_left, &h_D,  &h_state,
