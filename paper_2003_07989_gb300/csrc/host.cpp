@@ -352,14 +352,35 @@ void sort_edges(const HostInstance &I, float from, EdgeList &out) {
     for (int i = 0; i < nb; ++i) out.done[i].store(0, std::memory_order_relaxed);
 }
 
+// Dimensions p >= 2 up to this many points keep the threshold graph's rows
+// as bitsets for the cursors' scans of equal-diameter cofacets (n^2 / 8 bytes).
+constexpr int64_t LUNE_BITS_NMAX = 16384;
+
 struct Reducer {
     const HostInstance &I;
     int p;
     int64_t n;
     std::vector<uint64_t> top;  // app_tau[0], app_tau[STRIDE], ...
+    // Dimensions p >= 2: bit w of row a is set iff D[a][w] <= t and w != a.
+    // A cofacet of a simplex inside the threshold adds a vertex of every one
+    // of its vertices' rows, so a cursor's lune scan visits only the set bits
+    // of the AND of those rows (a handful below a sparse threshold, instead
+    // of all n vertices), testing each exactly.
+    std::vector<uint64_t> tbits;
+    int64_t tw = 0;  // words per row
 
-    Reducer(const HostInstance &I_, int p_) : I(I_), p(p_), n(I_.n) {
+    Reducer(const HostInstance &I_, int p_, int threads = 1) : I(I_), p(p_), n(I_.n) {
         for (uint64_t i = 0; i < I.napp; i += STRIDE) top.push_back(I.app_tau[i]);
+        if (p >= 2 && n <= LUNE_BITS_NMAX) {
+            tw = (n + 63) / 64;
+            tbits.assign((size_t)(n * tw), 0);
+            parallel_for(threads, n, [&](int64_t a) {
+                const float *Da = I.D + a * I.ld;
+                uint64_t *row = tbits.data() + a * tw;
+                for (int64_t w = 0; w < n; ++w)
+                    if (w != a && Da[w] <= I.t) row[w >> 6] |= 1ull << (w & 63);
+            });
+        }
     }
 
     bool is_apparent_tau(uint64_t tau) const {
@@ -423,8 +444,32 @@ struct Reducer {
         }
     }
 
+    // Next vertex at or below c.lune in the AND of the rows of c's vertices
+    // (-1: none).
+    int next_lune_candidate(const Cursor &c) const {
+        int64_t k = c.lune >> 6;
+        uint64_t mask = (c.lune & 63) == 63 ? ~0ull : ((2ull << (c.lune & 63)) - 1);
+        for (; k >= 0; --k, mask = ~0ull) {
+            uint64_t m = mask;
+            for (int i = 0; i <= p; ++i) m &= tbits[(int64_t)c.v[i] * tw + k];
+            if (m) return (int)(k << 6) + 63 - __builtin_clzll(m);
+        }
+        return -1;
+    }
+
     // Move the cursor to its next cofacet inside the threshold (or NONE).
     void advance(Cursor &c) const {
+        while (!tbits.empty() && c.lune >= 0) {  // the same scan over candidates only
+            const int w = next_lune_candidate(c);
+            c.lune = w - 1;
+            if (w < 0) break;
+            float m = 0.0f;
+            for (int i = 0; i <= p; ++i) m = std::max(m, I.dist(c.v[i], w));
+            if (m <= c.d) {
+                c.head = age_key(c.d, cofacet_idx(*I.B, c.v, p, w));
+                return;
+            }
+        }
         while (c.lune >= 0) {  // cofacets of diameter d, largest vertex first
             const int w = c.lune--;
             if (in_simplex(c.v, w)) continue;
@@ -585,24 +630,29 @@ inline int bits_of(uint64_t x) {  // bits needed to write x
 template <class K, class Col = std::vector<uint64_t>>
 struct Ledger {
     std::mutex m;
-    std::condition_variable cv;
     std::unordered_map<uint64_t, int64_t> owner;  // pivot index -> finished column
     std::vector<Col> &V;                          // reduced columns, final once finished
     std::vector<char> done;
     int64_t low = 0;                              // columns below are finished
-    int waiting = 0;                              // queries waiting (under m)
     // Per column, its current pivot as a 64-bit image that preserves the age
     // order (an image that is smaller or equal for every older key): exact
     // for 64-bit keys; for 128-bit ones the diameter bits over the top 32
     // bits of the complemented index, taken over idx_bits significant bits
     // (exact when they number 32 or fewer).
     std::unique_ptr<std::atomic<uint64_t>[]> front;
+    // done[] again, readable without the lock (set after the column's owner
+    // entry, under the lock)
+    std::unique_ptr<std::atomic<char>[]> fin;
     int idx_bits = 64;
 
     Ledger(std::vector<Col> &V_, int64_t ncols, int idx_bits_ = 64)
-        : V(V_), done(ncols, 0), front(new std::atomic<uint64_t>[ncols]), idx_bits(idx_bits_) {
+        : V(V_), done(ncols, 0), front(new std::atomic<uint64_t>[ncols]),
+          fin(new std::atomic<char>[ncols]), idx_bits(idx_bits_) {
         owner.reserve((size_t)ncols * 2);
-        for (int64_t j = 0; j < ncols; ++j) front[j].store(0, std::memory_order_relaxed);
+        for (int64_t j = 0; j < ncols; ++j) {
+            front[j].store(0, std::memory_order_relaxed);
+            fin[j].store(0, std::memory_order_relaxed);
+        }
     }
     uint64_t image(u128 k) const {
         if (k == NONE) return ~0ull;
@@ -618,42 +668,42 @@ struct Ledger {
     // The finished column that owns pivot k of column j, or -1 when k is
     // free for j; waits while an unfinished earlier column may still end at k
     // (its pivot's image is at most k's: pivots only move forward, and the
-    // image keeps their order).
+    // image keeps their order). The wait watches that one column's pivot and
+    // finished flag without the lock, so waiting columns do not hold up the
+    // column they wait for (its own queries take the lock).
     int64_t query(int64_t j, u128 k) {
         const uint64_t ub = image(k);
-        std::unique_lock<std::mutex> g(m);
-        for (int round = 0;; ++round) {
-            auto it = owner.find(key_index(k));
-            if (it != owner.end()) return it->second;
-            while (low < j && done[low]) ++low;
-            bool blocked = false;
-            for (int64_t i = low; i < j && !blocked; ++i)
-                blocked = !done[i] && front[i].load(std::memory_order_relaxed) <= ub;
-            if (!blocked) return -1;
-            // earlier columns move their pivots without notice: look again
-            // soon (a short spin first: a sleep's timer slack is longer than
-            // most waits)
-            if (round < 256) {
-                g.unlock();
-                std::this_thread::yield();
-                g.lock();
-                continue;
+        for (;;) {
+            int64_t blocker = -1;
+            {
+                std::lock_guard<std::mutex> g(m);
+                auto it = owner.find(key_index(k));
+                if (it != owner.end()) return it->second;
+                while (low < j && done[low]) ++low;
+                for (int64_t i = low; i < j; ++i)
+                    if (!done[i] && front[i].load(std::memory_order_relaxed) <= ub) {
+                        blocker = i;
+                        break;
+                    }
+                if (blocker < 0) return -1;
             }
-            ++waiting;
-            cv.wait_for(g, std::chrono::microseconds(round < 320 ? 10 : 100));
-            --waiting;
+            // a short spin first (a sleep's timer slack is longer than most
+            // waits), then yields, then short sleeps
+            for (int round = 0;; ++round) {
+                if (fin[blocker].load(std::memory_order_acquire) ||
+                    front[blocker].load(std::memory_order_relaxed) > ub)
+                    break;
+                if (round < 2048) std::this_thread::yield();
+                else std::this_thread::sleep_for(std::chrono::microseconds(20));
+            }
         }
     }
     // Column j is finished with pivot k (NONE: a zero column); V[j] is final.
     void finish(int64_t j, u128 k) {
-        bool wake;
-        {
-            std::lock_guard<std::mutex> g(m);
-            if (k != NONE) owner[key_index(k)] = j;
-            done[j] = 1;
-            wake = waiting > 0;
-        }
-        if (wake) cv.notify_all();
+        std::lock_guard<std::mutex> g(m);
+        if (k != NONE) owner[key_index(k)] = j;
+        done[j] = 1;
+        fin[j].store(1, std::memory_order_release);
     }
 };
 
@@ -794,7 +844,7 @@ constexpr double PHASE_B_SERIAL_MS = 4.0;
 // long, then concurrently.
 void reduce_general(const HostInstance &I, int p, const Leftover *left, int64_t nleft,
                     int threads, std::vector<HostPair> &out, ReduceStats &stats) {
-    Reducer R(I, p);
+    Reducer R(I, p, threads);
     std::vector<ColumnState> col(nleft);
     std::vector<SimplexSet> V(nleft);
     // cofacet indices (the pivots) stay below C(n, p+2)
