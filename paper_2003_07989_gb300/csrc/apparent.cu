@@ -448,7 +448,7 @@ void apparent_vec(const float *D, int64_t ld, int64_t n, const uint64_t *binom,
 
 // group: lanes per column G (4, 8, 16, 32) for one candidate block per step,
 // or 10 G + U for U blocks (42, 44, 82); 100 + 10 G + U for the vectorised
-// test with U windows of 4 G candidates a step (121, 141, 142, 181).
+// test with U windows of 4 G candidates a step (121, 122, 141-144, 181).
 template <int P>
 void apparent_p(int group, const float *D, int64_t ld, int64_t n, const uint64_t *binom,
                 const uint32_t *key_hi, const uint64_t *key_lo, uint64_t ncols,
@@ -465,6 +465,9 @@ void apparent_p(int group, const float *D, int64_t ld, int64_t n, const uint64_t
         case 141: apparent_vec<P, 4, 1>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, sms, s); break;
         case 142: apparent_vec<P, 4, 2>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, sms, s); break;
         case 181: apparent_vec<P, 8, 1>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, sms, s); break;
+        case 143: apparent_vec<P, 4, 3>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, sms, s); break;
+        case 144: apparent_vec<P, 4, 4>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, sms, s); break;
+        case 122: apparent_vec<P, 2, 2>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, sms, s); break;
         default: apparent_pg<P, 8, 1>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, sms, s); break;
     }
 }

@@ -383,7 +383,7 @@ static Status apparent_shape(rpp_context *ctx, Workspace &ws, int p, int64_t n, 
     const int fallback = *group;
     float base_ms = 0.0f, best = 0.0f;
     std::vector<std::pair<int, float>> timed;
-    for (int g : {fallback, 8, 82, 42, 44, 4, 141, 142, 181, 121}) {
+    for (int g : {fallback, 8, 82, 42, 44, 4, 141, 142, 181, 121, 143, 144, 122}) {
         if (g == fallback && !timed.empty()) continue;
         float ms = 0.0f, low = 0.0f;
         for (int rep = 0; rep < 4; ++rep) {
