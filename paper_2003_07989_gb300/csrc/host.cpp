@@ -30,6 +30,7 @@
 //     in V) is read from V's adjacency bits when a cursor reaches it, so even
 //     entries are skipped on the spot and never enter the heap.
 #include "host.h"
+#include "col_heap.h"
 
 #include <algorithm>
 #include <atomic>
@@ -187,8 +188,8 @@ void youngest_edge(const HostInstance &I, const int *v, int k, int32_t *u, int32
 namespace {
 
 // Column entries packed so that unsigned 128-bit order is "older first":
-// smaller diameter, then larger index (the simplex-wise refinement).
-typedef unsigned __int128 u128;
+// smaller diameter, then larger index (the simplex-wise refinement); u128 is
+// col_heap.h's.
 const u128 NONE = ~(u128)0;
 
 inline u128 age_key(float diam, uint64_t idx) {
@@ -711,19 +712,19 @@ struct Ledger {
 
 struct ColumnState {
     std::vector<Cursor> cur;
-    std::vector<std::pair<u128, int32_t>> heap;  // (head, cursor)
+    ColHeap heap;  // (head, cursor)
     std::vector<std::pair<uint64_t, float>> V;    // simplices whose coboundaries were added
     u128 cand = NONE;
     bool started = false;
     int64_t additions = 0, reads = 0, entries = 0;
 };
 
-typedef std::greater<std::pair<u128, int32_t>> HeapCmp;
-
 // Add the coboundary of simplex v (index idx, diameter d) to the working
-// column; `first` as in Reducer::init_cursor, or EMPTY_LUNE.
+// column; `first` as in Reducer::init_cursor, or EMPTY_LUNE. Entries older
+// than `floor` are skipped: the caller adds a reduced column whose pivot is
+// floor, the working column's own pivot, so those entries sum to zero.
 void add_cursor(const Reducer &R, ColumnState &S, const int *v, uint64_t idx, float d,
-                int first) {
+                int first, u128 floor = 0) {
     S.cur.emplace_back();
     Cursor &c = S.cur.back();
     if (first == EMPTY_LUNE) {
@@ -735,43 +736,34 @@ void add_cursor(const Reducer &R, ColumnState &S, const int *v, uint64_t idx, fl
     } else {
         R.init_cursor(c, v, d, first);
     }
-    if (c.head != NONE) {
-        S.heap.emplace_back(c.head, (int32_t)(S.cur.size() - 1));
-        std::push_heap(S.heap.begin(), S.heap.end(), HeapCmp());
-    }
+    while (c.head != NONE && c.head < floor) R.advance(c);
+    if (c.head != NONE) S.heap.push({c.head, (int32_t)(S.cur.size() - 1)});
     S.V.emplace_back(idx, d);
 }
 
-void add_cursor(const Reducer &R, ColumnState &S, uint64_t idx, float d) {
+void add_cursor(const Reducer &R, ColumnState &S, uint64_t idx, float d, u128 floor) {
     int v[RPP_MAX_DIM + 1];
     decode_host(*R.I.B, idx, R.p, R.n, v);
-    add_cursor(R, S, v, idx, d, -1);
+    add_cursor(R, S, v, idx, d, -1, floor);
 }
 
 // Oldest nonzero entry of the working column (NONE if it is zero).
 u128 pivot(const Reducer &R, ColumnState &S) {
     while (!S.heap.empty()) {
-        std::pop_heap(S.heap.begin(), S.heap.end(), HeapCmp());
-        const std::pair<u128, int32_t> a = S.heap.back();
-        S.heap.pop_back();
-        if (!S.heap.empty() && S.heap.front().first == a.first) {  // cancels over Z/2
-            std::pop_heap(S.heap.begin(), S.heap.end(), HeapCmp());
-            const std::pair<u128, int32_t> b = S.heap.back();
-            S.heap.pop_back();
+        const std::pair<u128, int32_t> a = S.heap.top();
+        if (S.heap.top_twice()) {  // cancels over Z/2
+            S.heap.pop();
+            const std::pair<u128, int32_t> b = S.heap.top();  // the same key
+            S.heap.pop();
             S.entries += 2;
             for (int32_t ci : {a.second, b.second}) {
                 Cursor &c = S.cur[ci];
                 R.advance(c);
-                if (c.head != NONE) {
-                    S.heap.emplace_back(c.head, ci);
-                    std::push_heap(S.heap.begin(), S.heap.end(), HeapCmp());
-                }
+                if (c.head != NONE) S.heap.push({c.head, ci});
             }
             continue;
         }
-        S.heap.push_back(a);
-        std::push_heap(S.heap.begin(), S.heap.end(), HeapCmp());
-        return a.first;
+        return a.first;  // the pivot stays in the column
     }
     return NONE;
 }
@@ -800,7 +792,7 @@ void walk(const Reducer &R, ColumnState &S, Ledger<Key128, SimplexSet> &led, int
         const int64_t i = led.query(j, k);
         if (i >= 0) {
             ++S.additions;
-            for (const auto &x : led.V[i]) add_cursor(R, S, x.first, x.second);
+            for (const auto &x : led.V[i]) add_cursor(R, S, x.first, x.second, k);
             continue;
         }
         S.cand = k;
@@ -888,7 +880,7 @@ void reduce_general(const HostInstance &I, int p, const Leftover *left, int64_t 
             if (i >= 0) {  // owned by an earlier leftover column: add it and walk on
                 if (!S.started) start_column(R, S, L);
                 ++S.additions;
-                for (const auto &x : led.V[i]) add_cursor(R, S, x.first, x.second);
+                for (const auto &x : led.V[i]) add_cursor(R, S, x.first, x.second, S.cand);
                 walk(R, S, led, j);
             }
         }
@@ -899,7 +891,7 @@ void reduce_general(const HostInstance &I, int p, const Leftover *left, int64_t 
             V[j].emplace_back(L.sigma, L.diam);
         }
         std::vector<Cursor>().swap(S.cur);
-        std::vector<std::pair<u128, int32_t>>().swap(S.heap);
+        S.heap.release();
         led.finish(j, S.cand);
     };
     if (threads <= 1 || nleft < 16) {

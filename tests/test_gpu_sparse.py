@@ -9,6 +9,8 @@ lists.
 * The thresholded and the dense construction give the same column arrays,
   apparent pairs, barcodes and realising edges, on random, tie-heavy and
   permutation inputs.
+* The O(3) workload on 2,000 points, with the long walk of its long-lived
+  H2 class, against the oracle.
 * A cloud whose C(n, 3) exceeds 2^32, which the dense construction cannot
   enumerate, against the oracle run on each connected component of the
   threshold graph on its own (the Rips complex of a disjoint union is the
@@ -136,3 +138,18 @@ def test_beyond_the_dense_index_range(rpp):
     with pytest.raises(N.RppError) as e:
         rpp.rpp_barcodes(X, max_dim=2, threshold=t, context=_ctx(rpp, 2))
     assert e.value.status == N.RPP_E_NOMEM
+
+
+def test_o3_long_h2_walks_match_the_oracle(rpp):
+    """2,000 random O(3) matrices at threshold 1.4, H0-H2 (the thresholded
+    workload of the bench on its first 2,000 points), against the coboundary
+    reduction with clearing: SO(3) = RP^3 carries a long-lived H2 class over
+    Z/2, whose column makes a long walk (13,130 additions in dimension 2 in
+    all), the case that the reduction's cofacet bitsets and column heap are
+    for."""
+    X = I.orthogonal3(4096)[:2000]
+    ref = O.barcodes(O.distance_matrix(X), 2, 1.4, O.MODE_COHOM_CLEAR)
+    got = rpp.rpp_barcodes(X, max_dim=2, threshold=1.4)
+    for q in range(3):
+        assert np.array_equal(got.intervals[q], ref.barcode(q)), q
+    assert got.stats["sparse"][2] == 1
