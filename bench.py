@@ -151,16 +151,17 @@ STAGE_FILES = {
 }
 
 
-def traffic_for(stage):
-    """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the current source of the kernel; else None."""
+def traffic_for(stage, key="dram_bytes_per_launch"):
+    """Bytes per launch (DRAM by default; `key` names another counter) from a
+    committed ncu summary, if it was taken on the current source of the
+    kernel; else None."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p) or stage not in STAGE_FILES:
         return None
     d = json.load(open(p)).get(stage)
     if not d or d.get("source_hash") != kernel_source_hash(STAGE_FILES[stage]):
         return None
-    return d.get("dram_bytes_per_launch")
+    return d.get(key)
 
 
 def algorithmic_bytes(stage, st):
@@ -176,9 +177,13 @@ def algorithmic_bytes(stage, st):
     if stage == "build_columns":
         return st["candidates"][p] * 4 + cols * 12
     if stage in ("sort_columns", "sort_pairs"):
-        # launches: (prep), histogram, offsets, one per pass, finish
-        launches = st["stage_launches"][3 if stage == "sort_columns" else 6]
-        passes = max(0, launches - (4 if stage == "sort_columns" else 3))
+        # the column sort reports the passes that ran (digits that were not
+        # constant); the pair sort's launches are (histogram, offsets, one per
+        # digit position, finish)
+        if stage == "sort_columns":
+            passes = st["sort_passes"][p]
+        else:
+            passes = max(0, st["stage_launches"][6] - 3)
         n = cols if stage == "sort_columns" else st["apparent"][p]
         w = 12 if stage == "sort_columns" else 16
         return n * w + passes * n * 2 * w  # histogram read + per pass one read and one write
@@ -408,6 +413,42 @@ def sphere_bench(rpp, torch, dev, reps: int = 10, stream_count: int = 512):
 # apparent-pair census of random edge orders (the paper's apparent-rate experiment)
 
 
+def l2_read_peak(rpp, torch, dev, reps: int = 64, trials: int = 5):
+    """The L2 read bandwidth of this GPU, measured by the library's probe
+    (rpp_l2_read_probe): a 16 MB buffer, the size of the 2000-point distance
+    matrix the apparent-pair pass reads, brought into L2 by one launch, then
+    read `reps` times per launch with L2-only loads; best of `trials` launches
+    per grid shape, CUDA events on the launching stream."""
+    nbytes = 16 << 20
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    buf = torch.ones(nbytes // 4, dtype=torch.int32, device=dev)
+    sink = torch.zeros(1, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    shapes = {}
+    for per_sm in (2, 4, 8):
+        blocks = per_sm * sms
+        rpp.rpp_l2_read_probe(buf, 1, blocks, sink, stream)
+        best = None
+        for _ in range(trials):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rpp.rpp_l2_read_probe(buf, reps, blocks, sink, stream)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        shapes[f"{per_sm}x{sms}x512"] = nbytes * reps / (best / 1e3) / 1e9
+    # every word is 1: the counter holds the number of words read (mod 2^32)
+    words = (nbytes // 4) * (1 + trials * reps) * len(shapes)
+    ok = int(sink.item()) % (1 << 32) == words % (1 << 32)
+    top = max(shapes, key=shapes.get)
+    return {"gbs": shapes[top], "grid": top, "per_grid_gbs": shapes, "buffer_bytes": nbytes,
+            "reps_per_launch": reps, "words_checked": ok,
+            "method": "rpp_l2_read_probe: ld.global.cg (L2 only) reads of an L2-resident "
+                      "buffer, best of %d launches per grid" % trials}
+
+
 def filtration_bench(rpp, torch, dev, reps: int = 5):
     """The HBM-bound stage: the dimension-2 filtration (every triangle inside
     the enclosing radius, no clearing) of the 2000-point torus, built and
@@ -422,15 +463,14 @@ def filtration_bench(rpp, torch, dev, reps: int = 5):
     try:
         rpp.rpp_filtration(X, 2, out=False, context=ctx)  # allocation, first launch
         torch.cuda.synchronize(dev)
-        builds, sorts, launches, st = [], [], [], None
+        builds, sorts, st = [], [], None
         for _ in range(reps):
             _, _, st = rpp.rpp_filtration(X, 2, out=False, context=ctx)
             builds.append(st["stage_ms"][2])
             sorts.append(st["stage_ms"][3])
-            launches.append(st["stage_launches"][3])
         m = st["columns"][2]
         cand = st["candidates"][2]
-        passes = max(0, launches[0] - 4)  # prep, histogram, offsets, passes, finish
+        passes = st["sort_passes"][2]  # digit positions that were not constant
         build_ms, sort_ms = statistics.median(builds), statistics.median(sorts)
         build_bytes = 12 * m + 4 * N_POINTS * N_POINTS  # columns written, D read once
         sort_bytes = m * (4 + 12 + passes * 24)
@@ -722,6 +762,15 @@ def main():
                 "traffic": traffic_for(dom), "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": (alg / launches) if alg else None,
                 "avg_launch_ms": dur_s * 1000.0}
+    # the apparent pass's rows stay in L2: its L2 read bytes (ncu, same
+    # kernel source) over its live launch time, against the probe's L2 peak
+    l2 = l2_read_peak(rpp, torch, dev)
+    l2_read = traffic_for(dom, "l2_read_bytes_per_launch")
+    roofline["l2"] = {"achieved": (l2_read / dur_s / 1e9) if (l2_read and dur_s > 0) else None,
+                      "peak": l2["gbs"], "unit": "GB/s", "peak_source": "measured (probe)",
+                      "frac": (l2_read / dur_s / 1e9 / l2["gbs"]) if (l2_read and dur_s > 0)
+                      else None,
+                      "l2_read_bytes_per_launch": l2_read, "probe": l2}
 
     cpu = None
     if not args.no_cpu_baseline:

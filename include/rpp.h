@@ -130,6 +130,9 @@ typedef struct {
                                              walks (they may overlap in time) */
     int64_t device_columns[RPP_MAX_DIM + 1]; /* leftover columns reduced on the device
                                              (batched clouds of <= 512 points) */
+    int64_t sort_passes[RPP_MAX_DIM + 1]; /* radix passes the column sort of dimension p ran:
+                                             9-bit digit positions of the key that were not
+                                             the same for every column (others are skipped) */
 } rpp_stats;
 
 typedef struct rpp_context rpp_context;
@@ -365,7 +368,7 @@ rpp_status rpp_distance_matrix(rpp_context *ctx, const float *points, int64_t n,
  *   capacity   must be >= C(n, 2).
  *   count_out  host, receives the number of edges written.
  * It allocates nothing: its scratch is one static device array of about
- * 3.3 MB (up to 262,144 edges) that every GPU loading the library holds until
+ * 3.8 MB (up to 262,144 edges) that every GPU loading the library holds until
  * the process exits. The first call on a device may be the one that loads the
  * library's device code there, and so the one that places that array on the
  * device; make that first call before any stream capture. Every call looks up
@@ -378,6 +381,30 @@ rpp_status rpp_distance_matrix(rpp_context *ctx, const float *points, int64_t n,
 rpp_status rpp_filtration_edges_noalloc(const float *D, int64_t n, float threshold,
                                         float *diam_out, uint64_t *cidx_out, int64_t capacity,
                                         int64_t *count_out, void *stream);
+
+/* ---- measurement: the L2 read-bandwidth ceiling ----
+ *
+ * Not a step of the method. The apparent-pair pass (Alg. 3) reads distance
+ * rows that stay in L2 (a 2000-point matrix is 16 MB), so the roofline that
+ * bounds its loads is the L2's read bandwidth, not HBM's. This call queues
+ * one kernel that reads the `bytes` bytes at buf `reps` times with loads
+ * cached in L2 only (never served by L1), over `blocks` blocks of 512
+ * threads, and adds the sum of every 32-bit word it read (mod 2^32, i.e.
+ * reps times the buffer's word sum) to *sink. The caller times the launch on
+ * its stream; with a buffer that fits in L2 and one launch before to bring
+ * it there, bytes * reps / time is the L2 read bandwidth.
+ *   buf     device memory of the current device, 16-byte aligned; read only.
+ *   bytes   a positive multiple of 16.
+ *   reps    1 <= reps <= 2^20.
+ *   blocks  1 <= blocks <= 65535.
+ *   sink    device memory of the current device, one uint32_t, 4-byte
+ *           aligned; the caller zeroes it.
+ *   stream  cudaStream_t of the current device, or NULL.
+ * Does not wait for the stream. Errors: RPP_E_INVALID (a NULL, misaligned or
+ * non-device pointer, a size, reps or blocks out of range, a stream of
+ * another device), RPP_E_CUDA (the launch failed). */
+rpp_status rpp_l2_read_probe(const void *buf, size_t bytes, int32_t reps, int32_t blocks,
+                             uint32_t *sink, void *stream);
 
 /* ---- recording of intermediate arrays (inspection and parity checks) ---- */
 

@@ -13,11 +13,12 @@ binding functions raises if the library was not built.
 """
 from ._native import RppError
 from .api import (Barcodes, Context, Server, default_context, rpp_apparent_census,
-                  rpp_barcodes, rpp_barcodes_batched, rpp_distance_matrix, rpp_filtration)
+                  rpp_barcodes, rpp_barcodes_batched, rpp_distance_matrix, rpp_filtration,
+                  rpp_l2_read_probe)
 
 __all__ = ["Barcodes", "Context", "RppError", "Server", "default_context", "rpp_apparent_census",
            "rpp_barcodes", "rpp_barcodes_batched", "rpp_distance_matrix", "rpp_filtration",
-           "rips_persistence",
+           "rpp_l2_read_probe", "rips_persistence",
            "total_persistence"]
 
 

@@ -25,6 +25,7 @@ EXPORTED = [
     "rpp_context_set_batch", "rpp_context_batch_tuning", "rpp_apparent_census",
     "rpp_results_gather", "rpp_results_stats", "rpp_results_free", "rpp_server_next",
     "rpp_filtration", "rpp_context_set_sparse", "rpp_context_set_device_reduce",
+    "rpp_l2_read_probe",
 ]
 RPP_RECORD_COLUMNS, RPP_RECORD_APPARENT, RPP_RECORD_TIMING = 1, 2, 4
 STAGES = ["distance", "enclosing_radius", "build_columns", "sort_columns", "apparent",
@@ -54,7 +55,7 @@ class Stats(C.Structure):
                 ("ms_device", C.c_double), ("ms_host_reduce", C.c_double),
                 ("ms_host_h0", C.c_double), ("ms_total", C.c_double), ("sparse", _A),
                 ("sweep_pivots", _A), ("sweep_idle", _A), ("ms_sweep_walks", C.c_double),
-                ("device_columns", _A)]
+                ("device_columns", _A), ("sort_passes", _A)]
 
 
 class ServerConfig(C.Structure):
@@ -133,13 +134,15 @@ def lib():
     L.rpp_context_set_device_reduce.argtypes = [vp, i32]
     L.rpp_filtration.argtypes = [vp, vp, C.c_int, i64, i32, i32, C.c_float, vp, vp, vp, i64,
                                  C.POINTER(i64), C.POINTER(Stats)]
+    L.rpp_l2_read_probe.argtypes = [vp, C.c_size_t, i32, i32, vp, vp]
     for name in ("rpp_context_set_batch", "rpp_context_batch_tuning",
                  "rpp_context_create", "rpp_barcodes", "rpp_barcodes_quantile",
                  "rpp_distance_matrix", "rpp_context_set_record", "rpp_filtration_edges_noalloc",
                  "rpp_result_stats", "rpp_barcodes_batched", "rpp_barcodes_backward",
                  "rpp_server_create", "rpp_server_submit", "rpp_server_poll",
                  "rpp_results_gather", "rpp_results_stats", "rpp_server_next",
-                 "rpp_filtration", "rpp_context_set_sparse", "rpp_context_set_device_reduce"):
+                 "rpp_filtration", "rpp_context_set_sparse", "rpp_context_set_device_reduce",
+                 "rpp_l2_read_probe"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L

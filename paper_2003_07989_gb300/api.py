@@ -305,6 +305,20 @@ def rpp_distance_matrix(points, stream=None, context: Context | None = None) -> 
     return out
 
 
+def rpp_l2_read_probe(buf, reps: int, blocks: int, sink, stream=None) -> None:
+    """Queue the L2 read-bandwidth probe (rpp_l2_read_probe): read the CUDA
+    tensor `buf` (16-byte aligned, nbytes a multiple of 16) `reps` times with
+    L2-only loads over `blocks` blocks of 512 threads, adding the sum of its
+    32-bit words (mod 2^32) to the one-element int32/uint32 CUDA tensor
+    `sink`. The caller times the launch on `stream`."""
+    if not (getattr(buf, "is_cuda", False) and getattr(sink, "is_cuda", False)):
+        raise ValueError("rpp_l2_read_probe: buf and sink must be CUDA tensors")
+    N.check(N.lib().rpp_l2_read_probe(buf.data_ptr(), buf.numel() * buf.element_size(),
+                                      int(reps), int(blocks), sink.data_ptr(),
+                                      _stream_ptr(stream, True)),
+            "rpp_l2_read_probe")
+
+
 def rpp_barcodes_batched(clouds, max_dim: int = 1, thresholds=None, quantiles=None,
                          stream=None, context: Context | None = None) -> list:
     """Barcodes of many clouds in one call (rpp_barcodes_batched)."""

@@ -28,6 +28,7 @@ struct DevState {
     unsigned long long nleft;  // leftover columns written by the partition kernel
     unsigned long long begin;  // first column inside a quantile threshold
     unsigned long long scanned;  // candidate vertices examined by the apparent pass
+    unsigned int sort_passes[8];  // radix passes that ran in the column sort of dimension p
 };
 
 // Kernels launched by the calling thread (incremented by every launcher).
@@ -95,16 +96,21 @@ size_t build_order_bytes(uint64_t total);
 // the sort needs nothing from the host. The result is left in (hi, lo, val);
 // tmp_* are buffers of the same sizes, scratch holds radix_scratch_bytes(n_cap)
 // bytes. A bounded wait that runs out ORs ERR_INTERNAL into *err (device).
-constexpr uint64_t RADIX_SORT_TILE = 2048;          // keys per tile of one sort pass
-constexpr size_t RADIX_SORT_CTL_BYTES = 64 * 1024;  // the sort's control block
+// Passes whose digit is the same for every key do no work; when passes_out
+// (device memory) is given, the number of passes that did is added to it.
+constexpr int RADIX_SORT_DIGIT_BITS = 9;                     // key bits sorted per pass
+constexpr int RADIX_SORT_BINS = 1 << RADIX_SORT_DIGIT_BITS;  // digit values of one pass
+constexpr uint64_t RADIX_SORT_TILE = 2048;                   // keys per tile of one pass
+constexpr size_t RADIX_SORT_CTL_BYTES = 128 * 1024;          // the sort's control block
 constexpr size_t radix_scratch_bound(uint64_t n_cap) {
     return RADIX_SORT_CTL_BYTES +
-           (size_t)((n_cap + RADIX_SORT_TILE - 1) / RADIX_SORT_TILE + 1) * 256 * 8;
+           (size_t)((n_cap + RADIX_SORT_TILE - 1) / RADIX_SORT_TILE + 1) * RADIX_SORT_BINS * 8;
 }
 size_t radix_scratch_bytes(uint64_t n_cap);  // = radix_scratch_bound(n_cap)
 void radix_sort(uint32_t *hi, uint64_t *lo, uint64_t *val, uint32_t *tmp_hi, uint64_t *tmp_lo,
                 uint64_t *tmp_val, void *scratch, uint64_t n_cap,
-                const unsigned long long *d_count, int lo_bits, unsigned *err, cudaStream_t s);
+                const unsigned long long *d_count, int lo_bits, unsigned *err, cudaStream_t s,
+                unsigned *passes_out = nullptr);
 
 // H0 of one instance on the device: the minimum spanning forest of the edges
 // inside st->t under the filtration's order of edges (Boruvka, a fixed number

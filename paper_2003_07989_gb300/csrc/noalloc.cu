@@ -29,7 +29,7 @@ constexpr size_t OFF_TMP_HI = up256(OFF_SORT + radix_scratch_bound(NA_MAX_EDGES)
 constexpr size_t OFF_TMP_LO = up256(OFF_TMP_HI + NA_MAX_EDGES * sizeof(uint32_t));
 constexpr size_t SCRATCH_BYTES = up256(OFF_TMP_LO + NA_MAX_EDGES * sizeof(uint64_t));
 
-// The scratch of rpp_filtration_edges_noalloc (about 3.3 MB per GPU). In host
+// The scratch of rpp_filtration_edges_noalloc (about 3.8 MB per GPU). In host
 // code this name is only a stand-in: its device address comes from
 // cudaGetSymbolAddress, looked up on every call with the caller's device
 // current (a cached address would go stale if the device were reset and the

@@ -537,7 +537,7 @@ Status run_filtration(rpp_context *ctx, Workspace &ws, const Instance &in, int p
     T.end();
     T.begin(ST_SORT);  // the columns arrive in index order: the diameter digits alone
     radix_sort(key_hi, key_lo, nullptr, tmp_hi, tmp_lo, nullptr, sort_scratch, cand,
-               &pro.st->ncols, 0, &pro.st->err, s);
+               &pro.st->ncols, 0, &pro.st->err, s, &pro.st->sort_passes[p]);
     T.end();
     RPP_CK(cudaGetLastError());
     const double a = now_ms();
@@ -551,6 +551,7 @@ Status run_filtration(rpp_context *ctx, Workspace &ws, const Instance &in, int p
     S.threshold = h.t;
     S.enclosing_radius = h.R;
     S.columns[p] = (int64_t)N;
+    S.sort_passes[p] = (int64_t)h.sort_passes[p];
     *count = (int64_t)N;
     if (diam_out || cidx_out) {
         if ((int64_t)N > capacity)
@@ -743,7 +744,7 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
         RPP_CK(cudaGetLastError());
         T.begin(ST_SORT);  // the edges arrive in index order: the diameter digits alone
         radix_sort(key_hi, key_lo, nullptr, tmp_hi, tmp_lo, nullptr, sort_scratch, m, &st->ncols,
-                   0, &st->err, s);
+                   0, &st->err, s, &st->sort_passes[1]);
         T.end();
         RPP_CK(cudaGetLastError());
         uint64_t begin = 0;
@@ -1004,7 +1005,8 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
             // the dense build writes its columns in index order (the
             // diameter digits alone); the thresholded one does not
             radix_sort(key_hi, key_lo, nullptr, tmp_hi, tmp_lo, nullptr, sort_scratch, cap,
-                       &st->ncols, S.sparse[p] ? bits_for(cand - 1) : 0, &st->err, s);
+                       &st->ncols, S.sparse[p] ? bits_for(cand - 1) : 0, &st->err, s,
+                       &st->sort_passes[p]);
             T.end();
             if (ctx->record & RPP_RECORD_COLUMNS) {
                 RPP_TRY(read_state());
@@ -1048,6 +1050,7 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
         if (hst->err & ERR_INTERNAL)
             return fail(RPP_E_CUDA, "a bounded device wait ran out (sort)");
         if (p >= 2) S.columns[p] = (int64_t)hst->ncols;
+        S.sort_passes[p] = (int64_t)hst->sort_passes[p];
         const uint64_t napp = hst->napp, nleft = hst->nleft;
         S.apparent[p] = (int64_t)napp;
         S.leftover[p] = (int64_t)nleft;

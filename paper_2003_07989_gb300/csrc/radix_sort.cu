@@ -7,8 +7,10 @@
 // ascending C is ascending (hi, lo). Keys that arrive in increasing lo (the
 // ordered filtration build) take C = hi - hi_min alone (lo_bits = 0): the
 // passes are stable, so lo stays increasing within equal hi, and the sort
-// needs no pass over the index bits. C is sorted 8 bits at a time, from the
-// least significant digit up, every pass stable. Nothing comes back to the
+// needs no pass over the index bits. C is sorted 9 bits at a time, from the
+// least significant digit up, every pass stable (diameter keys of a point
+// cloud span about 27 significant bits: three passes of 9 bits, where 8-bit
+// digits would take four). Nothing comes back to the
 // host: the key count may itself live in device memory, and the passes whose
 // digit is the same for every key are skipped by the kernels themselves.
 //   prep    : the smallest hi (one atomic per block);
@@ -37,14 +39,16 @@ namespace rpp {
 
 namespace {
 
-constexpr int RADIX = 256;
-constexpr int MAXP = 12;             // 96-bit composite keys at most
-constexpr int OS_THREADS = 256;
+constexpr int DIGIT_BITS = RADIX_SORT_DIGIT_BITS;
+constexpr int RADIX = RADIX_SORT_BINS;
+constexpr int MAXP = 12;             // 96-bit composite keys at most (11 digits)
+constexpr int OS_THREADS = RADIX;    // thread d owns digit value d in the look-back
 constexpr int OS_WARPS = OS_THREADS / 32;
-constexpr int OS_ITEMS = 8;          // keys per thread
+constexpr int OS_ITEMS = 4;          // keys per thread
 constexpr int OS_WARP_KEYS = 32 * OS_ITEMS;
 constexpr int OS_TILE = OS_THREADS * OS_ITEMS;
 static_assert(OS_TILE == RADIX_SORT_TILE, "tile size shared with the scratch bound");
+static_assert(RADIX <= (1 << 16), "digit and warp rank share one word");
 constexpr uint64_t LB_AGG = 1ull << 62;     // tile count only
 constexpr uint64_t LB_PREFIX = 2ull << 62;  // inclusive count of every tile up to this one
 constexpr uint64_t LB_FLAGS = 3ull << 62;
@@ -81,9 +85,9 @@ __device__ __forceinline__ unsigned digit_of(uint32_t h, uint64_t l, uint32_t hi
         // lo_bits = 0: the keys are in increasing lo already; hi alone
         const unsigned __int128 c =
             ((unsigned __int128)(h - hi_min) << lo_bits) | (lo_bits ? l : 0ull);
-        return (unsigned)(c >> shift) & 0xffu;
+        return (unsigned)(c >> shift) & (unsigned)(RADIX - 1);
     } else {
-        return shift < 64 ? (unsigned)(l >> shift) & 0xffu : 0u;
+        return shift < 64 ? (unsigned)(l >> shift) & (unsigned)(RADIX - 1) : 0u;
     }
 }
 
@@ -120,7 +124,7 @@ __global__ void __launch_bounds__(256) k_sort_hist(const uint32_t *__restrict__ 
         const uint64_t l = lo[i];
         const uint32_t h = HAS_HI ? hi[i] : 0u;
         for (int p = 0; p < passes; ++p)
-            atomicAdd(&sh[p * RADIX + digit_of<HAS_HI>(h, l, hmin, lo_bits, 8 * p)], 1u);
+            atomicAdd(&sh[p * RADIX + digit_of<HAS_HI>(h, l, hmin, lo_bits, DIGIT_BITS * p)], 1u);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < passes * RADIX; i += blockDim.x)
@@ -130,7 +134,8 @@ __global__ void __launch_bounds__(256) k_sort_hist(const uint32_t *__restrict__ 
 // One block of RADIX threads: thread d owns digit value d.
 __global__ void __launch_bounds__(RADIX) k_sort_offsets(uint64_t n_cap,
                                                         const unsigned long long *d_count,
-                                                        int passes, SortCtl *ctl) {
+                                                        int passes, SortCtl *ctl,
+                                                        unsigned *passes_out) {
     __shared__ unsigned long long s_warp[RADIX / 32];
     __shared__ unsigned int s_const[MAXP];
     const uint64_t n = key_count(d_count, n_cap);
@@ -153,19 +158,21 @@ __global__ void __launch_bounds__(RADIX) k_sort_offsets(uint64_t n_cap,
         __syncthreads();
     }
     if (d == 0) {
-        unsigned int parity = 0;
+        unsigned int parity = 0, ran = 0;
         for (int p = 0; p < passes; ++p) {
             const unsigned int act = (n > 1 && !s_const[p]) ? 1u : 0u;
             ctl->active[p] = act;
             ctl->src[p] = parity;
             parity ^= act;
+            ran += act;
         }
         ctl->final_src = parity;
+        if (passes_out) atomicAdd(passes_out, ran);
     }
 }
 
 template <bool HAS_HI, bool HAS_VAL>
-__global__ void __launch_bounds__(OS_THREADS, 4) k_onesweep(
+__global__ void __launch_bounds__(OS_THREADS, 2) k_onesweep(
     uint32_t *__restrict__ hi_a, uint64_t *__restrict__ lo_a, uint64_t *__restrict__ val_a,
     uint32_t *__restrict__ hi_b, uint64_t *__restrict__ lo_b, uint64_t *__restrict__ val_b,
     uint64_t n_cap, const unsigned long long *d_count, int lo_bits, int pass, SortCtl *ctl,
@@ -193,7 +200,7 @@ __global__ void __launch_bounds__(OS_THREADS, 4) k_onesweep(
     uint64_t *ld = from_b ? lo_a : lo_b;
     uint64_t *vd = from_b ? val_a : val_b;
     const uint32_t hmin = HAS_HI ? ~ctl->hi_min_inv : 0u;
-    const int shift = 8 * pass;
+    const int shift = DIGIT_BITS * pass;
 
     // keys of this warp: item j of lane l is key base + j * 32 + l (key order
     // is (warp, item, lane), so per-warp ranks in item order are stable)
@@ -336,12 +343,13 @@ size_t radix_scratch_bytes(uint64_t n_cap) { return radix_scratch_bound(n_cap); 
 
 void radix_sort(uint32_t *hi, uint64_t *lo, uint64_t *val, uint32_t *tmp_hi, uint64_t *tmp_lo,
                 uint64_t *tmp_val, void *scratch, uint64_t n_cap,
-                const unsigned long long *d_count, int lo_bits, unsigned *err, cudaStream_t s) {
+                const unsigned long long *d_count, int lo_bits, unsigned *err, cudaStream_t s,
+                unsigned *passes_out) {
     if (n_cap <= 1) return;
     if (lo_bits < 1 && !hi) lo_bits = 1;
     if (lo_bits < 0) lo_bits = 0;
     const int bits = lo_bits + (hi ? 32 : 0);
-    int passes = (bits + 7) / 8;
+    int passes = (bits + DIGIT_BITS - 1) / DIGIT_BITS;
     if (passes > MAXP) passes = MAXP;
     SortCtl *ctl = (SortCtl *)scratch;
     unsigned long long *lookback = (unsigned long long *)((char *)scratch + ctl_bytes());
@@ -359,7 +367,7 @@ void radix_sort(uint32_t *hi, uint64_t *lo, uint64_t *val, uint32_t *tmp_hi, uin
                                                         ctl);
     }
     ++g_launches;
-    k_sort_offsets<<<1, RADIX, 0, s>>>(n_cap, d_count, passes, ctl);
+    k_sort_offsets<<<1, RADIX, 0, s>>>(n_cap, d_count, passes, ctl, passes_out);
     if (hi && val)
         sort_passes<true, true>(hi, lo, val, tmp_hi, tmp_lo, tmp_val, ctl, lookback, n_cap, d_count,
                                 lo_bits, passes, err, s);

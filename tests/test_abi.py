@@ -84,3 +84,17 @@ def test_results_accessors_reject_bad_arguments(lib):
     assert lib.rpp_results_gather(two, 0, 0, C.addressof(offs), None, None) == N.RPP_OK
     assert offs[0] == 0
     lib.rpp_results_free(two, 2)  # NULL entries are skipped
+
+
+def test_l2_probe_rejects_bad_arguments_without_gpu(lib):
+    from paper_2003_07989_gb300 import _native as N
+    # every case below is refused by host checks before any CUDA call; the
+    # addresses are never dereferenced
+    buf, sink = 0x10000, 0x20000
+    for args in ((None, 16, 1, 1, sink), (buf, 16, 1, 1, None),   # NULL pointers
+                 (buf + 4, 16, 1, 1, sink), (buf, 24, 1, 1, sink),  # misaligned, ragged size
+                 (buf, 0, 1, 1, sink), (buf, 16, 1, 1, sink + 2),   # empty, misaligned sink
+                 (buf, 16, 0, 1, sink), (buf, 16, (1 << 20) + 1, 1, sink),  # reps
+                 (buf, 16, 1, 0, sink), (buf, 16, 1, 65536, sink)):        # blocks
+        assert lib.rpp_l2_read_probe(*args, None) == N.RPP_E_INVALID, args
+        assert lib.rpp_last_error().startswith(b"rpp_l2_read_probe")

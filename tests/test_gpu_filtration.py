@@ -61,6 +61,20 @@ def test_filtration_equals_oracle_columns(rpp, idx):
     assert np.array_equal(diam, od), name
     assert np.array_equal(cidx, _cidx(ov)), name
     assert st["candidates"][p] == math.comb(len(D), p + 1)
+    assert st["sort_passes"][p] == _passes_needed(od), name
+
+
+def _passes_needed(diam: np.ndarray) -> int:
+    """Radix passes a stable LSD sort of the columns needs when they arrive in
+    index order: the key is the diameter's float bits minus their smallest
+    value (ascending key = descending diameter after complementing the bits),
+    sorted in 9-bit digits, and a digit position where every key has the same
+    digit needs no pass."""
+    if len(diam) < 2:
+        return 0
+    key = (~diam.astype(np.float32).view(np.uint32)).astype(np.uint64)
+    key -= key.min()
+    return sum(1 for k in range(4) if len(np.unique((key >> np.uint64(9 * k)) & np.uint64(511))) > 1)
 
 
 def test_filtration_into_device_buffers_and_workspace(rpp):
