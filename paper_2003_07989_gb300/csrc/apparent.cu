@@ -24,17 +24,23 @@
 // lane). Groups of one warp advance independently: a group that finishes
 // takes its next column in the same iteration, so no lane idles while a
 // neighbour scans a long column.
-// While scanning, each lane also tracks its oldest cofacet inside the
-// threshold (smallest diameter, then largest vertex); for a column with no
-// equal-diameter cofacet the scan covers every vertex, and the group reduces
-// these minima into the column's unreduced pivot, which the host reduction
-// uses to skip columns whose pivot nobody owns.
+// While scanning, each lane also tracks the smallest max_i D[v_i][w] it has
+// seen (the largest w among equals). It is needed only for a column with no
+// equal-diameter cofacet: there the scan covers every vertex, every such
+// value exceeds diam(sigma) and is the diameter of the cofacet sigma + {w},
+// so the group's minimum is the column's oldest cofacet (its unreduced
+// pivot, kept if it lies inside the threshold), which the host reduction
+// uses to skip columns whose pivot nobody owns. Tracking that value rather
+// than max(diam, value) under the threshold test saves two instructions per
+// candidate.
 #include "device_common.cuh"
 #include "internal.h"
 
 namespace rpp {
 
 namespace {
+
+#define INF_F __uint_as_float(0x7f800000u)
 
 template <int P, int G, int U>
 __global__ void __launch_bounds__(256, 4) k_apparent(
@@ -72,7 +78,7 @@ __global__ void __launch_bounds__(256, 4) k_apparent(
 #pragma unroll
                 for (int i = 0; i <= P; ++i) row[i] = D + (int64_t)v[i] * ld;
                 scan = (int)n - 1;
-                best_d = __uint_as_float(0x7f800000u);
+                best_d = INF_F;
                 best_v = -1;
             }
         }
@@ -89,19 +95,23 @@ __global__ void __launch_bounds__(256, 4) k_apparent(
                 bool member = false;
 #pragma unroll
                 for (int i = 0; i <= P; ++i) member |= (x == v[i]);
-                if (!member) {
-                    float m = 0.0f;
+                // x <= n - 1: a vertex of sigma is read too (in bounds) and
+                // then excluded by an infinite m
+                float m = dv[u][0] = row[0][x];
 #pragma unroll
-                    for (int i = 0; i <= P; ++i) {
-                        dv[u][i] = row[i][x];
-                        m = fmaxf(m, dv[u][i]);
-                    }
-                    ok[u] = m <= diam;
-                    const float cd = fmaxf(m, diam);
-                    if (cd <= t && cd < best_d) {
-                        best_d = cd;
-                        best_v = x;
-                    }
+                for (int i = 1; i <= P; ++i) {
+                    dv[u][i] = row[i][x];
+                    m = fmaxf(m, dv[u][i]);
+                }
+                if (member) m = INF_F;
+                ok[u] = m <= diam;
+                // the oldest cofacet if no candidate qualifies: then every m
+                // exceeds diam and is the cofacet's diameter, so the smallest
+                // m (the largest vertex among equals: the scan descends) is
+                // it; the threshold is applied once, at the end
+                if (m < best_d) {
+                    best_d = m;
+                    best_v = x;
                 }
             }
         }
@@ -167,9 +177,10 @@ __global__ void __launch_bounds__(256, 4) k_apparent(
                     }
                 }
                 if (gl == 0) {
+                    const bool inside = best_v >= 0 && best_d <= t;
                     status[c] = COL_LEFTOVER;
-                    pivot[c] = best_v >= 0 ? cofacet_index<P>(v, best_v, B, n) : NO_PIVOT;
-                    pdiam[c] = best_d;
+                    pivot[c] = inside ? cofacet_index<P>(v, best_v, B, n) : NO_PIVOT;
+                    pdiam[c] = inside ? best_d : INF_F;
                     scanned += (unsigned long long)(n - (P + 1));
                 }
                 have = false;
@@ -229,7 +240,7 @@ __global__ void __launch_bounds__(256, 4) k_apparent_vec(
 #pragma unroll
                 for (int i = 0; i <= P; ++i) row[i] = D + (int64_t)v[i] * ld;
                 x0 = (int)(((n - 1) / W) * W);
-                best_d = __uint_as_float(0x7f800000u);
+                best_d = INF_F;
                 best_v = -1;
             }
         }
@@ -251,25 +262,30 @@ __global__ void __launch_bounds__(256, 4) k_apparent_vec(
         for (int u = 0; u < U; ++u) {
             hit[u] = 0;
             if (have && xb[u] >= 0) {
+                // bit k set: xb + k is no candidate (the row padding past n - 1,
+                // or a vertex of sigma), one mask per window
+                const int lim = (int)n - xb[u];
+                unsigned skip = lim >= 4 ? 0u : (lim <= 0 ? 0xfu : (0xfu << lim) & 0xfu);
+#pragma unroll
+                for (int i = 0; i <= P; ++i) {
+                    const unsigned d = (unsigned)(v[i] - xb[u]);
+                    if (d < 4u) skip |= 1u << d;
+                }
 #pragma unroll
                 for (int k = 3; k >= 0; --k) {
-                    const int x = xb[u] + k;
-                    bool member = x > (int)n - 1;
-#pragma unroll
-                    for (int i = 0; i <= P; ++i) member |= (x == v[i]);
-                    if (member) continue;
                     float m = 0.0f;
 #pragma unroll
                     for (int i = 0; i <= P; ++i) {
                         const float e = k == 0 ? f[u][i].x : k == 1 ? f[u][i].y
                                                    : k == 2 ? f[u][i].z : f[u][i].w;
-                        m = fmaxf(m, e);
+                        m = i == 0 ? e : fmaxf(m, e);
                     }
+                    if ((skip >> k) & 1u) m = INF_F;
                     if (m <= diam) hit[u] |= 1u << k;
-                    const float cd = fmaxf(m, diam);
-                    if (cd <= t && cd < best_d) {
-                        best_d = cd;
-                        best_v = x;
+                    // the oldest cofacet if no candidate qualifies (as in k_apparent)
+                    if (m < best_d) {
+                        best_d = m;
+                        best_v = xb[u] + k;
                     }
                 }
             }
@@ -346,9 +362,10 @@ __global__ void __launch_bounds__(256, 4) k_apparent_vec(
                     }
                 }
                 if (gl == 0) {
+                    const bool inside = best_v >= 0 && best_d <= t;
                     status[c] = COL_LEFTOVER;
-                    pivot[c] = best_v >= 0 ? cofacet_index<P>(v, best_v, B, n) : NO_PIVOT;
-                    pdiam[c] = best_d;
+                    pivot[c] = inside ? cofacet_index<P>(v, best_v, B, n) : NO_PIVOT;
+                    pdiam[c] = inside ? best_d : INF_F;
                     scanned += (unsigned long long)(n - (P + 1));
                 }
                 have = false;
