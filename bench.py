@@ -171,9 +171,12 @@ def algorithmic_bytes(stage, st):
     p = 1
     cols = st["columns"][p] + st["cleared"][p]
     if stage == "apparent":
-        # per column: (p+1) distance reads per candidate examined, the column
-        # key (12 B) and its outputs (status 1 B, pivot 8 B, pivot diameter 4 B)
-        return st["scanned"][p] * (p + 1) * 4 + cols * (12 + 13)
+        # the measurement plan's per-unit figure: (p+1) distance reads of 4 B
+        # per candidate a sequential scan examines, (p+1) p / 2 more for the
+        # facet test (one for p = 1), 12 B of column key in and 9 B out
+        # (status and pivot) per column
+        return (st["scanned"][p] * (p + 1) * 4 + cols * (p + 1) * p // 2 * 4
+                + cols * (12 + 9))
     if stage == "build_columns":
         return st["candidates"][p] * 4 + cols * 12
     if stage in ("sort_columns", "sort_pairs"):

@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(256, 4) k_apparent(
     bool smem_table, const uint32_t *__restrict__ key_hi, const uint64_t *__restrict__ key_lo,
     uint64_t ncols_cap, const unsigned long long *d_ncols, DevState *__restrict__ st,
     uint8_t *__restrict__ status, uint64_t *__restrict__ pivot, float *__restrict__ pdiam,
-    uint16_t *__restrict__ aw) {
+    uint16_t *__restrict__ aw, bool app_piv) {
     extern __shared__ uint64_t sB[];
     const uint64_t *B = stage_binomial(gB, n, P + 2, sB, smem_table);
     const float t = st->t;
@@ -65,6 +65,7 @@ __global__ void __launch_bounds__(256, 4) k_apparent(
     bool have = false;
     int v[P + 1];
     const float *row[P + 1];
+    uint64_t cidx = 0;  // the column's simplex index
     float diam = 0.0f, best_d = 0.0f;
     int scan = 0, best_v = -1;
 
@@ -74,7 +75,8 @@ __global__ void __launch_bounds__(256, 4) k_apparent(
             if (c < ncols) {
                 have = true;
                 diam = __uint_as_float(~key_hi[c]);
-                decode_simplex<P>(key_lo[c], B, n, v);
+                cidx = key_lo[c];
+                decode_simplex<P>(cidx, B, n, v);
 #pragma unroll
                 for (int i = 0; i <= P; ++i) row[i] = D + (int64_t)v[i] * ld;
                 scan = (int)n - 1;
@@ -155,9 +157,11 @@ __global__ void __launch_bounds__(256, 4) k_apparent(
                         }
                     }
                     status[c] = apparent ? COL_APPARENT : COL_LEFTOVER;
-                    pivot[c] = cofacet_index<P>(v, x, B, n);
-                    pdiam[c] = diam;
-                    if (P == 1 && aw && apparent) aw[key_lo[c]] = (uint16_t)x;
+                    if (!apparent || app_piv) {  // see launch_apparent
+                        pivot[c] = cofacet_index<P>(v, x, B, n);
+                        pdiam[c] = diam;
+                    }
+                    if (P == 1 && aw && apparent) aw[cidx] = (uint16_t)x;
                     int above = 0;  // vertices of sigma above x
 #pragma unroll
                     for (int i = 0; i <= P; ++i) above += v[i] > x;
@@ -210,13 +214,14 @@ __global__ void __launch_bounds__(256, 4) k_apparent_vec(
     bool smem_table, const uint32_t *__restrict__ key_hi, const uint64_t *__restrict__ key_lo,
     uint64_t ncols_cap, const unsigned long long *d_ncols, DevState *__restrict__ st,
     uint8_t *__restrict__ status, uint64_t *__restrict__ pivot, float *__restrict__ pdiam,
-    uint16_t *__restrict__ aw) {
+    uint16_t *__restrict__ aw, bool app_piv) {
     static_assert(4 * G <= 32, "a window must stay inside the 32-float row padding");
     extern __shared__ uint64_t sB[];
     const uint64_t *B = stage_binomial(gB, n, P + 2, sB, smem_table);
     const float t = st->t;
     const uint64_t ncols = count_of(d_ncols, ncols_cap);
     constexpr int W = 4 * G;  // candidates per window
+    const int x_top = (int)(((n - 1) / W) * W);  // a column's first window
     unsigned long long scanned = 0;
     const int lane = threadIdx.x & 31;
     const int grp = lane / G, gl = lane % G;
@@ -227,6 +232,7 @@ __global__ void __launch_bounds__(256, 4) k_apparent_vec(
     bool have = false;
     int v[P + 1];
     const float *row[P + 1];
+    uint64_t cidx = 0;  // the column's simplex index
     float diam = 0.0f, best_d = 0.0f;
     int x0 = 0, best_v = -1;  // x0: lowest candidate of the current step's first window
 
@@ -236,10 +242,11 @@ __global__ void __launch_bounds__(256, 4) k_apparent_vec(
             if (c < ncols) {
                 have = true;
                 diam = __uint_as_float(~key_hi[c]);
-                decode_simplex<P>(key_lo[c], B, n, v);
+                cidx = key_lo[c];
+                decode_simplex<P>(cidx, B, n, v);
 #pragma unroll
                 for (int i = 0; i <= P; ++i) row[i] = D + (int64_t)v[i] * ld;
-                x0 = (int)(((n - 1) / W) * W);
+                x0 = x_top;
                 best_d = INF_F;
                 best_v = -1;
             }
@@ -340,9 +347,11 @@ __global__ void __launch_bounds__(256, 4) k_apparent_vec(
                         }
                     }
                     status[c] = apparent ? COL_APPARENT : COL_LEFTOVER;
-                    pivot[c] = cofacet_index<P>(v, x, B, n);
-                    pdiam[c] = diam;
-                    if (P == 1 && aw && apparent) aw[key_lo[c]] = (uint16_t)x;
+                    if (!apparent || app_piv) {  // see launch_apparent
+                        pivot[c] = cofacet_index<P>(v, x, B, n);
+                        pdiam[c] = diam;
+                    }
+                    if (P == 1 && aw && apparent) aw[cidx] = (uint16_t)x;
                     int above = 0;  // vertices of sigma above x
 #pragma unroll
                     for (int i = 0; i <= P; ++i) above += v[i] > x;
@@ -399,7 +408,7 @@ __global__ void __launch_bounds__(256) k_partition(
             unsigned long long off = 0;
             if (lane == 0) off = atomicAdd(&st->napp, (unsigned long long)__popc(ba));
             off = __shfl_sync(FULL_MASK, off, 0);
-            if (a) {
+            if (a && app_tau) {  // no pair arrays: the apparent pairs are only counted
                 const uint64_t pos = off + __popc(ba & lanemask_lt());
                 app_tau[pos] = pivot[c];
                 app_sigma[pos] = key_lo[c];
@@ -427,7 +436,8 @@ template <int P, int G, int U>
 void apparent_pg(const float *D, int64_t ld, int64_t n, const uint64_t *binom,
                  const uint32_t *key_hi, const uint64_t *key_lo, uint64_t ncols,
                  const unsigned long long *d_ncols, DevState *st, uint8_t *status,
-                 uint64_t *pivot, float *pdiam, uint16_t *aw, int sms, cudaStream_t s) {
+                 uint64_t *pivot, float *pdiam, uint16_t *aw, bool app_piv, int sms,
+                  cudaStream_t s) {
     const size_t table = (size_t)(P + 3) * (n + 1) * sizeof(uint64_t);
     const bool smem = table <= 48 * 1024;
     int per_sm = 0;
@@ -440,14 +450,16 @@ void apparent_pg(const float *D, int64_t ld, int64_t n, const uint64_t *binom,
     if (blocks == 0) return;
     ++g_launches;
     k_apparent<P, G, U><<<(unsigned)blocks, 256, smem ? table : 0, s>>>(
-        D, ld, n, binom, smem, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw);
+        D, ld, n, binom, smem, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw,
+        app_piv);
 }
 
 template <int P, int G, int U>
 void apparent_vec(const float *D, int64_t ld, int64_t n, const uint64_t *binom,
                   const uint32_t *key_hi, const uint64_t *key_lo, uint64_t ncols,
                   const unsigned long long *d_ncols, DevState *st, uint8_t *status,
-                  uint64_t *pivot, float *pdiam, uint16_t *aw, int sms, cudaStream_t s) {
+                  uint64_t *pivot, float *pdiam, uint16_t *aw, bool app_piv, int sms,
+                  cudaStream_t s) {
     const size_t table = (size_t)(P + 3) * (n + 1) * sizeof(uint64_t);
     const bool smem = table <= 48 * 1024;
     int per_sm = 0;
@@ -460,7 +472,8 @@ void apparent_vec(const float *D, int64_t ld, int64_t n, const uint64_t *binom,
     if (blocks == 0) return;
     ++g_launches;
     k_apparent_vec<P, G, U><<<(unsigned)blocks, 256, smem ? table : 0, s>>>(
-        D, ld, n, binom, smem, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw);
+        D, ld, n, binom, smem, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw,
+        app_piv);
 }
 
 // group: lanes per column G (4, 8, 16, 32) for one candidate block per step,
@@ -470,22 +483,23 @@ template <int P>
 void apparent_p(int group, const float *D, int64_t ld, int64_t n, const uint64_t *binom,
                 const uint32_t *key_hi, const uint64_t *key_lo, uint64_t ncols,
                 const unsigned long long *d_ncols, DevState *st, uint8_t *status,
-                uint64_t *pivot, float *pdiam, uint16_t *aw, int sms, cudaStream_t s) {
+                uint64_t *pivot, float *pdiam, uint16_t *aw, bool app_piv, int sms,
+                  cudaStream_t s) {
     switch (group) {
-        case 4: apparent_pg<P, 4, 1>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, sms, s); break;
-        case 16: apparent_pg<P, 16, 1>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, sms, s); break;
-        case 32: apparent_pg<P, 32, 1>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, sms, s); break;
-        case 42: apparent_pg<P, 4, 2>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, sms, s); break;
-        case 82: apparent_pg<P, 8, 2>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, sms, s); break;
-        case 44: apparent_pg<P, 4, 4>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, sms, s); break;
-        case 121: apparent_vec<P, 2, 1>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, sms, s); break;
-        case 141: apparent_vec<P, 4, 1>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, sms, s); break;
-        case 142: apparent_vec<P, 4, 2>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, sms, s); break;
-        case 181: apparent_vec<P, 8, 1>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, sms, s); break;
-        case 143: apparent_vec<P, 4, 3>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, sms, s); break;
-        case 144: apparent_vec<P, 4, 4>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, sms, s); break;
-        case 122: apparent_vec<P, 2, 2>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, sms, s); break;
-        default: apparent_pg<P, 8, 1>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, sms, s); break;
+        case 4: apparent_pg<P, 4, 1>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, app_piv, sms, s); break;
+        case 16: apparent_pg<P, 16, 1>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, app_piv, sms, s); break;
+        case 32: apparent_pg<P, 32, 1>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, app_piv, sms, s); break;
+        case 42: apparent_pg<P, 4, 2>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, app_piv, sms, s); break;
+        case 82: apparent_pg<P, 8, 2>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, app_piv, sms, s); break;
+        case 44: apparent_pg<P, 4, 4>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, app_piv, sms, s); break;
+        case 121: apparent_vec<P, 2, 1>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, app_piv, sms, s); break;
+        case 141: apparent_vec<P, 4, 1>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, app_piv, sms, s); break;
+        case 142: apparent_vec<P, 4, 2>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, app_piv, sms, s); break;
+        case 181: apparent_vec<P, 8, 1>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, app_piv, sms, s); break;
+        case 143: apparent_vec<P, 4, 3>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, app_piv, sms, s); break;
+        case 144: apparent_vec<P, 4, 4>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, app_piv, sms, s); break;
+        case 122: apparent_vec<P, 2, 2>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, app_piv, sms, s); break;
+        default: apparent_pg<P, 8, 1>(D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, app_piv, sms, s); break;
     }
 }
 
@@ -495,13 +509,13 @@ void launch_apparent(const float *D, int64_t ld, int64_t n, int p, const uint64_
                      const uint32_t *key_hi, const uint64_t *key_lo, uint64_t ncols,
                      const unsigned long long *d_ncols, DevState *st, uint8_t *status,
                      uint64_t *pivot, float *pdiam, uint16_t *aw, int group, int sms,
-                     cudaStream_t s) {
+                     cudaStream_t s, bool app_piv) {
     if (ncols == 0) return;
     switch (p) {
-        case 1: apparent_p<1>(group, D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, sms, s); break;
-        case 2: apparent_p<2>(group, D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, sms, s); break;
-        case 3: apparent_p<3>(group, D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, sms, s); break;
-        case 4: apparent_p<4>(group, D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, sms, s); break;
+        case 1: apparent_p<1>(group, D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, app_piv, sms, s); break;
+        case 2: apparent_p<2>(group, D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, app_piv, sms, s); break;
+        case 3: apparent_p<3>(group, D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, app_piv, sms, s); break;
+        case 4: apparent_p<4>(group, D, ld, n, binom, key_hi, key_lo, ncols, d_ncols, st, status, pivot, pdiam, aw, app_piv, sms, s); break;
         default: break;
     }
 }

@@ -142,13 +142,17 @@ void launch_edge_pairs(const uint64_t *lo, uint64_t count, uint32_t *out, cudaSt
 // device memory, is given; grids are sized for ncols.)
 // aw (dimension 1, may be null): aw[edge index] = the vertex the edge's
 // apparent pair adds, written for apparent columns (the caller fills 0xFFFF).
+// app_piv = false: apparent columns get no pivot and pivot diameter (only
+// their status and aw), for a caller that never reads their tau; leftover
+// columns always get both.
 void launch_apparent(const float *D, int64_t ld, int64_t n, int p, const uint64_t *binom,
                      const uint32_t *key_hi, const uint64_t *key_lo, uint64_t ncols,
                      const unsigned long long *d_ncols, DevState *st, uint8_t *status,
                      uint64_t *pivot, float *pdiam, uint16_t *aw, int group, int sms,
-                     cudaStream_t s);
+                     cudaStream_t s, bool app_piv = true);
 
-// Partition: apparent columns -> (tau, sigma) pairs; leftover columns -> Leftover.
+// Partition: apparent columns -> (tau, sigma) pairs (app_tau and app_sigma
+// both null: counted in st->napp only); leftover columns -> Leftover.
 void launch_partition(const uint8_t *status, const uint32_t *key_hi, const uint64_t *key_lo,
                       const uint64_t *pivot, const float *pdiam, uint64_t ncols,
                       const unsigned long long *d_ncols, uint64_t *app_tau,

@@ -829,9 +829,15 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
                 RPP_TRY(ws.dev(ws.aw, B.at(2, n) * 2, (void **)&d_aw));
                 RPP_CK(cudaMemsetAsync(d_aw, 0xFF, B.at(2, n) * 2, s));
             }
+            // the apparent taus of dimension 1 are read only to clear
+            // dimension 2, to be recorded, or as the sorted owner test when
+            // the apparent vertices are not kept; otherwise the pass skips
+            // their indices and the partition only counts the pairs
+            const bool taus1 = d_aw == nullptr || max_dim >= 2 ||
+                               (ctx->record & RPP_RECORD_APPARENT) != 0;
             auto run = [&](int g, DevState *state) {
                 launch_apparent(D, ld, n, 1, d_binom, hi1, lo1, cols, d_cols, state, status,
-                                pivot, pdiam, d_aw, g, ctx->sms, s);
+                                pivot, pdiam, d_aw, g, ctx->sms, s, taus1);
             };
             int group;
             RPP_TRY(apparent_shape(ctx, ws, 1, n, st, run, s, &group));
@@ -839,8 +845,8 @@ Status run_instance(rpp_context *ctx, Workspace &ws, const Instance &in, cudaStr
             run(group, st);
             T.end();
             T.begin(ST_PARTITION);
-            launch_partition(status, hi1, lo1, pivot, pdiam, cols, d_cols, app_tau, app_sigma, left,
-                             st, s);
+            launch_partition(status, hi1, lo1, pivot, pdiam, cols, d_cols,
+                             taus1 ? app_tau : nullptr, taus1 ? app_sigma : nullptr, left, st, s);
             T.end();
             RPP_CK(cudaGetLastError());
         }
