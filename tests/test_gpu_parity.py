@@ -240,3 +240,29 @@ def test_apparent_shape_tuning_changes_nothing(rpp):
             assert np.array_equal(c.intervals[q], b.intervals[q])
         for k in ("columns", "apparent", "leftover", "scanned", "additions"):
             assert a.stats[k] == b.stats[k] == c.stats[k], k
+
+
+def test_unread_apparent_taus_change_nothing(rpp):
+    """With H0-H1 only, each edge's apparent vertex kept and no pairs
+    recorded, the apparent pass computes no cofacet index for apparent
+    columns and the partition only counts them. Recording the pairs (or a
+    second dimension, which clears with them) makes both write the taus. The
+    barcodes, realising edges and counters must not depend on which, and
+    the recorded pairs must be the oracle's."""
+    from paper_2003_07989_gb300 import _native as N
+    X = I.noisy_torus(400, seed=3)
+    D = O.distance_matrix(X)
+    plain = rpp.Context(0)
+    rec = rpp.Context(0, record=N.RPP_RECORD_APPARENT)
+    a = rpp.rpp_barcodes(_cuda(X), max_dim=1, context=plain)
+    b = rpp.rpp_barcodes(_cuda(X), max_dim=1, context=rec)
+    for q in (0, 1):
+        assert np.array_equal(a.intervals[q], b.intervals[q])
+        assert np.array_equal(a.critical[q], b.critical[q])
+    for k in ("columns", "apparent", "leftover", "free_pivot", "additions", "scanned"):
+        assert a.stats[k] == b.stats[k], k
+    _check_barcodes(a, O.barcodes(D, 1, O.enclosing_radius(D), O.MODE_COHOM_CLEAR), 1)
+    gs, gt = b.apparent[1]
+    assert len(gs) == a.stats["apparent"][1]
+    _, pairs = _oracle_dim_arrays(D, 1, a.stats["threshold"])
+    assert list(zip(gt.tolist(), gs.tolist())) == pairs
