@@ -113,6 +113,86 @@ def test_distance_matrix_within_float32_rounding_of_exact():
     assert rel.max() < 4 * 2.0 ** -24 * 3  # 3 adds + square root, each half an ulp
 
 
+def _f32_round(x):
+    """x (an exact Fraction) rounded to the nearest float32, ties to even,
+    as an exact Fraction (normal range only; zero stays zero)."""
+    from fractions import Fraction
+    if x == 0:
+        return Fraction(0)
+    sign = -1 if x < 0 else 1
+    a = abs(x)
+    e = a.numerator.bit_length() - a.denominator.bit_length()
+    if Fraction(2) ** e > a:
+        e -= 1
+    assert -126 <= e <= 127, "outside the float32 normal range"
+    ulp = Fraction(2) ** (e - 23)
+    q, r = divmod(a, ulp)  # q integer, 0 <= r < ulp
+    if r * 2 > ulp or (r * 2 == ulp and q % 2 == 1):
+        q += 1
+    return sign * q * ulp
+
+
+def _f32_sqrt(s):
+    """The float32 nearest to sqrt(s) for an exact Fraction s >= 0, chosen by
+    comparing squares exactly (no floating-point square root decides it)."""
+    from fractions import Fraction
+    import math
+    if s == 0:
+        return Fraction(0)
+    guess = _f32_round(Fraction(math.sqrt(float(s))))
+    e = guess.numerator.bit_length() - guess.denominator.bit_length()
+    if Fraction(2) ** e > guess:
+        e -= 1
+    ulp = Fraction(2) ** (e - 23)
+    best = None
+    for c in (guess - 2 * ulp, guess - ulp, guess, guess + ulp, guess + 2 * ulp):
+        c = _f32_round(c)
+        if best is None or abs(c * c - s) < abs(best * best - s):
+            best = c
+    return best
+
+
+def _emulated_distance(xi, xj, order, fused=False):
+    """The float32 distance with one rounding after every operation: per
+    coordinate in `order`, d = x_i - x_j, sq = d * d, s = s + sq; then sqrt.
+    fused: s + d * d rounded once (a fused multiply-add)."""
+    from fractions import Fraction
+    s = Fraction(0)
+    for k in order:
+        d = _f32_round(Fraction(float(xi[k])) - Fraction(float(xj[k])))
+        if fused:
+            s = _f32_round(s + d * d)
+        else:
+            s = _f32_round(s + _f32_round(d * d))
+    return _f32_sqrt(s)
+
+
+def test_distance_matrix_operation_order_exact():
+    """The oracle's float32 distances equal, bit for bit, an exact-arithmetic
+    emulation of the stated operation order (coordinates in increasing
+    index, a rounding after each subtraction, square and addition, no fused
+    multiply-add, then a correctly rounded square root). The fixture is
+    chosen so that summing the coordinates in reverse order, or fusing each
+    square into its addition, changes some distances: the pin tells the
+    stated order from other equally accurate ones."""
+    from fractions import Fraction
+    rng = np.random.default_rng(17)
+    n, dim = 10, 16
+    X = (rng.standard_normal((n, dim)) * np.float32(3.0)).astype(np.float32)
+    D = O.distance_matrix(X)
+    fwd, rev = list(range(dim)), list(range(dim - 1, -1, -1))
+    reordered = fused = 0
+    for i in range(n):
+        for j in range(i + 1, n):
+            want = _emulated_distance(X[i], X[j], fwd)
+            assert Fraction(float(D[i, j])) == want, (i, j)
+            assert D[j, i] == D[i, j]
+            reordered += _emulated_distance(X[i], X[j], rev) != want
+            fused += _emulated_distance(X[i], X[j], fwd, fused=True) != want
+    assert reordered > 0, "the fixture does not discriminate the summation order"
+    assert fused > 0, "the fixture does not discriminate a fused multiply-add"
+
+
 def test_enclosing_radius_closed_forms():
     """Closed forms, independent of any row max/min code: n collinear points
     at 0, 1, ..., n-1 have R = ceil((n-1)/2) (every point's farthest point is
