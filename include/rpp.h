@@ -371,8 +371,8 @@ rpp_status rpp_distance_matrix(rpp_context *ctx, const float *points, int64_t n,
  * 3.8 MB (up to 262,144 edges) that every GPU loading the library holds until
  * the process exits. The first call on a device may be the one that loads the
  * library's device code there, and so the one that places that array on the
- * device. Every call looks up the array's device address for the current
- * device, queries the pointers' attributes and waits for its stream. All calls share the
+ * device; make that first call before any stream capture. Every call looks up
+ * the array's device address for the current device. All calls share the
  * array, so calls that overlap on the GPU (other streams, other threads) race
  * and must be serialised by the caller. Returns RPP_E_INVALID for n above the
  * bound, a short capacity, D or an output not in memory of the current
