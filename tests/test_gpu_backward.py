@@ -96,7 +96,7 @@ def test_backward_matches_oracle_pairing_gradient_batch(rpp):
         ref = _ref_grad64(Xb[i], edges)
         scale = max(1.0, np.abs(ref).max())
         assert np.abs(g[i] - ref).max() <= 1e-5 * scale, i
-    assert abs(float(loss) - ref_loss) <= 1e-5 * max(1.0, abs(ref_loss))
+    assert abs(float(loss.detach()) - ref_loss) <= 1e-5 * max(1.0, abs(ref_loss))
 
 
 def test_backward_against_finite_differences(rpp):
