@@ -137,7 +137,8 @@ void launch_edge_pairs(const uint64_t *lo, uint64_t count, uint32_t *out, cudaSt
 
 
 // Apparent-pair pass (Alg. 3 with the Apparent Pairs Lemma) over the columns
-// [0, ncols) in coboundary order. Writes status, pivot and pivot diameter.
+// [0, ncols) in coboundary order. Writes each column's status, and its pivot
+// and pivot diameter (for apparent columns only when app_piv, below).
 // (ncols, d_ncols: the column count is min(*d_ncols, ncols) when d_ncols,
 // device memory, is given; grids are sized for ncols.)
 // aw (dimension 1, may be null): aw[edge index] = the vertex the edge's
